@@ -1,0 +1,415 @@
+"""Benchmark of the iterative-GP hot path on GB300.
+
+One step = one warm-started pathwise marginal-likelihood step on the pathwise
+workload (n=32768, d=16, Matern-3/2, s=64 probes -> 65 right-hand sides,
+m=2048 random features, CG to relative tolerance 0.01 with the stop rule of
+App. B):
+    random-feature prior samples -> pathwise right-hand sides -> CG solve
+    (warm start from the previous step) -> fused pathwise gradient -> gradient
+    to the host -> Adam ascent step in softplus coordinates.
+Inputs are synthetic (seeded generators) and resident in HBM for `value`.
+
+value = kernel-matrix pair x RHS work of the step (every H V product of the
+solve, including the initial residual, plus the gradient pass, each n^2 x 65)
+divided by the step time, in Gpair*RHS/s.  The plain FP64 GPU form of the same
+step (same tolerance, i.e. equal final residual norm) is timed beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With torchrun (N > 1) every rank runs an independent replica (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "kernel-MVM Gpair*RHS/s (whole warm-started pathwise MLL step; sec per step vs plain FP64 GPU form)"
+UNIT = "Gpair*RHS/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+class Replica:
+    """State of one warm-started marginal-likelihood optimisation run."""
+
+    def __init__(self, gp, torch, prob, dev, dtype, prec, max_iters):
+        self.gp = gp
+        self.torch = torch
+        self.p = prob
+        self.dev = dev
+        self.dtype = dtype
+        self.prec = prec
+        self.max_iters = max_iters
+        t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)  # noqa: E731
+        self.host = {k: np.ascontiguousarray(v, dtype=np.float64 if dtype == torch.float64 else np.float32)
+                     for k, v in dict(X=prob.X, om=prob.omega_hat, c2=prob.chi2, Wp=prob.W_probe, w=prob.Z).items()}
+        self.X = t(prob.X)
+        self.om = t(prob.omega_hat)
+        self.c2 = t(prob.chi2)
+        self.Wp = t(prob.W_probe)
+        self.w = t(prob.Z)
+        # fixed targets: one prior draw at the initial hyperparameters plus noise
+        fy = gp.gp_rff_prior_sample(prob.kind, prob.theta, self.X, self.om, self.c2, t(prob.W_y))[0]
+        self.y = (fy + prob.noise_y * t(prob.y_noise)).contiguous()
+        self.host["y"] = self.y.cpu().numpy()
+        self.theta = prob.theta.copy()
+        self.nu = np.log(np.expm1(self.theta))
+        self.m = np.zeros_like(self.nu)
+        self.v = np.zeros_like(self.nu)
+        self.t = 1
+        self.V = torch.zeros((prob.s + 1, prob.n), dtype=dtype, device=dev)
+        self.last = None
+
+    def pinned_inputs(self):
+        torch = self.torch
+        return {k: torch.from_numpy(v).pin_memory() for k, v in self.host.items()}
+
+    def load_inputs(self, pinned):
+        """Host-to-device copy of every input of a step (end-to-end timing)."""
+        self.X.copy_(pinned["X"], non_blocking=True)
+        self.om.copy_(pinned["om"], non_blocking=True)
+        self.c2.copy_(pinned["c2"], non_blocking=True)
+        self.Wp.copy_(pinned["Wp"], non_blocking=True)
+        self.w.copy_(pinned["w"], non_blocking=True)
+        self.y.copy_(pinned["y"], non_blocking=True)
+        return sum(v.numel() * v.element_size() for v in pinned.values())
+
+    def step(self):
+        gp, p = self.gp, self.p
+        th = self.theta
+        if self.dtype == self.torch.float64:
+            F = gp.gp_rff_prior_sample(p.kind, th, self.X, self.om, self.c2, self.Wp)
+            sig = th[-1]
+            B = self.torch.cat([self.y[None], F + sig * self.w], 0)
+        else:
+            F = gp.gp_rff_prior_sample(p.kind, th, self.X, self.om, self.c2, self.Wp)
+            B = gp.gp_pathwise_rhs(th, p.d, self.y, F, self.w)
+        V, info = gp.gp_solve_cg(p.kind, th, self.X, B, V0=self.V, max_iters=self.max_iters, tol=0.01,
+                                 prec=self.prec)
+        g = gp.gp_mll_grad_pathwise(p.kind, th, self.X, V, prec=self.prec)
+        gh = g.cpu().numpy()  # device -> host read of the step's result
+        self.theta = gp.gp_adam_softplus_step(self.nu, self.m, self.v, self.t, gh, lr=0.1)
+        self.t += 1
+        self.last = info
+        return info, gh
+
+    def work(self, info):
+        n, R = self.p.n, self.p.s + 1
+        return float(info.iters + 2) * n * n * R  # solve products (+1 initial residual) + gradient pass
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2405_18457_gb300 as gp
+    from paper_2405_18457_gb300 import workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gp.library()
+    prec = gp.GP_PREC_TC16 if args.prec == "tc16" else gp.GP_PREC_FP32
+    n = args.n
+    prob = workloads.pathwise(n=n, seed=rank)
+    rep = Replica(gp, torch, prob, dev, torch.float32, prec, args.max_iters)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        rep.step()
+    # ---- device-resident timed steps
+    clocks = Clocks(local)
+    barrier()
+    gp.gp_diag_reset(True)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    work = 0.0
+    iters = []
+    for k in range(args.steps):
+        flush_l2(torch, flush)
+        starts[k].record()
+        info, gh = rep.step()
+        ends[k].record()
+        work += rep.work(info)
+        iters.append(info.iters)
+    barrier()
+    clk = clocks.stop()
+    launches = gp.gp_diag_launches()
+    prod_ms, prod_cnt = gp.gp_diag_product_time()
+    gp.gp_diag_reset(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([total_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+        ww = torch.tensor([work], dtype=torch.float64, device=dev)
+        dist.all_reduce(ww)
+        work = float(ww.item())
+    value = work / total_s / 1e9
+
+    # ---- end-to-end: inputs copied from pinned host memory every step, gradient read back
+    pinned = rep.pinned_inputs()
+    barrier()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_work = 0.0
+    h2d = 0
+    e_start.record()
+    for k in range(args.steps):
+        h2d = rep.load_inputs(pinned)
+        info, gh = rep.step()
+        e_work += rep.work(info)
+    e_end.record()
+    barrier()
+    e_s = e_start.elapsed_time(e_end) / 1e3
+    if dist is not None:
+        tt = torch.tensor([e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_s = float(tt.item())
+        ww = torch.tensor([e_work], dtype=torch.float64, device=dev)
+        dist.all_reduce(ww)
+        e_work = float(ww.item())
+
+    # ---- plain FP64 GPU form of the same step, same tolerance (equal final residual norm)
+    fp64 = None
+    if args.fp64_steps > 0:
+        rep64 = Replica(gp, torch, prob, dev, torch.float64, gp.GP_PREC_FP32, args.max_iters)
+        rep64.step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = []
+        for _ in range(args.fp64_steps):
+            info64, _ = rep64.step()
+            res.append((info64.iters, info64.res_y, info64.res_z))
+        torch.cuda.synchronize()
+        fp64 = {"sec_per_step": (time.perf_counter() - t0) / args.fp64_steps,
+                "cg_iters": [r[0] for r in res], "res_y": res[-1][1], "res_z": res[-1][2]}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    d, R = prob.d, prob.s + 1
+    avg_launch_s = (prod_ms / 1e3) / max(prod_cnt, 1)
+    if prec == gp.GP_PREC_TC16:
+        flops_pair = 2.0 * d + 2.0 * R  # cross term x_i.x_j and the K V contraction
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak}
+    else:
+        flops_pair = 3.0 * d + 2.0 * R + 10.0
+        # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flops x max SM clock
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak}
+    achieved = flops_pair * n * n / avg_launch_s / 1e12 if prod_cnt else None
+    roof.update({"achieved": achieved, "frac": (achieved / roof["peak"]) if achieved else None,
+                 "traffic": None, "peak_source": peak_src, "kernel": "product (H V) kernel",
+                 "algorithmic_flops_per_pair": flops_pair, "avg_launch_ms": avg_launch_s * 1e3,
+                 "launches_timed": prod_cnt})
+    cpu = cpu_baseline(prob, R, budget_s=args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16-tensor/f32/f64" if prec == gp.GP_PREC_TC16 else "f32",
+        "data": "synthetic (seeded; shaped like the paper's UCI regression workloads)",
+        "config": {"workload": "pathwise MLL step: n=%d d=%d Matern-3/2 s=%d (R=%d) m=%d RFF, CG tol 0.01 warm start,"
+                               " pathwise gradient, Adam lr 0.1" % (n, d, prob.s, R, prob.m),
+                   "n": n, "d": d, "rhs": R, "precision": args.prec, "l2": "flushed between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "sec_per_step": total_s / args.steps,
+        "cg_iters_per_step": iters,
+        "fp64_form": fp64,
+        "speedup_vs_fp64_form": (fp64["sec_per_step"] / (total_s / args.steps)) if fp64 else None,
+        "e2e": {"value": e_work / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 8 * (d + 2)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prob, R, budget_s=15.0, rows_per_step=None):
+    """The FP64 CPU oracle (as it stands) on a bounded sample of the same product:
+    sampled rows of H V over all n columns and R right-hand sides."""
+    import oracle
+
+    X = prob.X
+    V = np.random.default_rng(0).standard_normal((R, prob.n))
+    rows = np.arange(16)
+    t0 = time.perf_counter()
+    oracle.kernel_mvm(prob.kind, prob.theta, X, X, V, add_noise=True, rows=rows)
+    t16 = time.perf_counter() - t0
+    k = rows_per_step or int(max(16, min(prob.n, 16 * budget_s / max(t16, 1e-6))))
+    rows = np.random.default_rng(1).choice(prob.n, size=k, replace=False)
+    t0 = time.perf_counter()
+    oracle.kernel_mvm(prob.kind, prob.theta, X, X, V, add_noise=True, rows=rows)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": k * prob.n * R / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d sampled rows of H V (n=%d, R=%d), FP64, %.1f s" % (k, prob.n, R, dt)}
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, one bounded sample of the product per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2405_18457_gb300 import workloads
+
+    import oracle
+
+    prob = workloads.pathwise(n=args.n, seed=0)
+    R = prob.s + 1
+    X = prob.X
+    V = np.random.default_rng(0).standard_normal((R, prob.n))
+    rows_per_step = args.ref_rows
+    for _ in range(args.warmup):
+        oracle.kernel_mvm(prob.kind, prob.theta, X, X, V, add_noise=True, rows=np.arange(rows_per_step))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        rows = np.random.default_rng(k).choice(prob.n, size=rows_per_step, replace=False)
+        oracle.kernel_mvm(prob.kind, prob.theta, X, X, V, add_noise=True, rows=rows)
+    dt = time.perf_counter() - t0
+    value = args.steps * rows_per_step * prob.n * R / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "pathwise workload product H V: %d sampled rows x n=%d x R=%d per step"
+                                  % (rows_per_step, prob.n, R), "n": prob.n, "d": prob.d, "rhs": R},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "%d rows per step" % rows_per_step},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["tc16", "fp32"], default=None)
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--max-iters", type=int, default=1000)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-rows", type=int, default=256)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.prec is None:
+        args.prec = "tc16" if _tc_ok() else "fp32"
+    run_ours(args)
+
+
+def _tc_ok():
+    import torch
+
+    import paper_2405_18457_gb300 as gp
+
+    try:
+        X = torch.zeros((1, 1), device="cuda")
+        gp.gp_kernel_mvm(0, [1.0, 1.0, 1.0], X, torch.zeros((1, 1), device="cuda"), prec=gp.GP_PREC_TC16)
+        return True
+    except gp.GPError:
+        return False
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,282 @@
+/*
+ * gp.h -- C ABI of the GB300 (sm_103a) iterative-GP library.
+ *
+ * The library implements the hot path of marginal-likelihood optimisation for
+ * iterative Gaussian processes (Lin et al., NeurIPS 2024, "Improving Linear System
+ * Solvers for Hyperparameter Optimisation in Iterative Gaussian Processes"):
+ * the matrix-free batched product H V = (K(X, X; theta) + sigma^2 I) V over s+1
+ * right-hand sides, the CG / alternating-projection / SGD solvers it drives
+ * (warm start, iteration budget, tolerance), random-Fourier-feature prior samples,
+ * the fused marginal-likelihood gradient estimators, pathwise-conditioned
+ * posterior samples and the softplus/Adam outer step.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns GP_OK (0) or a negative gp_status_t.  The
+ *     message of the last failure on the calling thread is gp_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - Hyperparameters: theta is a HOST array of d+2 doubles
+ *     [l_1 .. l_d, s_f, sigma] in natural (positive) units.  l_k are the ARD
+ *     length scales, s_f the signal amplitude (k(x, x) = s_f^2), sigma the noise
+ *     standard deviation.  Non-positive or non-finite entries -> GP_ERR_INVALID_ARG.
+ *   - kind: GP_RBF, k = s_f^2 exp(-r^2/2), or GP_MATERN32,
+ *     k = s_f^2 (1 + sqrt3 r) exp(-sqrt3 r), with r^2 = sum_k (x_k - x'_k)^2 / l_k^2.
+ *   - Points: X is n x d row-major in DEVICE memory (point i at X + i*d),
+ *     1 <= d <= GP_MAX_D.
+ *   - Blocks of vectors (right-hand sides, solutions, probes): "column-blocked",
+ *     vector c of a block occupies DEVICE memory V + c*ldv, ldv >= n.  In torch
+ *     terms a block is a contiguous (R, n) tensor.  Column 0 of a solver block
+ *     is the y system, columns 1..s the probe systems.
+ *   - Every pointer argument is borrowed: the caller owns all memory, the library
+ *     never allocates, frees or retains a pointer after the call returns.
+ *     Scratch memory is a caller-provided device buffer `ws` of at least the
+ *     bytes reported by the matching *_workspace() query (256-byte aligned).
+ *   - Work is stream-ordered on `stream`.  Functions that report solver
+ *     information (gp_solve_*) synchronise `stream` before returning; the others
+ *     return as soon as their work is enqueued.
+ *   - prec selects the arithmetic of the kernel-matrix tiles:
+ *       GP_PREC_FP32 : CUDA-core FP32 tiles (direct differences), FP32 vectors.
+ *       GP_PREC_TC16 : tcgen05 tensor cores, IEEE fp16 operands with FP32
+ *                      accumulation; the squared distance uses a three-term
+ *                      hi/lo split so that cancellation stays below 1e-6;
+ *                      FP32 vectors, FP64 solver scalars.
+ *     The *_f64 entry points are the plain FP64 GPU form (CUDA-core FP64 tiles
+ *     and FP64 vectors) used as the comparison baseline.
+ */
+#ifndef GP_GB300_H
+#define GP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_MAX_D 128
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_INVALID_ARG = -1, /* a null pointer, a size out of range, a bad theta */
+    GP_ERR_CUDA = -2,        /* a CUDA launch or runtime call failed            */
+    GP_ERR_BREAKDOWN = -3,   /* solver hit a non-finite or non-positive pivot    */
+    GP_ERR_DIVERGED = -4,    /* SGD residual estimate grew beyond 1e6 x start    */
+    GP_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                    */
+    GP_ERR_UNSUPPORTED = -6, /* valid request this build cannot serve            */
+    GP_ERR_WORKSPACE = -7    /* ws is null, misaligned or smaller than required  */
+} gp_status_t;
+
+typedef enum { GP_RBF = 0, GP_MATERN32 = 1 } gp_kernel_t;
+typedef enum { GP_PREC_FP32 = 1, GP_PREC_TC16 = 2 } gp_prec_t;
+
+/* Loop condition of Alg. 1-3.  GP_STOP_BOTH (default): iterate while
+ * t < budget and (||r_y|| > tol or ||r_z|| > tol), i.e. stop once BOTH split
+ * norms reach tol, as App. B "Linear System Solver" states.  GP_STOP_EITHER:
+ * the listing's conjunction, stop as soon as either norm reaches tol. */
+typedef enum { GP_STOP_BOTH = 0, GP_STOP_EITHER = 1 } gp_stop_t;
+
+/* Solver report.  res_y = ||r_y|| and res_z = (1/s) sum_j ||r_j|| are the
+ * relative residual norms of the normalised systems (App. B); for SGD they
+ * are the residual estimate of Alg. 3.  converged = 1 when the stop rule was
+ * met before the budget ran out (GP_OK with converged = 0 is not an error). */
+typedef struct {
+    int64_t iters;
+    int converged;
+    int status;
+    double res_y;
+    double res_z;
+} gp_solve_info_t;
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *gp_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int gp_version(void);
+
+/* Diagnostics (no counterpart in the paper; used by benchmarks).
+ * gp_diag_reset(t) zeroes the launch counter and, when t != 0, starts timing
+ * every kernel-matrix product kernel with CUDA events recorded on its launch
+ * stream (t == 0 stops timing).  gp_diag_launches() returns the number of
+ * library kernels launched since the reset.  gp_diag_product_time() waits for
+ * the recorded events and returns the summed duration (ms) and the number of
+ * timed product launches. */
+void gp_diag_reset(int time_products);
+long long gp_diag_launches(void);
+int gp_diag_product_time(double *total_ms, long long *count);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel matrix-vector products (Sec. 2 H_theta; Eq. standard_system,        */
+/* Eq. pathwise_system; every solver's "linear operator H(.)", Alg. 1-3)     */
+/* ------------------------------------------------------------------------ */
+
+/* Y[c] = K(X1, X2) V[c] (+ sigma^2 V[c] when add_noise), c < nrhs.
+ *   X1 : n1 x d device rows (output points), X2 : n2 x d device columns.
+ *   V  : nrhs vectors of length n2 (stride ldv >= n2), Y : nrhs x n1 (ldy >= n1).
+ *   add_noise = 1 requires X1 == X2 and n1 == n2 and gives H V.
+ *   n1 = 0 or n2 = 0 or nrhs = 0 is a valid no-op (Y is zeroed when n2 = 0).
+ * Y must not overlap V or X.  Error: GP_ERR_INVALID_ARG on bad sizes/pointers. */
+int gp_kernel_mvm(int kind, const double *theta, int d,
+                  const float *X1, int64_t n1, const float *X2, int64_t n2,
+                  const float *V, int64_t ldv, int nrhs, float *Y, int64_t ldy,
+                  int add_noise, int prec, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_kernel_mvm_workspace(int64_t n1, int64_t n2, int d, int nrhs, int prec);
+
+/* FP64 form of gp_kernel_mvm (plain CUDA-core FP64 tiles). */
+int gp_kernel_mvm_f64(int kind, const double *theta, int d,
+                      const double *X1, int64_t n1, const double *X2, int64_t n2,
+                      const double *V, int64_t ldv, int nrhs, double *Y, int64_t ldy,
+                      int add_noise, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_kernel_mvm_f64_workspace(int64_t n1, int64_t n2, int d, int nrhs);
+
+/* ------------------------------------------------------------------------ */
+/* Linear system solvers (App. B, Alg. 1-3) on H [v_y, v_1..v_s] = B          */
+/* ------------------------------------------------------------------------ */
+
+/* Batched conjugate gradients, Alg. 1 with P = identity.
+ *   B        : nrhs right-hand sides (device, stride n), unchanged.
+ *   V_inout  : warm start on entry (zeros for a cold start), solution on exit
+ *              (device, stride n).  Each column is solved on the normalised
+ *              system b / (||b|| + 1e-12) and rescaled on exit (App. B).
+ *   max_iters: iteration budget T (one CG iteration = one epoch).
+ *   tol      : relative residual tolerance tau; stop_rule a gp_stop_t.
+ * A column whose gamma = r^T r falls to <= 1e-30 is frozen.  Returns GP_OK with
+ * info filled (synchronises stream), GP_ERR_BREAKDOWN if a residual becomes
+ * non-finite. */
+int gp_solve_cg(int kind, const double *theta, int d, const float *X, int64_t n,
+                const float *B, int nrhs, float *V_inout, int64_t max_iters, double tol,
+                int stop_rule, int prec, gp_solve_info_t *info,
+                void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_cg_workspace(int64_t n, int d, int nrhs, int prec);
+
+int gp_solve_cg_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                    const double *B, int nrhs, double *V_inout, int64_t max_iters, double tol,
+                    int stop_rule, gp_solve_info_t *info, void *ws, size_t ws_bytes,
+                    cudaStream_t stream);
+size_t gp_solve_cg_f64_workspace(int64_t n, int d, int nrhs);
+
+/* Alternating projections, Alg. 2.  Blocks are contiguous row ranges
+ * [i*block_size, min((i+1)*block_size, n)); each iteration selects the block
+ * with the largest ||sum_c r_c[i]|| (ties: lowest index), adds
+ * H[i,i]^-1 r[i] to v[i] and subtracts H[:, i] H[i,i]^-1 r[i] from r.  The
+ * inverse of every diagonal block is computed once per call from its Cholesky
+ * factor (cached for the whole solve).  max_iters counts block iterations
+ * (epochs x n / block_size).  1 <= block_size <= 1024. */
+int gp_solve_ap(int kind, const double *theta, int d, const float *X, int64_t n,
+                const float *B, int nrhs, float *V_inout, int64_t block_size, int64_t max_iters,
+                double tol, int stop_rule, int prec, gp_solve_info_t *info,
+                void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_ap_workspace(int64_t n, int d, int nrhs, int64_t block_size, int prec);
+
+int gp_solve_ap_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                    const double *B, int nrhs, double *V_inout, int64_t block_size,
+                    int64_t max_iters, double tol, int stop_rule, gp_solve_info_t *info,
+                    void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_ap_f64_workspace(int64_t n, int d, int nrhs, int64_t block_size);
+
+/* Stochastic gradient descent with momentum, Alg. 3 (no Polyak averaging).
+ *   batch_idx : DEVICE int32 array of max_iters * batch row indices; iteration t
+ *               uses batch_idx[t*batch .. t*batch + batch - 1] (distinct rows
+ *               within one iteration; every index in [0, n)).
+ *   lr, momentum : gamma and rho of Alg. 3.  The momentum starts at zero.
+ * The residual estimate r starts at the normalised b and r[i] <- g[i] on the
+ * sampled rows.  GP_ERR_DIVERGED if the estimate exceeds 1e6 x its start. */
+int gp_solve_sgd(int kind, const double *theta, int d, const float *X, int64_t n,
+                 const float *B, int nrhs, float *V_inout, int64_t batch,
+                 const int32_t *batch_idx, double lr, double momentum, int64_t max_iters,
+                 double tol, int stop_rule, int prec, gp_solve_info_t *info,
+                 void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_sgd_workspace(int64_t n, int d, int nrhs, int64_t batch, int prec);
+
+int gp_solve_sgd_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                     const double *B, int nrhs, double *V_inout, int64_t batch,
+                     const int32_t *batch_idx, double lr, double momentum, int64_t max_iters,
+                     double tol, int stop_rule, gp_solve_info_t *info,
+                     void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_sgd_f64_workspace(int64_t n, int d, int nrhs, int64_t batch);
+
+/* ------------------------------------------------------------------------ */
+/* Random Fourier features (Sec. 2 "Pathwise Conditioning"; App. B "Kernel     */
+/* Function and Random Features")                                            */
+/* ------------------------------------------------------------------------ */
+
+/* F[j][i] = f_j(x_i) = s_f sqrt(2/m) sum_{l < m/2} ( W[j][l] cos(w_l . x_i)
+ *                                               + W[j][m/2 + l] sin(w_l . x_i) )
+ * with frequencies w_l = omega_hat_l / l (RBF) or omega_hat_l / l * sqrt(3 / u_l)
+ * (Matern-3/2; u_l ~ chi^2_3, the Student-t spectral density).  The random
+ * parameters are inputs, fixed across calls so that the prior sample stays the
+ * same function while theta changes (App. B).
+ *   omega_hat : (m/2) x d device, chi2 : m/2 device (may be NULL for RBF),
+ *   W : s x m device (row j = sample j), F : s x n device (stride ldf >= n).
+ * m must be even and >= 2. */
+int gp_rff_prior_sample(int kind, const double *theta, int d, const float *X, int64_t n,
+                        int m, const float *omega_hat, const float *chi2, const float *W,
+                        int s, float *F, int64_t ldf, cudaStream_t stream);
+int gp_rff_prior_sample_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                            int m, const double *omega_hat, const double *chi2, const double *W,
+                            int s, double *F, int64_t ldf, cudaStream_t stream);
+
+/* Pathwise probe right-hand sides (App. B): B = [y, xi_1 .. xi_s] with
+ * xi_j = F_j + sigma * w_j (epsilon = sigma w, w fixed).  y : n, F, w : s x n,
+ * B : (s+1) x n, all device, stride n. */
+int gp_pathwise_rhs(const double *theta, int d, const float *y, const float *F, const float *w,
+                    int64_t n, int s, float *B, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Marginal-likelihood gradient estimators (Eq. mll_grad, Eq. trace,           */
+/* Eq. pathwise_estimator), fused over kernel tiles                          */
+/* ------------------------------------------------------------------------ */
+
+/* Standard (Hutchinson) estimator:
+ *   grad_k = 1/2 v_y^T dH_k v_y - 1/(2s) sum_j v_j^T dH_k z_j
+ *   Vsol : (s+1) x n = [v_y, v_1..v_s] (solutions), Z : s x n probes.
+ * grad : DEVICE array of d+2 doubles, d L / d theta in theta's order (ascent
+ * direction of the log marginal likelihood). */
+int gp_mll_grad_standard(int kind, const double *theta, int d, const float *X, int64_t n,
+                         const float *Vsol, const float *Z, int s, double *grad, int prec,
+                         void *ws, size_t ws_bytes, cudaStream_t stream);
+/* Pathwise estimator:
+ *   grad_k = 1/2 v_y^T dH_k v_y - 1/(2s) sum_j zhat_j^T dH_k zhat_j,
+ *   Vsol = [v_y, zhat_1..zhat_s] solving H Vsol = [y, xi_1..xi_s]. */
+int gp_mll_grad_pathwise(int kind, const double *theta, int d, const float *X, int64_t n,
+                         const float *Vsol, int s, double *grad, int prec,
+                         void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_mll_grad_workspace(int64_t n, int d, int s, int prec);
+
+int gp_mll_grad_standard_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                             const double *Vsol, const double *Z, int s, double *grad,
+                             void *ws, size_t ws_bytes, cudaStream_t stream);
+int gp_mll_grad_pathwise_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                             const double *Vsol, int s, double *grad,
+                             void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_mll_grad_f64_workspace(int64_t n, int d, int s);
+
+/* ------------------------------------------------------------------------ */
+/* Posterior samples by pathwise conditioning (Eq. pathwise_conditioning,     */
+/* Sec. 3 "Amortising Linear Solves")                                        */
+/* ------------------------------------------------------------------------ */
+
+/* out[j](x*) = Fstar[j](x*) + k(x*, X) (v_y - zhat_j),  j < s.
+ *   Xstar : nstar x d, X : n x d, Vsol : (s+1) x n (stride n),
+ *   Fstar : s x nstar prior samples at Xstar (gp_rff_prior_sample with the same
+ *   random parameters), out : s x nstar.  All device. */
+int gp_posterior_samples(int kind, const double *theta, int d, const float *Xstar, int64_t nstar,
+                         const float *X, int64_t n, const float *Vsol, int s, const float *Fstar,
+                         float *out, int prec, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_posterior_samples_workspace(int64_t nstar, int64_t n, int d, int s, int prec);
+
+/* ------------------------------------------------------------------------ */
+/* Outer loop (Sec. 2.1 "Outer-Loop Optimiser"; App. B "Iterative Optimiser") */
+/* ------------------------------------------------------------------------ */
+
+/* One Adam ASCENT step on the softplus parameters nu (theta = log(1 + e^nu)).
+ * HOST arrays of P = d+2 doubles: nu, m, v (updated in place), grad_theta (the
+ * estimator output copied to the host), theta_out (softplus(nu) after the step).
+ * t >= 1 is the step count for bias correction. */
+int gp_adam_softplus_step(int P, double *nu, double *m, double *v, int64_t t,
+                          const double *grad_theta, double lr, double beta1, double beta2,
+                          double eps, double *theta_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_GB300_H */

@@ -1,0 +1,39 @@
+"""GB300 (sm_103a) iterative-GP hot path: Python binding of libgp_gb300.so.
+
+Every function here only marshals arguments (torch CUDA tensors -> raw device
+pointers, the current CUDA stream, caller-owned workspace) into the C ABI of
+``include/gp.h``; all arithmetic runs in the library's CUDA kernels.  There is
+no CPU fallback: if the library cannot be loaded or no CUDA device is present
+the call raises.
+
+Layouts follow the C ABI: points X are (n, d) float32/float64 row-major, blocks
+of vectors are (R, n) with one right-hand side per row, theta is a sequence of
+d+2 floats [l_1..l_d, s_f, sigma].
+"""
+from __future__ import annotations
+
+from ._binding import (  # noqa: F401
+    GP_MATERN32,
+    GP_PREC_FP32,
+    GP_PREC_TC16,
+    GP_RBF,
+    GP_STOP_BOTH,
+    GP_STOP_EITHER,
+    GPError,
+    SolveInfo,
+    gp_adam_softplus_step,
+    gp_diag_launches,
+    gp_diag_product_time,
+    gp_diag_reset,
+    gp_kernel_mvm,
+    gp_mll_grad_pathwise,
+    gp_mll_grad_standard,
+    gp_pathwise_rhs,
+    gp_posterior_samples,
+    gp_rff_prior_sample,
+    gp_solve_ap,
+    gp_solve_cg,
+    gp_solve_sgd,
+    library,
+    library_path,
+)

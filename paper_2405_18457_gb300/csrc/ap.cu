@@ -1,0 +1,487 @@
+// Alternating projections, Alg. 2 (App. B "Alternating Projections").
+//
+// Set-up per call (= per marginal-likelihood step): every diagonal block
+// H[i, i] (block_size x block_size, the ragged last block padded with the
+// identity) is materialised, Cholesky-factored and turned into its explicit
+// inverse H[i,i]^-1 = L^-T L^-1 by blocked batched kernels (32-wide panels,
+// the O(b^3) parts on a tiled batched GEMM).  The paper caches the Cholesky
+// factor and applies chol_solve; the explicit inverse gives the same
+// H[i,i]^-1 r[i] through one small matrix product per iteration instead of two
+// sequential triangular solves.
+//
+// Iteration: block score ||sum_c r_c[i]|| -> argmax on the device -> delta =
+// H[i,i]^-1 r[i] -> v[i] += delta -> r -= H[:, i] delta (kernel panel product
+// with a device-resident column offset) -> split norms and loop condition.
+#include "solver_common.cuh"
+
+#include <algorithm>
+#include <type_traits>
+
+namespace gp {
+
+namespace {
+
+constexpr int PW = 32;  // panel width of the blocked factorisation
+
+// ---------------------------------------------------------------- batched GEMM
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, 64x64 tiles.
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_batched_kernel(int M, int N, int K, T alpha, const T *A, int lda,
+                                                           int64_t sA, const T *B, int ldb, int64_t sB, T beta,
+                                                           T *C, int ldc, int64_t sC) {
+    __shared__ T As[16][64 + 1];
+    __shared__ T Bs[16][64 + 1];
+    const int b = blockIdx.z;
+    A += b * sA;
+    B += b * sB;
+    C += b * sC;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            int kk = e / 64, mm = e % 64;
+            int gm = m0 + mm, gk = k0 + kk;
+            T v = T(0);
+            if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+            As[kk][mm] = v;
+            int gn = n0 + mm;
+            T w = T(0);
+            if (gn < N && gk < K) w = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+            Bs[kk][mm] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            T *cp = C + (int64_t)gm * ldc + gn;
+            *cp = alpha * acc[i][j] + (beta == T(0) ? T(0) : beta * *cp);
+        }
+    }
+}
+
+template <typename T, bool TA, bool TB>
+int gemm_batched(int M, int N, int K, T alpha, const T *A, int lda, int64_t sA, const T *B, int ldb, int64_t sB,
+                 T beta, T *C, int ldc, int64_t sC, int batch, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return GP_OK;
+    dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64), (unsigned)batch);
+    gemm_batched_kernel<T, TA, TB><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    return check_launch("gemm_batched_kernel");
+}
+
+// H[b] block matrix: k(x_{lo+a}, x_{lo+a'}) + sigma^2 delta; padded rows -> identity.
+template <typename T>
+__global__ void ap_build_blocks_kernel(const KP<T> kp, const T *X, int64_t n, int bs, int bsp, T *Hb) {
+    const int b = blockIdx.z;
+    const int a = blockIdx.y * 16 + threadIdx.y;
+    const int ap = blockIdx.x * 16 + threadIdx.x;
+    if (a >= bsp || ap >= bsp) return;
+    const int64_t lo = (int64_t)b * bs;
+    const int64_t i = lo + a, j = lo + ap;
+    T v;
+    if (a >= bs || ap >= bs || i >= n || j >= n) {
+        v = (a == ap) ? T(1) : T(0);
+    } else {
+        T r2 = T(0);
+        for (int k = 0; k < kp.d; ++k) {
+            T t = (X[i * kp.d + k] - X[j * kp.d + k]) * kp.inv_ell[k];
+            r2 += t * t;
+        }
+        v = kval(kp.kind, kp.sf2, r2) + (a == ap ? kp.sigma2 : T(0));
+    }
+    Hb[(int64_t)b * bsp * bsp + (int64_t)a * bsp + ap] = v;
+}
+
+// Unblocked Cholesky of the 32x32 diagonal tile at (p, p), one warp per matrix.
+template <typename T>
+__global__ void potf2_kernel(T *Hb, int bsp, int p, int *fail) {
+    __shared__ T L[PW][PW + 1];
+    T *A = Hb + (int64_t)blockIdx.x * bsp * bsp;
+    const int lane = threadIdx.x;
+    for (int k = 0; k < PW; ++k) L[lane][k] = A[(int64_t)(p + lane) * bsp + p + k];
+    __syncwarp();
+    for (int j = 0; j < PW; ++j) {
+        T djj = L[j][j];
+        if (!(djj > T(0))) {
+            if (lane == 0) atomicExch(fail, 1);
+            djj = T(1);
+        }
+        T ljj = sqrt(djj);
+        __syncwarp();
+        if (lane == j) L[j][j] = ljj;
+        if (lane > j) L[lane][j] = L[lane][j] / ljj;
+        __syncwarp();
+        if (lane > j)
+            for (int k = j + 1; k <= lane; ++k) L[lane][k] -= L[lane][j] * L[k][j];
+        __syncwarp();
+    }
+    for (int k = 0; k < PW; ++k) A[(int64_t)(p + lane) * bsp + p + k] = (k <= lane) ? L[lane][k] : T(0);
+}
+
+// Rows i >= p+32: A[i, p:p+32] <- A[i, p:p+32] L_pp^-T  (one thread per row).
+template <typename T>
+__global__ void trsm_right_kernel(T *Hb, int bsp, int p) {
+    __shared__ T L[PW][PW + 1];
+    T *A = Hb + (int64_t)blockIdx.x * bsp * bsp;
+    for (int e = threadIdx.x; e < PW * PW; e += blockDim.x) L[e / PW][e % PW] = A[(int64_t)(p + e / PW) * bsp + p + e % PW];
+    __syncthreads();
+    const int i = p + PW + blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= bsp) return;
+    T x[PW];
+#pragma unroll
+    for (int j = 0; j < PW; ++j) x[j] = A[(int64_t)i * bsp + p + j];
+#pragma unroll
+    for (int j = 0; j < PW; ++j) {
+        T s = x[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= x[k] * L[j][k];
+        x[j] = s / L[j][j];
+    }
+#pragma unroll
+    for (int j = 0; j < PW; ++j) A[(int64_t)i * bsp + p + j] = x[j];
+}
+
+// Z[p:p+32, 0:p+32] <- L_pp^-1 Z[p:p+32, 0:p+32]  (one thread per column).
+template <typename T>
+__global__ void trsm_left_kernel(const T *Lb, T *Zb, int bsp, int p) {
+    __shared__ T L[PW][PW + 1];
+    const T *A = Lb + (int64_t)blockIdx.x * bsp * bsp;
+    T *Z = Zb + (int64_t)blockIdx.x * bsp * bsp;
+    for (int e = threadIdx.x; e < PW * PW; e += blockDim.x) L[e / PW][e % PW] = A[(int64_t)(p + e / PW) * bsp + p + e % PW];
+    __syncthreads();
+    const int col = blockIdx.y * blockDim.x + threadIdx.x;
+    if (col >= p + PW) return;
+    T z[PW];
+#pragma unroll
+    for (int i = 0; i < PW; ++i) z[i] = Z[(int64_t)(p + i) * bsp + col];
+#pragma unroll
+    for (int i = 0; i < PW; ++i) {
+        T s = z[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[i][k] * z[k];
+        z[i] = s / L[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < PW; ++i) Z[(int64_t)(p + i) * bsp + col] = z[i];
+}
+
+template <typename T>
+__global__ void identity_kernel(T *Zb, int bsp, int nb) {
+    const int64_t tot = (int64_t)nb * bsp * bsp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e % ((int64_t)bsp * bsp);
+        Zb[e] = (r / bsp == r % bsp) ? T(1) : T(0);
+    }
+}
+
+// score[b] = sum_{rows of block b} (sum_c r_c[row])^2
+template <typename T>
+__global__ void ap_score_kernel(const T *r, int64_t n, int R, int bs, double *score, const SolverState *st) {
+    if (st->done) return;
+    const int b = blockIdx.x;
+    const int64_t lo = (int64_t)b * bs, hi = min(n, lo + bs);
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        double t = 0.0;
+        for (int c = 0; c < R; ++c) t += (double)r[(int64_t)c * n + i];
+        s += t * t;
+    }
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        score[b] = t;
+    }
+}
+
+// argmax over blocks, ties to the lowest index; writes the row offset of the block.
+__global__ void ap_select_kernel(const double *score, int nb, int bs, int64_t *col0, const SolverState *st) {
+    if (st->done) return;
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    double best = -1.0;
+    int besti = 0x7fffffff;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double v = score[b];
+        if (v > best || (v == best && b < besti)) {
+            best = v;
+            besti = b;
+        }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            double v = bv[threadIdx.x + s];
+            int i = bi[threadIdx.x + s];
+            if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && i < bi[threadIdx.x])) {
+                bv[threadIdx.x] = v;
+                bi[threadIdx.x] = i;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *col0 = (int64_t)bi[0] * bs;
+}
+
+// delta[c][a] = sum_a' Hinv[blk][a][a'] r[c][lo + a'],  a < bs (rows beyond n -> 0)
+template <typename T>
+__global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, int bs, const T *r, int64_t n, int R,
+                                                       const int64_t *col0, T *delta, const SolverState *st) {
+    if (st->done) return;
+    __shared__ T Hs[64][33];
+    __shared__ T Rs[32][17];
+    const int64_t lo = *col0;
+    const int blk = (int)(lo / bs);
+    const int m = (int)min((int64_t)bs, n - lo);
+    const T *Hm = Hinv + (int64_t)blk * bsp * bsp;
+    const int a0 = blockIdx.x * 64, c0 = blockIdx.y * 16;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int k0 = 0; k0 < m; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 256) {
+            int aa = e / 32, kk = e % 32;
+            Hs[aa][kk] = (a0 + aa < m && k0 + kk < m) ? Hm[(int64_t)(a0 + aa) * bsp + k0 + kk] : T(0);
+        }
+        for (int e = tid; e < 32 * 16; e += 256) {
+            int cc = e / 32, kk = e % 32;
+            Rs[kk][cc] = (k0 + kk < m && c0 + cc < R) ? r[(int64_t)(c0 + cc) * n + lo + k0 + kk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            T rv = Rs[kk][tx];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] += Hs[ty + 16 * i][kk] * rv;
+        }
+        __syncthreads();
+    }
+    const int c = c0 + tx;
+    if (c >= R) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int a = a0 + ty + 16 * i;
+        if (a < bs) delta[(int64_t)c * bs + a] = (a < m) ? acc[i] : T(0);
+    }
+}
+
+// v[c][lo + a] += delta[c][a]
+template <typename T>
+__global__ void ap_vupdate_kernel(T *V, int64_t n, int bs, const int64_t *col0, const T *delta,
+                                  const SolverState *st) {
+    if (st->done) return;
+    const int c = blockIdx.y;
+    const int64_t lo = *col0;
+    const int m = (int)min((int64_t)bs, n - lo);
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x)
+        V[(int64_t)c * n + lo + a] += delta[(int64_t)c * bs + a];
+}
+
+__global__ void ap_norm_kernel(int R, int P, const double *part, SolverState *st, long long max_iters, double tol,
+                               int stop_rule, int first) {
+    if (threadIdx.x != 0) return;
+    if (!first && st->done) return;
+    double sq[512];
+    for (int c = 0; c < R; ++c) sq[c] = sum_parts(part, c, P);
+    if (first) {
+        st->done = 0;
+        st->status = GP_OK;
+    }
+    finish_norms(st, sq, R, first ? 0 : st->iter + 1, max_iters, tol, stop_rule);
+}
+
+}  // namespace
+
+template <typename T>
+static size_t ap_panel_ws(int64_t n, int64_t bs, int d, int R, int prec) {
+    (void)prec;
+    return mvm_simt_workspace<T>(n, bs, R);
+}
+
+template <typename T>
+size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec) {
+    const int P = nparts_for(n);
+    const int64_t nb = cdiv(n, bs), bsp = rup(bs, PW);
+    Carver c(nullptr);
+    c.take<T>((size_t)R * n);               // residual
+    c.take<T>((size_t)R * n);               // H v (set-up)
+    c.take<T>((size_t)R * bs);              // delta
+    c.take<T>((size_t)nb * bsp * bsp);      // factor / inverse
+    c.take<T>((size_t)nb * bsp * bsp);      // L^-1
+    c.take<double>((size_t)R * P);
+    c.take<double>((size_t)R);
+    c.take<double>((size_t)nb);
+    c.take<int64_t>(1);
+    c.take<int>(1);
+    c.take<SolverState>(1);
+    c.take<char>(std::max(ap_panel_ws<T>(n, bs, d, R, prec), mvm_workspace<T>(n, n, d, R, prec)));
+    return c.bytes();
+}
+
+template <typename T>
+int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t bs64, int64_t max_iters,
+             double tol, int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes,
+             cudaStream_t st) {
+    if (R > 512) {
+        set_error("nrhs must be <= 512");
+        return GP_ERR_INVALID_ARG;
+    }
+    const int bs = (int)std::min<int64_t>(bs64, n);
+    const int P = nparts_for(n);
+    const int nb = (int)cdiv(n, bs);
+    const int bsp = (int)rup(bs, PW);
+    Carver c(ws);
+    T *r = c.take<T>((size_t)R * n);
+    T *HV = c.take<T>((size_t)R * n);
+    T *delta = c.take<T>((size_t)R * bs);
+    T *Hb = c.take<T>((size_t)nb * bsp * bsp);
+    T *Zb = c.take<T>((size_t)nb * bsp * bsp);
+    double *part = c.take<double>((size_t)R * P);
+    double *scale = c.take<double>(R);
+    double *score = c.take<double>(nb);
+    int64_t *col0 = c.take<int64_t>(1);
+    int *fail = c.take<int>(1);
+    SolverState *sd = c.take<SolverState>(1);
+    size_t mwb = std::max(ap_panel_ws<T>(n, bs, kp.d, R, prec), mvm_workspace<T>(n, n, kp.d, R, prec));
+    void *mw = c.take<char>(mwb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+
+    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
+    const dim3 gp_((unsigned)P, (unsigned)R);
+    // ---- block inverses H[i,i]^-1 (cached for the whole solve)
+    GP_TRY_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
+    ap_build_blocks_kernel<T><<<dim3(bsp / 16, bsp / 16, nb), dim3(16, 16), 0, st>>>(kp, X, n, bs, bsp, Hb);
+    GP_TRY(check_launch("ap_build_blocks_kernel", 1));
+    for (int p = 0; p < bsp; p += PW) {
+        potf2_kernel<T><<<nb, 32, 0, st>>>(Hb, bsp, p, fail);
+        const int rest = bsp - p - PW;
+        if (rest > 0) {
+            trsm_right_kernel<T><<<dim3(nb, (unsigned)cdiv(rest, 128)), 128, 0, st>>>(Hb, bsp, p);
+            const int64_t off = (int64_t)(p + PW) * bsp;
+            GP_TRY((gemm_batched<T, false, true>(rest, rest, PW, T(-1), Hb + off + p, bsp, (int64_t)bsp * bsp,
+                                                 Hb + off + p, bsp, (int64_t)bsp * bsp, T(1), Hb + off + p + PW, bsp,
+                                                 (int64_t)bsp * bsp, nb, st)));
+        }
+        GP_TRY(check_launch("blocked cholesky", rest > 0 ? 2 : 1));
+    }
+    // L^-1 by blocked forward substitution on the identity
+    identity_kernel<T><<<1024, 256, 0, st>>>(Zb, bsp, nb);
+    GP_TRY(check_launch("identity_kernel"));
+    for (int p = 0; p < bsp; p += PW) {
+        if (p > 0)
+            GP_TRY((gemm_batched<T, false, false>(PW, p, p, T(-1), Hb + (int64_t)p * bsp, bsp, (int64_t)bsp * bsp, Zb,
+                                                  bsp, (int64_t)bsp * bsp, T(1), Zb + (int64_t)p * bsp, bsp,
+                                                  (int64_t)bsp * bsp, nb, st)));
+        trsm_left_kernel<T><<<dim3(nb, (unsigned)cdiv(p + PW, 128)), 128, 0, st>>>(Hb, Zb, bsp, p);
+        GP_TRY(check_launch("blocked triangular inverse"));
+    }
+    // H^-1 = L^-T L^-1
+    GP_TRY((gemm_batched<T, true, false>(bsp, bsp, bsp, T(1), Zb, bsp, (int64_t)bsp * bsp, Zb, bsp,
+                                         (int64_t)bsp * bsp, T(0), Hb, bsp, (int64_t)bsp * bsp, nb, st)));
+
+    // ---- normalisation and initial residual r = b~ - H v~
+    coldot_kernel<T><<<gp_, 256, 0, st>>>(B, B, n, P, part, nullptr);
+    norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
+    GP_TRY(check_launch("ap setup", 3));
+    GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
+    init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
+    coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
+    ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 1);
+    GP_TRY(check_launch("ap start", 3));
+
+    int hfail = 0;
+    GP_TRY_CUDA(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SolverState hs{};
+    GP_TRY(poll_state(sd, &hs, st));
+    if (hfail) {
+        scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
+        set_error("AP: a diagonal block of H is not positive definite");
+        GP_TRY_CUDA(cudaStreamSynchronize(st));
+        info->status = GP_ERR_BREAKDOWN;
+        return GP_ERR_BREAKDOWN;
+    }
+    MvmArgs<T> pa{};
+    pa.kp = kp;
+    pa.X1 = X;
+    pa.n1 = n;
+    pa.X2 = X;
+    pa.n2 = bs;
+    pa.n2_total = n;
+    pa.col0_dev = col0;
+    pa.V = delta;
+    pa.ldv = bs;
+    pa.R = R;
+    pa.Y = r;
+    pa.ldy = n;
+    pa.alpha = T(-1);
+    pa.beta = T(1);
+    pa.diag_coef = -kp.sigma2;
+    pa.Vd = delta;
+    pa.ldvd = bs;
+    pa.diag_from_col0 = 1;
+    pa.done = &sd->done;
+    const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16));
+    int64_t t = 0, chunk = 8;
+    while (!hs.done && t < max_iters) {
+        int64_t k = std::min<int64_t>(chunk, max_iters - t);
+        for (int64_t it = 0; it < k; ++it, ++t) {
+            ap_score_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, sd);
+            ap_select_kernel<<<1, 1024, 0, st>>>(score, nb, bs, col0, sd);
+            ap_delta_kernel<T><<<gdel, 256, 0, st>>>(Hb, bsp, bs, r, n, R, col0, delta, sd);
+            ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, col0, delta, sd);
+            GP_TRY(check_launch("ap iteration", 4));
+            GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
+            coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, &sd->done);
+            ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 0);
+            GP_TRY(check_launch("ap norms", 2));
+        }
+        chunk = std::min<int64_t>(chunk * 2, 64);
+        GP_TRY(poll_state(sd, &hs, st));
+    }
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
+    GP_TRY(check_launch("ap rescale"));
+    GP_TRY(poll_state(sd, &hs, st));
+    fill_info(hs, info);
+    if (hs.status != GP_OK) {
+        set_error("AP breakdown at iteration %lld", hs.iter);
+        return hs.status;
+    }
+    return GP_OK;
+}
+
+template size_t ap_workspace<float>(int64_t, int, int, int64_t, int);
+template size_t ap_workspace<double>(int64_t, int, int, int64_t, int);
+template int ap_solve<float>(const KP<float> &, const float *, int64_t, const float *, int, float *, int64_t,
+                             int64_t, double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t);
+template int ap_solve<double>(const KP<double> &, const double *, int64_t, const double *, int, double *, int64_t,
+                              int64_t, double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t);
+
+}  // namespace gp

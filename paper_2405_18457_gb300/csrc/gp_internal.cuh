@@ -1,0 +1,234 @@
+// Internal declarations shared by the translation units of libgp_gb300.so.
+// Nothing here is part of the C ABI (include/gp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <cmath>
+
+#include "gp.h"
+
+namespace gp {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define GP_TRY_CUDA(call)                                                              \
+    do {                                                                               \
+        cudaError_t gp_e_ = (call);                                                    \
+        if (gp_e_ != cudaSuccess) {                                                    \
+            ::gp::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(gp_e_), \
+                            __FILE__, __LINE__);                                       \
+            return GP_ERR_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+#define GP_TRY(call)                  \
+    do {                              \
+        int gp_s_ = (call);           \
+        if (gp_s_ != GP_OK)           \
+            return gp_s_;             \
+    } while (0)
+
+// Checks the launch(es) just enqueued and counts them for gp_diag_launches().
+int check_launch(const char *what, int count = 1);
+
+// Optional CUDA-event timing of the kernel-matrix product kernels
+// (gp_diag_reset(1) turns it on): events recorded on the launch stream around
+// each product kernel.
+void prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+__host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t rup(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// ---------------------------------------------------------------------------
+// Kernel hyperparameters, pre-digested on the host (theta is a host array)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct KP {
+    int kind;  // GP_RBF / GP_MATERN32
+    int d;
+    T inv_ell[GP_MAX_D];
+    T ell[GP_MAX_D];
+    T sf;      // signal amplitude s_f
+    T sf2;     // s_f^2
+    T sigma;   // noise std
+    T sigma2;  // sigma^2
+};
+
+// Validates theta (finite, positive) and fills kp.  Returns GP_OK or
+// GP_ERR_INVALID_ARG with the message set.
+template <typename T>
+int make_kp(int kind, const double *theta, int d, KP<T> *kp);
+
+// ---------------------------------------------------------------------------
+// Workspace carving: every buffer 256-byte aligned, sizes computed by the same
+// code path that carves them (dry run with base == nullptr).
+// ---------------------------------------------------------------------------
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename U>
+    U *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        U *p = base ? reinterpret_cast<U *>(base + off) : nullptr;
+        off += count * sizeof(U);
+        return p;
+    }
+    size_t bytes() const { return (off + 255) & ~size_t(255); }
+};
+
+int check_ws(void *ws, size_t ws_bytes, size_t need);
+
+// ---------------------------------------------------------------------------
+// Kernel function (Sec. 2; App. B): value and the radial factor of dk/dl
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float kval(int kind, float sf2, float r2) {
+    if (kind == GP_RBF) return sf2 * expf(-0.5f * r2);
+    float r = sqrtf(r2);
+    const float s3 = 1.7320508075688772f;
+    return sf2 * (1.0f + s3 * r) * expf(-s3 * r);
+}
+__device__ __forceinline__ double kval(int kind, double sf2, double r2) {
+    if (kind == GP_RBF) return sf2 * exp(-0.5 * r2);
+    double r = sqrt(r2);
+    const double s3 = 1.7320508075688772;
+    return sf2 * (1.0 + s3 * r) * exp(-s3 * r);
+}
+// phi(r) with dk/dl_k = phi(r) * (x_k - x'_k)^2 / l_k^3:
+//   RBF: phi = k ;  Matern-3/2: phi = 3 s_f^2 exp(-sqrt3 r).
+// Returns k through *kout.
+__device__ __forceinline__ float kphi(int kind, float sf2, float r2, float *kout) {
+    if (kind == GP_RBF) {
+        float k = sf2 * expf(-0.5f * r2);
+        *kout = k;
+        return k;
+    }
+    const float s3 = 1.7320508075688772f;
+    float r = sqrtf(r2);
+    float e = expf(-s3 * r);
+    *kout = sf2 * (1.0f + s3 * r) * e;
+    return 3.0f * sf2 * e;
+}
+__device__ __forceinline__ double kphi(int kind, double sf2, double r2, double *kout) {
+    if (kind == GP_RBF) {
+        double k = sf2 * exp(-0.5 * r2);
+        *kout = k;
+        return k;
+    }
+    const double s3 = 1.7320508075688772;
+    double r = sqrt(r2);
+    double e = exp(-s3 * r);
+    *kout = sf2 * (1.0 + s3 * r) * e;
+    return 3.0 * sf2 * e;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core (SIMT) products, T = float or double
+// ---------------------------------------------------------------------------
+// Y[c][i] = alpha * sum_j k(x1_i, x2_j) V[c][j] + beta * Y[c][i]
+//           + diag_coef * Vd[c][i - drow0]   for drow0 <= i < drow0 + ndiag
+// Columns may start at a device-resident offset col0 (points X2 + col0*d,
+// clipped to n2_total); the diagonal rows then start at col0 as well.
+template <typename T>
+struct MvmArgs {
+    KP<T> kp;
+    const T *X1;
+    int64_t n1;
+    const T *X2;
+    int64_t n2;           // number of columns (before clipping)
+    int64_t n2_total;     // points available in X2 when col0_dev is used
+    const int64_t *col0_dev;
+    const T *V;
+    int64_t ldv;
+    int R;
+    T *Y;
+    int64_t ldy;
+    T alpha, beta;
+    T diag_coef;          // 0 disables the diagonal term
+    const T *Vd;
+    int64_t ldvd;
+    int64_t drow0;        // ignored when diag_from_col0
+    int64_t ndiag;
+    int diag_from_col0;   // 1: diagonal rows are [col0, col0 + n2_eff)
+    const int *done;      // optional device flag: skip all work when *done != 0
+};
+
+template <typename T>
+size_t mvm_simt_workspace(int64_t n1, int64_t n2, int R);
+template <typename T>
+int mvm_simt(const MvmArgs<T> &a, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// Fused estimator reduction (Eq. mll_grad with Eq. trace / Eq. pathwise_estimator):
+// grad_p = sum_c lam_c U_c^T dH_p W_c.  Column 0 of U/W is U0/W0, columns
+// c >= 1 are U + (c-1)*ldu, W + (c-1)*ldw.
+template <typename T>
+struct GradArgs {
+    KP<T> kp;
+    const T *X;
+    int64_t n;
+    const T *U0, *U;
+    int64_t ldu;
+    const T *W0, *W;
+    int64_t ldw;
+    int R;
+    double lam0, lam_rest;  // lambda_0 and lambda_c for c >= 1
+    double *grad;           // device, d+2
+};
+template <typename T>
+size_t grad_simt_workspace(int64_t n, int d, int R);
+template <typename T>
+int grad_simt(const GradArgs<T> &a, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// tcgen05 path (fp16 operands, FP32 accumulation in tensor memory)
+// ---------------------------------------------------------------------------
+// Prepared operands for a point set under fixed theta.
+struct TcPoints {
+    const void *PA;   // n_pad x KD fp16, row operand (scaled, hi/lo split, norms)
+    const void *PB;   // n_pad x KD fp16, column operand
+    int64_t n, n_pad;
+    int KD;           // padded contraction length of the distance GEMM
+};
+size_t tc_points_bytes(int64_t n, int d);
+int tc_prepare_points(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out,
+                      cudaStream_t st);
+
+struct TcMvmArgs {
+    int kind;
+    TcPoints rows, cols;
+    const float *V;    // R x n2 fp32 (stride ldv)
+    int64_t ldv;
+    int R;
+    float *Y;
+    int64_t ldy;
+    float sf2;
+    float alpha, beta, diag_coef;
+    const float *Vd;
+    int64_t ldvd;
+    int64_t drow0, ndiag;
+    const int *done;
+};
+size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R);
+int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st);
+bool tc_available();
+
+// ---------------------------------------------------------------------------
+// Small device helpers used by several files
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace gp

@@ -1,0 +1,307 @@
+// Operator dispatch (CUDA-core vs tcgen05), random Fourier features, pathwise
+// right-hand sides and pathwise-conditioned posterior samples.
+#include "solvers.cuh"
+
+#include <algorithm>
+#include <type_traits>
+
+namespace gp {
+
+// ===========================================================================
+// H V / K V dispatch
+// ===========================================================================
+template <typename T>
+size_t mvm_workspace(int64_t n1, int64_t n2, int d, int R, int prec) {
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16) {
+        Carver c(nullptr);
+        c.take<char>(tc_points_bytes(n1, d));
+        c.take<char>(tc_points_bytes(n2, d));
+        c.take<char>(tc_mvm_workspace(n1, n2, R));
+        return c.bytes();
+    }
+    return mvm_simt_workspace<T>(n1, n2, R);
+}
+
+template <typename T>
+int apply_mvm(const KP<T> &kp, const T *X1, int64_t n1, const T *X2, int64_t n2, const T *V, int64_t ldv,
+              int R, T *Y, int64_t ldy, int add_noise, int prec, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (prec == GP_PREC_TC16) {
+            Carver c(ws);
+            void *pa = c.take<char>(tc_points_bytes(n1, kp.d));
+            void *pb = c.take<char>(tc_points_bytes(n2, kp.d));
+            size_t tcw = tc_mvm_workspace(n1, n2, R);
+            void *tw = c.take<char>(tcw);
+            GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+            TcMvmArgs a{};
+            a.kind = kp.kind;
+            GP_TRY(tc_prepare_points(kp, X1, n1, pa, &a.rows, st));
+            if (X2 == X1 && n2 == n1) {
+                a.cols = a.rows;
+            } else {
+                GP_TRY(tc_prepare_points(kp, X2, n2, pb, &a.cols, st));
+            }
+            a.V = V;
+            a.ldv = ldv;
+            a.R = R;
+            a.Y = Y;
+            a.ldy = ldy;
+            a.sf2 = kp.sf2;
+            a.alpha = 1.0f;
+            a.beta = 0.0f;
+            a.diag_coef = add_noise ? kp.sigma2 : 0.0f;
+            a.Vd = V;
+            a.ldvd = ldv;
+            a.drow0 = 0;
+            a.ndiag = add_noise ? n1 : 0;
+            a.done = nullptr;
+            return tc_mvm(a, tw, tcw, st);
+        }
+    }
+    MvmArgs<T> a{};
+    a.kp = kp;
+    a.X1 = X1;
+    a.n1 = n1;
+    a.X2 = X2;
+    a.n2 = n2;
+    a.n2_total = n2;
+    a.col0_dev = nullptr;
+    a.V = V;
+    a.ldv = ldv;
+    a.R = R;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.alpha = T(1);
+    a.beta = T(0);
+    a.diag_coef = add_noise ? kp.sigma2 : T(0);
+    a.Vd = V;
+    a.ldvd = ldv;
+    a.drow0 = 0;
+    a.ndiag = add_noise ? n1 : 0;
+    a.diag_from_col0 = 0;
+    a.done = nullptr;
+    return mvm_simt<T>(a, ws, ws_bytes, st);
+}
+
+template size_t mvm_workspace<float>(int64_t, int64_t, int, int, int);
+template size_t mvm_workspace<double>(int64_t, int64_t, int, int, int);
+template int apply_mvm<float>(const KP<float> &, const float *, int64_t, const float *, int64_t, const float *,
+                              int64_t, int, float *, int64_t, int, int, void *, size_t, cudaStream_t);
+template int apply_mvm<double>(const KP<double> &, const double *, int64_t, const double *, int64_t,
+                               const double *, int64_t, int, double *, int64_t, int, int, void *, size_t,
+                               cudaStream_t);
+
+// Gradient dispatch.  The fused tensor-core estimator lives in tc.cu; the
+// CUDA-core reduction serves FP32 and FP64.
+size_t tc_grad_workspace(int64_t n, int d, int R);
+int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st);
+
+template <typename T>
+size_t grad_workspace(int64_t n, int d, int R, int prec) {
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16) return tc_grad_workspace(n, d, R);
+    return grad_simt_workspace<T>(n, d, R);
+}
+
+template <typename T>
+int apply_grad(const GradArgs<T> &a, int prec, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (prec == GP_PREC_TC16) return tc_grad(a, ws, ws_bytes, st);
+    }
+    return grad_simt<T>(a, ws, ws_bytes, st);
+}
+template size_t grad_workspace<float>(int64_t, int, int, int);
+template size_t grad_workspace<double>(int64_t, int, int, int);
+template int apply_grad<float>(const GradArgs<float> &, int, void *, size_t, cudaStream_t);
+template int apply_grad<double>(const GradArgs<double> &, int, void *, size_t, cudaStream_t);
+
+// ===========================================================================
+// Random Fourier features (App. B "Kernel Function and Random Features")
+// ===========================================================================
+namespace {
+
+constexpr int RP = 64;   // points per block
+constexpr int RFC = 32;  // frequencies per chunk
+
+__device__ __forceinline__ void sc(float a, float *s, float *c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sc(double a, double *s, double *c) { sincos(a, s, c); }
+
+// F[j][i] = s_f sqrt(2/m) sum_l W[j][l] cos(w_l.x_i) + W[j][h+l] sin(w_l.x_i)
+template <typename T, int SPT>
+__global__ void __launch_bounds__(256) rff_kernel(const KP<T> kp, const T *X, int64_t n, int m,
+                                                  const T *omega_hat, const T *chi2, const T *W, int s, T *F,
+                                                  int64_t ldf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = kp.d, h = m / 2;
+    constexpr int SB = 16 * SPT;  // samples per block
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // RP x d
+    T *Om = Xs + RP * d;                      // RFC x d
+    T *Cs = Om + RFC * d;                     // RP x (RFC+1)
+    T *Sn = Cs + RP * (RFC + 1);              // RP x (RFC+1)
+    T *Wc = Sn + RP * (RFC + 1);              // SB x (RFC+1)
+    T *Wsn = Wc + SB * (RFC + 1);             // SB x (RFC+1)
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t p0 = (int64_t)blockIdx.x * RP;
+    const int j0 = blockIdx.y * SB;
+    for (int e = tid; e < RP * d; e += 256) {
+        int r = e / d, k = e - r * d;
+        Xs[e] = (p0 + r < n) ? X[(p0 + r) * d + k] : T(0);
+    }
+    T acc[4][SPT];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) acc[p][q] = T(0);
+    for (int l0 = 0; l0 < h; l0 += RFC) {
+        __syncthreads();
+        for (int e = tid; e < RFC * d; e += 256) {
+            int l = e / d, k = e - l * d;
+            T w = T(0);
+            if (l0 + l < h) {
+                T t = (kp.kind == GP_MATERN32) ? sqrt(T(3) / chi2[l0 + l]) : T(1);
+                w = omega_hat[(int64_t)(l0 + l) * d + k] * kp.inv_ell[k] * t;
+            }
+            Om[e] = w;
+        }
+        for (int e = tid; e < SB * RFC; e += 256) {
+            int j = e / RFC, l = e - j * RFC;
+            bool ok = (j0 + j < s) && (l0 + l < h);
+            Wc[j * (RFC + 1) + l] = ok ? W[(int64_t)(j0 + j) * m + l0 + l] : T(0);
+            Wsn[j * (RFC + 1) + l] = ok ? W[(int64_t)(j0 + j) * m + h + l0 + l] : T(0);
+        }
+        __syncthreads();
+        for (int e = tid; e < RP * RFC; e += 256) {
+            int p = e / RFC, l = e - p * RFC;
+            T arg = T(0);
+            for (int k = 0; k < d; ++k) arg += Om[l * d + k] * Xs[p * d + k];
+            T sv, cv;
+            sc(arg, &sv, &cv);
+            Cs[p * (RFC + 1) + l] = cv;
+            Sn[p * (RFC + 1) + l] = sv;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int l = 0; l < RFC; ++l) {
+            T cv[4], sv[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                cv[p] = Cs[(tx + 16 * p) * (RFC + 1) + l];
+                sv[p] = Sn[(tx + 16 * p) * (RFC + 1) + l];
+            }
+#pragma unroll
+            for (int q = 0; q < SPT; ++q) {
+                T wc = Wc[(ty + 16 * q) * (RFC + 1) + l];
+                T ws = Wsn[(ty + 16 * q) * (RFC + 1) + l];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[p][q] += cv[p] * wc + sv[p] * ws;
+            }
+        }
+    }
+    const T amp = kp.sf * sqrt(T(2) / T(m));
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        int64_t i = p0 + tx + 16 * p;
+        if (i >= n) continue;
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+            int j = j0 + ty + 16 * q;
+            if (j < s) F[(int64_t)j * ldf + i] = amp * acc[p][q];
+        }
+    }
+}
+
+template <typename T, int SPT>
+int launch_rff(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
+               int s, T *F, int64_t ldf, cudaStream_t st) {
+    const int d = kp.d;
+    constexpr int SB = 16 * SPT;
+    size_t smem = sizeof(T) * (size_t)(RP * d + RFC * d + 2 * RP * (RFC + 1) + 2 * SB * (RFC + 1));
+    if (smem > 227 * 1024) {
+        set_error("rff: d=%d too large", d);
+        return GP_ERR_UNSUPPORTED;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        GP_TRY_CUDA(cudaFuncSetAttribute(rff_kernel<T, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024));
+        attr_set = true;
+    }
+    dim3 grid((unsigned)cdiv(n, RP), (unsigned)cdiv(s, SB));
+    rff_kernel<T, SPT><<<grid, 256, smem, st>>>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf);
+    return check_launch("rff_kernel");
+}
+
+}  // namespace
+
+template <typename T>
+int rff_prior(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
+              int s, T *F, int64_t ldf, cudaStream_t st) {
+    if (s <= 16) return launch_rff<T, 1>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
+    if (s <= 32) return launch_rff<T, 2>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
+    return launch_rff<T, 4>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
+}
+template int rff_prior<float>(const KP<float> &, const float *, int64_t, int, const float *, const float *,
+                              const float *, int, float *, int64_t, cudaStream_t);
+template int rff_prior<double>(const KP<double> &, const double *, int64_t, int, const double *, const double *,
+                               const double *, int, double *, int64_t, cudaStream_t);
+
+// ===========================================================================
+// Pathwise right-hand sides: B = [y, F_j + sigma w_j]  (App. B)
+// ===========================================================================
+namespace {
+__global__ void pathwise_rhs_kernel(float sigma, const float *y, const float *F, const float *w, int64_t n,
+                                    int s, float *B) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (i >= n) return;
+    B[(int64_t)c * n + i] = (c == 0) ? y[i] : F[(int64_t)(c - 1) * n + i] + sigma * w[(int64_t)(c - 1) * n + i];
+}
+
+// Wd[j][i] = Vsol[0][i] - Vsol[j+1][i]
+__global__ void cond_weights_kernel(const float *Vsol, int64_t n, int s, float *Wd) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i < n) Wd[(int64_t)j * n + i] = Vsol[i] - Vsol[(int64_t)(j + 1) * n + i];
+}
+// out[j][i] += Fstar[j][i]
+__global__ void add_prior_kernel(const float *Fstar, float *out, int64_t count) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] += Fstar[e];
+}
+}  // namespace
+
+int pathwise_rhs(float sigma, const float *y, const float *F, const float *w, int64_t n, int s, float *B,
+                 cudaStream_t st) {
+    dim3 grid((unsigned)cdiv(n, 256), (unsigned)(s + 1));
+    pathwise_rhs_kernel<<<grid, 256, 0, st>>>(sigma, y, F, w, n, s, B);
+    return check_launch("pathwise_rhs_kernel");
+}
+
+// ===========================================================================
+// Posterior samples (Eq. pathwise_conditioning; Sec. 3):
+//   out_j = Fstar_j + K(X*, X) (v_y - zhat_j)
+// ===========================================================================
+size_t posterior_workspace(int64_t nstar, int64_t n, int d, int s, int prec) {
+    Carver c(nullptr);
+    c.take<float>((size_t)s * (size_t)n);
+    c.take<char>(mvm_workspace<float>(nstar, n, d, s, prec));
+    return c.bytes();
+}
+
+int posterior_samples(const KP<float> &kp, const float *Xstar, int64_t nstar, const float *X, int64_t n,
+                      const float *Vsol, int s, const float *Fstar, float *out, int prec, void *ws,
+                      size_t ws_bytes, cudaStream_t st) {
+    Carver c(ws);
+    float *Wd = c.take<float>((size_t)s * (size_t)n);
+    size_t mw = mvm_workspace<float>(nstar, n, kp.d, s, prec);
+    void *mws = c.take<char>(mw);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    dim3 g1((unsigned)cdiv(n, 256), (unsigned)s);
+    cond_weights_kernel<<<g1, 256, 0, st>>>(Vsol, n, s, Wd);
+    GP_TRY(check_launch("cond_weights_kernel"));
+    GP_TRY(apply_mvm<float>(kp, Xstar, nstar, X, n, Wd, n, s, out, nstar, 0, prec, mws, mw, st));
+    const int64_t cnt = (int64_t)s * nstar;
+    add_prior_kernel<<<(unsigned)std::min<int64_t>(cdiv(cnt, 256), 4096), 256, 0, st>>>(Fstar, out, cnt);
+    return check_launch("add_prior_kernel");
+}
+
+}  // namespace gp

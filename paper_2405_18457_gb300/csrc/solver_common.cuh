@@ -1,0 +1,110 @@
+// Internal helpers shared by the solver translation units (CG/SGD, AP).
+#pragma once
+
+#include "solvers.cuh"
+
+#include <algorithm>
+
+namespace gp {
+
+namespace {
+
+constexpr double kNormEps = 1e-12;   // eps of the normalisation b / (||b|| + eps)
+constexpr double kFreeze = 1e-30;    // CG column frozen once gamma <= this
+
+int nparts_for(int64_t n) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n, 8192))); }
+
+// part[c*P + p] = sum_{i in chunk p} A[c][i] * B[c][i]   (grid P x R)
+template <typename T>
+__global__ void coldot_kernel(const T *A, const T *B, int64_t n, int P, double *part, const int *done) {
+    if (done && *done) return;
+    const int p = blockIdx.x, c = blockIdx.y;
+    const int64_t per = cdiv(n, P);
+    const int64_t i0 = (int64_t)p * per, i1 = min(n, i0 + per);
+    const T *a = A + (int64_t)c * n, *b = B + (int64_t)c * n;
+    double s = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += (double)a[i] * (double)b[i];
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[(int64_t)c * P + p] = t;
+    }
+}
+
+__device__ __forceinline__ double sum_parts(const double *part, int c, int P) {
+    double s = 0.0;
+    for (int p = 0; p < P; ++p) s += part[(int64_t)c * P + p];
+    return s;
+}
+
+// scale[c] = sqrt(sum parts) + eps
+__global__ void norm_scale_kernel(int R, int P, const double *part, double *scale) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) scale[c] = sqrt(sum_parts(part, c, P)) + kNormEps;
+}
+
+// V[c] *= (inv ? 1/scale[c] : scale[c])
+template <typename T>
+__global__ void scale_cols_kernel(T *V, int64_t n, const double *scale, int inv) {
+    const int c = blockIdx.y;
+    const double f = inv ? 1.0 / scale[c] : scale[c];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        V[(int64_t)c * n + i] = (T)((double)V[(int64_t)c * n + i] * f);
+}
+
+// r = B / scale - HV ; d = r
+template <typename T>
+__global__ void init_residual_kernel(const T *B, const T *HV, T *r, T *d, int64_t n, const double *scale) {
+    const int c = blockIdx.y;
+    const double f = 1.0 / scale[c];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = (int64_t)c * n + i;
+        T v = (T)((double)B[e] * f) - HV[e];
+        r[e] = v;
+        if (d) d[e] = v;
+    }
+}
+
+// Split norms and the loop condition (App. B): res_y = ||r_y||, res_z = mean_j ||r_j||.
+__device__ void finish_norms(SolverState *st, const double *sq, int R, long long t, long long max_iters,
+                             double tol, int stop_rule) {
+    double ry = sqrt(sq[0]);
+    double rz = 0.0;
+    for (int c = 1; c < R; ++c) rz += sqrt(sq[c]);
+    rz = (R > 1) ? rz / (double)(R - 1) : 0.0;
+    st->res_y = ry;
+    st->res_z = rz;
+    st->iter = t;
+    bool finite = isfinite(ry) && isfinite(rz);
+    bool conv = (stop_rule == GP_STOP_EITHER) ? (ry <= tol || rz <= tol) : (ry <= tol && rz <= tol);
+    st->converged = conv ? 1 : 0;
+    if (!finite) {
+        st->status = GP_ERR_BREAKDOWN;
+        st->done = 1;
+    } else if (conv || t >= max_iters) {
+        st->done = 1;
+    }
+}
+
+}  // namespace
+
+// Host-side polling of the device state.
+static inline int poll_state(const SolverState *dev, SolverState *host, cudaStream_t st) {
+    GP_TRY_CUDA(cudaMemcpyAsync(host, dev, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+    GP_TRY_CUDA(cudaStreamSynchronize(st));
+    return GP_OK;
+}
+
+static inline void fill_info(const SolverState &s, gp_solve_info_t *info) {
+    info->iters = s.iter;
+    info->converged = s.converged;
+    info->status = s.status;
+    info->res_y = s.res_y;
+    info->res_z = s.res_z;
+}
+
+
+}  // namespace gp

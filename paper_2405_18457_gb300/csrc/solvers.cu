@@ -1,0 +1,531 @@
+// Linear system solvers of App. B: conjugate gradients (Alg. 1), stochastic
+// gradient descent (Alg. 3); alternating projections (Alg. 2) is in ap.cu.
+//
+// All solvers run on the normalised systems H u~ = b / (||b|| + eps) and
+// rescale on exit.  Vectors are stored column-blocked (vector c at base + c*n)
+// in T; every inner product, norm and step size is FP64.  The loop condition
+// is evaluated on the device each iteration and latched into a `done` flag
+// that every later kernel of the solve checks first, so the host only polls
+// the flag every few iterations and never waits per iteration.
+#include "solver_common.cuh"
+
+#include <algorithm>
+#include <type_traits>
+
+namespace gp {
+
+namespace {
+
+// ---------------------------------------------------------------- CG kernels
+// gamma = ||r||^2 after the initial residual; sets done if already converged.
+__global__ void cg_start_kernel(int R, int P, const double *part, double *gamma, SolverState *st,
+                                long long max_iters, double tol, int stop_rule) {
+    if (threadIdx.x != 0) return;
+    double sq[512];
+    for (int c = 0; c < R; ++c) {
+        sq[c] = sum_parts(part, c, P);
+        gamma[c] = sq[c];
+    }
+    st->done = 0;
+    st->status = GP_OK;
+    finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
+}
+
+// alpha = gamma / d^T H d, frozen columns get 0.
+__global__ void cg_alpha_kernel(int R, int P, const double *part, const double *gamma, double *alpha,
+                                SolverState *st) {
+    if (st->done) return;
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double dHd = sum_parts(part, c, P);
+        double g = gamma[c];
+        alpha[c] = (g > kFreeze && dHd > 0.0 && isfinite(dHd)) ? g / dHd : 0.0;
+    }
+}
+
+// v += alpha d ; r -= alpha Hd ; part = ||r||^2 partial sums   (grid P x R)
+template <typename T>
+__global__ void cg_update_kernel(T *v, T *r, const T *d, const T *Hd, int64_t n, int P, const double *alpha,
+                                 double *part, const SolverState *st) {
+    if (st->done) return;
+    const int p = blockIdx.x, c = blockIdx.y;
+    const int64_t per = cdiv(n, P);
+    const int64_t i0 = (int64_t)p * per, i1 = min(n, i0 + per);
+    const T a = (T)alpha[c];
+    const int64_t off = (int64_t)c * n;
+    double s = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        v[off + i] += a * d[off + i];
+        T rv = r[off + i] - a * Hd[off + i];
+        r[off + i] = rv;
+        s += (double)rv * (double)rv;
+    }
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[(int64_t)c * P + p] = t;
+    }
+}
+
+// beta = gamma_new / gamma ; gamma = gamma_new ; norms ; t++ ; loop condition.
+__global__ void cg_beta_kernel(int R, int P, const double *part, double *gamma, const double *alpha, double *beta,
+                               SolverState *st, long long max_iters, double tol, int stop_rule) {
+    if (st->done) return;
+    if (threadIdx.x != 0) return;
+    double sq[512];
+    for (int c = 0; c < R; ++c) {
+        double gn = sum_parts(part, c, P);
+        bool active = alpha[c] != 0.0;
+        beta[c] = active ? gn / gamma[c] : 0.0;
+        if (active) gamma[c] = gn;
+        sq[c] = active ? gn : gamma[c];
+    }
+    finish_norms(st, sq, R, st->iter + 1, max_iters, tol, stop_rule);
+}
+
+// d = r + beta d
+template <typename T>
+__global__ void cg_dir_kernel(T *d, const T *r, int64_t n, const double *beta, const SolverState *st) {
+    if (st->done) return;
+    const int c = blockIdx.y;
+    const T b = (T)beta[c];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = (int64_t)c * n + i;
+        d[e] = r[e] + b * d[e];
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// Operator: H applied to R column-blocked vectors of stride n, skipping when done
+// ===========================================================================
+template <typename T>
+struct HOp {
+    KP<T> kp;
+    const T *X;
+    int64_t n;
+    int R;
+    int prec;
+    void *ws;
+    size_t wsb;
+    TcPoints pts{};
+    bool tc = false;
+
+    static size_t workspace(int64_t n, int d, int R, int prec) {
+        Carver c(nullptr);
+        if (std::is_same<T, float>::value && prec == GP_PREC_TC16) {
+            c.take<char>(tc_points_bytes(n, d));
+            c.take<char>(tc_mvm_workspace(n, n, R));
+        } else {
+            c.take<char>(mvm_simt_workspace<T>(n, n, R));
+        }
+        return c.bytes();
+    }
+    int init(const KP<T> &k, const T *Xp, int64_t np, int Rp, int pr, void *w, size_t wb, cudaStream_t st) {
+        kp = k;
+        X = Xp;
+        n = np;
+        R = Rp;
+        prec = pr;
+        if constexpr (std::is_same<T, float>::value) {
+            if (prec == GP_PREC_TC16) {
+                tc = true;
+                Carver c(w);
+                void *pbuf = c.take<char>(tc_points_bytes(n, kp.d));
+                wsb = tc_mvm_workspace(n, n, R);
+                ws = c.take<char>(wsb);
+                GP_TRY(check_ws(w, wb, c.bytes()));
+                return tc_prepare_points(kp, X, n, pbuf, &pts, st);
+            }
+        }
+        ws = w;
+        wsb = wb;
+        return GP_OK;
+    }
+    // Y = alpha * K V + beta * Y + diag (sigma^2 V unless overridden)
+    int apply(const T *V, T *Y, const int *done, cudaStream_t st) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc) {
+                TcMvmArgs a{};
+                a.kind = kp.kind;
+                a.rows = pts;
+                a.cols = pts;
+                a.V = V;
+                a.ldv = n;
+                a.R = R;
+                a.Y = Y;
+                a.ldy = n;
+                a.sf2 = kp.sf2;
+                a.alpha = 1.0f;
+                a.beta = 0.0f;
+                a.diag_coef = kp.sigma2;
+                a.Vd = V;
+                a.ldvd = n;
+                a.drow0 = 0;
+                a.ndiag = n;
+                a.done = done;
+                return tc_mvm(a, ws, wsb, st);
+            }
+        }
+        MvmArgs<T> a{};
+        a.kp = kp;
+        a.X1 = X;
+        a.n1 = n;
+        a.X2 = X;
+        a.n2 = n;
+        a.n2_total = n;
+        a.V = V;
+        a.ldv = n;
+        a.R = R;
+        a.Y = Y;
+        a.ldy = n;
+        a.alpha = T(1);
+        a.beta = T(0);
+        a.diag_coef = kp.sigma2;
+        a.Vd = V;
+        a.ldvd = n;
+        a.ndiag = n;
+        a.done = done;
+        return mvm_simt<T>(a, ws, wsb, st);
+    }
+};
+
+// ===========================================================================
+// Conjugate gradients, Alg. 1 (P = identity)
+// ===========================================================================
+template <typename T>
+size_t cg_workspace(int64_t n, int d, int R, int prec) {
+    const int P = nparts_for(n);
+    Carver c(nullptr);
+    c.take<T>((size_t)3 * R * n);      // r, d, Hd
+    c.take<double>((size_t)R * P);     // partial sums
+    c.take<double>((size_t)4 * R);     // scale, gamma, alpha, beta
+    c.take<SolverState>(1);
+    c.take<char>(HOp<T>::workspace(n, d, R, prec));
+    return c.bytes();
+}
+
+template <typename T>
+int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t max_iters, double tol,
+             int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (R > 512) {
+        set_error("nrhs must be <= 512");
+        return GP_ERR_INVALID_ARG;
+    }
+    const int P = nparts_for(n);
+    Carver c(ws);
+    T *r = c.take<T>((size_t)R * n);
+    T *dd = c.take<T>((size_t)R * n);
+    T *Hd = c.take<T>((size_t)R * n);
+    double *part = c.take<double>((size_t)R * P);
+    double *scale = c.take<double>(R);
+    double *gamma = c.take<double>(R);
+    double *alpha = c.take<double>(R);
+    double *beta = c.take<double>(R);
+    SolverState *sd = c.take<SolverState>(1);
+    size_t opb = HOp<T>::workspace(n, kp.d, R, prec);
+    void *opw = c.take<char>(opb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+
+    HOp<T> op;
+    GP_TRY(op.init(kp, X, n, R, prec, opw, opb, st));
+    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
+    const dim3 gp_((unsigned)P, (unsigned)R);
+    const int *done = &sd->done;
+
+    // normalisation (App. B): scale_c = ||b_c|| + eps, v <- v / scale
+    coldot_kernel<T><<<gp_, 256, 0, st>>>(B, B, n, P, part, nullptr);
+    norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
+    GP_TRY(check_launch("cg setup", 3));
+    // r = b~ - H v ; d = r ; gamma = r^T r
+    GP_TRY(op.apply(V, Hd, nullptr, st));
+    init_residual_kernel<T><<<gv, 256, 0, st>>>(B, Hd, r, dd, n, scale);
+    coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
+    cg_start_kernel<<<1, 32, 0, st>>>(R, P, part, gamma, sd, (long long)max_iters, tol, stop_rule);
+    GP_TRY(check_launch("cg start", 3));
+
+    SolverState hs{};
+    GP_TRY(poll_state(sd, &hs, st));
+    int64_t launched = 0, chunk = 2;
+    while (!hs.done && launched < max_iters) {
+        int64_t k = std::min<int64_t>(chunk, max_iters - launched);
+        for (int64_t it = 0; it < k; ++it) {
+            GP_TRY(op.apply(dd, Hd, done, st));
+            coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
+            cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
+            cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
+            cg_beta_kernel<<<1, 32, 0, st>>>(R, P, part, gamma, alpha, beta, sd, (long long)max_iters, tol,
+                                             stop_rule);
+            cg_dir_kernel<T><<<gv, 256, 0, st>>>(dd, r, n, beta, sd);
+            GP_TRY(check_launch("cg iteration", 5));
+        }
+        launched += k;
+        chunk = std::min<int64_t>(chunk * 2, 16);
+        GP_TRY(poll_state(sd, &hs, st));
+    }
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
+    GP_TRY(check_launch("cg rescale"));
+    GP_TRY(poll_state(sd, &hs, st));
+    fill_info(hs, info);
+    if (hs.status != GP_OK) {
+        set_error("CG breakdown: residual became non-finite at iteration %lld", hs.iter);
+        return hs.status;
+    }
+    return GP_OK;
+}
+
+template size_t cg_workspace<float>(int64_t, int, int, int);
+template size_t cg_workspace<double>(int64_t, int, int, int);
+template int cg_solve<float>(const KP<float> &, const float *, int64_t, const float *, int, float *, int64_t,
+                             double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t);
+template int cg_solve<double>(const KP<double> &, const double *, int64_t, const double *, int, double *,
+                              int64_t, double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t);
+
+// ===========================================================================
+// Stochastic gradient descent, Alg. 3
+// ===========================================================================
+namespace {
+
+// Gather the batch rows of X into Xb (batch x d) and mark them in slot[].
+template <typename T>
+__global__ void sgd_gather_kernel(const T *X, int d, const int32_t *idx, int64_t batch, T *Xb, int *slot,
+                                  const SolverState *st) {
+    if (st->done) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < batch * d; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = e / d, k = e - q * d;
+        int64_t i = idx[q];
+        Xb[e] = X[i * d + k];
+        if (k == 0) slot[i] = (int)q;
+    }
+}
+
+// g[c][q] = (K V)[c][q] + sigma^2 v[c][idx q] - b~[c][idx q]  (in place in G)
+// and the residual estimate update r[c][idx q] <- g, maintaining sum r^2 per
+// column incrementally in FP64: rsq[c] += g^2 - r_old^2.
+template <typename T>
+__global__ void sgd_grad_kernel(T *G, const T *V, const T *Bn, T *r, int64_t n, const int32_t *idx,
+                                int64_t batch, T sigma2, const int *slot, double *rsq_delta_part,
+                                const SolverState *st) {
+    if (st->done) return;
+    const int c = blockIdx.y;
+    double s = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < batch; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx[q];
+        int64_t e = (int64_t)c * n + i;
+        T g = G[(int64_t)c * batch + q] + sigma2 * V[e] - Bn[e];
+        G[(int64_t)c * batch + q] = g;
+        if (slot[i] == (int)q) {  // one writer per row even if an index repeats
+            T old = r[e];
+            s += (double)g * (double)g - (double)old * (double)old;
+        }
+    }
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        rsq_delta_part[(int64_t)c * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// Dense step over all rows: m = rho m - (lr/b) g ; v += m ; r[i] = g on batch rows.
+template <typename T>
+__global__ void sgd_step_kernel(T *Vv, T *M, T *r, const T *G, int64_t n, int64_t batch, const int *slot,
+                                T rho, T lrb, const SolverState *st) {
+    if (st->done) return;
+    const int c = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = (int64_t)c * n + i;
+        int q = slot[i];
+        T g = (q >= 0) ? G[(int64_t)c * batch + q] : T(0);
+        T m = rho * M[e] - lrb * g;
+        M[e] = m;
+        Vv[e] += m;
+        if (q >= 0) r[e] = g;
+    }
+}
+
+__global__ void sgd_clear_slots_kernel(const int32_t *idx, int64_t batch, int *slot, const SolverState *st) {
+    if (st->done) return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < batch; q += (int64_t)gridDim.x * blockDim.x)
+        slot[idx[q]] = -1;
+}
+
+__global__ void fill_int_kernel(int *p, int64_t cnt, int v) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = v;
+}
+
+// rsq[c] = sum parts (initial, exact) and loop condition.
+__global__ void sgd_start_kernel(int R, int P, const double *part, double *rsq, SolverState *st,
+                                 long long max_iters, double tol, int stop_rule) {
+    if (threadIdx.x != 0) return;
+    double sq[512];
+    for (int c = 0; c < R; ++c) {
+        sq[c] = sum_parts(part, c, P);
+        rsq[c] = sq[c];
+    }
+    st->done = 0;
+    st->status = GP_OK;
+    double r0 = 0.0;
+    for (int c = 0; c < R; ++c) r0 += sq[c];
+    st->res0 = r0;
+    finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
+}
+
+__global__ void sgd_norm_kernel(int R, int nb, const double *dpart, double *rsq, SolverState *st,
+                                long long max_iters, double tol, int stop_rule) {
+    if (st->done) return;
+    if (threadIdx.x != 0) return;
+    double sq[512];
+    double tot = 0.0;
+    for (int c = 0; c < R; ++c) {
+        double s = rsq[c];
+        for (int b = 0; b < nb; ++b) s += dpart[(int64_t)c * nb + b];
+        s = fmax(s, 0.0);
+        rsq[c] = s;
+        sq[c] = s;
+        tot += s;
+    }
+    finish_norms(st, sq, R, st->iter + 1, max_iters, tol, stop_rule);
+    if (!(tot <= 1e12 * fmax(st->res0, 1e-300))) {
+        st->status = GP_ERR_DIVERGED;
+        st->done = 1;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+static size_t sgd_panel_ws(int64_t batch, int64_t n, int d, int R, int prec) {
+    return mvm_workspace<T>(batch, n, d, R, prec);
+}
+
+template <typename T>
+size_t sgd_workspace(int64_t n, int d, int R, int64_t batch, int prec) {
+    const int P = nparts_for(n);
+    Carver c(nullptr);
+    c.take<T>((size_t)3 * R * n);     // normalised b, momentum, residual estimate
+    c.take<T>((size_t)R * batch);     // batch gradient
+    c.take<T>((size_t)batch * d);     // gathered batch points
+    c.take<int>((size_t)n);           // row -> batch slot
+    c.take<double>((size_t)R * P);
+    c.take<double>((size_t)R * 64);
+    c.take<double>((size_t)2 * R);
+    c.take<SolverState>(1);
+    c.take<char>(sgd_panel_ws<T>(batch, n, d, R, prec));
+    return c.bytes();
+}
+
+template <typename T>
+int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t batch,
+              const int32_t *idx, double lr, double rho, int64_t max_iters, double tol, int stop_rule, int prec,
+              gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (R > 512) {
+        set_error("nrhs must be <= 512");
+        return GP_ERR_INVALID_ARG;
+    }
+    const int d = kp.d;
+    const int P = nparts_for(n);
+    Carver c(ws);
+    T *Bn = c.take<T>((size_t)R * n);
+    T *M = c.take<T>((size_t)R * n);
+    T *r = c.take<T>((size_t)R * n);
+    T *G = c.take<T>((size_t)R * batch);
+    T *Xb = c.take<T>((size_t)batch * d);
+    int *slot = c.take<int>((size_t)n);
+    double *part = c.take<double>((size_t)R * P);
+    double *dpart = c.take<double>((size_t)R * 64);
+    double *scale = c.take<double>(R);
+    double *rsq = c.take<double>(R);
+    SolverState *sd = c.take<SolverState>(1);
+    size_t pwb = sgd_panel_ws<T>(batch, n, d, R, prec);
+    void *pw = c.take<char>(pwb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+
+    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 2048), (unsigned)R);
+    const dim3 gp_((unsigned)P, (unsigned)R);
+    const int nbg = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(batch, 256)));
+    // b~ = b / (||b|| + eps), v <- v / scale, m = 0, r = b~
+    coldot_kernel<T><<<gp_, 256, 0, st>>>(B, B, n, P, part, nullptr);
+    norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
+    GP_TRY_CUDA(cudaMemcpyAsync(Bn, B, sizeof(T) * R * n, cudaMemcpyDeviceToDevice, st));
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(Bn, n, scale, 1);
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
+    GP_TRY_CUDA(cudaMemsetAsync(M, 0, sizeof(T) * R * n, st));
+    GP_TRY_CUDA(cudaMemcpyAsync(r, Bn, sizeof(T) * R * n, cudaMemcpyDeviceToDevice, st));
+    fill_int_kernel<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 4096), 256, 0, st>>>(slot, n, -1);
+    coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
+    sgd_start_kernel<<<1, 32, 0, st>>>(R, P, part, rsq, sd, (long long)max_iters, tol, stop_rule);
+    GP_TRY(check_launch("sgd setup", 7));
+
+    SolverState hs{};
+    GP_TRY(poll_state(sd, &hs, st));
+    int64_t t = 0, chunk = 8;
+    const T lrb = (T)(lr / (double)batch);
+    while (!hs.done && t < max_iters) {
+        int64_t k = std::min<int64_t>(chunk, max_iters - t);
+        for (int64_t it = 0; it < k; ++it, ++t) {
+            const int32_t *bi = idx + t * batch;
+            sgd_gather_kernel<T><<<(unsigned)cdiv(batch * d, 256), 256, 0, st>>>(X, d, bi, batch, Xb, slot, sd);
+            GP_TRY(check_launch("sgd gather"));
+            // G = K(X_b, X) V   (row panel H[i, :] v without the noise term)
+            if constexpr (std::is_same<T, float>::value) {
+                if (prec == GP_PREC_TC16) {
+                    // The tensor-core panel re-prepares the batch points each iteration.
+                    GP_TRY(apply_mvm<float>(kp, Xb, batch, X, n, V, n, R, G, batch, 0, prec, pw, pwb, st));
+                } else {
+                    MvmArgs<T> a{};
+                    a.kp = kp; a.X1 = Xb; a.n1 = batch; a.X2 = X; a.n2 = n; a.n2_total = n;
+                    a.V = V; a.ldv = n; a.R = R; a.Y = G; a.ldy = batch;
+                    a.alpha = T(1); a.beta = T(0); a.diag_coef = T(0); a.done = &sd->done;
+                    GP_TRY(mvm_simt<T>(a, pw, pwb, st));
+                }
+            } else {
+                MvmArgs<T> a{};
+                a.kp = kp; a.X1 = Xb; a.n1 = batch; a.X2 = X; a.n2 = n; a.n2_total = n;
+                a.V = V; a.ldv = n; a.R = R; a.Y = G; a.ldy = batch;
+                a.alpha = T(1); a.beta = T(0); a.diag_coef = T(0); a.done = &sd->done;
+                GP_TRY(mvm_simt<T>(a, pw, pwb, st));
+            }
+            sgd_grad_kernel<T><<<dim3(nbg, R), 256, 0, st>>>(G, V, Bn, r, n, bi, batch, kp.sigma2, slot, dpart, sd);
+            sgd_step_kernel<T><<<gv, 256, 0, st>>>(V, M, r, G, n, batch, slot, (T)rho, lrb, sd);
+            sgd_clear_slots_kernel<<<(unsigned)cdiv(batch, 256), 256, 0, st>>>(bi, batch, slot, sd);
+            sgd_norm_kernel<<<1, 32, 0, st>>>(R, nbg, dpart, rsq, sd, (long long)max_iters, tol, stop_rule);
+            GP_TRY(check_launch("sgd iteration", 4));
+        }
+        chunk = std::min<int64_t>(chunk * 2, 64);
+        GP_TRY(poll_state(sd, &hs, st));
+    }
+    scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
+    GP_TRY(check_launch("sgd rescale"));
+    GP_TRY(poll_state(sd, &hs, st));
+    fill_info(hs, info);
+    if (hs.status == GP_ERR_DIVERGED) {
+        set_error("SGD diverged at iteration %lld (residual estimate grew beyond 1e6 x its start)", hs.iter);
+        return hs.status;
+    }
+    if (hs.status != GP_OK) {
+        set_error("SGD breakdown at iteration %lld", hs.iter);
+        return hs.status;
+    }
+    return GP_OK;
+}
+
+template size_t sgd_workspace<float>(int64_t, int, int, int64_t, int);
+template size_t sgd_workspace<double>(int64_t, int, int, int64_t, int);
+template int sgd_solve<float>(const KP<float> &, const float *, int64_t, const float *, int, float *, int64_t,
+                              const int32_t *, double, double, int64_t, double, int, int, gp_solve_info_t *,
+                              void *, size_t, cudaStream_t);
+template int sgd_solve<double>(const KP<double> &, const double *, int64_t, const double *, int, double *,
+                               int64_t, const int32_t *, double, double, int64_t, double, int, int,
+                               gp_solve_info_t *, void *, size_t, cudaStream_t);
+
+}  // namespace gp

@@ -1,0 +1,64 @@
+// Internal: operator dispatch, solvers, random features (declarations).
+#pragma once
+
+#include "gp_internal.cuh"
+
+namespace gp {
+
+// H V / K V dispatch over precision (CUDA-core FP32/FP64 or tcgen05 fp16).
+template <typename T>
+size_t mvm_workspace(int64_t n1, int64_t n2, int d, int R, int prec);
+template <typename T>
+int apply_mvm(const KP<T> &kp, const T *X1, int64_t n1, const T *X2, int64_t n2, const T *V, int64_t ldv,
+              int R, T *Y, int64_t ldy, int add_noise, int prec, void *ws, size_t ws_bytes, cudaStream_t st);
+
+template <typename T>
+size_t grad_workspace(int64_t n, int d, int R, int prec);
+template <typename T>
+int apply_grad(const GradArgs<T> &a, int prec, void *ws, size_t ws_bytes, cudaStream_t st);
+
+template <typename T>
+int rff_prior(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
+              int s, T *F, int64_t ldf, cudaStream_t st);
+int pathwise_rhs(float sigma, const float *y, const float *F, const float *w, int64_t n, int s, float *B,
+                 cudaStream_t st);
+
+size_t posterior_workspace(int64_t nstar, int64_t n, int d, int s, int prec);
+int posterior_samples(const KP<float> &kp, const float *Xstar, int64_t nstar, const float *X, int64_t n,
+                      const float *Vsol, int s, const float *Fstar, float *out, int prec, void *ws,
+                      size_t ws_bytes, cudaStream_t st);
+
+// Solvers (App. B, Alg. 1-3).
+template <typename T>
+size_t cg_workspace(int64_t n, int d, int R, int prec);
+template <typename T>
+int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t max_iters, double tol,
+             int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st);
+
+template <typename T>
+size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec);
+template <typename T>
+int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t bs, int64_t max_iters,
+             double tol, int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes,
+             cudaStream_t st);
+
+template <typename T>
+size_t sgd_workspace(int64_t n, int d, int R, int64_t batch, int prec);
+template <typename T>
+int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t batch,
+              const int32_t *idx, double lr, double rho, int64_t max_iters, double tol, int stop_rule,
+              int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// Device-resident solver state, read back once per poll.
+struct SolverState {
+    int done;
+    int status;
+    int converged;
+    int pad;
+    long long iter;
+    double res_y;
+    double res_z;
+    double res0;  // SGD: initial residual estimate (divergence guard)
+};
+
+}  // namespace gp

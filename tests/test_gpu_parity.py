@@ -1,0 +1,286 @@
+"""GPU-vs-oracle parity of every C-ABI entry point (CUDA-core FP64 and FP32
+forms, and the tcgen05 fp16 form where it is built).  Inputs come from the
+seeded generators; expected values come from the FP64 CPU oracle only.
+
+Tolerances (relative Frobenius unless stated):
+  FP64 path  : 1e-10 (same arithmetic, different summation order)
+  FP32 path  : MVM 1e-5, solutions/gradients 1e-4
+  TC16 path  : MVM 1e-3, gradient 1e-3 (fp16 operands, FP32 accumulation)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_18457_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+gp = pytest.importorskip("paper_2405_18457_gb300")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available()
+    gp.library()  # fail loudly if the CUDA library is missing
+    return torch.device("cuda:0")
+
+
+def t(a, dev, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def tc_built():
+    try:
+        X = torch.zeros((1, 1), device="cuda")
+        gp.gp_kernel_mvm(0, [1.0, 1.0, 1.0], X, torch.zeros((1, 1), device="cuda"), prec=gp.GP_PREC_TC16)
+        return True
+    except gp.GPError as e:
+        if e.status == -6:
+            return False
+        raise
+
+
+PRECS = [("f64", None, 1e-10), ("f32", gp.GP_PREC_FP32, 1e-5), ("tc16", gp.GP_PREC_TC16, 1e-3)]
+
+
+def run_mvm(prec_name, prec, kind, th, X1, X2, V, add_noise, dev):
+    if prec_name == "tc16" and not tc_built():
+        pytest.skip("tensor-core path not built")
+    dt = torch.float64 if prec_name == "f64" else torch.float32
+    X1t = t(X1, dev, dt)
+    X2t = X1t if X2 is None else t(X2, dev, dt)
+    Y = gp.gp_kernel_mvm(kind, th, X1t, t(V, dev, dt), X2=X2t, add_noise=add_noise,
+                         prec=prec if prec is not None else gp.GP_PREC_FP32)
+    torch.cuda.synchronize()
+    return Y.double().cpu().numpy()
+
+
+# --------------------------------------------------------------------------- MVM
+@pytest.mark.parametrize("prec_name,prec,tol", PRECS)
+@pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
+@pytest.mark.parametrize("n,d,R", [(333, 5, 9), (257, 16, 65), (130, 26, 70), (1, 3, 1), (64, 1, 17)])
+def test_hv_matches_oracle(dev, prec_name, prec, tol, kind, n, d, R):
+    rng = np.random.default_rng(n * 100 + d)
+    X = rng.uniform(-1, 1, size=(n, d))
+    th = np.concatenate([rng.uniform(0.5, 1.5, size=d), [1.2, 0.3]])
+    V = rng.standard_normal((R, n))
+    Y = run_mvm(prec_name, prec, kind, th, X, None, V, True, dev)
+    ref = oracle.kernel_mvm(kind, th, X, X, V, add_noise=True)
+    assert rel(Y, ref) < tol
+
+
+@pytest.mark.parametrize("prec_name,prec,tol", PRECS)
+def test_cross_kernel_product_matches_oracle(dev, prec_name, prec, tol):
+    rng = np.random.default_rng(11)
+    X1 = rng.standard_normal((301, 7))
+    X2 = rng.standard_normal((517, 7))
+    th = np.concatenate([rng.uniform(0.8, 2.0, size=7), [0.9, 0.2]])
+    V = rng.standard_normal((12, 517))
+    Y = run_mvm(prec_name, prec, oracle.MATERN32, th, X1, X2, V, False, dev)
+    assert rel(Y, oracle.kernel_mvm(oracle.MATERN32, th, X1, X2, V)) < tol
+
+
+@pytest.mark.parametrize("prec_name,prec,tol", PRECS)
+def test_small_problem_workload_matches_oracle(dev, prec_name, prec, tol):
+    """The small workload (n=2048, d=8, RBF, s=8 probes): full product."""
+    p = workloads.small()
+    B = np.vstack([p.y, p.Z])
+    Y = run_mvm(prec_name, prec, p.kind, p.theta, p.X, None, B, True, dev)
+    assert rel(Y, oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, B, add_noise=True)) < tol
+
+
+@pytest.mark.parametrize("prec_name,prec,tol", PRECS[1:])
+def test_full_size_pathwise_workload_sampled_rows(dev, prec_name, prec, tol):
+    """The pathwise workload at its full size (n=32768, d=16, R=65, Matern-3/2):
+    the GPU product is compared with the oracle on 48 sampled rows."""
+    p = workloads.pathwise()
+    V = workloads.vectors(65, p.n, seed=1)
+    Y = run_mvm(prec_name, prec, p.kind, p.theta, p.X.astype(np.float32), None, V.astype(np.float32), True, dev)
+    rows = np.random.default_rng(2).choice(p.n, size=48, replace=False)
+    Xr = p.X.astype(np.float32).astype(np.float64)
+    ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float32).astype(np.float64), add_noise=True,
+                            rows=rows)
+    assert rel(Y[:, rows], ref) < tol
+
+
+def test_empty_column_set_gives_zeros(dev):
+    X1 = t(np.ones((5, 2)), dev)
+    X2 = torch.zeros((0, 2), device=dev)
+    V = torch.zeros((3, 0), device=dev)
+    Y = gp.gp_kernel_mvm(0, [1.0, 1.0, 1.0, 0.1], X1, V, X2=X2, prec=gp.GP_PREC_FP32)
+    assert torch.count_nonzero(Y).item() == 0
+
+
+# --------------------------------------------------------------------------- gradients
+@pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-10), ("f32", gp.GP_PREC_FP32, 1e-4),
+                                                ("tc16", gp.GP_PREC_TC16, 1e-3)])
+@pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
+@pytest.mark.parametrize("estimator", ["standard", "pathwise"])
+def test_gradient_estimators_match_oracle(dev, prec_name, prec, tol, kind, estimator):
+    if prec_name == "tc16" and not tc_built():
+        pytest.skip("tensor-core path not built")
+    rng = np.random.default_rng(5)
+    n, d, s = 203, 6, 8
+    X = rng.uniform(-1, 1, size=(n, d))
+    th = np.concatenate([rng.uniform(0.5, 1.5, size=d), [1.1, 0.4]])
+    Vsol = rng.standard_normal((s + 1, n))
+    Z = rng.standard_normal((s, n))
+    dt = torch.float64 if prec_name == "f64" else torch.float32
+    Xr = X.astype(np.float32).astype(np.float64) if dt == torch.float32 else X
+    Vr = Vsol.astype(np.float32).astype(np.float64) if dt == torch.float32 else Vsol
+    Zr = Z.astype(np.float32).astype(np.float64) if dt == torch.float32 else Z
+    pr = prec if prec is not None else gp.GP_PREC_FP32
+    if estimator == "standard":
+        g = gp.gp_mll_grad_standard(kind, th, t(X, dev, dt), t(Vsol, dev, dt), t(Z, dev, dt), prec=pr)
+        ref = oracle.grad_standard(kind, th, Xr, Vr, Zr)
+    else:
+        g = gp.gp_mll_grad_pathwise(kind, th, t(X, dev, dt), t(Vsol, dev, dt), prec=pr)
+        ref = oracle.grad_pathwise(kind, th, Xr, Vr)
+    g = g.cpu().numpy()
+    assert np.abs(g - ref).max() <= tol * np.abs(ref).max()
+
+
+# --------------------------------------------------------------------------- solvers
+@pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-9), ("f32", gp.GP_PREC_FP32, 1e-4),
+                                                ("tc16", gp.GP_PREC_TC16, 2e-3)])
+def test_cg_iterates_match_oracle(dev, prec_name, prec, tol):
+    """Fixed 6 iterations from a warm start: iterate-by-iterate parity with Alg. 1."""
+    if prec_name == "tc16" and not tc_built():
+        pytest.skip("tensor-core path not built")
+    rng = np.random.default_rng(7)
+    n, d, R = 300, 4, 5
+    X = rng.standard_normal((n, d))
+    th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.5]])
+    B = rng.standard_normal((R, n))
+    V0 = 0.1 * rng.standard_normal((R, n))
+    dt = torch.float64 if prec_name == "f64" else torch.float32
+    V, info = gp.gp_solve_cg(oracle.MATERN32, th, t(X, dev, dt), t(B, dev, dt), V0=t(V0, dev, dt), max_iters=6,
+                             tol=0.0, prec=prec if prec is not None else gp.GP_PREC_FP32)
+    Vr, ir = oracle.solve_cg(oracle.MATERN32, th, X, B, V0=V0, max_iters=6, tol=0.0)
+    assert info.iters == ir["iters"] == 6
+    assert rel(V.double().cpu().numpy(), Vr) < tol
+    assert info.res_y == pytest.approx(ir["res_y"], rel=100 * tol)
+
+
+@pytest.mark.parametrize("prec_name,prec", [("f64", None), ("f32", gp.GP_PREC_FP32), ("tc16", gp.GP_PREC_TC16)])
+@pytest.mark.parametrize("stop_rule", [0, 1])
+def test_cg_reaches_tolerance_with_true_residual(dev, prec_name, prec, stop_rule):
+    if prec_name == "tc16" and not tc_built():
+        pytest.skip("tensor-core path not built")
+    p = workloads.small(n=700, s=8, seed=1)
+    B = np.vstack([p.y, p.Z])
+    dt = torch.float64 if prec_name == "f64" else torch.float32
+    tol = 1e-6 if prec_name == "f64" else 1e-4
+    V, info = gp.gp_solve_cg(p.kind, p.theta, t(p.X, dev, dt), t(B, dev, dt), max_iters=500, tol=tol,
+                             stop_rule=stop_rule, prec=prec if prec is not None else gp.GP_PREC_FP32)
+    assert info.converged
+    Vh = V.double().cpu().numpy()
+    Xr = p.X if dt == torch.float64 else p.X.astype(np.float32).astype(np.float64)
+    Br = B if dt == torch.float64 else B.astype(np.float32).astype(np.float64)
+    r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, Vh, add_noise=True)
+    rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
+    slack = 1.5 if prec_name != "tc16" else 5.0
+    if stop_rule == 0:
+        assert rn[0] <= slack * tol and rn[1:].mean() <= slack * tol
+    else:
+        assert min(rn[0], rn[1:].mean()) <= slack * tol
+
+
+@pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-9), ("f32", gp.GP_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("n,bs", [(250, 64), (97, 32), (130, 130)])
+def test_ap_iterates_match_oracle(dev, prec_name, prec, tol, n, bs):
+    rng = np.random.default_rng(n)
+    d, R = 3, 4
+    X = rng.standard_normal((n, d))
+    th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.4]])
+    B = rng.standard_normal((R, n))
+    dt = torch.float64 if prec_name == "f64" else torch.float32
+    iters = 7
+    V, info = gp.gp_solve_ap(oracle.RBF, th, t(X, dev, dt), t(B, dev, dt), block_size=bs, max_iters=iters, tol=0.0,
+                             prec=prec if prec is not None else gp.GP_PREC_FP32)
+    Vr, ir = oracle.solve_ap(oracle.RBF, th, X, B, block_size=bs, max_iters=iters, tol=0.0)
+    assert info.iters == ir["iters"]
+    assert rel(V.double().cpu().numpy(), Vr) < tol
+    assert info.res_z == pytest.approx(ir["res_z"], rel=1e3 * tol)
+
+
+def test_ap_converges_to_dense_solution(dev):
+    rng = np.random.default_rng(3)
+    n, d, R = 200, 3, 3
+    X = rng.standard_normal((n, d))
+    th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.5]])
+    B = rng.standard_normal((R, n))
+    V, info = gp.gp_solve_ap(oracle.MATERN32, th, t(X, dev, torch.float64), t(B, dev, torch.float64),
+                             block_size=50, max_iters=5000, tol=1e-10)
+    assert info.converged
+    H = oracle.H_matrix(oracle.MATERN32, th, X)
+    assert rel(V.cpu().numpy(), np.linalg.solve(H, B.T).T) < 1e-8
+
+
+@pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-9), ("f32", gp.GP_PREC_FP32, 1e-4)])
+def test_sgd_iterates_match_oracle(dev, prec_name, prec, tol):
+    rng = np.random.default_rng(9)
+    n, d, R, batch, iters = 180, 3, 4, 16, 25
+    X = rng.standard_normal((n, d))
+    th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.6]])
+    B = rng.standard_normal((R, n))
+    idx = workloads.sgd_batches(n, batch, iters, seed=4)
+    dt = torch.float64 if prec_name == "f64" else torch.float32
+    V, info = gp.gp_solve_sgd(oracle.MATERN32, th, t(X, dev, dt), t(B, dev, dt),
+                              torch.tensor(idx, dtype=torch.int32, device=dev), lr=2.0, momentum=0.9, tol=0.0,
+                              prec=prec if prec is not None else gp.GP_PREC_FP32)
+    Vr, ir = oracle.solve_sgd(oracle.MATERN32, th, X, B, idx, batch=batch, lr=2.0, momentum=0.9, max_iters=iters,
+                              tol=0.0)
+    assert info.iters == ir["iters"] == iters
+    assert rel(V.double().cpu().numpy(), Vr) < tol
+    assert info.res_y == pytest.approx(ir["res_y"], rel=100 * tol)
+    assert info.res_z == pytest.approx(ir["res_z"], rel=100 * tol)
+
+
+def test_sgd_reports_divergence(dev):
+    rng = np.random.default_rng(1)
+    n = 64
+    X = rng.standard_normal((n, 2))
+    th = [1.0, 1.0, 1.0, 0.5]
+    B = rng.standard_normal((2, n))
+    idx = torch.tensor(workloads.sgd_batches(n, 16, 200), dtype=torch.int32, device=dev)
+    with pytest.raises(gp.GPError) as e:
+        gp.gp_solve_sgd(0, th, t(X, dev), t(B, dev), idx, lr=1e4, momentum=0.9, tol=0.0, prec=gp.GP_PREC_FP32)
+    assert e.value.status == -4
+
+
+# --------------------------------------------------------------------------- random features, posterior
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 2e-5)])
+@pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
+def test_rff_prior_sample_matches_oracle(dev, dtype, tol, kind):
+    p = workloads.pathwise(n=517, d=9, s=33, m=130, seed=2)
+    F = gp.gp_rff_prior_sample(kind, p.theta, t(p.X, dev, dtype), t(p.omega_hat, dev, dtype),
+                               t(p.chi2, dev, dtype), t(p.W_probe, dev, dtype))
+    cast = (lambda a: a) if dtype == torch.float64 else (lambda a: a.astype(np.float32).astype(np.float64))
+    ref = oracle.rff_prior(kind, p.theta, cast(p.X), cast(p.omega_hat), cast(p.chi2), cast(p.W_probe))
+    assert rel(F.double().cpu().numpy(), ref) < tol
+
+
+def test_pathwise_rhs_and_posterior_samples_match_oracle(dev):
+    p = workloads.pathwise(n=400, d=4, s=10, m=64, seed=5)
+    f = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    F = oracle.rff_prior(p.kind, p.theta, f(p.X), f(p.omega_hat), f(p.chi2), f(p.W_probe))
+    y = f(p.y_noise)
+    B = gp.gp_pathwise_rhs(p.theta, p.d, t(y, dev), t(F, dev), t(p.Z, dev))
+    Bref = np.vstack([y, f(F) + p.theta[-1] * f(p.Z)])
+    assert rel(B.double().cpu().numpy(), Bref) < 1e-6
+    rng = np.random.default_rng(0)
+    Xs = rng.standard_normal((150, 4))
+    Vsol = rng.standard_normal((11, 400))
+    Fs = rng.standard_normal((10, 150))
+    out = gp.gp_posterior_samples(p.kind, p.theta, t(Xs, dev), t(p.X, dev), t(Vsol, dev), t(Fs, dev),
+                                  prec=gp.GP_PREC_FP32)
+    ref = oracle.posterior_samples(p.kind, p.theta, f(Xs), f(p.X), f(Vsol), f(Fs))
+    assert rel(out.double().cpu().numpy(), ref) < 1e-5
