@@ -43,6 +43,10 @@ int check_launch(const char *what, int count = 1);
 void prof_begin(cudaStream_t st);
 void prof_end(cudaStream_t st);
 
+// Dynamic shared memory a kernel may opt into (227 KB per block on sm_103,
+// minus headroom for the kernels' small static arrays).
+constexpr int kMaxDynSmem = 220 * 1024;
+
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t rup(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 

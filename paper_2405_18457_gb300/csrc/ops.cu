@@ -215,14 +215,14 @@ int launch_rff(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat
     const int d = kp.d;
     constexpr int SB = 16 * SPT;
     size_t smem = sizeof(T) * (size_t)(RP * d + RFC * d + 2 * RP * (RFC + 1) + 2 * SB * (RFC + 1));
-    if (smem > 227 * 1024) {
+    if (smem > kMaxDynSmem) {
         set_error("rff: d=%d too large", d);
         return GP_ERR_UNSUPPORTED;
     }
     static bool attr_set = false;
     if (!attr_set) {
         GP_TRY_CUDA(cudaFuncSetAttribute(rff_kernel<T, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024));
+                                         kMaxDynSmem));
         attr_set = true;
     }
     dim3 grid((unsigned)cdiv(n, RP), (unsigned)cdiv(s, SB));

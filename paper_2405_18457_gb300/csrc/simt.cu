@@ -189,7 +189,7 @@ int launch_mvm(const MvmArgs<T> &a, const SplitPlan<T> &pl, T *partial, cudaStre
     static bool attr_set = false;
     if (!attr_set) {
         GP_TRY_CUDA(cudaFuncSetAttribute(mvm_simt_kernel<T, CPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
         attr_set = true;
     }
     dim3 grid((unsigned)cdiv(a.n1, BM), (unsigned)pl.nsplit, (unsigned)pl.zchunks);
@@ -219,7 +219,7 @@ template <typename T>
 int mvm_simt(const MvmArgs<T> &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (a.n1 == 0 || a.R == 0) return GP_OK;
     SplitPlan<T> pl = plan_mvm<T>(a.n1, a.n2, a.R);
-    if (mvm_smem<T>(a.kp.d, pl.cpt) > 227 * 1024) {
+    if (mvm_smem<T>(a.kp.d, pl.cpt) > kMaxDynSmem) {
         set_error("mvm: d=%d too large for the CUDA-core tile in this precision", a.kp.d);
         return GP_ERR_UNSUPPORTED;
     }
@@ -462,7 +462,7 @@ int launch_grad(const GradArgs<T> &a, const GradPlan<T> &pl, double *partial, do
     static bool attr_set = false;
     if (!attr_set) {
         GP_TRY_CUDA(cudaFuncSetAttribute(grad_simt_kernel<T, DMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
         attr_set = true;
     }
     size_t smem = grad_smem<T>(a.kp.d, a.R);
@@ -491,7 +491,7 @@ size_t grad_simt_workspace(int64_t n, int d, int R) {
 template <typename T>
 int grad_simt(const GradArgs<T> &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int d = a.kp.d;
-    if (grad_smem<T>(d, a.R) > 227 * 1024) {
+    if (grad_smem<T>(d, a.R) > kMaxDynSmem) {
         set_error("mll_grad: d=%d with %d right-hand sides exceeds the CUDA-core tile", d, a.R);
         return GP_ERR_UNSUPPORTED;
     }

@@ -201,9 +201,9 @@ template <typename T>
 size_t cg_workspace(int64_t n, int d, int R, int prec) {
     const int P = nparts_for(n);
     Carver c(nullptr);
-    c.take<T>((size_t)3 * R * n);      // r, d, Hd
-    c.take<double>((size_t)R * P);     // partial sums
-    c.take<double>((size_t)4 * R);     // scale, gamma, alpha, beta
+    for (int k = 0; k < 3; ++k) c.take<T>((size_t)R * n);  // r, d, Hd
+    c.take<double>((size_t)R * P);                          // partial sums
+    for (int k = 0; k < 4; ++k) c.take<double>(R);          // scale, gamma, alpha, beta
     c.take<SolverState>(1);
     c.take<char>(HOp<T>::workspace(n, d, R, prec));
     return c.bytes();
@@ -412,13 +412,13 @@ template <typename T>
 size_t sgd_workspace(int64_t n, int d, int R, int64_t batch, int prec) {
     const int P = nparts_for(n);
     Carver c(nullptr);
-    c.take<T>((size_t)3 * R * n);     // normalised b, momentum, residual estimate
-    c.take<T>((size_t)R * batch);     // batch gradient
-    c.take<T>((size_t)batch * d);     // gathered batch points
-    c.take<int>((size_t)n);           // row -> batch slot
+    for (int k = 0; k < 3; ++k) c.take<T>((size_t)R * n);  // normalised b, momentum, residual estimate
+    c.take<T>((size_t)R * batch);                           // batch gradient
+    c.take<T>((size_t)batch * d);                           // gathered batch points
+    c.take<int>((size_t)n);                                 // row -> batch slot
     c.take<double>((size_t)R * P);
     c.take<double>((size_t)R * 64);
-    c.take<double>((size_t)2 * R);
+    for (int k = 0; k < 2; ++k) c.take<double>(R);
     c.take<SolverState>(1);
     c.take<char>(sgd_panel_ws<T>(batch, n, d, R, prec));
     return c.bytes();
