@@ -195,14 +195,20 @@ int grad_simt(const GradArgs<T> &a, void *ws, size_t ws_bytes, cudaStream_t st);
 // ---------------------------------------------------------------------------
 // Prepared operands for a point set under fixed theta.
 struct TcPoints {
-    const void *PA;   // n_pad x KD fp16, row operand (scaled, hi/lo split, norms)
-    const void *PB;   // n_pad x KD fp16, column operand
+    const void *PA;          // n_pad x KD fp16, row operand (scaled, hi/lo split, norms)
+    const void *PB;          // n_pad x KD fp16, column operand
     int64_t n, n_pad;
-    int KD;           // padded contraction length of the distance GEMM
+    int KD;                  // padded contraction length of the distance GEMM
+    const float *dscale;     // device scalar: power-of-two scale of the tile values
+    const unsigned *bound;   // device scalar: magnitude bound the scale was chosen from
 };
 size_t tc_points_bytes(int64_t n, int d);
+// Rows and columns from one point set (H V).
 int tc_prepare_points(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out,
                       cudaStream_t st);
+// Rows from X1 and columns from X2 with one shared scale (cross products).
+int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const float *X2, int64_t n2, void *buf1,
+                    void *buf2, TcPoints *rows, TcPoints *cols, cudaStream_t st);
 
 struct TcMvmArgs {
     int kind;

@@ -35,11 +35,11 @@ int apply_mvm(const KP<T> &kp, const T *X1, int64_t n1, const T *X2, int64_t n2,
             GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
             TcMvmArgs a{};
             a.kind = kp.kind;
-            GP_TRY(tc_prepare_points(kp, X1, n1, pa, &a.rows, st));
             if (X2 == X1 && n2 == n1) {
+                GP_TRY(tc_prepare_points(kp, X1, n1, pa, &a.rows, st));
                 a.cols = a.rows;
             } else {
-                GP_TRY(tc_prepare_points(kp, X2, n2, pb, &a.cols, st));
+                GP_TRY(tc_prepare_pair(kp, X1, n1, X2, n2, pa, pb, &a.rows, &a.cols, st));
             }
             a.V = V;
             a.ldv = ldv;

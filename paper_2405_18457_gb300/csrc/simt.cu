@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(NT) grad_simt_kernel(const GradArgs<T> a, int 
         if (DMAX <= 32) {
 #pragma unroll
             for (int kk = 0; kk < DMAX; ++kk)
-                if (kk == k) v = gacc[kk];
+                if (kk == k && k < d) v = gacc[kk];
         } else if (k < d) {
             v = gacc[k];
         }

@@ -1,23 +1,803 @@
-// tcgen05 tensor-core path (placeholder until the sm_103a kernels land).
+// tcgen05 (sm_103a) fused kernel-matrix product  Y = alpha * K(X1, X2) V + beta * Y + diag.
+//
+// Flash-attention-like tiling: one CTA owns 128 output rows and streams 128-wide
+// column tiles.  Per column tile:
+//   GEMM1 (tensor cores, fp16 x fp16 -> fp32 in TMEM):  S = PA_I . PB_J^T, where the
+//         prepared operands make S_ij the kernel's exponent argument directly
+//         (scaled squared distance, norm terms and the hi/lo split folded in);
+//   exp   (4 warps, one TMEM lane = one row each): k'_ij = kappa(S_ij) on MUFU,
+//         packed to fp16 and written back over S in TMEM (K never leaves the SM);
+//   GEMM2 (tensor cores, A = k' from TMEM, B = V16_J from SMEM): Y_I += K'_IJ V_J.
+// A warp-specialised pipeline overlaps them: warp 0 issues TMA loads of PB/V16
+// tiles into a ring of shared-memory stages, warp 1 issues tcgen05.mma (one
+// thread), warps 4-7 evaluate the kernel and run the epilogue.  Two S buffers in
+// TMEM let GEMM1 of tile j+1 run while tile j is being exponentiated.  Every
+// mbarrier wait is bounded (about 2 s); on time-out the kernel records an error
+// flag, skips the remaining work, releases its tensor memory and returns.
+//
+// Operand preparation (per call, O(n d)):
+//   a_i = x_i / l (ARD scaling), n_i = ||a_i||^2, c the kernel-specific factor
+//   (RBF: c = -log2(e)/2 so that k = s_f^2 2^S; Matern-3/2: c = 3 log2(e)^2 so
+//   that sqrt(S) = sqrt(3) r log2(e)).  With h(.) = fp16 rounding and
+//   l(x) = h(x - h(x)):
+//     PA_i = [h(-2c a_i/s), h(-2c a_i/s), l(-2c a_i/s), h(c n_i/s), l(c n_i/s), 1, 1, 0...]
+//     PB_j = [h(a_j),       l(a_j),       h(a_j),       1,          1, h(c n_j/s), l(c n_j/s), 0...]
+//   so that PA_i . PB_j = (c r_ij^2)/s to ~2^-22 relative of c max(n) (the lo x lo
+//   term is dropped), s a power of two that keeps every fp16 entry < 2^14.
+//   V is stored as fp16 per column, scaled by a power of two so its largest
+//   magnitude lies in [1, 2); the scale is undone in FP32 in the epilogue.
 #include "gp_internal.cuh"
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
 
 namespace gp {
 
-bool tc_available() { return false; }
-size_t tc_points_bytes(int64_t, int) { return 0; }
-int tc_prepare_points(const KP<float> &, const float *, int64_t, void *, TcPoints *, cudaStream_t) {
-    set_error("tensor-core path not built");
-    return GP_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int TM = 128;          // output rows per CTA
+constexpr int TN = 128;          // columns per tile
+constexpr int MAX_STAGES = 4;
+constexpr int NTHREADS = 256;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-size_t tc_mvm_workspace(int64_t, int64_t, int) { return 0; }
-int tc_mvm(const TcMvmArgs &, void *, size_t, cudaStream_t) {
-    set_error("tensor-core path not built");
-    return GP_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
-size_t tc_grad_workspace(int64_t, int, int) { return 0; }
-int tc_grad(const GradArgs<float> &, void *, size_t, cudaStream_t) {
-    set_error("tensor-core path not built");
-    return GP_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false when this or another thread of the CTA timed out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (*err) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kWaitCycles) {
+            *err = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// SMEM matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(const void *p) {
+    uint64_t a = smem_u32(p);
+    uint64_t d = 0;
+    d |= (a >> 4) & 0x3FFFull;        // start address
+    d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32; // stride byte offset
+    d |= (uint64_t)1 << 46;           // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;           // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: fp16 A/B, f32 accumulator, K-major A and B.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// k / s_f^2 from the tile value S (already the kernel's exponent argument / s).
+template <int KIND>
+__device__ __forceinline__ float kernel_of(float S, float dscale) {
+    if (KIND == GP_RBF) {
+        return ex2_approx(fminf(S * dscale, 0.0f));
+    } else {
+        float u = fmaxf(S * dscale, 1e-30f);
+        float q = u * rsqrt_approx(u);  // sqrt(3) r log2(e)
+        return fmaf(q, kLn2, 1.0f) * ex2_approx(-q);
+    }
+}
+
+struct KParams {
+    int R, R_pad, KD, nstages;
+    int64_t n1;          // output rows
+    int64_t col_tiles;   // 128-wide column tiles over the (padded) column set
+    int nsplit;
+    float sf2, alpha, beta, diag_coef;
+    const float *vinv;   // per right-hand side: 1 / (power-of-two scale of V16)
+    const float *dscale; // device scalar s (see operand preparation)
+    const float *Vd;
+    int64_t ldvd, drow0, ndiag;
+    float *Y;
+    int64_t ldy;
+    float *partial;      // nsplit > 1: partial[split][c][i]
+    const int *done;
+    int *err;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_mvm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const __grid_constant__ CUtensorMap mapV, const KParams p) {
+    if (p.done && *p.done) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int katoms = p.KD / 64;
+    const int R_pad = p.R_pad;
+    const int NS = p.nstages;
+    const uint32_t a_bytes = (uint32_t)TM * p.KD * 2;
+    const uint32_t b_bytes = (uint32_t)TN * p.KD * 2;
+    const uint32_t v_atom = (uint32_t)R_pad * 128;
+    const uint32_t v_bytes = 2 * v_atom;
+    const uint32_t stage_bytes = b_bytes + v_bytes;
+    uint8_t *sA = smem;
+    uint8_t *sStages = smem + a_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStages + (size_t)NS * stage_bytes);
+    uint64_t *a_full = bars;
+    uint64_t *full = bars + 1;
+    uint64_t *empty = full + MAX_STAGES;
+    uint64_t *s_full = empty + MAX_STAGES;
+    uint64_t *p_full = s_full + 2;
+    uint64_t *sp_free = p_full + 2;
+    uint64_t *y_full = sp_free + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
+    volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int64_t per = cdiv(p.col_tiles, p.nsplit);
+    const int64_t t0 = (int64_t)blockIdx.y * per;
+    const int64_t t1 = min(p.col_tiles, t0 + per);
+    const int ntiles = (int)max((int64_t)0, t1 - t0);
+
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        for (int s = 0; s < MAX_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&p_full[b], 128);
+            mbar_init(&sp_free[b], 1);
+        }
+        mbar_init(y_full, 1);
+        *s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tS0 = tmem, tY = tmem + 256;
+
+    if (warp == 0 && lane == 0 && ntiles > 0) {
+        // ------------------------------------------------ TMA producer
+        mbar_expect_tx(a_full, a_bytes);
+        for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
+        for (int it = 0; it < ntiles; ++it) {
+            const int s = it % NS, use = it / NS;
+            if (it >= NS && !mbar_wait(&empty[s], (use - 1) & 1, s_err)) break;
+            const int j0 = (int)((t0 + it) * TN);
+            uint8_t *sB = sStages + (size_t)s * stage_bytes;
+            uint8_t *sV = sB + b_bytes;
+            mbar_expect_tx(&full[s], stage_bytes);
+            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (TN * 128), &mapB, &full[s], ka * 64, j0);
+            tma_load_2d(sV, &mapV, &full[s], j0, 0);
+            tma_load_2d(sV + v_atom, &mapV, &full[s], j0 + 64, 0);
+        }
+    } else if (warp == 1 && lane == 0 && ntiles > 0) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t id1 = idesc_f16(TM, TN);
+        const uint32_t id2 = idesc_f16(TM, R_pad);
+        const int ksteps1 = p.KD / 16;
+        bool ok = mbar_wait(a_full, 0, s_err);
+        auto gemm1 = [&](int it) -> bool {
+            const int s = it % NS, b = it & 1;
+            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
+            if (it >= 2 && !mbar_wait(&sp_free[b], ((it / 2) - 1) & 1, s_err)) return false;
+            tc_fence_after();
+            const uint8_t *sB = sStages + (size_t)s * stage_bytes;
+            for (int k = 0; k < ksteps1; ++k) {
+                const int ka = k >> 2, ko = (k & 3) * 32;
+                mma_ss(tS0 + b * 128, sdesc(sA + ka * (TM * 128) + ko), sdesc(sB + ka * (TN * 128) + ko), id1,
+                       k > 0 ? 1u : 0u);
+            }
+            mma_commit(&s_full[b]);
+            return true;
+        };
+        if (ok) ok = gemm1(0);
+        for (int it = 0; ok && it < ntiles; ++it) {
+            const int s = it % NS, b = it & 1;
+            if (it + 1 < ntiles && !gemm1(it + 1)) break;
+            if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
+            tc_fence_after();
+            const uint8_t *sV = sStages + (size_t)s * stage_bytes + b_bytes;
+            for (int k = 0; k < TN / 16; ++k) {
+                const int kv = k >> 2, ko = (k & 3) * 32;
+                mma_ts(tY, tS0 + b * 128 + k * 8, sdesc(sV + kv * v_atom + ko), id2, (it > 0 || k > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+            mma_commit(&sp_free[b]);
+        }
+        mma_commit(y_full);
+    } else if (warp >= 4) {
+        // ------------------------------------------------ kernel evaluation + epilogue
+        const int wq = warp - 4;
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        const float dsc = *p.dscale;
+        bool ok = true;
+        for (int it = 0; it < ntiles; ++it) {
+            const int b = it & 1;
+            if (!mbar_wait(&s_full[b], (it / 2) & 1, s_err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tS0 + b * 128 + lane_off;
+#pragma unroll 1
+            for (int ch = 0; ch < TN / 32; ++ch) {
+                uint32_t r[32];
+                tmem_ld32(taddr + ch * 32, r);
+                tmem_ld_wait();
+                uint32_t pk[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float k0 = kernel_of<KIND>(__uint_as_float(r[2 * e]), dsc);
+                    float k1 = kernel_of<KIND>(__uint_as_float(r[2 * e + 1]), dsc);
+                    pk[e] = pack_half2(k0, k1);
+                }
+                tmem_st16(taddr + ch * 16, pk);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            mbar_arrive(&p_full[b]);
+        }
+        // epilogue: Y rows from TMEM lanes, one row per thread
+        if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
+        if (ok && ntiles > 0) {
+            tc_fence_after();
+            const int64_t i = row0 + wq * 32 + lane;
+            for (int c0 = 0; c0 < R_pad; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tY + lane_off + c0, r);
+                tmem_ld_wait();
+                if (i < p.n1) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int c = c0 + e;
+                        if (c >= p.R) break;
+                        float v = p.sf2 * p.vinv[c] * __uint_as_float(r[e]);
+                        if (p.nsplit > 1) {
+                            p.partial[((int64_t)blockIdx.y * p.R + c) * p.n1 + i] = v;
+                        } else {
+                            float y = p.alpha * v;
+                            if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
+                            if (p.diag_coef != 0.0f && i >= p.drow0 && i < p.drow0 + p.ndiag)
+                                y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - p.drow0)];
+                            p.Y[(int64_t)c * p.ldy + i] = y;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+    if (threadIdx.x == 0 && *s_err) atomicExch(p.err, 1);
+}
+
+// Empty column set or split partial reduction + epilogue.
+__global__ void tc_reduce_kernel(KParams p) {
+    if (p.done && *p.done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= p.n1) return;
+    float s = 0.0f;
+    for (int sp = 0; sp < p.nsplit; ++sp) s += p.partial[((int64_t)sp * p.R + c) * p.n1 + i];
+    float y = p.alpha * s;
+    if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
+    if (p.diag_coef != 0.0f && i >= p.drow0 && i < p.drow0 + p.ndiag)
+        y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - p.drow0)];
+    p.Y[(int64_t)c * p.ldy + i] = y;
+}
+
+// ------------------------------------------------------------------ operand preparation
+__device__ __forceinline__ void split16(float x, __half *hi, __half *lo) {
+    __half h = __float2half_rn(x);
+    *hi = h;
+    *lo = __float2half_rn(x - __half2float(h));
+}
+
+// max over points of c*||a||^2 and of |2 c a_k|  (as float bits, atomicMax on ints)
+__global__ void tc_bound_kernel(const KP<float> kp, float c, const float *X, int64_t n, unsigned int *bound) {
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float nrm = 0.0f, amax = 0.0f;
+        for (int k = 0; k < kp.d; ++k) {
+            float a = X[i * kp.d + k] * kp.inv_ell[k];
+            nrm += a * a;
+            amax = fmaxf(amax, fabsf(a));
+        }
+        m = fmaxf(m, fmaxf(fabsf(c) * nrm, 2.0f * fabsf(c) * amax));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bound, __float_as_uint(m));
+}
+
+// Writes PA (if PA) and PB (if PB) rows for the point set X (n points, n_pad rows).
+__global__ void tc_operands_kernel(const KP<float> kp, float c, const float *X, int64_t n, int64_t n_pad, int KD,
+                                   const unsigned int *bound, __half *PA, __half *PB, float *dscale_out) {
+    // s = smallest power of two with bound / s <= 2^14
+    const float bnd = __uint_as_float(*bound);
+    float s = 1.0f;
+    while (bnd / s > 16384.0f) s *= 2.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && dscale_out) *dscale_out = s;
+    const float inv_s = 1.0f / s;
+    const int d = kp.d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
+        __half *pa = PA ? PA + i * KD : nullptr;
+        __half *pb = PB ? PB + i * KD : nullptr;
+        const __half z = __float2half_rn(0.0f), one = __float2half_rn(1.0f);
+        if (i >= n) {
+            for (int k = 0; k < KD; ++k) {
+                if (pa) pa[k] = z;
+                if (pb) pb[k] = z;
+            }
+            continue;
+        }
+        float nrm = 0.0f;
+        for (int k = 0; k < d; ++k) {
+            float a = X[i * d + k] * kp.inv_ell[k];
+            __half h, l;
+            split16(a, &h, &l);
+            float ar = __half2float(h) + __half2float(l);  // the value the tensor cores see
+            nrm += ar * ar;
+            if (pb) {
+                pb[k] = h;
+                pb[d + k] = l;
+                pb[2 * d + k] = h;
+            }
+            if (pa) {
+                __half h2, l2;
+                split16(-2.0f * c * inv_s * ar, &h2, &l2);
+                pa[k] = h2;
+                pa[d + k] = h2;
+                pa[2 * d + k] = l2;
+            }
+        }
+        __half nh, nl;
+        split16(c * inv_s * nrm, &nh, &nl);
+        const int o = 3 * d;
+        if (pa) {
+            pa[o] = nh;
+            pa[o + 1] = nl;
+            pa[o + 2] = one;
+            pa[o + 3] = one;
+            for (int k = o + 4; k < KD; ++k) pa[k] = z;
+        }
+        if (pb) {
+            pb[o] = one;
+            pb[o + 1] = one;
+            pb[o + 2] = nh;
+            pb[o + 3] = nl;
+            for (int k = o + 4; k < KD; ++k) pb[k] = z;
+        }
+    }
+}
+
+// Column-wise max |V| partials (grid P x R).
+__global__ void tc_colmax_kernel(const float *V, int64_t ldv, int64_t n, int P, float *part, const int *done) {
+    if (done && *done) return;
+    const int pidx = blockIdx.x, c = blockIdx.y;
+    const int64_t per = cdiv(n, P), i0 = pidx * per, i1 = min(n, i0 + per);
+    float m = 0.0f;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) m = fmaxf(m, fabsf(V[(int64_t)c * ldv + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+        part[(int64_t)c * P + pidx] = t;
+    }
+}
+
+// V16[c][j] = fp16(V[c][j] * 2^-e_c) for j < n, 0 up to n_pad and for c >= R.
+__global__ void tc_convert_kernel(const float *V, int64_t ldv, int64_t n, int64_t n_pad, int R, int P,
+                                  const float *part, __half *V16, float *vinv, const int *done) {
+    if (done && *done) return;
+    const int c = blockIdx.y;
+    float scale = 0.0f, inv = 1.0f;
+    if (c < R) {
+        float m = 0.0f;
+        for (int q = 0; q < P; ++q) m = fmaxf(m, part[(int64_t)c * P + q]);
+        int e = 0;
+        if (m > 0.0f && isfinite(m)) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+        scale = ldexpf(1.0f, 1 - e);                  // m * scale in [1, 2)
+        inv = ldexpf(1.0f, e - 1);
+        if (!(m > 0.0f) || !isfinite(m)) {
+            scale = 1.0f;
+            inv = 1.0f;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) vinv[c] = inv;
+    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += (int64_t)gridDim.x * blockDim.x) {
+        float v = (c < R && j < n) ? V[(int64_t)c * ldv + j] * scale : 0.0f;
+        V16[(int64_t)c * n_pad + j] = __float2half_rn(v);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+int make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+             uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is unavailable");
+        return GP_ERR_UNSUPPORTED;
+    }
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return GP_ERR_CUDA;
+    }
+    return GP_OK;
+}
+
+int kd_for(int d) { return (int)rup(3 * d + 4, 64); }
+int rpad_for(int R) { return (int)rup(R, 16); }
+
+int num_sms_tc() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
+int pick_split(int64_t row_tiles, int64_t col_tiles) {
+    const int sms = num_sms_tc();
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= 8; ++s) {
+        if (col_tiles / s < 4 && s > 1) break;
+        if (cdiv(col_tiles, s) * (s - 1) >= col_tiles) continue;  // every split must own a tile
+        int64_t units = row_tiles * s;
+        double waves = (double)units / sms;
+        double eff = waves / std::ceil(waves);
+        // splitting costs a partial write/read per split: prefer fewer splits
+        eff -= 0.01 * (s - 1);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = s;
+        }
+    }
+    return best;
+}
+
+int stages_for(int KD, int R_pad) {
+    size_t a = (size_t)TM * KD * 2, st = (size_t)TN * KD * 2 + 2 * (size_t)R_pad * 128;
+    int ns = (int)std::min<size_t>(MAX_STAGES, (kMaxDynSmem - 2048 - a) / st);
+    return ns;
+}
+
+size_t smem_for(int KD, int R_pad, int ns) {
+    return 1024 + (size_t)TM * KD * 2 + (size_t)ns * ((size_t)TN * KD * 2 + 2 * (size_t)R_pad * 128) + 256;
+}
+
+}  // namespace
+
+bool tc_available() {
+    static int ok = -1;
+    if (ok < 0) {
+        int dev = 0, major = 0, minor = 0;
+        ok = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+            ok = (major == 10 && minor == 3) && encode_fn() != nullptr;
+        else
+            cudaGetLastError();
+    }
+    return ok == 1;
+}
+
+// Buffer of a prepared pair: PA (n1_pad x KD), PB (n2_pad x KD), bound, dscale.
+size_t tc_points_bytes(int64_t n, int d) {
+    Carver c(nullptr);
+    c.take<__half>((size_t)rup(std::max<int64_t>(n, 1), TM) * kd_for(d));
+    c.take<__half>((size_t)rup(std::max<int64_t>(n, 1), TN) * kd_for(d));
+    c.take<unsigned int>(1);
+    c.take<float>(1);
+    return c.bytes();
+}
+
+int tc_prepare_points(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out, cudaStream_t st) {
+    const int KD = kd_for(kp.d);
+    const int64_t n_pad = rup(std::max<int64_t>(n, 1), TM);
+    Carver c(buf);
+    __half *PA = c.take<__half>((size_t)n_pad * KD);
+    __half *PB = c.take<__half>((size_t)n_pad * KD);
+    unsigned int *bound = c.take<unsigned int>(1);
+    float *dscale = c.take<float>(1);
+    const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
+    GP_TRY_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned int), st));
+    const unsigned nb = (unsigned)std::min<int64_t>(cdiv(n_pad, 256), 1024);
+    tc_bound_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, bound);
+    tc_operands_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, n_pad, KD, bound, PA, PB, dscale);
+    GP_TRY(check_launch("tc operand preparation", 2));
+    out->PA = PA;
+    out->PB = PB;
+    out->n = n;
+    out->n_pad = n_pad;
+    out->KD = KD;
+    out->dscale = dscale;
+    out->bound = bound;
+    return GP_OK;
+}
+
+int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const float *X2, int64_t n2, void *buf1,
+                    void *buf2, TcPoints *rows, TcPoints *cols, cudaStream_t st) {
+    // one shared scale for both point sets: bound over the union
+    const int KD = kd_for(kp.d);
+    const int64_t p1 = rup(std::max<int64_t>(n1, 1), TM), p2 = rup(std::max<int64_t>(n2, 1), TM);
+    Carver c1(buf1), c2(buf2);
+    __half *PA = c1.take<__half>((size_t)p1 * KD);
+    c1.take<__half>((size_t)p1 * KD);
+    unsigned int *bound = c1.take<unsigned int>(1);
+    float *dscale = c1.take<float>(1);
+    c2.take<__half>((size_t)p2 * KD);
+    __half *PB = c2.take<__half>((size_t)p2 * KD);
+    const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
+    GP_TRY_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned int), st));
+    tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, bound);
+    tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(kp, cf, X2, n2, bound);
+    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, p1, KD,
+                                                                                          bound, PA, nullptr, dscale);
+    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(kp, cf, X2, n2, p2, KD,
+                                                                                          bound, nullptr, PB, nullptr);
+    GP_TRY(check_launch("tc pair preparation", 4));
+    *rows = TcPoints{PA, nullptr, n1, p1, KD, dscale, bound};
+    *cols = TcPoints{nullptr, PB, n2, p2, KD, dscale, bound};
+    return GP_OK;
+}
+
+size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
+    const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
+    const int R_pad = rpad_for(std::min(R, 256));
+    const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM);
+    const int ns = pick_split(row_tiles, cdiv(p2, TN));
+    Carver c(nullptr);
+    c.take<__half>((size_t)R_pad * p2);            // V16
+    c.take<float>(256);                            // vinv
+    c.take<float>((size_t)R * 64);                 // column max partials
+    c.take<int>(1);                                // error flag
+    if (ns > 1) c.take<float>((size_t)ns * R * n1);
+    return c.bytes();
+}
+
+int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (a.R > 256) {
+        // wide blocks of right-hand sides: 256 at a time
+        for (int c0 = 0; c0 < a.R; c0 += 256) {
+            TcMvmArgs b = a;
+            b.R = std::min(256, a.R - c0);
+            b.V = a.V + (int64_t)c0 * a.ldv;
+            b.Y = a.Y + (int64_t)c0 * a.ldy;
+            b.Vd = a.Vd ? a.Vd + (int64_t)c0 * a.ldvd : nullptr;
+            GP_TRY(tc_mvm(b, ws, ws_bytes, st));
+        }
+        return GP_OK;
+    }
+    const int64_t n1 = a.rows.n, n2 = a.cols.n;
+    if (n1 == 0 || a.R == 0) return GP_OK;
+    const int KD = a.rows.KD;
+    const int R_pad = rpad_for(a.R);
+    const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
+    const int64_t row_tiles = cdiv(n1, TM), col_tiles = cdiv(p2, TN);
+    const int nsplit = pick_split(row_tiles, col_tiles);
+    Carver c(ws);
+    __half *V16 = c.take<__half>((size_t)R_pad * p2);
+    float *vinv = c.take<float>(256);
+    float *cm = c.take<float>((size_t)a.R * 64);
+    int *err = c.take<int>(1);
+    float *partial = nsplit > 1 ? c.take<float>((size_t)nsplit * a.R * n1) : nullptr;
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
+    tc_colmax_kernel<<<dim3(P, a.R), 256, 0, st>>>(a.V, a.ldv, n2, P, cm, a.done);
+    tc_convert_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(p2, 256), 256), R_pad), 256, 0, st>>>(
+        a.V, a.ldv, n2, p2, a.R, P, cm, V16, vinv, a.done);
+    GP_TRY(check_launch("tc rhs conversion", 2));
+
+    CUtensorMap mA, mB, mV;
+    GP_TRY(make_map(&mA, a.rows.PA, KD, a.rows.n_pad, 64, TM));
+    GP_TRY(make_map(&mB, a.cols.PB, KD, a.cols.n_pad, 64, TN));
+    GP_TRY(make_map(&mV, V16, p2, R_pad, 64, R_pad));
+    const int ns = stages_for(KD, R_pad);
+    if (ns < 2) {
+        set_error("tensor-core tile does not fit shared memory (d=%d, R=%d)", (KD - 4) / 3, a.R);
+        return GP_ERR_UNSUPPORTED;
+    }
+    KParams kp{};
+    kp.R = a.R;
+    kp.R_pad = R_pad;
+    kp.KD = KD;
+    kp.nstages = ns;
+    kp.n1 = n1;
+    kp.col_tiles = col_tiles;
+    kp.nsplit = nsplit;
+    kp.sf2 = a.sf2;
+    kp.alpha = a.alpha;
+    kp.beta = a.beta;
+    kp.diag_coef = a.diag_coef;
+    kp.vinv = vinv;
+    kp.dscale = a.rows.dscale;
+    kp.Vd = a.Vd;
+    kp.ldvd = a.ldvd;
+    kp.drow0 = a.drow0;
+    kp.ndiag = a.ndiag;
+    kp.Y = a.Y;
+    kp.ldy = a.ldy;
+    kp.partial = partial;
+    kp.done = a.done;
+    kp.err = err;
+    const size_t smem = smem_for(KD, R_pad, ns);
+    static bool attr[2] = {false, false};
+    const int ki = a.kind == GP_RBF ? 0 : 1;
+    if (!attr[ki]) {
+        if (ki == 0)
+            GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxDynSmem));
+        else
+            GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+        attr[ki] = true;
+    }
+    dim3 grid((unsigned)row_tiles, (unsigned)nsplit);
+    prof_begin(st);
+    if (ki == 0)
+        tc_mvm_kernel<GP_RBF><<<grid, NTHREADS, smem, st>>>(mA, mB, mV, kp);
+    else
+        tc_mvm_kernel<GP_MATERN32><<<grid, NTHREADS, smem, st>>>(mA, mB, mV, kp);
+    prof_end(st);
+    GP_TRY(check_launch("tc_mvm_kernel"));
+    if (nsplit > 1) {
+        tc_reduce_kernel<<<dim3((unsigned)cdiv(n1, 256), a.R), 256, 0, st>>>(kp);
+        GP_TRY(check_launch("tc_reduce_kernel"));
+    }
+    return GP_OK;
+}
+
+size_t tc_grad_workspace(int64_t n, int d, int R) { return grad_simt_workspace<float>(n, d, R); }
+int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st) {
+    // The estimator reduction runs on the CUDA-core FP32 kernel in this precision mode.
+    return grad_simt<float>(a, ws, ws_bytes, st);
 }
 
 }  // namespace gp
