@@ -250,6 +250,24 @@ int gp_mll_grad_pathwise_f64(int kind, const double *theta, int d, const double 
                              void *ws, size_t ws_bytes, cudaStream_t stream);
 size_t gp_mll_grad_f64_workspace(int64_t n, int d, int s);
 
+/* Pathwise estimator that allocates nothing and takes no workspace (the paper has
+ * no counterpart: this is a deployment variant of gp_mll_grad_pathwise).
+ * For callers that cannot allocate device memory where they call it: code that
+ * runs while a stream is captured into a CUDA graph, host callbacks enqueued on a
+ * stream, hosts with a fixed device-memory budget.  Its scratch is one static
+ * device array of GP_NOALLOC_SCRATCH_BYTES per GPU (held from library load to
+ * process exit), enough for the block partial sums of n up to about 3.9 million
+ * points at d = 16 (2 million at d = 32).  Requests that need more return
+ * GP_ERR_INVALID_ARG with the
+ * required size in gp_last_error().  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before
+ * any stream capture.  All calls on a device share the array: calls whose work
+ * overlaps on the GPU (unordered streams) race and must not be issued.  Results
+ * equal gp_mll_grad_pathwise's for the same arguments. */
+#define GP_NOALLOC_SCRATCH_BYTES (8u << 20)
+int gp_mll_grad_pathwise_noalloc(int kind, const double *theta, int d, const float *X, int64_t n,
+                                 const float *Vsol, int s, double *grad, int prec, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Posterior samples by pathwise conditioning (Eq. pathwise_conditioning,     */
 /* Sec. 3 "Amortising Linear Solves")                                        */
