@@ -129,6 +129,8 @@ class Replica:
         self.t = 1
         self.V = torch.zeros((prob.s + 1, prob.n), dtype=dtype, device=dev)
         self.last = None
+        self.phase_ms = None
+        self._events = []
 
     def pinned_inputs(self):
         torch = self.torch
@@ -144,9 +146,17 @@ class Replica:
         self.y.copy_(pinned["y"], non_blocking=True)
         return sum(v.numel() * v.element_size() for v in pinned.values())
 
+    def _mark(self, name):
+        if self.phase_ms is not None:
+            ev = self.torch.cuda.Event(enable_timing=True)
+            ev.record()
+            self._events.append((name, ev))
+
     def step(self):
         gp, p = self.gp, self.p
         th = self.theta
+        self._events = []
+        self._mark("start")
         if self.dtype == self.torch.float64:
             F = gp.gp_rff_prior_sample(p.kind, th, self.X, self.om, self.c2, self.Wp)
             sig = th[-1]
@@ -154,10 +164,16 @@ class Replica:
         else:
             F = gp.gp_rff_prior_sample(p.kind, th, self.X, self.om, self.c2, self.Wp)
             B = gp.gp_pathwise_rhs(th, p.d, self.y, F, self.w)
+        self._mark("rff+rhs")
         V, info = gp.gp_solve_cg(p.kind, th, self.X, B, V0=self.V, max_iters=self.max_iters, tol=0.01,
                                  prec=self.prec)
+        self._mark("cg")
         g = gp.gp_mll_grad_pathwise(p.kind, th, self.X, V, prec=self.prec)
+        self._mark("grad")
         gh = g.cpu().numpy()  # device -> host read of the step's result
+        if self.phase_ms is not None:
+            for (_, e0), (name, e1) in zip(self._events[:-1], self._events[1:]):
+                self.phase_ms[name] = self.phase_ms.get(name, 0.0) + e0.elapsed_time(e1)
         self.theta = gp.gp_adam_softplus_step(self.nu, self.m, self.v, self.t, gh, lr=0.1)
         self.t += 1
         self.last = info
@@ -226,6 +242,11 @@ def run_ours(args):
     gp.gp_diag_reset(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = sum(step_ms) / 1e3
+    # one extra, separately timed step for the per-phase breakdown (not in `value`)
+    rep.phase_ms = {}
+    rep.step()
+    phases = {k: round(v, 3) for k, v in rep.phase_ms.items()}
+    rep.phase_ms = None
     if dist is not None:
         tt = torch.tensor([total_s], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -306,6 +327,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "sec_per_step": total_s / args.steps,
         "cg_iters_per_step": iters,
+        "phase_ms_one_step": phases,
         "fp64_form": fp64,
         "speedup_vs_fp64_form": (fp64["sec_per_step"] / (total_s / args.steps)) if fp64 else None,
         "e2e": {"value": e_work / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -378,7 +400,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["tc16", "fp32"], default=None)
