@@ -256,9 +256,12 @@ size_t gp_mll_grad_f64_workspace(int64_t n, int d, int s);
  * runs while a stream is captured into a CUDA graph, host callbacks enqueued on a
  * stream, hosts with a fixed device-memory budget.  Its scratch is one static
  * device array of GP_NOALLOC_SCRATCH_BYTES per GPU (held from library load to
- * process exit), enough for the block partial sums of n up to about 3.9 million
- * points at d = 16 (2 million at d = 32).  Requests that need more return
- * GP_ERR_INVALID_ARG with the
+ * process exit).  With prec = GP_PREC_FP32 the scratch holds only block partial
+ * sums, enough for n up to about 3.9 million points at d = 16 (2 million at
+ * d = 32); with GP_PREC_TC16 it also holds the fp16 tensor-core operands (about
+ * 0.9 KB per point at d = 16, s = 64), enough for n up to about 9000 points.
+ * gp_mll_grad_workspace(n, d, s, prec) is the amount a call needs.  Requests
+ * that need more return GP_ERR_INVALID_ARG with the
  * required size in gp_last_error().  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress), so make that first call before
  * any stream capture.  All calls on a device share the array: calls whose work

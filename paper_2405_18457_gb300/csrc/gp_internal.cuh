@@ -185,6 +185,10 @@ struct GradArgs {
     double lam0, lam_rest;  // lambda_0 and lambda_c for c >= 1
     double *grad;           // device, d+2
 };
+// The sigma term (dH/dsigma = 2 sigma I, an O(n R) dot product) and the final
+// assembly of grad from per-block partial sums (256 doubles of scratch in dpart).
+template <typename T>
+int grad_tail(const GradArgs<T> &a, int nblocks, const double *partial, double *dpart, cudaStream_t st);
 template <typename T>
 size_t grad_simt_workspace(int64_t n, int d, int R);
 template <typename T>

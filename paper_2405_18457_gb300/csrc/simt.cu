@@ -479,6 +479,18 @@ int launch_grad(const GradArgs<T> &a, const GradPlan<T> &pl, double *partial, do
 
 }  // namespace
 
+// sigma term and final assembly shared with the tensor-core estimator:
+// partial[b][k] (k < d: length-scale sums before 1/l_k; k = d: signal sum
+// before 2/s_f) over nblocks blocks -> grad (d+2).
+template <typename T>
+int grad_tail(const GradArgs<T> &a, int nblocks, const double *partial, double *dpart, cudaStream_t st) {
+    diag_dot_kernel<T><<<DIAG_BLOCKS, 256, 0, st>>>(a, dpart);
+    GP_TRY(check_launch("diag_dot_kernel"));
+    grad_finalize_kernel<T><<<a.kp.d + 2, 256, 0, st>>>(a.kp, nblocks, partial, DIAG_BLOCKS, dpart, a.grad);
+    return check_launch("grad_finalize_kernel");
+}
+template int grad_tail<float>(const GradArgs<float> &, int, const double *, double *, cudaStream_t);
+
 template <typename T>
 size_t grad_simt_workspace(int64_t n, int d, int R) {
     GradPlan<T> pl = plan_grad<T>(n);

@@ -794,10 +794,448 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     return GP_OK;
 }
 
-size_t tc_grad_workspace(int64_t n, int d, int R) { return grad_simt_workspace<float>(n, d, R); }
+// ===========================================================================
+// Fused gradient estimator on tcgen05 (Eq. mll_grad with Eq. trace or
+// Eq. pathwise_estimator):
+//   g_l_k = (1/l_k) sum_ij phi_ij M_ij (a_ik - a_jk)^2,  g_sf = (2/s_f) sum_ij k_ij M_ij,
+//   M_ij = sum_c lambda_c U_ci W_cj.
+// Per 128-row x 64-column tile:
+//   GEMM1  S = PA_I PB_J^T            (the kernel's exponent argument, as in the product)
+//   GEMM-M M = U16_I W16_J^T          (K = right-hand sides, lambda folded into U16)
+//   exp    W1 = phi' M (fp16, back into TMEM), row sums of W1, sum of k' M
+//   GEMM3  D3 += W1 [A_J | A_J^2]     (hi/lo fp16 splits of the scaled coordinates)
+// and per row i: sum_j W1_ij (a_ik - a_jk)^2 = a_ik^2 rs_i - 2 a_ik (W1 A)_ik + (W1 A^2)_ik,
+// an exact identity for the rounded W1 (rs_i sums the same fp16 values).
+// ===========================================================================
+namespace {
+
+constexpr int GTN = 64;  // gradient column tile
+
+struct GParams {
+    int KD, KM, N3p, d, nstages;
+    int64_t n, col_tiles;
+    int nsplit;
+    const float *dscale;
+    const float *guw;  // 1 / (G_u G_w)
+    const float *X;
+    float inv_ell[GP_MAX_D];
+    float cphi_sf2;  // phi = cphi_sf2 * phi'  (3 s_f^2 Matern, s_f^2 RBF)
+    float sf2;
+    double *partial;
+    int *err;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_grad_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapW,
+                   const __grid_constant__ CUtensorMap mapB3, const GParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int katoms = p.KD / 64, matoms = p.KM / 64;
+    const int NS = p.nstages;
+    const uint32_t a_bytes = (uint32_t)TM * p.KD * 2, u_bytes = (uint32_t)TM * p.KM * 2;
+    const uint32_t b_bytes = (uint32_t)GTN * p.KD * 2, w_bytes = (uint32_t)GTN * p.KM * 2;
+    const uint32_t b3_bytes = (uint32_t)p.N3p * 128;
+    const uint32_t stage_bytes = b_bytes + w_bytes + b3_bytes;
+    uint8_t *sA = smem;
+    uint8_t *sU = sA + a_bytes;
+    uint8_t *sStages = sU + u_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStages + (size_t)NS * stage_bytes);
+    uint64_t *a_full = bars;
+    uint64_t *full = bars + 1;
+    uint64_t *empty = full + MAX_STAGES;
+    uint64_t *s_full = empty + MAX_STAGES;
+    uint64_t *p_full = s_full + 2;
+    uint64_t *sp_free = p_full + 2;
+    uint64_t *y_full = sp_free + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
+    volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    double *red = reinterpret_cast<double *>(smem_raw);  // reused after the pipeline (reduction scratch)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int64_t per = cdiv(p.col_tiles, p.nsplit);
+    const int64_t t0 = (int64_t)blockIdx.y * per;
+    const int64_t t1 = min(p.col_tiles, t0 + per);
+    const int ntiles = (int)max((int64_t)0, t1 - t0);
+
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        for (int s = 0; s < MAX_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&p_full[b], 128);
+            mbar_init(&sp_free[b], 1);
+        }
+        mbar_init(y_full, 1);
+        *s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tS = tmem, tM = tmem + 128, tD = tmem + 256;
+
+    double g_acc[1];  // silence unused warnings in non-epilogue warps
+    (void)g_acc;
+    float gk[64];
+    double rs_acc = 0.0, s_acc = 0.0;
+
+    if (warp == 0 && lane == 0 && ntiles > 0) {
+        mbar_expect_tx(a_full, a_bytes + u_bytes);
+        for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
+        for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sU + ka * (TM * 128), &mapU, a_full, ka * 64, (int)row0);
+        for (int it = 0; it < ntiles; ++it) {
+            const int s = it % NS, use = it / NS;
+            if (it >= NS && !mbar_wait(&empty[s], (use - 1) & 1, s_err)) break;
+            const int j0 = (int)((t0 + it) * GTN);
+            uint8_t *sB = sStages + (size_t)s * stage_bytes;
+            uint8_t *sW = sB + b_bytes;
+            uint8_t *sB3 = sW + w_bytes;
+            mbar_expect_tx(&full[s], stage_bytes);
+            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (GTN * 128), &mapB, &full[s], ka * 64, j0);
+            for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sW + ka * (GTN * 128), &mapW, &full[s], ka * 64, j0);
+            tma_load_2d(sB3, &mapB3, &full[s], j0, 0);
+        }
+    } else if (warp == 1 && lane == 0 && ntiles > 0) {
+        const uint32_t id1 = idesc_f16(TM, GTN);
+        const uint32_t id3 = idesc_f16(TM, p.N3p);
+        bool ok = mbar_wait(a_full, 0, s_err);
+        auto gemm1 = [&](int it) -> bool {
+            const int s = it % NS, b = it & 1;
+            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
+            if (it >= 2 && !mbar_wait(&sp_free[b], ((it / 2) - 1) & 1, s_err)) return false;
+            tc_fence_after();
+            const uint8_t *sB = sStages + (size_t)s * stage_bytes;
+            const uint8_t *sW = sB + b_bytes;
+            for (int k = 0; k < p.KD / 16; ++k) {
+                const int ka = k >> 2, ko = (k & 3) * 32;
+                mma_ss(tS + b * GTN, sdesc(sA + ka * (TM * 128) + ko), sdesc(sB + ka * (GTN * 128) + ko), id1,
+                       k > 0 ? 1u : 0u);
+            }
+            for (int k = 0; k < p.KM / 16; ++k) {
+                const int ka = k >> 2, ko = (k & 3) * 32;
+                mma_ss(tM + b * GTN, sdesc(sU + ka * (TM * 128) + ko), sdesc(sW + ka * (GTN * 128) + ko), id1,
+                       k > 0 ? 1u : 0u);
+            }
+            mma_commit(&s_full[b]);
+            return true;
+        };
+        if (ok) ok = gemm1(0);
+        for (int it = 0; ok && it < ntiles; ++it) {
+            const int s = it % NS, b = it & 1;
+            if (it + 1 < ntiles && !gemm1(it + 1)) break;
+            if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
+            tc_fence_after();
+            const uint8_t *sB3 = sStages + (size_t)s * stage_bytes + b_bytes + w_bytes;
+            for (int k = 0; k < GTN / 16; ++k)
+                mma_ts(tD, tS + b * GTN + k * 8, sdesc(sB3 + k * 32), id3, (it > 0 || k > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            mma_commit(&sp_free[b]);
+        }
+        mma_commit(y_full);
+    } else if (warp >= 4) {
+        const int wq = warp - 4;
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        const float dsc = *p.dscale;
+        bool ok = true;
+        for (int it = 0; it < ntiles; ++it) {
+            const int b = it & 1;
+            if (!mbar_wait(&s_full[b], (it / 2) & 1, s_err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t taS = tS + b * GTN + lane_off, taM = tM + b * GTN + lane_off;
+            float rs = 0.0f, sk = 0.0f;
+#pragma unroll 1
+            for (int ch = 0; ch < GTN / 32; ++ch) {
+                uint32_t rS[32], rM[32];
+                tmem_ld32(taS + ch * 32, rS);
+                tmem_ld32(taM + ch * 32, rM);
+                tmem_ld_wait();
+                uint32_t pk[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float w[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float S = __uint_as_float(rS[2 * e + h]);
+                        const float M = __uint_as_float(rM[2 * e + h]);
+                        float kp_, phi_;
+                        if (KIND == GP_RBF) {
+                            kp_ = ex2_approx(fminf(S * dsc, 0.0f));
+                            phi_ = kp_;
+                        } else {
+                            float u = fmaxf(S * dsc, 1e-30f);
+                            float q = u * rsqrt_approx(u);
+                            phi_ = ex2_approx(-q);
+                            kp_ = fmaf(q, kLn2, 1.0f) * phi_;
+                        }
+                        w[h] = phi_ * M;
+                        sk = fmaf(kp_, M, sk);
+                    }
+                    pk[e] = pack_half2(w[0], w[1]);
+                    __half2 hw = *reinterpret_cast<__half2 *>(&pk[e]);
+                    float2 fw = __half22float2(hw);
+                    rs += fw.x + fw.y;
+                }
+                tmem_st16(taS + ch * 16, pk);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            mbar_arrive(&p_full[b]);
+            rs_acc += (double)rs;
+            s_acc += (double)sk;
+        }
+        if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
+        // per-row contributions sum_j W1_ij (a_ik - a_jk)^2
+        const int64_t i = row0 + wq * 32 + lane;
+        const int d = p.d;
+        for (int k = 0; k < 64; ++k) gk[k] = 0.0f;
+        if (ok && ntiles > 0) {
+            tc_fence_after();
+            float a[64];
+            for (int k = 0; k < d; ++k) a[k] = (i < p.n) ? p.X[i * d + k] * p.inv_ell[k] : 0.0f;
+            for (int k = 0; k < d; ++k) gk[k] = a[k] * a[k] * (float)rs_acc;
+            for (int f0 = 0; f0 < p.N3p; f0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tD + lane_off + f0, r);
+                tmem_ld_wait();
+                for (int e = 0; e < 16; ++e) {
+                    const int f = f0 + e;
+                    if (f >= 4 * d) break;
+                    const int part = f / d, k = f - part * d;
+                    const float v = __uint_as_float(r[e]);
+                    if (part < 2) gk[k] -= 2.0f * a[k] * v;
+                    else gk[k] += v;
+                }
+            }
+            if (i >= p.n) {
+                for (int k = 0; k < d; ++k) gk[k] = 0.0f;
+                s_acc = 0.0;
+            }
+        } else {
+            s_acc = 0.0;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+    // block reduction over the 128 epilogue threads, fixed order
+    double *out = p.partial + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * (p.d + 1);
+    const double gscale = (double)p.cphi_sf2 * (double)(*p.guw);
+    const double sscale = (double)p.sf2 * (double)(*p.guw);
+    for (int k = 0; k <= p.d; ++k) {
+        double v = 0.0;
+        if (warp >= 4) v = (k < p.d) ? (double)gk[k] * gscale : s_acc * sscale;
+        v = warp_sum(v);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) out[k] = red[4] + red[5] + red[6] + red[7];
+    }
+    if (threadIdx.x == 0 && *s_err) atomicExch(p.err, 1);
+}
+
+// max |lambda_c U_ci| and max |W_cj| over i < n, c < R (float bits).
+__global__ void tc_uw_bound_kernel(GradArgs<float> a, unsigned int *bnd) {
+    float mu = 0.0f, mw = 0.0f;
+    const int64_t n = a.n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * a.R; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const int64_t i = e - (int64_t)c * n;
+        const float u = (c == 0) ? a.U0[i] * (float)a.lam0 : a.U[(int64_t)(c - 1) * a.ldu + i] * (float)a.lam_rest;
+        const float w = (c == 0) ? a.W0[i] : a.W[(int64_t)(c - 1) * a.ldw + i];
+        mu = fmaxf(mu, fabsf(u));
+        mw = fmaxf(mw, fabsf(w));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&bnd[0], __float_as_uint(mu));
+        atomicMax(&bnd[1], __float_as_uint(mw));
+    }
+}
+
+__device__ __forceinline__ float pow2_norm(float m) {  // 2^-e with m 2^-e in [1, 2); 1 for 0 / non-finite
+    if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
+    int e;
+    frexpf(m, &e);
+    return ldexpf(1.0f, 1 - e);
+}
+
+// U16[i][c] = fp16(lambda_c U_ci G_u), W16[j][c] = fp16(W_cj G_w), [n_pad x KM]; guw = 1/(G_u G_w).
+__global__ void tc_uw_convert_kernel(GradArgs<float> a, int64_t n_pad, int KM, const unsigned int *bnd, __half *U16,
+                                     __half *W16, float *guw) {
+    const float gu = pow2_norm(__uint_as_float(bnd[0]));
+    const float gw = pow2_norm(__uint_as_float(bnd[1]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *guw = 1.0f / (gu * gw);
+    const int64_t n = a.n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_pad * KM; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / KM;
+        const int c = (int)(e - i * KM);
+        float u = 0.0f, w = 0.0f;
+        if (i < n && c < a.R) {
+            u = (c == 0) ? a.U0[i] * (float)a.lam0 : a.U[(int64_t)(c - 1) * a.ldu + i] * (float)a.lam_rest;
+            w = (c == 0) ? a.W0[i] : a.W[(int64_t)(c - 1) * a.ldw + i];
+        }
+        U16[e] = __float2half_rn(u * gu);
+        W16[e] = __float2half_rn(w * gw);
+    }
+}
+
+// B3[f][j] (N3p x n_pad): f = part * d + k, parts hi(a), lo(a), hi(a^2), lo(a^2) of a_jk = x_jk / l_k.
+__global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int64_t n_pad, int N3p, __half *B3) {
+    const int d = kp.d;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)N3p * n_pad; e += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(e / n_pad);
+        const int64_t j = e - (int64_t)f * n_pad;
+        float v = 0.0f;
+        if (j < n && f < 4 * d) {
+            const int part = f / d, k = f - part * d;
+            const float a = X[j * d + k] * kp.inv_ell[k];
+            const float x = (part < 2) ? a : a * a;
+            const __half h = __float2half_rn(x);
+            v = (part & 1) ? (x - __half2float(h)) : __half2float(h);
+        }
+        B3[e] = __float2half_rn(v);
+    }
+}
+
+struct GradPlanTc {
+    int KD, KM, N3p, ns, nsplit;
+    int64_t n_pad, row_tiles, col_tiles;
+    size_t smem;
+};
+
+GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
+    GradPlanTc g;
+    g.KD = kd_for(d);
+    g.KM = (int)rup(R, 64);
+    g.N3p = (int)rup(4 * d, 16);
+    g.n_pad = rup(std::max<int64_t>(n, 1), TM);
+    g.row_tiles = g.n_pad / TM;
+    g.col_tiles = g.n_pad / GTN;
+    g.nsplit = pick_split(g.row_tiles, g.col_tiles);
+    const size_t a = (size_t)TM * g.KD * 2 + (size_t)TM * g.KM * 2;
+    const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2 + (size_t)g.N3p * 128;
+    g.ns = (int)std::min<size_t>(MAX_STAGES, (kMaxDynSmem - 2048 - a) / st);
+    g.smem = 1024 + a + (size_t)g.ns * st + 256;
+    return g;
+}
+
+}  // namespace
+
+size_t tc_grad_workspace(int64_t n, int d, int R) {
+    GradPlanTc g = plan_tc_grad(n, d, R);
+    Carver c(nullptr);
+    c.take<char>(tc_points_bytes(n, d));
+    c.take<__half>((size_t)g.n_pad * g.KM);
+    c.take<__half>((size_t)g.n_pad * g.KM);
+    c.take<__half>((size_t)g.N3p * g.n_pad);
+    c.take<unsigned int>(2);
+    c.take<float>(1);
+    c.take<int>(1);
+    c.take<double>((size_t)g.row_tiles * g.nsplit * (d + 1));
+    c.take<double>(256);
+    return c.bytes();
+}
+
 int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st) {
-    // The estimator reduction runs on the CUDA-core FP32 kernel in this precision mode.
-    return grad_simt<float>(a, ws, ws_bytes, st);
+    const int d = a.kp.d;
+    if (d > 64 || a.R > 256) {
+        set_error("tensor-core gradient supports d <= 64 and s + 1 <= 256 (got d=%d, R=%d)", d, a.R);
+        return GP_ERR_UNSUPPORTED;
+    }
+    GradPlanTc g = plan_tc_grad(a.n, d, a.R);
+    if (g.ns < 2) {
+        set_error("tensor-core gradient tile does not fit shared memory");
+        return GP_ERR_UNSUPPORTED;
+    }
+    Carver c(ws);
+    void *pbuf = c.take<char>(tc_points_bytes(a.n, d));
+    __half *U16 = c.take<__half>((size_t)g.n_pad * g.KM);
+    __half *W16 = c.take<__half>((size_t)g.n_pad * g.KM);
+    __half *B3 = c.take<__half>((size_t)g.N3p * g.n_pad);
+    unsigned int *bnd = c.take<unsigned int>(2);
+    float *guw = c.take<float>(1);
+    int *err = c.take<int>(1);
+    const int nblocks = (int)(g.row_tiles * g.nsplit);
+    double *partial = c.take<double>((size_t)nblocks * (d + 1));
+    double *dpart = c.take<double>(256);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+
+    TcPoints pts;
+    GP_TRY(tc_prepare_points(a.kp, a.X, a.n, pbuf, &pts, st));
+    GP_TRY_CUDA(cudaMemsetAsync(bnd, 0, 2 * sizeof(unsigned int), st));
+    const unsigned nb1 = (unsigned)std::min<int64_t>(cdiv(a.n * a.R, 256), 2048);
+    tc_uw_bound_kernel<<<nb1, 256, 0, st>>>(a, bnd);
+    tc_uw_convert_kernel<<<(unsigned)std::min<int64_t>(cdiv(g.n_pad * g.KM, 256), 4096), 256, 0, st>>>(
+        a, g.n_pad, g.KM, bnd, U16, W16, guw);
+    tc_b3_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)g.N3p * g.n_pad, 256), 4096), 256, 0, st>>>(
+        a.kp, a.X, a.n, g.n_pad, g.N3p, B3);
+    GP_TRY(check_launch("tc gradient operand preparation", 3));
+
+    CUtensorMap mA, mB, mU, mW, mB3;
+    GP_TRY(make_map(&mA, pts.PA, g.KD, g.n_pad, 64, TM));
+    GP_TRY(make_map(&mB, pts.PB, g.KD, g.n_pad, 64, GTN));
+    GP_TRY(make_map(&mU, U16, g.KM, g.n_pad, 64, TM));
+    GP_TRY(make_map(&mW, W16, g.KM, g.n_pad, 64, GTN));
+    GP_TRY(make_map(&mB3, B3, g.n_pad, g.N3p, 64, g.N3p));
+    GParams p{};
+    p.KD = g.KD;
+    p.KM = g.KM;
+    p.N3p = g.N3p;
+    p.d = d;
+    p.nstages = g.ns;
+    p.n = a.n;
+    p.col_tiles = g.col_tiles;
+    p.nsplit = g.nsplit;
+    p.dscale = pts.dscale;
+    p.guw = guw;
+    p.X = a.X;
+    for (int k = 0; k < d; ++k) p.inv_ell[k] = a.kp.inv_ell[k];
+    p.cphi_sf2 = (a.kp.kind == GP_RBF ? 1.0f : 3.0f) * a.kp.sf2;
+    p.sf2 = a.kp.sf2;
+    p.partial = partial;
+    p.err = err;
+    static bool attr[2] = {false, false};
+    const int ki = a.kp.kind == GP_RBF ? 0 : 1;
+    if (!attr[ki]) {
+        if (ki == 0)
+            GP_TRY_CUDA(cudaFuncSetAttribute(tc_grad_kernel<GP_RBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxDynSmem));
+        else
+            GP_TRY_CUDA(cudaFuncSetAttribute(tc_grad_kernel<GP_MATERN32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+        attr[ki] = true;
+    }
+    dim3 grid((unsigned)g.row_tiles, (unsigned)g.nsplit);
+    prof_begin(st);
+    if (ki == 0)
+        tc_grad_kernel<GP_RBF><<<grid, NTHREADS, g.smem, st>>>(mA, mB, mU, mW, mB3, p);
+    else
+        tc_grad_kernel<GP_MATERN32><<<grid, NTHREADS, g.smem, st>>>(mA, mB, mU, mW, mB3, p);
+    prof_end(st);
+    GP_TRY(check_launch("tc_grad_kernel"));
+    return grad_tail<float>(a, nblocks, partial, dpart, st);
 }
 
 }  // namespace gp
