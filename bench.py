@@ -238,7 +238,8 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     launches = gp.gp_diag_launches()
-    prod_ms, prod_cnt = gp.gp_diag_product_time()
+    prod_ms, prod_cnt = gp.gp_diag_kernel_time(0)
+    grad_ms, grad_cnt = gp.gp_diag_kernel_time(1)
     gp.gp_diag_reset(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = sum(step_ms) / 1e3
@@ -301,20 +302,34 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     d, R = prob.d, prob.s + 1
     avg_launch_s = (prod_ms / 1e3) / max(prod_cnt, 1)
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    pairs = float(n) * n
     if prec == gp.GP_PREC_TC16:
-        flops_pair = 2.0 * d + 2.0 * R  # cross term x_i.x_j and the K V contraction
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak}
+        # Matern-3/2 needs one rsqrt (16/clk/SM) and one ex2 (32/clk/SM) per pair on the MUFU
+        # (special-function unit); rates measured on this GB300 with a CUDA-event probe.
+        mufu_pairs_per_clk = 1.0 / (1.0 / 16 + 1.0 / 32) if prob.kind == 1 else 32.0
+        peak = 152 * mufu_pairs_per_clk * clk_mhz * 1e6 / 1e9
+        achieved = pairs / avg_launch_s / 1e9 if prod_cnt else None
+        tflops = (2.0 * d + 2.0 * R) * pairs / avg_launch_s / 1e12 if prod_cnt else None
+        tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "alu", "unit": "Gpair/s", "peak": peak,
+                "peak_derivation": "MUFU: 152 SMs x (1/(1/16 + 1/32)) pairs/clk x %.0f MHz" % clk_mhz,
+                "tensor_tflops": tflops, "tensor_frac_of_measured_bf16_sustained": (tflops / tpeak) if tflops else None}
     else:
-        flops_pair = 3.0 * d + 2.0 * R + 10.0
         # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flops x max SM clock
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak}
-    achieved = flops_pair * n * n / avg_launch_s / 1e12 if prod_cnt else None
+        flops_pair = 3.0 * d + 2.0 * R + 10.0
+        peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        achieved = flops_pair * pairs / avg_launch_s / 1e12 if prod_cnt else None
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "algorithmic_flops_per_pair": flops_pair}
     roof.update({"achieved": achieved, "frac": (achieved / roof["peak"]) if achieved else None,
-                 "traffic": None, "peak_source": peak_src, "kernel": "product (H V) kernel",
-                 "algorithmic_flops_per_pair": flops_pair, "avg_launch_ms": avg_launch_s * 1e3,
-                 "launches_timed": prod_cnt})
+                 "traffic": None, "peak_source": peak_src, "kernel": "tc_mvm_kernel (H V)" if prec == 2 else
+                 "mvm_simt_kernel (H V)", "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": prod_cnt,
+                 "pairs_per_launch": pairs})
+    grad_kernel = None
+    if grad_cnt:
+        g_avg = grad_ms / 1e3 / grad_cnt
+        grad_kernel = {"kernel": "tc_grad_kernel", "avg_launch_ms": g_avg * 1e3, "launches_timed": grad_cnt,
+                       "gpairs_per_s": pairs / g_avg / 1e9}
     cpu = cpu_baseline(prob, R, budget_s=args.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -334,6 +349,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * (d + 2)},
         "gpu_launches": launches,
         "roofline": roof,
+        "gradient_kernel": grad_kernel,
         "cpu_baseline": cpu,
         "clocks": clk,
     }

@@ -97,11 +97,13 @@ int gp_version(void);
  * gp_diag_reset(t) zeroes the launch counter and, when t != 0, starts timing
  * every kernel-matrix product kernel with CUDA events recorded on its launch
  * stream (t == 0 stops timing).  gp_diag_launches() returns the number of
- * library kernels launched since the reset.  gp_diag_product_time() waits for
+ * library kernels launched since the reset.  gp_diag_kernel_time() waits for
  * the recorded events and returns the summed duration (ms) and the number of
- * timed product launches. */
+ * timed launches of the kernel-matrix product kernels (which = 0) or of the
+ * tensor-core gradient kernel (which = 1); gp_diag_product_time() is which = 0. */
 void gp_diag_reset(int time_products);
 long long gp_diag_launches(void);
+int gp_diag_kernel_time(int which, double *total_ms, long long *count);
 int gp_diag_product_time(double *total_ms, long long *count);
 
 /* ------------------------------------------------------------------------ */

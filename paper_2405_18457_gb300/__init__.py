@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     GPError,
     SolveInfo,
     gp_adam_softplus_step,
+    gp_diag_kernel_time,
     gp_diag_launches,
     gp_diag_product_time,
     gp_diag_reset,

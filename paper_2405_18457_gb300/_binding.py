@@ -91,7 +91,17 @@ _SIGS = {
     "gp_diag_reset": (None, [_i]),
     "gp_diag_launches": (ctypes.c_longlong, []),
     "gp_diag_product_time": (_i, [_pd, ctypes.POINTER(ctypes.c_longlong)]),
+    "gp_diag_kernel_time": (_i, [_i, _pd, ctypes.POINTER(ctypes.c_longlong)]),
 }
+
+
+def gp_diag_kernel_time(which: int):
+    """(total milliseconds, launches) since the reset of the product kernels (0) or
+    the tensor-core gradient kernel (1)."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_longlong()
+    _check(library().gp_diag_kernel_time(int(which), ctypes.byref(ms), ctypes.byref(cnt)))
+    return float(ms.value), int(cnt.value)
 
 
 def gp_diag_reset(time_products: bool = False) -> None:

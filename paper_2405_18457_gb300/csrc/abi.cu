@@ -37,12 +37,17 @@ int check_launch(const char *what, int count) {
 
 // Event pool for the optional product-kernel timing.
 namespace {
+struct Span {
+    cudaEvent_t start, end;
+    int tag;
+};
 struct Prof {
     std::mutex mu;
     bool on = false;
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans;
+    std::vector<Span> spans;
     cudaEvent_t open = nullptr;
+    int open_tag = 0;
 };
 Prof &prof() {
     static Prof p;
@@ -60,11 +65,12 @@ cudaEvent_t take_event(Prof &p) {
 }
 }  // namespace
 
-void prof_begin(cudaStream_t st) {
+void prof_begin(cudaStream_t st, int tag) {
     Prof &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     if (!p.on) return;
     p.open = take_event(p);
+    p.open_tag = tag;
     cudaEventRecord(p.open, st);
 }
 
@@ -74,7 +80,7 @@ void prof_end(cudaStream_t st) {
     if (!p.on || p.open == nullptr) return;
     cudaEvent_t e = take_event(p);
     cudaEventRecord(e, st);
-    p.spans.emplace_back(p.open, e);
+    p.spans.push_back(Span{p.open, e, p.open_tag});
     p.open = nullptr;
 }
 
@@ -219,8 +225,8 @@ void gp_diag_reset(int time_products) {
     Prof &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     for (auto &s : p.spans) {
-        p.pool.push_back(s.first);
-        p.pool.push_back(s.second);
+        p.pool.push_back(s.start);
+        p.pool.push_back(s.end);
     }
     p.spans.clear();
     p.on = time_products != 0;
@@ -229,23 +235,29 @@ void gp_diag_reset(int time_products) {
 
 long long gp_diag_launches(void) { return g_launches.load(); }
 
-int gp_diag_product_time(double *total_ms, long long *count) {
+int gp_diag_kernel_time(int which, double *total_ms, long long *count) {
     GP_API_BEGIN
     REQ(total_ms && count, "null pointer argument");
+    REQ(which == 0 || which == 1, "which must be 0 (products) or 1 (gradients)");
     Prof &p = prof();
     std::lock_guard<std::mutex> g(p.mu);
     double tot = 0.0;
+    long long cnt = 0;
     for (auto &s : p.spans) {
-        GP_TRY_CUDA(cudaEventSynchronize(s.second));
+        if (s.tag != which) continue;
+        GP_TRY_CUDA(cudaEventSynchronize(s.end));
         float ms = 0.0f;
-        GP_TRY_CUDA(cudaEventElapsedTime(&ms, s.first, s.second));
+        GP_TRY_CUDA(cudaEventElapsedTime(&ms, s.start, s.end));
         tot += ms;
+        ++cnt;
     }
     *total_ms = tot;
-    *count = (long long)p.spans.size();
+    *count = cnt;
     return GP_OK;
     GP_API_END
 }
+
+int gp_diag_product_time(double *total_ms, long long *count) { return gp_diag_kernel_time(0, total_ms, count); }
 
 // ------------------------------------------------------------------ MVM
 size_t gp_kernel_mvm_workspace(int64_t n1, int64_t n2, int d, int nrhs, int prec) {

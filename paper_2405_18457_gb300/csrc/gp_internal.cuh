@@ -40,7 +40,8 @@ int check_launch(const char *what, int count = 1);
 // Optional CUDA-event timing of the kernel-matrix product kernels
 // (gp_diag_reset(1) turns it on): events recorded on the launch stream around
 // each product kernel.
-void prof_begin(cudaStream_t st);
+// tag 0: kernel-matrix product kernels, tag 1: gradient-estimator kernels.
+void prof_begin(cudaStream_t st, int tag = 0);
 void prof_end(cudaStream_t st);
 
 // Dynamic shared memory a kernel may opt into (227 KB per block on sm_103,

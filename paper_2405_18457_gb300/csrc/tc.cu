@@ -42,7 +42,8 @@ namespace {
 constexpr int TM = 128;          // output rows per CTA
 constexpr int TN = 128;          // columns per tile
 constexpr int MAX_STAGES = 4;
-constexpr int NTHREADS = 256;
+constexpr int NTHREADS = 256;     // gradient kernel: producer, MMA, 2 idle, 4 evaluation warps
+constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -174,16 +175,27 @@ __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// k / s_f^2 from the tile value S (already the kernel's exponent argument / s).
-template <int KIND>
+// k / s_f^2 from the tile value S (the kernel's exponent argument / s; SCALED
+// multiplies by s, skipped when the preparation chose s = 1).
+template <int KIND, bool SCALED>
 __device__ __forceinline__ float kernel_of(float S, float dscale) {
+    const float v = SCALED ? S * dscale : S;
     if (KIND == GP_RBF) {
-        return ex2_approx(fminf(S * dscale, 0.0f));
+        return ex2_approx(fminf(v, 0.0f));
     } else {
-        float u = fmaxf(S * dscale, 1e-30f);
+        float u = fmaxf(v, 1e-30f);
         float q = u * rsqrt_approx(u);  // sqrt(3) r log2(e)
         return fmaf(q, kLn2, 1.0f) * ex2_approx(-q);
     }
+}
+
+// 32 tile values of one row -> 16 packed fp16 pairs of k / s_f^2.
+template <int KIND, bool SCALED>
+__device__ __forceinline__ void eval_chunk(const uint32_t (&r)[32], uint32_t (&pk)[16], float dscale) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        pk[e] = pack_half2(kernel_of<KIND, SCALED>(__uint_as_float(r[2 * e]), dscale),
+                           kernel_of<KIND, SCALED>(__uint_as_float(r[2 * e + 1]), dscale));
 }
 
 struct KParams {
@@ -204,7 +216,7 @@ struct KParams {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(MVM_THREADS, 1)
     tc_mvm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapV, const KParams p) {
     if (p.done && *p.done) return;
@@ -317,11 +329,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mma_commit(y_full);
     } else if (warp >= 4) {
         // ------------------------------------------------ kernel evaluation + epilogue
-        const int wq = warp - 4;
+        // Two warpgroups ping-pong: warpgroup wg owns S buffer wg, i.e. the tiles with
+        // it % 2 == wg, so one group evaluates while the other waits on tensor memory.
+        const int wg = (warp - 4) >> 2;
+        const int wq = warp & 3;  // TMEM lane quarter this warp may access
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         const float dsc = *p.dscale;
+        const bool unit = (dsc == 1.0f);
         bool ok = true;
-        for (int it = 0; it < ntiles; ++it) {
+        for (int it = wg; it < ntiles; it += 2) {
             const int b = it & 1;
             if (!mbar_wait(&s_full[b], (it / 2) & 1, s_err)) {
                 ok = false;
@@ -335,24 +351,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(taddr + ch * 32, r);
                 tmem_ld_wait();
                 uint32_t pk[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float k0 = kernel_of<KIND>(__uint_as_float(r[2 * e]), dsc);
-                    float k1 = kernel_of<KIND>(__uint_as_float(r[2 * e + 1]), dsc);
-                    pk[e] = pack_half2(k0, k1);
-                }
+                if (unit)
+                    eval_chunk<KIND, false>(r, pk, dsc);
+                else
+                    eval_chunk<KIND, true>(r, pk, dsc);
                 tmem_st16(taddr + ch * 16, pk);
             }
             tmem_st_wait();
             tc_fence_before();
             mbar_arrive(&p_full[b]);
         }
-        // epilogue: Y rows from TMEM lanes, one row per thread
+        // epilogue: Y rows from TMEM lanes, one row per thread; the two warpgroups
+        // take alternate 16-column chunks of the right-hand sides
         if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
         if (ok && ntiles > 0) {
             tc_fence_after();
             const int64_t i = row0 + wq * 32 + lane;
-            for (int c0 = 0; c0 < R_pad; c0 += 16) {
+            for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
                 uint32_t r[16];
                 tmem_ld16(tY + lane_off + c0, r);
                 tmem_ld_wait();
@@ -782,9 +797,9 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     dim3 grid((unsigned)row_tiles, (unsigned)nsplit);
     prof_begin(st);
     if (ki == 0)
-        tc_mvm_kernel<GP_RBF><<<grid, NTHREADS, smem, st>>>(mA, mB, mV, kp);
+        tc_mvm_kernel<GP_RBF><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
     else
-        tc_mvm_kernel<GP_MATERN32><<<grid, NTHREADS, smem, st>>>(mA, mB, mV, kp);
+        tc_mvm_kernel<GP_MATERN32><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
     prof_end(st);
     GP_TRY(check_launch("tc_mvm_kernel"));
     if (nsplit > 1) {
@@ -1228,7 +1243,7 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
         attr[ki] = true;
     }
     dim3 grid((unsigned)g.row_tiles, (unsigned)g.nsplit);
-    prof_begin(st);
+    prof_begin(st, 1);
     if (ki == 0)
         tc_grad_kernel<GP_RBF><<<grid, NTHREADS, g.smem, st>>>(mA, mB, mU, mW, mB3, p);
     else
