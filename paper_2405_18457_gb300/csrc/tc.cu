@@ -44,6 +44,7 @@ constexpr int TN = 128;          // columns per tile
 constexpr int MAX_STAGES = 4;
 constexpr int NTHREADS = 256;     // gradient kernel: producer, MMA, 2 idle, 4 evaluation warps
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
+constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -236,10 +237,11 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     uint64_t *a_full = bars;
     uint64_t *full = bars + 1;
     uint64_t *empty = full + MAX_STAGES;
-    uint64_t *s_full = empty + MAX_STAGES;
-    uint64_t *p_full = s_full + 2;
-    uint64_t *sp_free = p_full + 2;
-    uint64_t *y_full = sp_free + 2;
+    uint64_t *s_full = empty + MAX_STAGES;  // GEMM1 of a tile landed in S[b]
+    uint64_t *s_free = s_full + 2;          // evaluation warpgroup has read S[b]
+    uint64_t *p_full = s_free + 2;          // kernel values of the tile are in P[b]
+    uint64_t *p_free = p_full + 2;          // GEMM2 has consumed P[b]
+    uint64_t *y_full = p_free + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -258,8 +260,9 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
+            mbar_init(&s_free[b], 128);
             mbar_init(&p_full[b], 128);
-            mbar_init(&sp_free[b], 1);
+            mbar_init(&p_free[b], 1);
         }
         mbar_init(y_full, 1);
         *s_err = 0;
@@ -274,8 +277,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // Tensor memory: S[0..1] fp32 tiles at columns 0 / 128, P[0..1] packed fp16 kernel
+    // values at 256 / 320, the Y accumulator at 384 (R_pad <= 128 columns).
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tS0 = tmem, tY = tmem + 256;
+    const uint32_t tS0 = tmem, tP0 = tmem + 256, tY = tmem + 384;
 
     if (warp == 0 && lane == 0 && ntiles > 0) {
         // ------------------------------------------------ TMA producer
@@ -298,10 +303,11 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         const uint32_t id2 = idesc_f16(TM, R_pad);
         const int ksteps1 = p.KD / 16;
         bool ok = mbar_wait(a_full, 0, s_err);
+        // GEMM1 of tile it into S[it % 2], once the warpgroup has read S for tile it - 2.
         auto gemm1 = [&](int it) -> bool {
             const int s = it % NS, b = it & 1;
             if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
-            if (it >= 2 && !mbar_wait(&sp_free[b], ((it / 2) - 1) & 1, s_err)) return false;
+            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
             tc_fence_after();
             const uint8_t *sB = sStages + (size_t)s * stage_bytes;
             for (int k = 0; k < ksteps1; ++k) {
@@ -313,18 +319,19 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             return true;
         };
         if (ok) ok = gemm1(0);
+        if (ok && ntiles > 1) ok = gemm1(1);
         for (int it = 0; ok && it < ntiles; ++it) {
             const int s = it % NS, b = it & 1;
-            if (it + 1 < ntiles && !gemm1(it + 1)) break;
+            if (it + 2 < ntiles && !gemm1(it + 2)) break;
             if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
             tc_fence_after();
             const uint8_t *sV = sStages + (size_t)s * stage_bytes + b_bytes;
             for (int k = 0; k < TN / 16; ++k) {
                 const int kv = k >> 2, ko = (k & 3) * 32;
-                mma_ts(tY, tS0 + b * 128 + k * 8, sdesc(sV + kv * v_atom + ko), id2, (it > 0 || k > 0) ? 1u : 0u);
+                mma_ts(tY, tP0 + b * 64 + k * 8, sdesc(sV + kv * v_atom + ko), id2, (it > 0 || k > 0) ? 1u : 0u);
             }
             mma_commit(&empty[s]);
-            mma_commit(&sp_free[b]);
+            mma_commit(&p_free[b]);
         }
         mma_commit(y_full);
     } else if (warp >= 4) {
@@ -344,19 +351,39 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t taddr = tS0 + b * 128 + lane_off;
+            const uint32_t taS = tS0 + b * 128 + lane_off;
+            const uint32_t taP = tP0 + b * 64 + lane_off;
 #pragma unroll 1
-            for (int ch = 0; ch < TN / 32; ++ch) {
-                uint32_t r[32];
-                tmem_ld32(taddr + ch * 32, r);
+            for (int half = 0; half < 2; ++half) {
+                uint32_t r0[32], r1[32];
+                tmem_ld32(taS + half * 64, r0);
+                tmem_ld32(taS + half * 64 + 32, r1);
                 tmem_ld_wait();
+                if (half == 1) {
+                    // S[b] fully read: GEMM1 of tile it + 2 may overwrite it while we compute
+                    tc_fence_before();
+                    mbar_arrive(&s_free[b]);
+                } else if (it >= 2) {
+                    // P[b] must have been consumed by GEMM2 of tile it - 2
+                    if (!mbar_wait(&p_free[b], ((it / 2) - 1) & 1, s_err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
                 uint32_t pk[16];
                 if (unit)
-                    eval_chunk<KIND, false>(r, pk, dsc);
+                    eval_chunk<KIND, false>(r0, pk, dsc);
                 else
-                    eval_chunk<KIND, true>(r, pk, dsc);
-                tmem_st16(taddr + ch * 16, pk);
+                    eval_chunk<KIND, true>(r0, pk, dsc);
+                tmem_st16(taP + half * 32, pk);
+                if (unit)
+                    eval_chunk<KIND, false>(r1, pk, dsc);
+                else
+                    eval_chunk<KIND, true>(r1, pk, dsc);
+                tmem_st16(taP + half * 32 + 16, pk);
             }
+            if (!ok) break;
             tmem_st_wait();
             tc_fence_before();
             mbar_arrive(&p_full[b]);
@@ -705,7 +732,7 @@ int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const floa
 
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
     const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
-    const int R_pad = rpad_for(std::min(R, 256));
+    const int R_pad = rpad_for(std::min(R, kMaxRhsPerPass));
     const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM);
     const int ns = pick_split(row_tiles, cdiv(p2, TN));
     Carver c(nullptr);
@@ -718,11 +745,12 @@ size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
 }
 
 int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
-    if (a.R > 256) {
-        // wide blocks of right-hand sides: 256 at a time
-        for (int c0 = 0; c0 < a.R; c0 += 256) {
+    if (a.R > kMaxRhsPerPass) {
+        // wide blocks of right-hand sides: kMaxRhsPerPass at a time (the Y accumulator's
+        // share of tensor memory)
+        for (int c0 = 0; c0 < a.R; c0 += kMaxRhsPerPass) {
             TcMvmArgs b = a;
-            b.R = std::min(256, a.R - c0);
+            b.R = std::min(kMaxRhsPerPass, a.R - c0);
             b.V = a.V + (int64_t)c0 * a.ldv;
             b.Y = a.Y + (int64_t)c0 * a.ldy;
             b.Vd = a.Vd ? a.Vd + (int64_t)c0 * a.ldvd : nullptr;

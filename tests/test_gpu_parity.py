@@ -65,7 +65,8 @@ def run_mvm(prec_name, prec, kind, th, X1, X2, V, add_noise, dev):
 # --------------------------------------------------------------------------- MVM
 @pytest.mark.parametrize("prec_name,prec,tol", PRECS)
 @pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
-@pytest.mark.parametrize("n,d,R", [(333, 5, 9), (257, 16, 65), (130, 26, 70), (1, 3, 1), (64, 1, 17)])
+@pytest.mark.parametrize("n,d,R", [(333, 5, 9), (257, 16, 65), (130, 26, 70), (1, 3, 1), (64, 1, 17),
+                                   (200, 4, 150)])
 def test_hv_matches_oracle(dev, prec_name, prec, tol, kind, n, d, R):
     rng = np.random.default_rng(n * 100 + d)
     X = rng.uniform(-1, 1, size=(n, d))
