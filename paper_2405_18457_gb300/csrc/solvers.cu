@@ -249,10 +249,12 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     cg_start_kernel<<<1, 32, 0, st>>>(R, P, part, gamma, sd, (long long)max_iters, tol, stop_rule);
     GP_TRY(check_launch("cg start", 3));
 
+    // Iterations are enqueued speculatively in chunks without waiting for the start-up
+    // kernels: once the device-side loop condition latches `done`, the remaining kernels
+    // of a chunk return immediately, so a chunk overshoot costs only empty launches.
     SolverState hs{};
-    GP_TRY(poll_state(sd, &hs, st));
-    int64_t launched = 0, chunk = 2;
-    while (!hs.done && launched < max_iters) {
+    int64_t launched = 0, chunk = 8;
+    while (launched < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - launched);
         for (int64_t it = 0; it < k; ++it) {
             GP_TRY(op.apply(dd, Hd, done, st));
@@ -265,8 +267,9 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             GP_TRY(check_launch("cg iteration", 5));
         }
         launched += k;
-        chunk = std::min<int64_t>(chunk * 2, 16);
+        chunk = std::min<int64_t>(chunk * 2, 32);
         GP_TRY(poll_state(sd, &hs, st));
+        if (hs.done) break;
     }
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
     GP_TRY(check_launch("cg rescale"));

@@ -42,7 +42,7 @@ namespace {
 constexpr int TM = 128;          // output rows per CTA
 constexpr int TN = 128;          // columns per tile
 constexpr int MAX_STAGES = 4;
-constexpr int NTHREADS = 256;     // gradient kernel: producer, MMA, 2 idle, 4 evaluation warps
+constexpr int NTHREADS = 384;     // gradient kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -895,6 +895,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red = reinterpret_cast<double *>(smem_raw);  // reused after the pipeline (reduction scratch)
+    double *xch = reinterpret_cast<double *>(bars + 32);   // 256 doubles: per-row sums of warpgroup 1
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TM;
@@ -989,11 +990,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         mma_commit(y_full);
     } else if (warp >= 4) {
-        const int wq = warp - 4;
+        // two evaluation warpgroups; warpgroup wg owns buffers wg (tiles it % 2 == wg)
+        const int wg = (warp - 4) >> 2;
+        const int wq = warp & 3;
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         const float dsc = *p.dscale;
         bool ok = true;
-        for (int it = 0; it < ntiles; ++it) {
+        for (int it = wg; it < ntiles; it += 2) {
             const int b = it & 1;
             if (!mbar_wait(&s_full[b], (it / 2) & 1, s_err)) {
                 ok = false;
@@ -1042,7 +1045,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             rs_acc += (double)rs;
             s_acc += (double)sk;
         }
-        if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
+        // combine the two warpgroups' per-row sums (named barrier over the 256 evaluation threads)
+        const int row = wq * 32 + lane;
+        if (wg == 1) {
+            xch[row] = rs_acc;
+            xch[128 + row] = s_acc;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (wg == 0) {
+            rs_acc += xch[row];
+            s_acc += xch[128 + row];
+        } else {
+            s_acc = 0.0;
+            ok = false;
+        }
+        if (wg == 0 && ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
         // per-row contributions sum_j W1_ij (a_ik - a_jk)^2
         const int64_t i = row0 + wq * 32 + lane;
         const int d = p.d;
@@ -1085,7 +1102,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const double sscale = (double)p.sf2 * (double)(*p.guw);
     for (int k = 0; k <= p.d; ++k) {
         double v = 0.0;
-        if (warp >= 4) v = (k < p.d) ? (double)gk[k] * gscale : s_acc * sscale;
+        if (warp >= 4 && warp < 8) v = (k < p.d) ? (double)gk[k] * gscale : s_acc * sscale;
         v = warp_sum(v);
         __syncthreads();
         if (lane == 0) red[warp] = v;
@@ -1179,8 +1196,8 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
     g.nsplit = pick_split(g.row_tiles, g.col_tiles);
     const size_t a = (size_t)TM * g.KD * 2 + (size_t)TM * g.KM * 2;
     const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2 + (size_t)g.N3p * 128;
-    g.ns = (int)std::min<size_t>(MAX_STAGES, (kMaxDynSmem - 2048 - a) / st);
-    g.smem = 1024 + a + (size_t)g.ns * st + 256;
+    g.ns = (int)std::min<size_t>(MAX_STAGES, (kMaxDynSmem - 4096 - a) / st);
+    g.smem = 1024 + a + (size_t)g.ns * st + 256 + 2048;  // + barriers, + row-sum exchange
     return g;
 }
 
