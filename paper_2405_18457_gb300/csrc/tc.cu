@@ -888,10 +888,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t *a_full = bars;
     uint64_t *full = bars + 1;
     uint64_t *empty = full + MAX_STAGES;
-    uint64_t *s_full = empty + MAX_STAGES;
-    uint64_t *p_full = s_full + 2;
-    uint64_t *sp_free = p_full + 2;
-    uint64_t *y_full = sp_free + 2;
+    uint64_t *s_full = empty + MAX_STAGES;  // GEMM1 + GEMM-M of a tile landed in S[b], M[b]
+    uint64_t *s_free = s_full + 2;          // evaluation warpgroup has read S[b] and M[b]
+    uint64_t *p_full = s_free + 2;          // W1 of the tile is in P[b]
+    uint64_t *p_free = p_full + 2;          // GEMM3 has consumed P[b]
+    uint64_t *y_full = p_free + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red = reinterpret_cast<double *>(smem_raw);  // reused after the pipeline (reduction scratch)
@@ -912,8 +913,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
+            mbar_init(&s_free[b], 128);
             mbar_init(&p_full[b], 128);
-            mbar_init(&sp_free[b], 1);
+            mbar_init(&p_free[b], 1);
         }
         mbar_init(y_full, 1);
         *s_err = 0;
@@ -928,8 +930,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // Tensor memory: S[0..1] at columns 0 / 64, M[0..1] at 128 / 192, P[0..1] (packed fp16
+    // W1) at 256 / 288, the D3 accumulator at 320 (N3p <= 192 columns).
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tS = tmem, tM = tmem + 128, tD = tmem + 256;
+    const uint32_t tS = tmem, tM = tmem + 128, tP = tmem + 256, tD = tmem + 320;
 
     double g_acc[1];  // silence unused warnings in non-epilogue warps
     (void)g_acc;
@@ -959,7 +963,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         auto gemm1 = [&](int it) -> bool {
             const int s = it % NS, b = it & 1;
             if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
-            if (it >= 2 && !mbar_wait(&sp_free[b], ((it / 2) - 1) & 1, s_err)) return false;
+            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
             tc_fence_after();
             const uint8_t *sB = sStages + (size_t)s * stage_bytes;
             const uint8_t *sW = sB + b_bytes;
@@ -977,16 +981,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             return true;
         };
         if (ok) ok = gemm1(0);
+        if (ok && ntiles > 1) ok = gemm1(1);
         for (int it = 0; ok && it < ntiles; ++it) {
             const int s = it % NS, b = it & 1;
-            if (it + 1 < ntiles && !gemm1(it + 1)) break;
+            if (it + 2 < ntiles && !gemm1(it + 2)) break;
             if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
             tc_fence_after();
             const uint8_t *sB3 = sStages + (size_t)s * stage_bytes + b_bytes + w_bytes;
             for (int k = 0; k < GTN / 16; ++k)
-                mma_ts(tD, tS + b * GTN + k * 8, sdesc(sB3 + k * 32), id3, (it > 0 || k > 0) ? 1u : 0u);
+                mma_ts(tD, tP + b * 32 + k * 8, sdesc(sB3 + k * 32), id3, (it > 0 || k > 0) ? 1u : 0u);
             mma_commit(&empty[s]);
-            mma_commit(&sp_free[b]);
+            mma_commit(&p_free[b]);
         }
         mma_commit(y_full);
     } else if (warp >= 4) {
@@ -1004,6 +1009,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t taS = tS + b * GTN + lane_off, taM = tM + b * GTN + lane_off;
+            const uint32_t taP = tP + b * (GTN / 2) + lane_off;
             float rs = 0.0f, sk = 0.0f;
 #pragma unroll 1
             for (int ch = 0; ch < GTN / 32; ++ch) {
@@ -1011,6 +1017,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(taS + ch * 32, rS);
                 tmem_ld32(taM + ch * 32, rM);
                 tmem_ld_wait();
+                if (ch == GTN / 32 - 1) {
+                    // S[b] and M[b] fully read: the next GEMMs into them may start
+                    tc_fence_before();
+                    mbar_arrive(&s_free[b]);
+                }
+                if (ch == 0 && it >= 2) {
+                    // P[b] must have been consumed by GEMM3 of tile it - 2
+                    if (!mbar_wait(&p_free[b], ((it / 2) - 1) & 1, s_err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
                 uint32_t pk[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
@@ -1037,8 +1056,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     float2 fw = __half22float2(hw);
                     rs += fw.x + fw.y;
                 }
-                tmem_st16(taS + ch * 16, pk);
+                tmem_st16(taP + ch * 16, pk);
             }
+            if (!ok) break;
             tmem_st_wait();
             tc_fence_before();
             mbar_arrive(&p_full[b]);
@@ -1203,7 +1223,12 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
 
 }  // namespace
 
+// The tensor-core estimator covers d <= 48 (D3 accumulator of 4d columns in tensor
+// memory) and s + 1 <= 256; wider problems use the CUDA-core FP32 reduction.
+static bool tc_grad_fits(int d, int R) { return d <= 48 && R <= 256; }
+
 size_t tc_grad_workspace(int64_t n, int d, int R) {
+    if (!tc_grad_fits(d, R)) return grad_simt_workspace<float>(n, d, R);
     GradPlanTc g = plan_tc_grad(n, d, R);
     Carver c(nullptr);
     c.take<char>(tc_points_bytes(n, d));
@@ -1220,10 +1245,7 @@ size_t tc_grad_workspace(int64_t n, int d, int R) {
 
 int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int d = a.kp.d;
-    if (d > 64 || a.R > 256) {
-        set_error("tensor-core gradient supports d <= 64 and s + 1 <= 256 (got d=%d, R=%d)", d, a.R);
-        return GP_ERR_UNSUPPORTED;
-    }
+    if (!tc_grad_fits(d, a.R)) return grad_simt<float>(a, ws, ws_bytes, st);
     GradPlanTc g = plan_tc_grad(a.n, d, a.R);
     if (g.ns < 2) {
         set_error("tensor-core gradient tile does not fit shared memory");
