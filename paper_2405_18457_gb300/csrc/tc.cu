@@ -41,7 +41,8 @@ namespace {
 
 constexpr int TM = 128;          // output rows per CTA
 constexpr int TN = 128;          // columns per tile
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_STAGES = 4;  // gradient kernel ring depth
+constexpr int MAX_RING = 8;    // product kernel: slots per ring (barrier arrays are sized for this)
 constexpr int NTHREADS = 384;     // gradient kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
@@ -200,7 +201,8 @@ __device__ __forceinline__ void eval_chunk(const uint32_t (&r)[32], uint32_t (&p
 }
 
 struct KParams {
-    int R, R_pad, KD, nstages;
+    int R, R_pad, KD;
+    int npb, nv;         // depths of the PB-tile and V-tile shared-memory rings
     int64_t n1;          // output rows
     int64_t col_tiles;   // 128-wide column tiles over the (padded) column set
     int nsplit;
@@ -225,19 +227,24 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int katoms = p.KD / 64;
     const int R_pad = p.R_pad;
-    const int NS = p.nstages;
+    const int NPB = p.npb, NV = p.nv;
     const uint32_t a_bytes = (uint32_t)TM * p.KD * 2;
     const uint32_t b_bytes = (uint32_t)TN * p.KD * 2;
     const uint32_t v_atom = (uint32_t)R_pad * 128;
     const uint32_t v_bytes = 2 * v_atom;
-    const uint32_t stage_bytes = b_bytes + v_bytes;
+    // Two independent rings: PB tiles are needed by GEMM1 about two tiles before the
+    // V tiles are needed by GEMM2, and each ring slot is released as soon as its own
+    // GEMM has read it, so the loads run several tiles ahead of the tensor cores.
     uint8_t *sA = smem;
-    uint8_t *sStages = smem + a_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sStages + (size_t)NS * stage_bytes);
+    uint8_t *sPB = smem + a_bytes;
+    uint8_t *sVr = sPB + (size_t)NPB * b_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sVr + (size_t)NV * v_bytes);
     uint64_t *a_full = bars;
-    uint64_t *full = bars + 1;
-    uint64_t *empty = full + MAX_STAGES;
-    uint64_t *s_full = empty + MAX_STAGES;  // GEMM1 of a tile landed in S[b]
+    uint64_t *pb_full = bars + 1;
+    uint64_t *pb_empty = pb_full + MAX_RING;
+    uint64_t *v_full = pb_empty + MAX_RING;
+    uint64_t *v_empty = v_full + MAX_RING;
+    uint64_t *s_full = v_empty + MAX_RING;  // GEMM1 of a tile landed in S[b]
     uint64_t *s_free = s_full + 2;          // evaluation warpgroup has read S[b]
     uint64_t *p_full = s_free + 2;          // kernel values of the tile are in P[b]
     uint64_t *p_free = p_full + 2;          // GEMM2 has consumed P[b]
@@ -254,9 +261,11 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
-        for (int s = 0; s < MAX_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < MAX_RING; ++s) {
+            mbar_init(&pb_full[s], 1);
+            mbar_init(&pb_empty[s], 1);
+            mbar_init(&v_full[s], 1);
+            mbar_init(&v_empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
@@ -283,19 +292,27 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     const uint32_t tS0 = tmem, tP0 = tmem + 256, tY = tmem + 384;
 
     if (warp == 0 && lane == 0 && ntiles > 0) {
-        // ------------------------------------------------ TMA producer
+        // ------------------------------------------------ TMA producer: row operand + PB ring
         mbar_expect_tx(a_full, a_bytes);
         for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
         for (int it = 0; it < ntiles; ++it) {
-            const int s = it % NS, use = it / NS;
-            if (it >= NS && !mbar_wait(&empty[s], (use - 1) & 1, s_err)) break;
+            const int s = it % NPB;
+            if (it >= NPB && !mbar_wait(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
             const int j0 = (int)((t0 + it) * TN);
-            uint8_t *sB = sStages + (size_t)s * stage_bytes;
-            uint8_t *sV = sB + b_bytes;
-            mbar_expect_tx(&full[s], stage_bytes);
-            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (TN * 128), &mapB, &full[s], ka * 64, j0);
-            tma_load_2d(sV, &mapV, &full[s], j0, 0);
-            tma_load_2d(sV + v_atom, &mapV, &full[s], j0 + 64, 0);
+            uint8_t *sB = sPB + (size_t)s * b_bytes;
+            mbar_expect_tx(&pb_full[s], b_bytes);
+            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
+        }
+    } else if (warp == 2 && lane == 0 && ntiles > 0) {
+        // ------------------------------------------------ TMA producer: V ring
+        for (int it = 0; it < ntiles; ++it) {
+            const int s = it % NV;
+            if (it >= NV && !mbar_wait(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
+            const int j0 = (int)((t0 + it) * TN);
+            uint8_t *sV = sVr + (size_t)s * v_bytes;
+            mbar_expect_tx(&v_full[s], v_bytes);
+            tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
+            tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
         }
     } else if (warp == 1 && lane == 0 && ntiles > 0) {
         // ------------------------------------------------ MMA issuer
@@ -305,32 +322,34 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         bool ok = mbar_wait(a_full, 0, s_err);
         // GEMM1 of tile it into S[it % 2], once the warpgroup has read S for tile it - 2.
         auto gemm1 = [&](int it) -> bool {
-            const int s = it % NS, b = it & 1;
-            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
+            const int s = it % NPB, b = it & 1;
+            if (!mbar_wait(&pb_full[s], (it / NPB) & 1, s_err)) return false;
             if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
             tc_fence_after();
-            const uint8_t *sB = sStages + (size_t)s * stage_bytes;
+            const uint8_t *sB = sPB + (size_t)s * b_bytes;
             for (int k = 0; k < ksteps1; ++k) {
                 const int ka = k >> 2, ko = (k & 3) * 32;
                 mma_ss(tS0 + b * 128, sdesc(sA + ka * (TM * 128) + ko), sdesc(sB + ka * (TN * 128) + ko), id1,
                        k > 0 ? 1u : 0u);
             }
+            mma_commit(&pb_empty[s]);
             mma_commit(&s_full[b]);
             return true;
         };
         if (ok) ok = gemm1(0);
         if (ok && ntiles > 1) ok = gemm1(1);
         for (int it = 0; ok && it < ntiles; ++it) {
-            const int s = it % NS, b = it & 1;
+            const int s = it % NV, b = it & 1;
             if (it + 2 < ntiles && !gemm1(it + 2)) break;
+            if (!mbar_wait(&v_full[s], (it / NV) & 1, s_err)) break;
             if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
             tc_fence_after();
-            const uint8_t *sV = sStages + (size_t)s * stage_bytes + b_bytes;
+            const uint8_t *sV = sVr + (size_t)s * v_bytes;
             for (int k = 0; k < TN / 16; ++k) {
                 const int kv = k >> 2, ko = (k & 3) * 32;
                 mma_ts(tY, tP0 + b * 64 + k * 8, sdesc(sV + kv * v_atom + ko), id2, (it > 0 || k > 0) ? 1u : 0u);
             }
-            mma_commit(&empty[s]);
+            mma_commit(&v_empty[s]);
             mma_commit(&p_free[b]);
         }
         mma_commit(y_full);
@@ -643,14 +662,20 @@ int pick_split(int64_t row_tiles, int64_t col_tiles) {
     return best;
 }
 
-int stages_for(int KD, int R_pad) {
-    size_t a = (size_t)TM * KD * 2, st = (size_t)TN * KD * 2 + 2 * (size_t)R_pad * 128;
-    int ns = (int)std::min<size_t>(MAX_STAGES, (kMaxDynSmem - 2048 - a) / st);
-    return ns;
+// Ring depths of the product kernel: up to 4 V slots (GEMM2 runs about two tiles behind
+// GEMM1), the rest of shared memory for PB slots (at most MAX_RING).
+void rings_for(int KD, int R_pad, int *npb, int *nv) {
+    const size_t a = (size_t)TM * KD * 2, b = (size_t)TN * KD * 2, v = 2 * (size_t)R_pad * 128;
+    const size_t budget = kMaxDynSmem - 4096 - a;
+    int nvv = 4;
+    while (nvv > 2 && nvv * v + 3 * b > budget) --nvv;
+    size_t left = budget > nvv * v ? budget - nvv * v : 0;
+    *nv = nvv;
+    *npb = (int)std::min<size_t>(MAX_RING, left / b);
 }
 
-size_t smem_for(int KD, int R_pad, int ns) {
-    return 1024 + (size_t)TM * KD * 2 + (size_t)ns * ((size_t)TN * KD * 2 + 2 * (size_t)R_pad * 128) + 256;
+size_t smem_for(int KD, int R_pad, int npb, int nv) {
+    return 1024 + (size_t)TM * KD * 2 + (size_t)npb * TN * KD * 2 + (size_t)nv * 2 * R_pad * 128 + 512;
 }
 
 }  // namespace
@@ -782,8 +807,9 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     GP_TRY(make_map(&mA, a.rows.PA, KD, a.rows.n_pad, 64, TM));
     GP_TRY(make_map(&mB, a.cols.PB, KD, a.cols.n_pad, 64, TN));
     GP_TRY(make_map(&mV, V16, p2, R_pad, 64, R_pad));
-    const int ns = stages_for(KD, R_pad);
-    if (ns < 2) {
+    int npb = 0, nv = 0;
+    rings_for(KD, R_pad, &npb, &nv);
+    if (npb < 2 || nv < 2) {
         set_error("tensor-core tile does not fit shared memory (d=%d, R=%d)", (KD - 4) / 3, a.R);
         return GP_ERR_UNSUPPORTED;
     }
@@ -791,7 +817,8 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.R = a.R;
     kp.R_pad = R_pad;
     kp.KD = KD;
-    kp.nstages = ns;
+    kp.npb = npb;
+    kp.nv = nv;
     kp.n1 = n1;
     kp.col_tiles = col_tiles;
     kp.nsplit = nsplit;
@@ -810,7 +837,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.partial = partial;
     kp.done = a.done;
     kp.err = err;
-    const size_t smem = smem_for(KD, R_pad, ns);
+    const size_t smem = smem_for(KD, R_pad, npb, nv);
     static bool attr[2] = {false, false};
     const int ki = a.kind == GP_RBF ? 0 : 1;
     if (!attr[ki]) {
