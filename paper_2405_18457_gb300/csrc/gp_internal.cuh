@@ -27,9 +27,9 @@ void clear_error();
         }                                                                              \
     } while (0)
 
-#define GP_TRY(call)                  \
+#define GP_TRY(...)                   \
     do {                              \
-        int gp_s_ = (call);           \
+        int gp_s_ = (__VA_ARGS__);    \
         if (gp_s_ != GP_OK)           \
             return gp_s_;             \
     } while (0)

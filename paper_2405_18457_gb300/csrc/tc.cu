@@ -218,7 +218,7 @@ struct KParams {
     int *err;
 };
 
-template <int KIND>
+template <int KIND, int KAT>  // KAT: 64-wide atoms of the distance contraction (KD / 64)
 __global__ void __launch_bounds__(MVM_THREADS, 1)
     tc_mvm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapV, const KParams p) {
@@ -316,9 +316,12 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0 && ntiles > 0) {
         // ------------------------------------------------ MMA issuer
+        // One thread issues every MMA, so its instruction stream is on the critical path:
+        // descriptors are built once and advanced by constant offsets (16-byte units).
         const uint32_t id1 = idesc_f16(TM, TN);
         const uint32_t id2 = idesc_f16(TM, R_pad);
-        const int ksteps1 = p.KD / 16;
+        const uint64_t dA = sdesc(sA), dPB = sdesc(sPB), dV = sdesc(sVr);
+        const uint32_t b_units = b_bytes >> 4, v_units = v_bytes >> 4, va_units = v_atom >> 4;
         bool ok = mbar_wait(a_full, 0, s_err);
         // GEMM1 of tile it into S[it % 2], once the warpgroup has read S for tile it - 2.
         auto gemm1 = [&](int it) -> bool {
@@ -326,11 +329,13 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             if (!mbar_wait(&pb_full[s], (it / NPB) & 1, s_err)) return false;
             if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
             tc_fence_after();
-            const uint8_t *sB = sPB + (size_t)s * b_bytes;
-            for (int k = 0; k < ksteps1; ++k) {
-                const int ka = k >> 2, ko = (k & 3) * 32;
-                mma_ss(tS0 + b * 128, sdesc(sA + ka * (TM * 128) + ko), sdesc(sB + ka * (TN * 128) + ko), id1,
-                       k > 0 ? 1u : 0u);
+            const uint64_t db = dPB + (uint64_t)s * b_units;
+            const uint32_t dS = tS0 + b * 128;
+#pragma unroll
+            for (int k = 0; k < 4 * KAT; ++k) {
+                constexpr uint32_t a_atom = (TM * 128) >> 4, b_atom = (TN * 128) >> 4;
+                const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
             }
             mma_commit(&pb_empty[s]);
             mma_commit(&s_full[b]);
@@ -344,10 +349,12 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             if (!mbar_wait(&v_full[s], (it / NV) & 1, s_err)) break;
             if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
             tc_fence_after();
-            const uint8_t *sV = sVr + (size_t)s * v_bytes;
+            const uint64_t dv = dV + (uint64_t)s * v_units;
+            const uint32_t aP = tP0 + b * 64;
+#pragma unroll
             for (int k = 0; k < TN / 16; ++k) {
-                const int kv = k >> 2, ko = (k & 3) * 32;
-                mma_ts(tY, tP0 + b * 64 + k * 8, sdesc(sV + kv * v_atom + ko), id2, (it > 0 || k > 0) ? 1u : 0u);
+                const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
             }
             mma_commit(&v_empty[s]);
             mma_commit(&p_free[b]);
@@ -678,6 +685,19 @@ size_t smem_for(int KD, int R_pad, int npb, int nv) {
     return 1024 + (size_t)TM * KD * 2 + (size_t)npb * TN * KD * 2 + (size_t)nv * 2 * R_pad * 128 + 512;
 }
 
+template <int KIND, int KAT>
+int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mV,
+                      const KParams &kp, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<KIND, KAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem));
+        attr = true;
+    }
+    tc_mvm_kernel<KIND, KAT><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+    return GP_OK;
+}
+
 }  // namespace
 
 bool tc_available() {
@@ -838,23 +858,22 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.done = a.done;
     kp.err = err;
     const size_t smem = smem_for(KD, R_pad, npb, nv);
-    static bool attr[2] = {false, false};
-    const int ki = a.kind == GP_RBF ? 0 : 1;
-    if (!attr[ki]) {
-        if (ki == 0)
-            GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxDynSmem));
-        else
-            GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr[ki] = true;
-    }
     dim3 grid((unsigned)row_tiles, (unsigned)nsplit);
+    const int kat = KD / 64;
+    if (kat > 3) {
+        set_error("tensor-core product supports d <= 62 (got KD=%d)", KD);
+        return GP_ERR_UNSUPPORTED;
+    }
     prof_begin(st);
-    if (ki == 0)
-        tc_mvm_kernel<GP_RBF><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
-    else
-        tc_mvm_kernel<GP_MATERN32><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+    if (a.kind == GP_RBF) {
+        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_RBF, 1>(grid, smem, mA, mB, mV, kp, st));
+        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_RBF, 2>(grid, smem, mA, mB, mV, kp, st));
+        else GP_TRY(launch_mvm_kernel<GP_RBF, 3>(grid, smem, mA, mB, mV, kp, st));
+    } else {
+        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_MATERN32, 1>(grid, smem, mA, mB, mV, kp, st));
+        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_MATERN32, 2>(grid, smem, mA, mB, mV, kp, st));
+        else GP_TRY(launch_mvm_kernel<GP_MATERN32, 3>(grid, smem, mA, mB, mV, kp, st));
+    }
     prof_end(st);
     GP_TRY(check_launch("tc_mvm_kernel"));
     if (nsplit > 1) {
@@ -895,7 +914,7 @@ struct GParams {
     int *err;
 };
 
-template <int KIND>
+template <int KIND, int KAT>  // KAT: 64-wide atoms of the distance contraction (KD / 64)
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_grad_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapW,
@@ -986,23 +1005,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1 && lane == 0 && ntiles > 0) {
         const uint32_t id1 = idesc_f16(TM, GTN);
         const uint32_t id3 = idesc_f16(TM, p.N3p);
+        // descriptors built once, advanced in 16-byte units (single-thread issue path)
+        const uint64_t dA = sdesc(sA), dU = sdesc(sU), dSt = sdesc(sStages);
+        const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4, w_units = w_bytes >> 4;
+        constexpr uint32_t a_atom = (TM * 128) >> 4, g_atom = (GTN * 128) >> 4;
         bool ok = mbar_wait(a_full, 0, s_err);
         auto gemm1 = [&](int it) -> bool {
             const int s = it % NS, b = it & 1;
             if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
             if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
             tc_fence_after();
-            const uint8_t *sB = sStages + (size_t)s * stage_bytes;
-            const uint8_t *sW = sB + b_bytes;
-            for (int k = 0; k < p.KD / 16; ++k) {
-                const int ka = k >> 2, ko = (k & 3) * 32;
-                mma_ss(tS + b * GTN, sdesc(sA + ka * (TM * 128) + ko), sdesc(sB + ka * (GTN * 128) + ko), id1,
-                       k > 0 ? 1u : 0u);
+            const uint64_t dB = dSt + (uint64_t)s * st_units;
+            const uint64_t dW = dB + b_units;
+#pragma unroll
+            for (int k = 0; k < 4 * KAT; ++k) {
+                const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                mma_ss(tS + b * GTN, dA + ka * a_atom + ko, dB + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
             }
-            for (int k = 0; k < p.KM / 16; ++k) {
-                const int ka = k >> 2, ko = (k & 3) * 32;
-                mma_ss(tM + b * GTN, sdesc(sU + ka * (TM * 128) + ko), sdesc(sW + ka * (GTN * 128) + ko), id1,
-                       k > 0 ? 1u : 0u);
+            const int km = p.KM / 16;
+            for (int k = 0; k < km; ++k) {
+                const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                mma_ss(tM + b * GTN, dU + ka * a_atom + ko, dW + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
             }
             mma_commit(&s_full[b]);
             return true;
@@ -1014,9 +1037,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (it + 2 < ntiles && !gemm1(it + 2)) break;
             if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
             tc_fence_after();
-            const uint8_t *sB3 = sStages + (size_t)s * stage_bytes + b_bytes + w_bytes;
+            const uint64_t dB3 = dSt + (uint64_t)s * st_units + b_units + w_units;
+#pragma unroll
             for (int k = 0; k < GTN / 16; ++k)
-                mma_ts(tD, tP + b * 32 + k * 8, sdesc(sB3 + k * 32), id3, (it > 0 || k > 0) ? 1u : 0u);
+                mma_ts(tD, tP + b * 32 + k * 8, dB3 + (uint32_t)k * 2, id3, (it > 0 || k > 0) ? 1u : 0u);
             mma_commit(&empty[s]);
             mma_commit(&p_free[b]);
         }
@@ -1232,6 +1256,19 @@ struct GradPlanTc {
     size_t smem;
 };
 
+template <int KIND, int KAT>
+int launch_grad_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mU,
+                       const CUtensorMap &mW, const CUtensorMap &mB3, const GParams &p, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        GP_TRY_CUDA(cudaFuncSetAttribute(tc_grad_kernel<KIND, KAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem));
+        attr = true;
+    }
+    tc_grad_kernel<KIND, KAT><<<grid, NTHREADS, smem, st>>>(mA, mB, mU, mW, mB3, p);
+    return GP_OK;
+}
+
 GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
     GradPlanTc g;
     g.KD = kd_for(d);
@@ -1325,23 +1362,18 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     p.sf2 = a.kp.sf2;
     p.partial = partial;
     p.err = err;
-    static bool attr[2] = {false, false};
-    const int ki = a.kp.kind == GP_RBF ? 0 : 1;
-    if (!attr[ki]) {
-        if (ki == 0)
-            GP_TRY_CUDA(cudaFuncSetAttribute(tc_grad_kernel<GP_RBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxDynSmem));
-        else
-            GP_TRY_CUDA(cudaFuncSetAttribute(tc_grad_kernel<GP_MATERN32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr[ki] = true;
-    }
     dim3 grid((unsigned)g.row_tiles, (unsigned)g.nsplit);
+    const int kat = g.KD / 64;  // <= 3 since d <= 48
     prof_begin(st, 1);
-    if (ki == 0)
-        tc_grad_kernel<GP_RBF><<<grid, NTHREADS, g.smem, st>>>(mA, mB, mU, mW, mB3, p);
-    else
-        tc_grad_kernel<GP_MATERN32><<<grid, NTHREADS, g.smem, st>>>(mA, mB, mU, mW, mB3, p);
+    if (a.kp.kind == GP_RBF) {
+        if (kat == 1) GP_TRY(launch_grad_kernel<GP_RBF, 1>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
+        else if (kat == 2) GP_TRY(launch_grad_kernel<GP_RBF, 2>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
+        else GP_TRY(launch_grad_kernel<GP_RBF, 3>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
+    } else {
+        if (kat == 1) GP_TRY(launch_grad_kernel<GP_MATERN32, 1>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
+        else if (kat == 2) GP_TRY(launch_grad_kernel<GP_MATERN32, 2>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
+        else GP_TRY(launch_grad_kernel<GP_MATERN32, 3>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
+    }
     prof_end(st);
     GP_TRY(check_launch("tc_grad_kernel"));
     return grad_tail<float>(a, nblocks, partial, dpart, st);
