@@ -70,6 +70,9 @@ def _load():
                 "gpo_mll": (_d, [_i, _i, _pd, _pd, _i64, _pd]),
                 "gpo_mll_grad_exact": (_i, [_i, _i, _pd, _pd, _i64, _pd, _pd]),
                 "gpo_grad_bilinear": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _pd, _i, _pd]),
+                "gpo_bilinear_value": (_d, [_i, _i, _pd, _pd, _i64, _pd, _pd, _pd, _i]),
+                "gpo_dkernel_dx": (None, [_i, _i, _pd, _pd, _pd, _pd]),
+                "gpo_grad_bilinear_X": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _pd, _i, _pd]),
                 "gpo_grad_standard": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _i, _pd]),
                 "gpo_grad_pathwise": (None, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd]),
                 "gpo_solve_cg": (_i, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd, _i64, _d, _i,
@@ -222,6 +225,38 @@ def grad_bilinear(kind, theta, X, U, W, lam):
     _load().gpo_grad_bilinear(kind, d, _p(theta), _p(X), X.shape[0], _p(U), _p(W), _p(lam),
                               U.shape[0], _p(g))
     return g
+
+
+def bilinear_value(kind, theta, X, U, W, lam):
+    """sum_c lam_c U[c]^T H W[c] (Sec. 2 H = K + sigma^2 I)."""
+    X, theta, d = _dims(X, theta)
+    U = _a(U)
+    W = _a(W)
+    lam = _a(lam)
+    return float(_load().gpo_bilinear_value(kind, d, _p(theta), _p(X), X.shape[0], _p(U), _p(W), _p(lam),
+                                            U.shape[0]))
+
+
+def dkernel_dx(kind, theta, x, xp):
+    """Gradient of k(x, x') with respect to x."""
+    theta = _a(theta)
+    x = _a(x)
+    xp = _a(xp)
+    g = np.empty(x.shape[0])
+    _load().gpo_dkernel_dx(kind, x.shape[0], _p(theta), _p(x), _p(xp), _p(g))
+    return g
+
+
+def grad_bilinear_X(kind, theta, X, U, W, lam):
+    """d/dX of sum_c lam_c U[c]^T H(theta, X) W[c], n x d."""
+    X, theta, d = _dims(X, theta)
+    U = _a(U)
+    W = _a(W)
+    lam = _a(lam)
+    dX = np.empty_like(X)
+    _load().gpo_grad_bilinear_X(kind, d, _p(theta), _p(X), X.shape[0], _p(U), _p(W), _p(lam),
+                                U.shape[0], _p(dX))
+    return dX
 
 
 def grad_standard(kind, theta, X, Vsol, Z):

@@ -339,6 +339,86 @@ void gpo_grad_bilinear(int kind, int d, const double *theta, const double *X, in
     }
 }
 
+/*
+ * Value of the same bilinear form, f = sum_c lambda_c U[c]^T H W[c] with
+ * H = K + sigma^2 I (Sec. 2), matrix-free.
+ */
+double gpo_bilinear_value(int kind, int d, const double *theta, const double *X, int64_t n,
+                          const double *U, const double *W, const double *lambda, int R)
+{
+    double s2 = theta[d + 1] * theta[d + 1];
+    double total = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : total)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double h = gpo_kernel(kind, d, theta, X + i * d, X + j * d) + (i == j ? s2 : 0.0);
+            double m = 0.0;
+            for (int c = 0; c < R; ++c)
+                m += lambda[c] * U[(int64_t)c * n + i] * W[(int64_t)c * n + j];
+            total += m * h;
+        }
+    }
+    return total;
+}
+
+/*
+ * Gradient of k(x, x') with respect to its first argument, g (d values).
+ * By the chain rule through r (r^2 = sum_p (x_p - x'_p)^2 / l_p^2):
+ *   RBF:      dk/dx_p = -k (x_p - x'_p) / l_p^2
+ *   Matern32: dk/dr = -3 s_f^2 r exp(-sqrt3 r), dr/dx_p = (x_p - x'_p) / (r l_p^2)
+ *             => dk/dx_p = -3 s_f^2 exp(-sqrt3 r) (x_p - x'_p) / l_p^2
+ * (finite at r = 0, where it is 0).
+ */
+void gpo_dkernel_dx(int kind, int d, const double *theta, const double *x, const double *xp, double *g)
+{
+    double sf = theta[d];
+    double r2 = sqdist(d, theta, x, xp);
+    double rad;
+    if (kind == GPO_RBF)
+        rad = sf * sf * exp(-0.5 * r2);
+    else
+        rad = 3.0 * sf * sf * exp(-sqrt(3.0) * sqrt(r2));
+    for (int p = 0; p < d; ++p)
+        g[p] = -rad * (x[p] - xp[p]) / (theta[p] * theta[p]);
+}
+
+/*
+ * Gradient of f(X) = sum_c lambda_c U[c]^T H(theta, X) W[c] with respect to the
+ * points, dX (n x d).  With M_ab = sum_c lambda_c U[c][a] W[c][b],
+ *   df/dx_a = sum_b M_ab d k(x_a, x_b)/d x_a + sum_b M_ba d k(x_b, x_a)/d x_a,
+ * and for a stationary kernel d k(x_b, x_a)/d x_a = -d k(x_b, x_a)/d x_b
+ * (k depends on x_b - x_a only).  sigma^2 I does not depend on X.
+ */
+void gpo_grad_bilinear_X(int kind, int d, const double *theta, const double *X, int64_t n,
+                         const double *U, const double *W, const double *lambda, int R, double *dX)
+{
+#pragma omp parallel
+    {
+        double *g = (double *)malloc(sizeof(double) * (size_t)d);
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t a = 0; a < n; ++a) {
+            for (int p = 0; p < d; ++p)
+                dX[a * d + p] = 0.0;
+            for (int64_t b = 0; b < n; ++b) {
+                double mab = 0.0, mba = 0.0;
+                for (int c = 0; c < R; ++c) {
+                    mab += lambda[c] * U[(int64_t)c * n + a] * W[(int64_t)c * n + b];
+                    mba += lambda[c] * U[(int64_t)c * n + b] * W[(int64_t)c * n + a];
+                }
+                /* first argument: k(x_a, x_b) */
+                gpo_dkernel_dx(kind, d, theta, X + a * d, X + b * d, g);
+                for (int p = 0; p < d; ++p)
+                    dX[a * d + p] += mab * g[p];
+                /* second argument: k(x_b, x_a) */
+                gpo_dkernel_dx(kind, d, theta, X + b * d, X + a * d, g);
+                for (int p = 0; p < d; ++p)
+                    dX[a * d + p] -= mba * g[p];
+            }
+        }
+        free(g);
+    }
+}
+
 void gpo_grad_standard(int kind, int d, const double *theta, const double *X, int64_t n,
                        const double *Vsol, const double *Z, int s, double *grad)
 {
