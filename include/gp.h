@@ -252,6 +252,38 @@ int gp_mll_grad_pathwise_f64(int kind, const double *theta, int d, const double 
                              void *ws, size_t ws_bytes, cudaStream_t stream);
 size_t gp_mll_grad_f64_workspace(int64_t n, int d, int s);
 
+/* Reverse-mode derivatives of the bilinear form
+ *   f(theta, X, U, W) = sum_c lam_c u_c^T H(theta, X) w_c,
+ *   lam_0 = lam0, lam_c = lam_rest for c >= 1, H = K + sigma^2 I (Sec. 2).
+ * Its theta-gradient is the estimator reduction of Eq. mll_grad (standard:
+ * U = [v_y, v_1..v_s], W = [v_y, z_1..z_s]; pathwise: U = W = [v_y, zhat_1..]
+ * with lam0 = 1/2, lam_rest = -1/(2s)), and with lam0 = lam_rest = 1 and
+ * U = G (an upstream gradient), W = V it is the backward pass of Y = H V with
+ * respect to theta and X (the V-gradient is H G, i.e. gp_kernel_mvm).
+ *   U, W : R vectors of length n (device, strides ldu, ldw >= n).  U == W with
+ *          ldu == ldw is recognised as the symmetric form.
+ *   value  : DEVICE double, f itself, or NULL.
+ *   dtheta : DEVICE array of d+2 doubles, df/dtheta in theta's order, or NULL.
+ *   dX     : DEVICE n x d row-major (same layout as X), df/dX, or NULL.
+ *            dk(x, x')/dx = -psi(r) (x - x') / l^2 with psi = k (RBF) or
+ *            3 s_f^2 exp(-sqrt3 r) (Matern-3/2); kernel tiles are recomputed.
+ * prec applies to value/dtheta as in gp_mll_grad_*; dX always uses CUDA-core
+ * tiles in the element type (FP32 here, FP64 in the _f64 form) with FP64
+ * accumulation across tiles.  NULL outputs are skipped; all NULL is a no-op.
+ * Errors: GP_ERR_INVALID_ARG (sizes, pointers, theta, non-finite lam),
+ * GP_ERR_UNSUPPORTED when d and R exceed the point-gradient tile (shared
+ * memory), GP_ERR_WORKSPACE. */
+int gp_bilinear_grad(int kind, const double *theta, int d, const float *X, int64_t n,
+                     const float *U, int64_t ldu, const float *W, int64_t ldw, int R,
+                     double lam0, double lam_rest, double *value, double *dtheta, float *dX,
+                     int prec, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_bilinear_grad_workspace(int64_t n, int d, int R, int prec);
+int gp_bilinear_grad_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                         const double *U, int64_t ldu, const double *W, int64_t ldw, int R,
+                         double lam0, double lam_rest, double *value, double *dtheta, double *dX,
+                         void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_bilinear_grad_f64_workspace(int64_t n, int d, int R);
+
 /* Pathwise estimator that allocates nothing and takes no workspace (the paper has
  * no counterpart: this is a deployment variant of gp_mll_grad_pathwise).
  * For callers that cannot allocate device memory where they call it: code that

@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     GPError,
     SolveInfo,
     gp_adam_softplus_step,
+    gp_bilinear_grad,
     gp_diag_kernel_time,
     gp_diag_launches,
     gp_diag_product_time,
@@ -38,3 +39,4 @@ from ._binding import (  # noqa: F401
     library,
     library_path,
 )
+from .autograd import bilinear_form, kernel_matvec  # noqa: F401,E402

@@ -76,6 +76,12 @@ _SIGS = {
     "gp_solve_sgd_f64": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i64, _vp, _d, _d, _i64, _d, _i,
                               ctypes.POINTER(_Info), _vp, _sz, _vp]),
     "gp_solve_sgd_f64_workspace": (_sz, [_i64, _i, _i, _i64]),
+    "gp_bilinear_grad": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i64, _vp, _i64, _i, _d, _d, _vp, _vp, _vp, _i, _vp, _sz,
+                              _vp]),
+    "gp_bilinear_grad_workspace": (_sz, [_i64, _i, _i, _i]),
+    "gp_bilinear_grad_f64": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i64, _vp, _i64, _i, _d, _d, _vp, _vp, _vp, _vp, _sz,
+                                  _vp]),
+    "gp_bilinear_grad_f64_workspace": (_sz, [_i64, _i, _i]),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
@@ -367,6 +373,37 @@ def gp_mll_grad_pathwise(kind, theta, X, Vsol, prec=GP_PREC_TC16):
         _check(lib.gp_mll_grad_pathwise(kind, thp, d, _ptr(X), n, _ptr(Vsol), s, _ptr(g), prec, _ptr(ws), wsb,
                                         _stream()))
     return g
+
+
+def gp_bilinear_grad(kind, theta, X, U, W, lam0=1.0, lam_rest=1.0, value=True, dtheta=True, dX=True,
+                     prec=GP_PREC_TC16):
+    """Derivatives of f = sum_c lam_c U[c]^T H W[c] (lam_0 = lam0, lam_c = lam_rest for c >= 1).
+    Returns (value, dtheta, dX): a CUDA float64 tensor of shape (1,), a CUDA float64 tensor of
+    d+2 and an (n, d) tensor in X's dtype; outputs not requested are None.  Passing the same
+    tensor as U and W selects the symmetric form."""
+    lib = library()
+    dt = X.dtype
+    _dev(X, dt, "X", 2)
+    _dev(U, dt, "U", 2)
+    _dev(W, dt, "W", 2)
+    n, d = X.shape
+    R = U.shape[0]
+    if U.shape != (R, n) or W.shape != (R, n):
+        raise ValueError("U and W must be (R, n)")
+    th, thp = _theta(theta, d)
+    dev = X.device
+    v = torch.empty(1, dtype=torch.float64, device=dev) if value else None
+    g = torch.empty(d + 2, dtype=torch.float64, device=dev) if dtheta else None
+    gx = torch.empty((n, d), dtype=dt, device=dev) if dX else None
+    if _f64(X):
+        ws, wsb = _ws(lib.gp_bilinear_grad_f64_workspace(n, d, R), dev)
+        _check(lib.gp_bilinear_grad_f64(kind, thp, d, _ptr(X), n, _ptr(U), n, _ptr(W), n, R, float(lam0),
+                                        float(lam_rest), _ptr(v), _ptr(g), _ptr(gx), _ptr(ws), wsb, _stream()))
+    else:
+        ws, wsb = _ws(lib.gp_bilinear_grad_workspace(n, d, R, prec), dev)
+        _check(lib.gp_bilinear_grad(kind, thp, d, _ptr(X), n, _ptr(U), n, _ptr(W), n, R, float(lam0),
+                                    float(lam_rest), _ptr(v), _ptr(g), _ptr(gx), prec, _ptr(ws), wsb, _stream()))
+    return v, g, gx
 
 
 def gp_posterior_samples(kind, theta, Xstar, X, Vsol, Fstar, prec=GP_PREC_TC16):

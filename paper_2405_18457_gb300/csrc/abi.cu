@@ -502,6 +502,87 @@ int gp_mll_grad_pathwise_f64(int kind, const double *theta, int d, const double 
     GP_API_END
 }
 
+// ------------------------------------------------------------------ bilinear-form derivatives
+}  // extern "C"
+
+template <typename T>
+static size_t bilinear_ws(int64_t n, int d, int R, int prec) {
+    Carver c(nullptr);
+    c.take<double>((size_t)d + 2);
+    c.take<char>(grad_workspace<T>(n, d, R, prec));
+    c.take<char>(bilinear_dx_workspace<T>(n, d));
+    return c.bytes();
+}
+
+template <typename T>
+static int bilinear_common(int kind, const double *theta, int d, const T *X, int64_t n, const T *U, int64_t ldu,
+                           const T *W, int64_t ldw, int R, double lam0, double lam_rest, double *value,
+                           double *dtheta, T *dX, int prec, void *ws, size_t ws_bytes, cudaStream_t st) {
+    KP<T> kp;
+    GP_TRY(make_kp<T>(kind, theta, d, &kp));
+    REQ(n >= 1 && R >= 1, "need n >= 1 and R >= 1");
+    REQ(X && U && W, "null pointer argument");
+    REQ(ldu >= n && ldw >= n, "ldu and ldw must be >= n");
+    REQ(std::isfinite(lam0) && std::isfinite(lam_rest), "lam0 and lam_rest must be finite");
+    if (sizeof(T) == sizeof(float)) GP_TRY(check_prec(prec));
+    if (!value && !dtheta && !dX) return GP_OK;
+    Carver c(ws);
+    double *gbuf = c.take<double>((size_t)d + 2);
+    const size_t gwb = grad_workspace<T>(n, d, R, prec);
+    void *gws = c.take<char>(gwb);
+    const size_t xwb = bilinear_dx_workspace<T>(n, d);
+    void *xws = c.take<char>(xwb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    GradArgs<T> a;
+    a.kp = kp;
+    a.X = X;
+    a.n = n;
+    a.U0 = U;
+    a.U = U + ldu;
+    a.ldu = ldu;
+    a.W0 = W;
+    a.W = W + ldw;
+    a.ldw = ldw;
+    a.R = R;
+    a.lam0 = lam0;
+    a.lam_rest = lam_rest;
+    a.grad = dtheta ? dtheta : gbuf;
+    if (value || dtheta) {
+        GP_TRY(apply_grad<T>(a, prec, gws, gwb, st));
+        if (value) GP_TRY(bilinear_value<T>(kp, a.grad, value, st));
+    }
+    if (dX) GP_TRY(bilinear_dx<T>(a, (U == W && ldu == ldw) ? 1 : 0, dX, xws, xwb, st));
+    return GP_OK;
+}
+
+extern "C" {
+
+size_t gp_bilinear_grad_workspace(int64_t n, int d, int R, int prec) {
+    return bilinear_ws<float>(n, d, R, prec);
+}
+size_t gp_bilinear_grad_f64_workspace(int64_t n, int d, int R) {
+    return bilinear_ws<double>(n, d, R, GP_PREC_FP32);
+}
+
+int gp_bilinear_grad(int kind, const double *theta, int d, const float *X, int64_t n, const float *U,
+                     int64_t ldu, const float *W, int64_t ldw, int R, double lam0, double lam_rest, double *value,
+                     double *dtheta, float *dX, int prec, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    return bilinear_common<float>(kind, theta, d, X, n, U, ldu, W, ldw, R, lam0, lam_rest, value, dtheta, dX,
+                                  prec, ws, ws_bytes, stream);
+    GP_API_END
+}
+
+int gp_bilinear_grad_f64(int kind, const double *theta, int d, const double *X, int64_t n, const double *U,
+                         int64_t ldu, const double *W, int64_t ldw, int R, double lam0, double lam_rest,
+                         double *value, double *dtheta, double *dX, void *ws, size_t ws_bytes,
+                         cudaStream_t stream) {
+    GP_API_BEGIN
+    return bilinear_common<double>(kind, theta, d, X, n, U, ldu, W, ldw, R, lam0, lam_rest, value, dtheta, dX,
+                                   GP_PREC_FP32, ws, ws_bytes, stream);
+    GP_API_END
+}
+
 // ------------------------------------------------------------------ posterior samples
 size_t gp_posterior_samples_workspace(int64_t nstar, int64_t n, int d, int s, int prec) {
     return posterior_workspace(nstar, n, d, s, prec);

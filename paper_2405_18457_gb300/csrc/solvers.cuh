@@ -17,6 +17,15 @@ size_t grad_workspace(int64_t n, int d, int R, int prec);
 template <typename T>
 int apply_grad(const GradArgs<T> &a, int prec, void *ws, size_t ws_bytes, cudaStream_t st);
 
+// Point gradient of sum_c lam_c u_c^T H w_c (backward.cu); sym = 1 when U and W
+// are the same block.  value = the form itself from its theta-gradient g.
+template <typename T>
+size_t bilinear_dx_workspace(int64_t n, int d);
+template <typename T>
+int bilinear_dx(const GradArgs<T> &a, int sym, T *dX, void *ws, size_t ws_bytes, cudaStream_t st);
+template <typename T>
+int bilinear_value(const KP<T> &kp, const double *g, double *value, cudaStream_t st);
+
 template <typename T>
 int rff_prior(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
               int s, T *F, int64_t ldf, cudaStream_t st);
