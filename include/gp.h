@@ -331,6 +331,80 @@ int gp_adam_softplus_step(int P, double *nu, double *m, double *v, int64_t t,
                           const double *grad_theta, double lr, double beta1, double beta2,
                           double eps, double *theta_out);
 
+/* ------------------------------------------------------------------------ */
+/* Batches of independent GPs of uneven size (many problems of Sec. 2 solved  */
+/* and optimised together; the paper treats one problem at a time)           */
+/* ------------------------------------------------------------------------ */
+
+/* A batch plan: G members, member g with n[g] >= 1 points of dimension
+ * 1 <= d[g] <= 32, all with the same kernel kind and s probes (R = s+1 vectors
+ * per member, R <= 128).  The plan is a HOST object (gp_batch_create allocates
+ * it with new; gp_batch_destroy frees it); it owns no device memory.
+ *
+ * Packed layouts (all DEVICE memory owned by the caller; offsets from
+ * gp_batch_member_offsets):
+ *   X      : member g's n_g x d_g row-major points at X + x_off[g]
+ *            (x_off[g] = sum_{h<g} n_h d_h; total x_len floats).
+ *   vectors: member g's block of R vectors at V + vec_off[g], vector c at
+ *            V + vec_off[g] + c*n_g (vec_off[g] = R sum_{h<g} n_h; total vec_len).
+ *            Right-hand sides B = [y, z_1..z_s] and solutions use this layout.
+ *   theta  : member g's d_g+2 doubles [l_1..l_d, s_f, sigma] at theta + theta_off[g]
+ *            (DEVICE, so that a step can update it without the host).
+ *
+ * gp_batch_bind() carves the caller's workspace (gp_batch_workspace() bytes,
+ * 256-byte aligned) and copies the plan's tables into it; it synchronises
+ * `stream` and must be called once, before any stream capture.  The calls below
+ * it never synchronise, allocate or copy from the host: a sequence of them can be
+ * captured into a CUDA graph and replayed.  Calls on one plan must not run
+ * concurrently (they share the workspace).  Device-side failures (a non-positive
+ * theta, a timed-out wait) set a flag read by gp_batch_status(), which synchronises.
+ * Arithmetic: tcgen05 fp16 tiles as GP_PREC_TC16 for the products, FP32 vectors,
+ * FP64 solver scalars, CUDA-core FP32 tiles for the gradient. */
+typedef struct gp_batch gp_batch_t;
+int gp_batch_create(int kind, int G, const int64_t *n, const int *d, int s, gp_batch_t **out);
+void gp_batch_destroy(gp_batch_t *b);
+size_t gp_batch_workspace(const gp_batch_t *b);
+int gp_batch_layout(const gp_batch_t *b, int64_t *x_len, int64_t *vec_len, int64_t *theta_len);
+/* HOST arrays of G entries each (any may be NULL). */
+int gp_batch_member_offsets(const gp_batch_t *b, int64_t *x_off, int64_t *vec_off, int64_t *theta_off);
+int gp_batch_bind(gp_batch_t *b, void *ws, size_t ws_bytes, cudaStream_t stream);
+int gp_batch_status(const gp_batch_t *b, cudaStream_t stream);
+
+/* Tensor-core operands of every member for the current theta (Sec. 2 H_theta);
+ * needed before gp_batch_mvm / gp_batch_solve_cg after theta or X changes. */
+int gp_batch_prepare(gp_batch_t *b, const double *theta, const float *X, cudaStream_t stream);
+/* Y_g = H_g V_g (add_noise = 1) or K_g V_g for every member (R vectors each). */
+int gp_batch_mvm(gp_batch_t *b, const float *V, float *Y, int add_noise, cudaStream_t stream);
+/* Alg. 1 on every member (normalised systems, split norms, loop condition
+ * GP_STOP_BOTH or GP_STOP_EITHER as gp_solve_cg), V_inout the warm start and
+ * the solution.  Exactly `iters` iterations are enqueued; a member whose loop
+ * condition fails is skipped from then on.  info: DEVICE array of G reports
+ * (or NULL), written at the end. */
+int gp_batch_solve_cg(gp_batch_t *b, const float *B, float *V_inout, int64_t iters, double tol,
+                      int stop_rule, gp_solve_info_t *info, cudaStream_t stream);
+/* Eq. mll_grad per member into grad (DEVICE, packed like theta): standard
+ * estimator (Eq. trace) with probes B[1..s] (pathwise = 0), or the pathwise
+ * estimator (Eq. pathwise_estimator, B unused).  Needs gp_batch_prepare's
+ * parameters for the same theta. */
+int gp_batch_mll_grad(gp_batch_t *b, const double *theta, const float *X, const float *Vsol,
+                      const float *B, int pathwise, double *grad, cudaStream_t stream);
+/* Adam ascent on softplus parameters, as gp_adam_softplus_step, for all members
+ * on the device: nu, m, v, grad, theta packed like theta; *t (DEVICE) counts the
+ * completed steps and is incremented.  gp_batch_adam_init sets nu = softplus^-1(theta),
+ * m = v = 0, *t = 0. */
+int gp_batch_adam_init(gp_batch_t *b, const double *theta, double *nu, double *m, double *v,
+                       long long *t, cudaStream_t stream);
+int gp_batch_adam_step(gp_batch_t *b, double *nu, double *m, double *v, long long *t,
+                       const double *grad, double lr, double beta1, double beta2, double eps,
+                       double *theta, cudaStream_t stream);
+/* One marginal-likelihood step for every member: prepare(theta), warm-started
+ * CG with `iters` iterations and tolerance tol (GP_STOP_BOTH) on B = [y, z],
+ * the standard estimator, and an Adam step (beta1 0.9, beta2 0.999, eps 1e-8)
+ * that updates theta, nu, m, v and *t in place. */
+int gp_batch_step(gp_batch_t *b, const float *X, double *theta, const float *B, float *V_inout,
+                  int64_t iters, double tol, double *grad, double *nu, double *m, double *v,
+                  long long *t, double lr, gp_solve_info_t *info, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

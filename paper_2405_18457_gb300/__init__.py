@@ -40,3 +40,4 @@ from ._binding import (  # noqa: F401
     library_path,
 )
 from .autograd import bilinear_form, kernel_matvec  # noqa: F401,E402
+from .batched import GPBatch  # noqa: F401,E402

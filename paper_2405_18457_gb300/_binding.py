@@ -82,6 +82,20 @@ _SIGS = {
     "gp_bilinear_grad_f64": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i64, _vp, _i64, _i, _d, _d, _vp, _vp, _vp, _vp, _sz,
                                   _vp]),
     "gp_bilinear_grad_f64_workspace": (_sz, [_i64, _i, _i]),
+    "gp_batch_create": (_i, [_i, _i, _vp, _vp, _i, ctypes.POINTER(_vp)]),
+    "gp_batch_destroy": (None, [_vp]),
+    "gp_batch_workspace": (_sz, [_vp]),
+    "gp_batch_layout": (_i, [_vp, _vp, _vp, _vp]),
+    "gp_batch_member_offsets": (_i, [_vp, _vp, _vp, _vp]),
+    "gp_batch_bind": (_i, [_vp, _vp, _sz, _vp]),
+    "gp_batch_status": (_i, [_vp, _vp]),
+    "gp_batch_prepare": (_i, [_vp, _vp, _vp, _vp]),
+    "gp_batch_mvm": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "gp_batch_solve_cg": (_i, [_vp, _vp, _vp, _i64, _d, _i, _vp, _vp]),
+    "gp_batch_mll_grad": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp]),
+    "gp_batch_adam_init": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "gp_batch_adam_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _d, _d, _vp, _vp]),
+    "gp_batch_step": (_i, [_vp, _vp, _vp, _vp, _vp, _i64, _d, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp]),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),

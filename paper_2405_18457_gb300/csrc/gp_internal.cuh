@@ -235,6 +235,80 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st);
 bool tc_available();
 
 // ---------------------------------------------------------------------------
+// Batches of independent GPs (batched.cu): device tables shared with tc.cu
+// ---------------------------------------------------------------------------
+constexpr int kBatchMaxD = 32;
+
+// One member GP of a batch.  Points, vectors and hyperparameters are packed
+// member after member; the tensor-core operands of members with the same
+// contraction depth share one row space (a "class").
+struct BMember {
+    int64_t n;      // points
+    int64_t xo;     // offset of its points in the packed X (floats)
+    int64_t vo;     // offset of its vector block in packed vectors (R vectors of n)
+    int64_t to;     // offset of its hyperparameters in the packed theta (d + 2 doubles)
+    int64_t cb;     // first column of its points in the packed fp16 V (multiple of 128)
+    int64_t rb;     // first row of its points in its class's PA/PB (multiple of 128)
+    int d, cls, kind;
+    int ch0, nch;   // its point chunks in the batch's chunk table
+    int gi0, ngi;   // its gradient work items
+    // set from theta on the device before every use
+    float inv_ell[kBatchMaxD];
+    float sf, sf2, sigma, sigma2;
+    float dscale;   // power-of-two scale of the distance operands
+    unsigned bound; // magnitude bound it was chosen from (float bits)
+};
+
+// Rows [start, start + kBatchChunk) of a member (clipped to its 128-padded size): the
+// unit of the batch's per-point kernels (operand preparation, vector updates, dots).
+constexpr int kBatchChunk = 1024;
+struct BChunk {
+    int member;
+    int start;
+};
+
+// A unit of work of the grouped product kernel: 128 rows of one member against a
+// run of its 128-wide column tiles.
+struct BItem {
+    int row_tile;   // in the class row space (PA)
+    int pb_tile;    // first column tile in the class row space (PB)
+    int v_tile;     // first column tile in the packed fp16 V
+    int ntiles;
+    int member;
+    int pad0, pad1, pad2;
+};
+
+// Grouped H V / K V over a batch (tc.cu).  PA/PB are the class's operand arrays,
+// V16 the packed fp16 right-hand sides [R_pad][cols], vinv[member][R_pad] their
+// scales.  Y, Vd (the diagonal term's vectors) are packed vector blocks.
+struct TcGroupArgs {
+    int kind, KD, R, R_pad;
+    const void *PA, *PB;
+    int64_t class_rows;  // rows of PA / PB
+    const void *V16;
+    int64_t v_cols;      // columns of V16
+    const float *vinv;
+    const BItem *items;
+    int nitems;
+    const BMember *members;
+    const int *mdone;    // per member: skip when nonzero (may be null)
+    float *Y;
+    const float *Vd;
+    float diag;          // 1: add sigma_g^2 Vd (H V), 0: K V
+    int *err;
+};
+int tc_group_mvm(const TcGroupArgs &a, cudaStream_t st);
+// Operands of every member from its device-side parameters (BMember inv_ell, bound):
+// PA/PB rows of class c at PA[c], PB[c] (KD[c] halves per row).
+int tc_group_prepare(int kind, BMember *members, int G, const BChunk *chunks, int nchunks, const float *X,
+                     void *const *PA, void *const *PB, const int *KD, cudaStream_t st);
+// fp16 right-hand sides: V16[c][cb_g + i] = V_g[c][i] * 2^-e_gc, vinv[g][c] = 2^e_gc.
+int tc_group_convert(const BMember *members, int G, const BChunk *chunks, int nchunks, const float *V, int R,
+                     int R_pad, unsigned *colmax, void *V16, int64_t v_cols, float *vinv, const int *mdone,
+                     cudaStream_t st);
+int tc_group_setup();  // one-time kernel attributes (call before any stream capture)
+
+// ---------------------------------------------------------------------------
 // Small device helpers used by several files
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

@@ -216,6 +216,10 @@ struct KParams {
     float *partial;      // nsplit > 1: partial[split][c][i]
     const int *done;
     int *err;
+    // grouped mode (a batch of independent GPs): one work item per CTA
+    const BItem *items;     // null: single problem, grid = row tiles x splits
+    const BMember *members;
+    const int *mdone;
 };
 
 template <int KIND, int KAT>  // KAT: 64-wide atoms of the distance contraction (KD / 64)
@@ -253,11 +257,43 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TM;
-    const int64_t per = cdiv(p.col_tiles, p.nsplit);
-    const int64_t t0 = (int64_t)blockIdx.y * per;
-    const int64_t t1 = min(p.col_tiles, t0 + per);
-    const int ntiles = (int)max((int64_t)0, t1 - t0);
+    // Work of this CTA: rows [row0, row0 + 128) of PA against ntiles column tiles of PB
+    // starting at tile tb0 (V16 tile tv0); output rows are local rows ioff + lane row
+    // of the vectors at Yp.
+    int64_t row0, tb0, tv0, ioff;
+    int ntiles;
+    int64_t n1 = p.n1, ldy = p.ldy, ldvd = p.ldvd, drow0 = p.drow0, ndiag = p.ndiag;
+    float sf2 = p.sf2, diag_coef = p.diag_coef, dsc;
+    const float *vinv = p.vinv, *Vd = p.Vd;
+    float *Yp = p.Y;
+    if (p.items) {
+        const BItem itm = p.items[blockIdx.x];
+        if (p.mdone && p.mdone[itm.member]) return;
+        const BMember &m = p.members[itm.member];
+        row0 = (int64_t)itm.row_tile * TM;
+        tb0 = itm.pb_tile;
+        tv0 = itm.v_tile;
+        ntiles = itm.ntiles;
+        ioff = row0 - m.rb;
+        n1 = m.n;
+        ldy = ldvd = ndiag = m.n;
+        drow0 = 0;
+        sf2 = m.sf2;
+        diag_coef = p.diag_coef * m.sigma2;
+        dsc = m.dscale;
+        vinv = p.vinv + (int64_t)itm.member * R_pad;
+        Yp = p.Y + m.vo;
+        Vd = p.Vd ? p.Vd + m.vo : nullptr;
+    } else {
+        row0 = (int64_t)blockIdx.x * TM;
+        const int64_t per = cdiv(p.col_tiles, p.nsplit);
+        tb0 = (int64_t)blockIdx.y * per;
+        const int64_t t1 = min(p.col_tiles, tb0 + per);
+        ntiles = (int)max((int64_t)0, t1 - tb0);
+        tv0 = tb0;
+        ioff = row0;
+        dsc = *p.dscale;
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
@@ -298,7 +334,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NPB;
             if (it >= NPB && !mbar_wait(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
-            const int j0 = (int)((t0 + it) * TN);
+            const int j0 = (int)((tb0 + it) * TN);
             uint8_t *sB = sPB + (size_t)s * b_bytes;
             mbar_expect_tx(&pb_full[s], b_bytes);
             for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
@@ -308,7 +344,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NV;
             if (it >= NV && !mbar_wait(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
-            const int j0 = (int)((t0 + it) * TN);
+            const int j0 = (int)((tv0 + it) * TN);
             uint8_t *sV = sVr + (size_t)s * v_bytes;
             mbar_expect_tx(&v_full[s], v_bytes);
             tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
@@ -367,7 +403,6 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         const int wg = (warp - 4) >> 2;
         const int wq = warp & 3;  // TMEM lane quarter this warp may access
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
-        const float dsc = *p.dscale;
         const bool unit = (dsc == 1.0f);
         bool ok = true;
         for (int it = wg; it < ntiles; it += 2) {
@@ -419,25 +454,25 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
         if (ok && ntiles > 0) {
             tc_fence_after();
-            const int64_t i = row0 + wq * 32 + lane;
+            const int64_t i = ioff + wq * 32 + lane;
             for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
                 uint32_t r[16];
                 tmem_ld16(tY + lane_off + c0, r);
                 tmem_ld_wait();
-                if (i < p.n1) {
+                if (i < n1) {
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int c = c0 + e;
                         if (c >= p.R) break;
-                        float v = p.sf2 * p.vinv[c] * __uint_as_float(r[e]);
+                        float v = sf2 * vinv[c] * __uint_as_float(r[e]);
                         if (p.nsplit > 1) {
-                            p.partial[((int64_t)blockIdx.y * p.R + c) * p.n1 + i] = v;
+                            p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v;
                         } else {
                             float y = p.alpha * v;
-                            if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
-                            if (p.diag_coef != 0.0f && i >= p.drow0 && i < p.drow0 + p.ndiag)
-                                y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - p.drow0)];
-                            p.Y[(int64_t)c * p.ldy + i] = y;
+                            if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
+                            if (diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
+                                y += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
+                            Yp[(int64_t)c * ldy + i] = y;
                         }
                     }
                 }
@@ -491,63 +526,201 @@ __global__ void tc_bound_kernel(const KP<float> kp, float c, const float *X, int
     if ((threadIdx.x & 31) == 0) atomicMax(bound, __float_as_uint(m));
 }
 
+// One prepared row (see the header comment): x is the point (d coordinates), a = x / l.
+// pa / pb may be null (row or column operand only).
+__device__ __forceinline__ void operand_row(const float *x, const float *inv_ell, int d, float c, float inv_s, int KD,
+                                            __half *pa, __half *pb) {
+    const __half z = __float2half_rn(0.0f), one = __float2half_rn(1.0f);
+    float nrm = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        float a = x[k] * inv_ell[k];
+        __half h, l;
+        split16(a, &h, &l);
+        float ar = __half2float(h) + __half2float(l);  // the value the tensor cores see
+        nrm += ar * ar;
+        if (pb) {
+            pb[k] = h;
+            pb[d + k] = l;
+            pb[2 * d + k] = h;
+        }
+        if (pa) {
+            __half h2, l2;
+            split16(-2.0f * c * inv_s * ar, &h2, &l2);
+            pa[k] = h2;
+            pa[d + k] = h2;
+            pa[2 * d + k] = l2;
+        }
+    }
+    __half nh, nl;
+    split16(c * inv_s * nrm, &nh, &nl);
+    const int o = 3 * d;
+    if (pa) {
+        pa[o] = nh;
+        pa[o + 1] = nl;
+        pa[o + 2] = one;
+        pa[o + 3] = one;
+        for (int k = o + 4; k < KD; ++k) pa[k] = z;
+    }
+    if (pb) {
+        pb[o] = one;
+        pb[o + 1] = one;
+        pb[o + 2] = nh;
+        pb[o + 3] = nl;
+        for (int k = o + 4; k < KD; ++k) pb[k] = z;
+    }
+}
+
+__device__ __forceinline__ void zero_row(int KD, __half *pa, __half *pb) {
+    const __half z = __float2half_rn(0.0f);
+    for (int k = 0; k < KD; ++k) {
+        if (pa) pa[k] = z;
+        if (pb) pb[k] = z;
+    }
+}
+
+// s = smallest power of two with bound / s <= 2^14
+__device__ __forceinline__ float operand_scale(float bnd) {
+    float s = 1.0f;
+    while (bnd / s > 16384.0f) s *= 2.0f;
+    return s;
+}
+
 // Writes PA (if PA) and PB (if PB) rows for the point set X (n points, n_pad rows).
 __global__ void tc_operands_kernel(const KP<float> kp, float c, const float *X, int64_t n, int64_t n_pad, int KD,
                                    const unsigned int *bound, __half *PA, __half *PB, float *dscale_out) {
-    // s = smallest power of two with bound / s <= 2^14
-    const float bnd = __uint_as_float(*bound);
-    float s = 1.0f;
-    while (bnd / s > 16384.0f) s *= 2.0f;
+    const float s = operand_scale(__uint_as_float(*bound));
     if (blockIdx.x == 0 && threadIdx.x == 0 && dscale_out) *dscale_out = s;
     const float inv_s = 1.0f / s;
     const int d = kp.d;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
         __half *pa = PA ? PA + i * KD : nullptr;
         __half *pb = PB ? PB + i * KD : nullptr;
-        const __half z = __float2half_rn(0.0f), one = __float2half_rn(1.0f);
-        if (i >= n) {
-            for (int k = 0; k < KD; ++k) {
-                if (pa) pa[k] = z;
-                if (pb) pb[k] = z;
+        if (i >= n)
+            zero_row(KD, pa, pb);
+        else
+            operand_row(X + i * d, kp.inv_ell, d, c, inv_s, KD, pa, pb);
+    }
+}
+
+// ------------------------------------------------------------------ batches (grouped operands)
+// Per member bound (float bits, atomicMax) over its chunks: max of c ||a||^2 and 2 c |a_k|.
+__global__ void tc_group_bound_kernel(BMember *mem, const BChunk *chunks, int nchunks, const float *X, float c) {
+    __shared__ float red[8];
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const BChunk k = chunks[ch];
+        const BMember &m = mem[k.member];
+        const int d = m.d;
+        float mx = 0.0f;
+        for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
+            const int64_t i = (int64_t)k.start + r;
+            if (i >= m.n) break;
+            const float *x = X + m.xo + i * d;
+            float nrm = 0.0f, amax = 0.0f;
+            for (int q = 0; q < d; ++q) {
+                float a = x[q] * m.inv_ell[q];
+                nrm += a * a;
+                amax = fmaxf(amax, fabsf(a));
             }
-            continue;
+            mx = fmaxf(mx, fmaxf(fabsf(c) * nrm, 2.0f * fabsf(c) * amax));
         }
-        float nrm = 0.0f;
-        for (int k = 0; k < d; ++k) {
-            float a = X[i * d + k] * kp.inv_ell[k];
-            __half h, l;
-            split16(a, &h, &l);
-            float ar = __half2float(h) + __half2float(l);  // the value the tensor cores see
-            nrm += ar * ar;
-            if (pb) {
-                pb[k] = h;
-                pb[d + k] = l;
-                pb[2 * d + k] = h;
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+            atomicMax(&mem[k.member].bound, __float_as_uint(t));
+        }
+        __syncthreads();
+    }
+}
+
+struct GroupOut {
+    __half *PA[3], *PB[3];
+    int KD[3];
+};
+
+__global__ void tc_group_operands_kernel(BMember *mem, const BChunk *chunks, int nchunks, const float *X, float c,
+                                         GroupOut o) {
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const BChunk k = chunks[ch];
+        const BMember &m = mem[k.member];
+        const float s = operand_scale(__uint_as_float(m.bound));
+        if (k.start == 0 && threadIdx.x == 0) mem[k.member].dscale = s;
+        const float inv_s = 1.0f / s;
+        const int KD = o.KD[m.cls];
+        const int64_t n_pad = rup(m.n, TM);
+        for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
+            const int64_t i = (int64_t)k.start + r;
+            if (i >= n_pad) break;
+            __half *pa = o.PA[m.cls] + (m.rb + i) * KD;
+            __half *pb = o.PB[m.cls] + (m.rb + i) * KD;
+            if (i >= m.n)
+                zero_row(KD, pa, pb);
+            else
+                operand_row(X + m.xo + i * m.d, m.inv_ell, m.d, c, inv_s, KD, pa, pb);
+        }
+    }
+}
+
+// colmax[g][c] = max |V_g[c][i]| over the member's rows (float bits, atomicMax)
+__global__ void tc_group_colmax_kernel(const BMember *mem, const BChunk *chunks, int nchunks, const float *V, int R,
+                                       int R_pad, unsigned *colmax, const int *mdone) {
+    __shared__ float red[8];
+    const int c = blockIdx.y;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const BChunk k = chunks[ch];
+        if (mdone && mdone[k.member]) continue;
+        const BMember &m = mem[k.member];
+        const float *v = V + m.vo + (int64_t)c * m.n;
+        float mx = 0.0f;
+        for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
+            const int64_t i = (int64_t)k.start + r;
+            if (i >= m.n) break;
+            mx = fmaxf(mx, fabsf(v[i]));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+            if (t > 0.0f) atomicMax(&colmax[(int64_t)k.member * R_pad + c], __float_as_uint(t));
+        }
+        __syncthreads();
+    }
+}
+
+// V16[c][cb + i] = fp16(V[c][i] 2^(1-e)) with max |V[c]| = f 2^e, f in [0.5, 1) (0 rows up to
+// the 128-padded size and for c >= R); vinv = 2^(e-1).
+__global__ void tc_group_convert_kernel(const BMember *mem, const BChunk *chunks, int nchunks, const float *V, int R,
+                                        int R_pad, const unsigned *colmax, __half *V16, int64_t v_cols, float *vinv,
+                                        const int *mdone) {
+    const int c = blockIdx.y;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const BChunk k = chunks[ch];
+        if (mdone && mdone[k.member]) continue;
+        const BMember &m = mem[k.member];
+        float scale = 0.0f, inv = 1.0f;
+        if (c < R) {
+            const float mx = __uint_as_float(colmax[(int64_t)k.member * R_pad + c]);
+            int e = 0;
+            if (mx > 0.0f && isfinite(mx)) {
+                frexpf(mx, &e);
+                scale = ldexpf(1.0f, 1 - e);
+                inv = ldexpf(1.0f, e - 1);
+            } else {
+                scale = 1.0f;
             }
-            if (pa) {
-                __half h2, l2;
-                split16(-2.0f * c * inv_s * ar, &h2, &l2);
-                pa[k] = h2;
-                pa[d + k] = h2;
-                pa[2 * d + k] = l2;
-            }
         }
-        __half nh, nl;
-        split16(c * inv_s * nrm, &nh, &nl);
-        const int o = 3 * d;
-        if (pa) {
-            pa[o] = nh;
-            pa[o + 1] = nl;
-            pa[o + 2] = one;
-            pa[o + 3] = one;
-            for (int k = o + 4; k < KD; ++k) pa[k] = z;
-        }
-        if (pb) {
-            pb[o] = one;
-            pb[o + 1] = one;
-            pb[o + 2] = nh;
-            pb[o + 3] = nl;
-            for (int k = o + 4; k < KD; ++k) pb[k] = z;
+        if (k.start == 0 && threadIdx.x == 0) vinv[(int64_t)k.member * R_pad + c] = inv;
+        const int64_t n_pad = rup(m.n, TM);
+        const float *v = V + m.vo + (int64_t)c * m.n;
+        __half *out = V16 + (int64_t)c * v_cols + m.cb;
+        for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
+            const int64_t i = (int64_t)k.start + r;
+            if (i >= n_pad) break;
+            out[i] = __float2half_rn((c < R && i < m.n) ? v[i] * scale : 0.0f);
         }
     }
 }
@@ -881,6 +1054,109 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         GP_TRY(check_launch("tc_reduce_kernel"));
     }
     return GP_OK;
+}
+
+// Grouped product over a batch of independent GPs: one CTA per work item (128 rows of a
+// member against a run of its own column tiles), items ordered longest first so the
+// block scheduler fills the SMs like a longest-processing-time list schedule.
+int tc_group_setup() {
+    static bool done = false;
+    if (done) return GP_OK;
+    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxDynSmem));
+    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxDynSmem));
+    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxDynSmem));
+    done = true;
+    return GP_OK;
+}
+
+int tc_group_mvm(const TcGroupArgs &a, cudaStream_t st) {
+    if (a.nitems == 0) return GP_OK;
+    if (a.R > kMaxRhsPerPass) {
+        set_error("batched product supports at most %d right-hand sides", kMaxRhsPerPass);
+        return GP_ERR_UNSUPPORTED;
+    }
+    const int kat = a.KD / 64;
+    if (kat < 1 || kat > 3) {
+        set_error("batched product supports d <= 62 (got KD=%d)", a.KD);
+        return GP_ERR_UNSUPPORTED;
+    }
+    GP_TRY(tc_group_setup());
+    CUtensorMap mA, mB, mV;
+    GP_TRY(make_map(&mA, a.PA, a.KD, a.class_rows, 64, TM));
+    GP_TRY(make_map(&mB, a.PB, a.KD, a.class_rows, 64, TN));
+    GP_TRY(make_map(&mV, a.V16, a.v_cols, a.R_pad, 64, a.R_pad));
+    int npb = 0, nv = 0;
+    rings_for(a.KD, a.R_pad, &npb, &nv);
+    if (npb < 2 || nv < 2) {
+        set_error("tensor-core tile does not fit shared memory (KD=%d, R=%d)", a.KD, a.R);
+        return GP_ERR_UNSUPPORTED;
+    }
+    KParams kp{};
+    kp.R = a.R;
+    kp.R_pad = a.R_pad;
+    kp.KD = a.KD;
+    kp.npb = npb;
+    kp.nv = nv;
+    kp.nsplit = 1;
+    kp.alpha = 1.0f;
+    kp.beta = 0.0f;
+    kp.diag_coef = a.diag;
+    kp.vinv = a.vinv;
+    kp.Vd = a.Vd;
+    kp.Y = a.Y;
+    kp.err = a.err;
+    kp.items = a.items;
+    kp.members = a.members;
+    kp.mdone = a.mdone;
+    const size_t smem = smem_for(a.KD, a.R_pad, npb, nv);
+    dim3 grid((unsigned)a.nitems, 1);
+    prof_begin(st);
+    if (a.kind == GP_RBF) {
+        if (kat == 1) tc_mvm_kernel<GP_RBF, 1><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+        else if (kat == 2) tc_mvm_kernel<GP_RBF, 2><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+        else tc_mvm_kernel<GP_RBF, 3><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+    } else {
+        if (kat == 1) tc_mvm_kernel<GP_MATERN32, 1><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+        else if (kat == 2) tc_mvm_kernel<GP_MATERN32, 2><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+        else tc_mvm_kernel<GP_MATERN32, 3><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+    }
+    prof_end(st);
+    return check_launch("tc_mvm_kernel (batched)");
+}
+
+int tc_group_prepare(int kind, BMember *members, int G, const BChunk *chunks, int nchunks, const float *X,
+                     void *const *PA, void *const *PB, const int *KD, cudaStream_t st) {
+    (void)G;
+    if (nchunks == 0) return GP_OK;
+    const float cf = (kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
+    const unsigned nb = (unsigned)std::min(nchunks, 8 * num_sms_tc());
+    tc_group_bound_kernel<<<nb, 256, 0, st>>>(members, chunks, nchunks, X, cf);
+    GroupOut o{};
+    for (int c = 0; c < 3; ++c) {
+        o.PA[c] = static_cast<__half *>(PA[c]);
+        o.PB[c] = static_cast<__half *>(PB[c]);
+        o.KD[c] = KD[c];
+    }
+    tc_group_operands_kernel<<<nb, 256, 0, st>>>(members, chunks, nchunks, X, cf, o);
+    return check_launch("batched operand preparation", 2);
+}
+
+int tc_group_convert(const BMember *members, int G, const BChunk *chunks, int nchunks, const float *V, int R,
+                     int R_pad, unsigned *colmax, void *V16, int64_t v_cols, float *vinv, const int *mdone,
+                     cudaStream_t st) {
+    if (nchunks == 0) return GP_OK;
+    GP_TRY_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned) * (size_t)G * R_pad, st));
+    const unsigned nb = (unsigned)std::min(nchunks, 4 * num_sms_tc());
+    tc_group_colmax_kernel<<<dim3(nb, R), 256, 0, st>>>(members, chunks, nchunks, V, R, R_pad, colmax, mdone);
+    tc_group_convert_kernel<<<dim3(nb, R_pad), 256, 0, st>>>(members, chunks, nchunks, V, R, R_pad, colmax,
+                                                            static_cast<__half *>(V16), v_cols, vinv, mdone);
+    return check_launch("batched rhs conversion", 2);
 }
 
 // ===========================================================================

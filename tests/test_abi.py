@@ -89,3 +89,44 @@ def test_adam_step_matches_oracle(lib):
         th2 = oracle.adam_softplus(nu2, m2, v2, t, g, lr=0.05)
         np.testing.assert_allclose(th1, th2, rtol=1e-14)
         np.testing.assert_allclose(nu1, nu2, rtol=1e-14)
+
+
+def test_batch_plan_layout_on_the_host(lib):
+    """The batch plan is a host object: packed offsets and workspace size need no device."""
+    vp = ctypes.c_void_p
+    n = np.array([5, 300, 1000], dtype=np.int64)
+    d = np.array([4, 32, 16], dtype=np.int32)
+    s = 2
+    h = vp()
+    assert lib.gp_batch_create(0, 3, n.ctypes.data_as(vp), d.ctypes.data_as(vp), s, ctypes.byref(h)) == 0
+    try:
+        xl, vl, tl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        assert lib.gp_batch_layout(h, ctypes.byref(xl), ctypes.byref(vl), ctypes.byref(tl)) == 0
+        assert xl.value == int((n * d).sum())
+        assert vl.value == (s + 1) * int(n.sum())
+        assert tl.value == int((d + 2).sum())
+        xo, vo, to = (np.zeros(3, dtype=np.int64) for _ in range(3))
+        assert lib.gp_batch_member_offsets(h, xo.ctypes.data_as(vp), vo.ctypes.data_as(vp),
+                                           to.ctypes.data_as(vp)) == 0
+        np.testing.assert_array_equal(xo, [0, 20, 20 + 300 * 32])
+        np.testing.assert_array_equal(vo, [0, 15, 15 + 900])
+        np.testing.assert_array_equal(to, [0, 6, 40])
+        ws = lib.gp_batch_workspace(h)
+        assert ws > 0 and ws % 256 == 0
+        # device work before gp_batch_bind is refused on the host
+        assert lib.gp_batch_prepare(h, vp(16), vp(16), None) == -1
+        assert b"bind" in lib.gp_last_error()
+    finally:
+        lib.gp_batch_destroy(h)
+
+
+@pytest.mark.parametrize("kind,nn,dd,s,msg", [(0, [10, 0], [4, 4], 2, b"n ="), (0, [10], [33], 2, b"d ="),
+                                              (0, [10], [4], 0, b"s must"), (5, [10], [4], 2, b"kind")])
+def test_batch_plan_rejects_bad_shapes(lib, kind, nn, dd, s, msg):
+    vp = ctypes.c_void_p
+    n = np.array(nn, dtype=np.int64)
+    d = np.array(dd, dtype=np.int32)
+    h = vp()
+    assert lib.gp_batch_create(kind, len(nn), n.ctypes.data_as(vp), d.ctypes.data_as(vp), s,
+                               ctypes.byref(h)) == -1
+    assert msg in lib.gp_last_error() and not h.value
