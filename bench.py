@@ -371,6 +371,160 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+BATCH_METRIC = "batched MLL step time (256 independent uneven RBF GPs, one captured CUDA graph per step)"
+
+
+def run_batched(args):
+    """The batched workload: 256 independent RBF-ARD GPs, n ~ LogUniform[512, 65536],
+    d in {4, 8, 16, 32}, X ~ U[0,1]^d, y = RFF prior draw + N(0, 0.1^2), s = 16 standard
+    probes (R = 17); per step: operands from theta, warm-started CG with a budget of 50
+    iterations (tolerance 0.01, per-member early stop), standard estimator, Adam (lr 0.1),
+    all captured once into a CUDA graph and replayed.  Reports p50/p99 step time."""
+    import torch
+
+    import paper_2405_18457_gb300 as gp
+    from paper_2405_18457_gb300 import workloads
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gp.library()
+    s, iters, tol, lr = 16, 50, 0.01, 0.1
+    ns, ds = workloads.batched_sizes(n_gps=args.n_gps, seed=rank)
+    mem = [workloads.batched_member(int(n), int(d), s=s, m=1024, seed=rank, index=g)
+           for g, (n, d) in enumerate(zip(ns, ds))]
+    b = gp.GPBatch(gp.GP_RBF, ns, ds, s, device=dev)
+    Bs = []
+    for p in mem:
+        Xg = torch.tensor(p.X, dtype=torch.float32, device=dev)
+        tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+        F = gp.gp_rff_prior_sample(p.kind, p.theta, Xg, tf(p.omega_hat), None, tf(p.W_y))
+        # y = f(X) + 0.1 w  (the second block of [y', F + sigma w] with sigma = 0.1)
+        y = gp.gp_pathwise_rhs(p.theta, p.d, torch.zeros(p.n, device=dev), F, tf(p.y_noise[None]))[1]
+        Bs.append(torch.cat([y[None], tf(p.Z)], 0).cpu().numpy())
+    X = b.pack_points([p.X for p in mem])
+    B = b.pack_vectors(Bs)
+    theta = b.pack_theta([p.theta for p in mem])
+    V = torch.zeros_like(B)
+    grad = torch.empty_like(theta)
+    st = b.adam_init(theta)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    # one eager step (attributes, tensor maps), then capture the step once
+    b.step(X, theta, B, V, iters, tol, st, lr, grad)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.step(X, theta, B, V, iters, tol, st, lr, grad)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    b.status()
+    nsq = np.asarray(ns, dtype=np.float64) ** 2
+    R = s + 1
+    clocks = Clocks(local)
+    clocks.start()
+    times, work, its = [], 0.0, []
+    for _ in range(args.steps):
+        flush_l2(torch, flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        info = b.info()  # outside the timed region
+        it = np.array([r["iters"] for r in info], dtype=np.float64)
+        its.append(float(it.mean()))
+        work += float(((it + 2.0) * nsq).sum()) * R  # CG products (+1 initial residual) + gradient pass
+    clk = clocks.stop()
+    b.status()
+    total_s = sum(times) / 1e3
+    # dominant kernel: the grouped product (one launch per contraction class), events per launch
+    gp.gp_diag_reset(True)
+    for _ in range(args.kernel_reps):
+        flush_l2(torch, flush)
+        b.mvm(V, add_noise=True)
+    torch.cuda.synchronize()
+    prod_ms, prod_cnt = gp.gp_diag_kernel_time(0)
+    gp.gp_diag_reset(False)
+    prod_s = prod_ms / 1e3 / args.kernel_reps  # all classes of one batched product
+    pairs = float(nsq.sum())
+    peaks, peak_src = _peaks()
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1e12
+    # per pair: GEMM1 2 KD + GEMM2 2 R_pad flops on the tensor pipe; one ex2 on the MUFU (RBF)
+    kd = np.where(np.asarray(ds) <= 20, 64, 128)
+    t_tensor = float((nsq * (2.0 * kd + 2.0 * 32)).sum()) / tpeak
+    t_mufu = pairs / (152 * 32.0 * clk_mhz * 1e6)
+    bound_s = max(t_tensor, t_mufu)
+    achieved = pairs / prod_s / 1e9
+    roof = {"bound": "tensor" if t_tensor >= t_mufu else "alu", "unit": "Gpair/s", "achieved": achieved,
+            "peak": pairs / bound_s / 1e9, "frac": bound_s / prod_s, "traffic": None,
+            "peak_derivation": "max(tensor: sum n^2 (2 KD + 2 R_pad) flops / measured bf16 sustained, "
+                               "MUFU: sum n^2 / (152 x 32 ex2/clk x %.0f MHz))" % clk_mhz,
+            "peak_source": peak_src, "kernel": "tc_mvm_kernel (grouped H V, all classes)",
+            "avg_launch_ms": prod_s * 1e3, "launches_timed": prod_cnt, "pairs_per_launch": pairs}
+    # end to end: points and right-hand sides from pinned host memory every step, theta read back
+    Xh = X.cpu().pin_memory()
+    Bh = B.cpu().pin_memory()
+    th_h = torch.empty(theta.numel(), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        X.copy_(Xh, non_blocking=True)
+        B.copy_(Bh, non_blocking=True)
+        graph.replay()
+        th_h.copy_(theta, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e_s = e0.elapsed_time(e1) / 1e3
+    cpu = None
+    if rank == 0:
+        big = int(np.argmax(ns))
+        p = mem[big]
+        Vh = np.random.default_rng(0).standard_normal((R, p.n))
+        rows = np.arange(8)
+        t0 = time.perf_counter()
+        import oracle
+
+        oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, Vh, add_noise=True, rows=rows)
+        t8 = time.perf_counter() - t0
+        k = int(max(8, min(p.n, 8 * args.cpu_seconds / max(t8, 1e-6))))
+        rows = np.random.default_rng(1).choice(p.n, size=k, replace=False)
+        t0 = time.perf_counter()
+        oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, Vh, add_noise=True, rows=rows)
+        dt = time.perf_counter() - t0
+        cpu = {"value": k * p.n * R / dt / 1e9, "unit": "Gpair*RHS/s",
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": "%d sampled rows of H V of the largest member (n=%d, d=%d, R=%d), FP64, %.1f s"
+                         % (k, p.n, p.d, R, dt)}
+    if rank != 0:
+        return
+    ts = np.array(times)
+    out = {
+        "metric": BATCH_METRIC, "value": float(np.percentile(ts, 50)), "unit": "ms per step (p50)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(ts.mean()),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16-tensor/f32/f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": "batched: %d RBF GPs, n~LogUniform[512,65536] (sum n=%d), d in {4,8,16,32}, s=%d, "
+                               "CG budget %d tol %.2g warm, standard estimator, Adam lr %.2g"
+                               % (len(ns), int(np.sum(ns)), s, iters, tol, lr),
+                   "l2": "flushed between timed steps", "parallelism": "single GPU"},
+        "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+        "pair_rhs_per_s": work / total_s, "mean_cg_iters_per_member": its,
+        "e2e": {"value": 1e3 * e_s / args.steps, "unit": "ms per step (mean)",
+                "h2d_bytes_per_step": int(Xh.numel() * 4 + Bh.numel() * 4), "d2h_bytes_per_step": int(th_h.numel() * 8)},
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "fp64_form": None,
+    }
+    print(json.dumps(out))
+
+
 def cpu_baseline(prob, R, budget_s=15.0, rows_per_step=None):
     """The FP64 CPU oracle (as it stands) on a bounded sample of the same product:
     sampled rows of H V over all n columns and R right-hand sides."""
@@ -439,11 +593,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--kernel-reps", type=int, default=10)
+    ap.add_argument("--workload", choices=["pathwise", "batched"], default="pathwise")
+    ap.add_argument("--n-gps", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
     if args.prec is None:
         args.prec = "tc16" if _tc_ok() else "fp32"

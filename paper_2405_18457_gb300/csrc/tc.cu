@@ -351,19 +351,22 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
         }
     } else if (warp == 1 && lane == 0 && ntiles > 0) {
-        // ------------------------------------------------ MMA issuer
-        // One thread issues every MMA, so its instruction stream is on the critical path:
-        // descriptors are built once and advanced by constant offsets (16-byte units).
+        // ------------------------------------------------ GEMM1 issuer
+        // GEMM1 and GEMM2 are issued by two threads (warps 1 and 3): each thread's stream of
+        // barrier waits, MMAs and commits is then half as long, and the waits of one overlap
+        // the MMAs of the other.  Their MMAs touch disjoint tensor memory (S vs P / Y) and
+        // every dependency between them runs through the evaluation warpgroups' barriers;
+        // a commit tracks the MMAs of its own thread.  Descriptors are built once and
+        // advanced by constant offsets (16-byte units).
         const uint32_t id1 = idesc_f16(TM, TN);
-        const uint32_t id2 = idesc_f16(TM, R_pad);
-        const uint64_t dA = sdesc(sA), dPB = sdesc(sPB), dV = sdesc(sVr);
-        const uint32_t b_units = b_bytes >> 4, v_units = v_bytes >> 4, va_units = v_atom >> 4;
+        const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
+        const uint32_t b_units = b_bytes >> 4;
         bool ok = mbar_wait(a_full, 0, s_err);
         // GEMM1 of tile it into S[it % 2], once the warpgroup has read S for tile it - 2.
-        auto gemm1 = [&](int it) -> bool {
+        for (int it = 0; ok && it < ntiles; ++it) {
             const int s = it % NPB, b = it & 1;
-            if (!mbar_wait(&pb_full[s], (it / NPB) & 1, s_err)) return false;
-            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
+            if (!mbar_wait(&pb_full[s], (it / NPB) & 1, s_err)) break;
+            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t db = dPB + (uint64_t)s * b_units;
             const uint32_t dS = tS0 + b * 128;
@@ -375,15 +378,23 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             }
             mma_commit(&pb_empty[s]);
             mma_commit(&s_full[b]);
-            return true;
-        };
-        if (ok) ok = gemm1(0);
-        if (ok && ntiles > 1) ok = gemm1(1);
-        for (int it = 0; ok && it < ntiles; ++it) {
+        }
+    } else if (warp == 3 && lane == 0 && ntiles > 0) {
+        // ------------------------------------------------ GEMM2 issuer: Y += P V
+        const uint32_t id2 = idesc_f16(TM, R_pad);
+        const uint64_t dV = sdesc(sVr);
+        const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
+        bool ok = true;
+        for (int it = 0; it < ntiles; ++it) {
             const int s = it % NV, b = it & 1;
-            if (it + 2 < ntiles && !gemm1(it + 2)) break;
-            if (!mbar_wait(&v_full[s], (it / NV) & 1, s_err)) break;
-            if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
+            if (!mbar_wait(&v_full[s], (it / NV) & 1, s_err)) {
+                ok = false;
+                break;
+            }
+            if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
             const uint64_t dv = dV + (uint64_t)s * v_units;
             const uint32_t aP = tP0 + b * 64;
@@ -395,6 +406,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             mma_commit(&v_empty[s]);
             mma_commit(&p_free[b]);
         }
+        (void)ok;
         mma_commit(y_full);
     } else if (warp >= 4) {
         // ------------------------------------------------ kernel evaluation + epilogue
@@ -1231,7 +1243,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(a_full, 1);
         for (int s = 0; s < MAX_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], 2);  // released by the GEMM1 and the GEMM3 issuer
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
@@ -1279,17 +1291,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tma_load_2d(sB3, &mapB3, &full[s], j0, 0);
         }
     } else if (warp == 1 && lane == 0 && ntiles > 0) {
+        // GEMM1 + GEMM-M issuer (GEMM3 has its own thread, warp 3: see the product kernel).
+        // A stage is released by two commits, one per issuing thread (empty[] counts 2).
         const uint32_t id1 = idesc_f16(TM, GTN);
-        const uint32_t id3 = idesc_f16(TM, p.N3p);
         // descriptors built once, advanced in 16-byte units (single-thread issue path)
         const uint64_t dA = sdesc(sA), dU = sdesc(sU), dSt = sdesc(sStages);
-        const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4, w_units = w_bytes >> 4;
+        const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4;
         constexpr uint32_t a_atom = (TM * 128) >> 4, g_atom = (GTN * 128) >> 4;
         bool ok = mbar_wait(a_full, 0, s_err);
-        auto gemm1 = [&](int it) -> bool {
+        for (int it = 0; ok && it < ntiles; ++it) {
             const int s = it % NS, b = it & 1;
-            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) return false;
-            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) return false;
+            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) break;
+            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t dB = dSt + (uint64_t)s * st_units;
             const uint64_t dW = dB + b_units;
@@ -1303,14 +1316,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
                 mma_ss(tM + b * GTN, dU + ka * a_atom + ko, dW + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
             }
+            mma_commit(&empty[s]);
             mma_commit(&s_full[b]);
-            return true;
-        };
-        if (ok) ok = gemm1(0);
-        if (ok && ntiles > 1) ok = gemm1(1);
-        for (int it = 0; ok && it < ntiles; ++it) {
+        }
+    } else if (warp == 3 && lane == 0 && ntiles > 0) {
+        // GEMM3 issuer: D3 += W1 [A | A^2]
+        const uint32_t id3 = idesc_f16(TM, p.N3p);
+        const uint64_t dSt = sdesc(sStages);
+        const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4, w_units = w_bytes >> 4;
+        for (int it = 0; it < ntiles; ++it) {
             const int s = it % NS, b = it & 1;
-            if (it + 2 < ntiles && !gemm1(it + 2)) break;
+            // the stage cannot be refilled before this thread's own release, so its phase
+            // is still the one GEMM1 saw
+            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) break;
             if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t dB3 = dSt + (uint64_t)s * st_units + b_units + w_units;
