@@ -121,112 +121,131 @@ namespace {
 
 constexpr int RP = 64;   // points per block
 constexpr int RFC = 32;  // frequencies per chunk
+constexpr int RS = 64;   // samples per block
 
 __device__ __forceinline__ void sc(float a, float *s, float *c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sc(double a, double *s, double *c) { sincos(a, s, c); }
 
+// Four consecutive shared-memory values (16-byte aligned for float).
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
 // F[j][i] = s_f sqrt(2/m) sum_l W[j][l] cos(w_l.x_i) + W[j][h+l] sin(w_l.x_i)
-template <typename T, int SPT>
+// Per block: 64 points x 64 samples; per chunk of 32 frequencies the block evaluates the
+// 64 x 32 cos/sin features into shared memory (frequency-major), then every thread
+// accumulates a 4 x 4 register tile (4 points x 4 samples) over the chunk.  Shared-memory
+// layouts avoid bank conflicts: point rows have an odd stride, and the weights (written
+// transposed) have their 4-sample groups XOR-swizzled by the frequency index.
+template <typename T>
 __global__ void __launch_bounds__(256) rff_kernel(const KP<T> kp, const T *X, int64_t n, int m,
                                                   const T *omega_hat, const T *chi2, const T *W, int s, T *F,
                                                   int64_t ldf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int d = kp.d, h = m / 2;
-    constexpr int SB = 16 * SPT;  // samples per block
-    T *Xs = reinterpret_cast<T *>(smem_raw);  // RP x d
-    T *Om = Xs + RP * d;                      // RFC x d
-    T *Cs = Om + RFC * d;                     // RP x (RFC+1)
-    T *Sn = Cs + RP * (RFC + 1);              // RP x (RFC+1)
-    T *Wc = Sn + RP * (RFC + 1);              // SB x (RFC+1)
-    T *Wsn = Wc + SB * (RFC + 1);             // SB x (RFC+1)
+    T *Cs = reinterpret_cast<T *>(smem_raw);  // RFC x RP   cos features
+    T *Sn = Cs + RFC * RP;                     // RFC x RP   sin features
+    T *Wc = Sn + RFC * RP;                     // RFC x RS   cos weights
+    T *Ws = Wc + RFC * RS;                     // RFC x RS   sin weights
+    T *Xs = Ws + RFC * RS;                     // RP x xd
+    const int xd = d | 1;
+    T *Om = Xs + RP * xd;                      // RFC x d    frequencies
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t p0 = (int64_t)blockIdx.x * RP;
-    const int j0 = blockIdx.y * SB;
+    const int j0 = blockIdx.y * RS;
     for (int e = tid; e < RP * d; e += 256) {
-        int r = e / d, k = e - r * d;
-        Xs[e] = (p0 + r < n) ? X[(p0 + r) * d + k] : T(0);
+        const int r = e / d, k = e - r * d;
+        Xs[r * xd + k] = (p0 + r < n) ? X[(p0 + r) * d + k] : T(0);
     }
-    T acc[4][SPT];
+    T acc[4][4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int q = 0; q < SPT; ++q) acc[p][q] = T(0);
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
     for (int l0 = 0; l0 < h; l0 += RFC) {
         __syncthreads();
         for (int e = tid; e < RFC * d; e += 256) {
-            int l = e / d, k = e - l * d;
+            const int l = e / d, k = e - l * d;
             T w = T(0);
             if (l0 + l < h) {
-                T t = (kp.kind == GP_MATERN32) ? sqrt(T(3) / chi2[l0 + l]) : T(1);
+                const T t = (kp.kind == GP_MATERN32) ? sqrt(T(3) / chi2[l0 + l]) : T(1);
                 w = omega_hat[(int64_t)(l0 + l) * d + k] * kp.inv_ell[k] * t;
             }
             Om[e] = w;
         }
-        for (int e = tid; e < SB * RFC; e += 256) {
-            int j = e / RFC, l = e - j * RFC;
-            bool ok = (j0 + j < s) && (l0 + l < h);
-            Wc[j * (RFC + 1) + l] = ok ? W[(int64_t)(j0 + j) * m + l0 + l] : T(0);
-            Wsn[j * (RFC + 1) + l] = ok ? W[(int64_t)(j0 + j) * m + h + l0 + l] : T(0);
+        for (int e = tid; e < RS * RFC; e += 256) {
+            const int j = e / RFC, l = e - j * RFC;
+            const bool ok = (j0 + j < s) && (l0 + l < h);
+            const int js = j ^ ((l & 7) << 2);
+            Wc[l * RS + js] = ok ? W[(int64_t)(j0 + j) * m + l0 + l] : T(0);
+            Ws[l * RS + js] = ok ? W[(int64_t)(j0 + j) * m + h + l0 + l] : T(0);
         }
         __syncthreads();
         for (int e = tid; e < RP * RFC; e += 256) {
-            int p = e / RFC, l = e - p * RFC;
+            const int l = e / RP, pnt = e - l * RP;
             T arg = T(0);
-            for (int k = 0; k < d; ++k) arg += Om[l * d + k] * Xs[p * d + k];
+            for (int k = 0; k < d; ++k) arg += Om[l * d + k] * Xs[pnt * xd + k];
             T sv, cv;
             sc(arg, &sv, &cv);
-            Cs[p * (RFC + 1) + l] = cv;
-            Sn[p * (RFC + 1) + l] = sv;
+            Cs[l * RP + pnt] = cv;
+            Sn[l * RP + pnt] = sv;
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
         for (int l = 0; l < RFC; ++l) {
-            T cv[4], sv[4];
+            T cv[4], sv[4], wc[4], ws[4];
+            ld4(Cs + l * RP + 4 * tx, cv);
+            ld4(Sn + l * RP + 4 * tx, sv);
+            const int jo = (4 * ty) ^ ((l & 7) << 2);
+            ld4(Wc + l * RS + jo, wc);
+            ld4(Ws + l * RS + jo, ws);
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                cv[p] = Cs[(tx + 16 * p) * (RFC + 1) + l];
-                sv[p] = Sn[(tx + 16 * p) * (RFC + 1) + l];
-            }
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int q = 0; q < SPT; ++q) {
-                T wc = Wc[(ty + 16 * q) * (RFC + 1) + l];
-                T ws = Wsn[(ty + 16 * q) * (RFC + 1) + l];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) acc[p][q] += cv[p] * wc + sv[p] * ws;
-            }
+                for (int b = 0; b < 4; ++b) acc[a][b] += cv[a] * wc[b] + sv[a] * ws[b];
         }
     }
     const T amp = kp.sf * sqrt(T(2) / T(m));
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        int64_t i = p0 + tx + 16 * p;
-        if (i >= n) continue;
+    for (int b = 0; b < 4; ++b) {
+        const int j = j0 + 4 * ty + b;
+        if (j >= s) continue;
 #pragma unroll
-        for (int q = 0; q < SPT; ++q) {
-            int j = j0 + ty + 16 * q;
-            if (j < s) F[(int64_t)j * ldf + i] = amp * acc[p][q];
+        for (int a = 0; a < 4; ++a) {
+            const int64_t i = p0 + 4 * tx + a;
+            if (i < n) F[(int64_t)j * ldf + i] = amp * acc[a][b];
         }
     }
 }
 
-template <typename T, int SPT>
+template <typename T>
 int launch_rff(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
                int s, T *F, int64_t ldf, cudaStream_t st) {
     const int d = kp.d;
-    constexpr int SB = 16 * SPT;
-    size_t smem = sizeof(T) * (size_t)(RP * d + RFC * d + 2 * RP * (RFC + 1) + 2 * SB * (RFC + 1));
+    size_t smem = sizeof(T) * (size_t)(2 * RFC * RP + 2 * RFC * RS + RP * (d | 1) + RFC * d);
     if (smem > kMaxDynSmem) {
         set_error("rff: d=%d too large", d);
         return GP_ERR_UNSUPPORTED;
     }
     static bool attr_set = false;
     if (!attr_set) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(rff_kernel<T, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxDynSmem));
+        GP_TRY_CUDA(cudaFuncSetAttribute(rff_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
         attr_set = true;
     }
-    dim3 grid((unsigned)cdiv(n, RP), (unsigned)cdiv(s, SB));
-    rff_kernel<T, SPT><<<grid, 256, smem, st>>>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf);
+    dim3 grid((unsigned)cdiv(n, RP), (unsigned)cdiv(s, RS));
+    rff_kernel<T><<<grid, 256, smem, st>>>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf);
     return check_launch("rff_kernel");
 }
 
@@ -235,9 +254,7 @@ int launch_rff(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat
 template <typename T>
 int rff_prior(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
               int s, T *F, int64_t ldf, cudaStream_t st) {
-    if (s <= 16) return launch_rff<T, 1>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
-    if (s <= 32) return launch_rff<T, 2>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
-    return launch_rff<T, 4>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
+    return launch_rff<T>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
 }
 template int rff_prior<float>(const KP<float> &, const float *, int64_t, int, const float *, const float *,
                               const float *, int, float *, int64_t, cudaStream_t);

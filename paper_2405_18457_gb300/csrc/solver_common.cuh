@@ -12,7 +12,9 @@ namespace {
 constexpr double kNormEps = 1e-12;   // eps of the normalisation b / (||b|| + eps)
 constexpr double kFreeze = 1e-30;    // CG column frozen once gamma <= this
 
-int nparts_for(int64_t n) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n, 8192))); }
+// Row partitions of the per-column partial sums: enough blocks (partitions x columns)
+// to fill the GPU for the vector updates, at most 64 partials per column.
+int nparts_for(int64_t n) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n, 2048))); }
 
 // part[c*P + p] = sum_{i in chunk p} A[c][i] * B[c][i]   (grid P x R)
 template <typename T>
@@ -68,12 +70,13 @@ __global__ void init_residual_kernel(const T *B, const T *HV, T *r, T *d, int64_
     }
 }
 
-// Split norms and the loop condition (App. B): res_y = ||r_y||, res_z = mean_j ||r_j||.
-__device__ void finish_norms(SolverState *st, const double *sq, int R, long long t, long long max_iters,
-                             double tol, int stop_rule) {
-    double ry = sqrt(sq[0]);
+// Split norms and the loop condition (App. B): res_y = ||r_y||, res_z = mean_j ||r_j||,
+// from rt[c] = ||r_c|| (the column norms, square roots already taken).
+__device__ void finish_state(SolverState *st, const double *rt, int R, long long t, long long max_iters, double tol,
+                             int stop_rule) {
+    double ry = rt[0];
     double rz = 0.0;
-    for (int c = 1; c < R; ++c) rz += sqrt(sq[c]);
+    for (int c = 1; c < R; ++c) rz += rt[c];
     rz = (R > 1) ? rz / (double)(R - 1) : 0.0;
     st->res_y = ry;
     st->res_z = rz;
@@ -87,6 +90,23 @@ __device__ void finish_norms(SolverState *st, const double *sq, int R, long long
     } else if (conv || t >= max_iters) {
         st->done = 1;
     }
+}
+
+// Single-thread form: sq[c] = ||r_c||^2.
+__device__ void finish_norms(SolverState *st, const double *sq, int R, long long t, long long max_iters,
+                             double tol, int stop_rule) {
+    double rt[512];
+    for (int c = 0; c < R; ++c) rt[c] = sqrt(sq[c]);
+    finish_state(st, rt, R, t, max_iters, tol, stop_rule);
+}
+
+// Block form, called by every thread of the block: sq (shared, R values) holds
+// ||r_c||^2 on entry and is overwritten with the norms.
+__device__ void finish_norms_block(SolverState *st, double *sq, int R, long long t, long long max_iters, double tol,
+                                   int stop_rule) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) sq[c] = sqrt(sq[c]);
+    __syncthreads();
+    if (threadIdx.x == 0) finish_state(st, sq, R, t, max_iters, tol, stop_rule);
 }
 
 }  // namespace

@@ -18,17 +18,20 @@ namespace {
 
 // ---------------------------------------------------------------- CG kernels
 // gamma = ||r||^2 after the initial residual; sets done if already converged.
+// One block, one thread per column (R <= 512).
 __global__ void cg_start_kernel(int R, int P, const double *part, double *gamma, SolverState *st,
                                 long long max_iters, double tol, int stop_rule) {
-    if (threadIdx.x != 0) return;
-    double sq[512];
-    for (int c = 0; c < R; ++c) {
+    __shared__ double sq[512];
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
         sq[c] = sum_parts(part, c, P);
         gamma[c] = sq[c];
     }
-    st->done = 0;
-    st->status = GP_OK;
-    finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
+    if (threadIdx.x == 0) {
+        st->done = 0;
+        st->status = GP_OK;
+    }
+    __syncthreads();
+    finish_norms_block(st, sq, R, 0, max_iters, tol, stop_rule);
 }
 
 // alpha = gamma / d^T H d, frozen columns get 0.
@@ -71,19 +74,21 @@ __global__ void cg_update_kernel(T *v, T *r, const T *d, const T *Hd, int64_t n,
 }
 
 // beta = gamma_new / gamma ; gamma = gamma_new ; norms ; t++ ; loop condition.
+// One block, one thread per column.
 __global__ void cg_beta_kernel(int R, int P, const double *part, double *gamma, const double *alpha, double *beta,
                                SolverState *st, long long max_iters, double tol, int stop_rule) {
     if (st->done) return;
-    if (threadIdx.x != 0) return;
-    double sq[512];
-    for (int c = 0; c < R; ++c) {
+    __shared__ double sq[512];
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
         double gn = sum_parts(part, c, P);
         bool active = alpha[c] != 0.0;
         beta[c] = active ? gn / gamma[c] : 0.0;
         if (active) gamma[c] = gn;
         sq[c] = active ? gn : gamma[c];
     }
-    finish_norms(st, sq, R, st->iter + 1, max_iters, tol, stop_rule);
+    const long long t = st->iter + 1;
+    __syncthreads();
+    finish_norms_block(st, sq, R, t, max_iters, tol, stop_rule);
 }
 
 // d = r + beta d
@@ -246,14 +251,17 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(op.apply(V, Hd, nullptr, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, Hd, r, dd, n, scale);
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
-    cg_start_kernel<<<1, 32, 0, st>>>(R, P, part, gamma, sd, (long long)max_iters, tol, stop_rule);
+    cg_start_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, sd, (long long)max_iters, tol, stop_rule);
     GP_TRY(check_launch("cg start", 3));
 
     // Iterations are enqueued speculatively in chunks without waiting for the start-up
     // kernels: once the device-side loop condition latches `done`, the remaining kernels
     // of a chunk return immediately, so a chunk overshoot costs only empty launches.
+    // Chunks of 8, 4, 4, 4, 8, 16, 32, 32, ... iterations between polls: a warm-started solve
+    // typically needs about ten, so few empty iterations are enqueued past convergence.
     SolverState hs{};
     int64_t launched = 0, chunk = 8;
+    int polls = 0;
     while (launched < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - launched);
         for (int64_t it = 0; it < k; ++it) {
@@ -261,13 +269,14 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
             cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
             cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
-            cg_beta_kernel<<<1, 32, 0, st>>>(R, P, part, gamma, alpha, beta, sd, (long long)max_iters, tol,
-                                             stop_rule);
+            cg_beta_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, beta, sd, (long long)max_iters, tol,
+                                              stop_rule);
             cg_dir_kernel<T><<<gv, 256, 0, st>>>(dd, r, n, beta, sd);
             GP_TRY(check_launch("cg iteration", 5));
         }
         launched += k;
-        chunk = std::min<int64_t>(chunk * 2, 32);
+        ++polls;
+        chunk = polls < 4 ? 4 : std::min<int64_t>(polls == 4 ? 8 : chunk * 2, 32);
         GP_TRY(poll_state(sd, &hs, st));
         if (hs.done) break;
     }

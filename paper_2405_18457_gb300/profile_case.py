@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--s", type=int, default=64)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--prec", choices=["tc16", "fp32"], default="tc16")
+    ap.add_argument("--time", action="store_true", help="print the mean time per call (CUDA events)")
     args = ap.parse_args()
     prec = gp.GP_PREC_TC16 if args.prec == "tc16" else gp.GP_PREC_FP32
     dev = torch.device("cuda:0")
@@ -34,15 +35,32 @@ def main():
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
     X = t(p.X)
     V = t(workloads.vectors(p.s + 1, p.n, seed=1))
-    for _ in range(args.repeat):
+    om, c2, Wp = t(p.omega_hat), t(p.chi2), t(p.W_probe)
+
+    def call():
         if args.op == "mvm":
             gp.gp_kernel_mvm(p.kind, p.theta, X, V, add_noise=True, prec=prec)
         elif args.op == "grad":
             gp.gp_mll_grad_pathwise(p.kind, p.theta, X, V, prec=prec)
         elif args.op == "rff":
-            gp.gp_rff_prior_sample(p.kind, p.theta, X, t(p.omega_hat), t(p.chi2), t(p.W_probe))
+            gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, Wp)
         else:
             gp.gp_solve_cg(p.kind, p.theta, X, V, max_iters=10, tol=0.0, prec=prec)
+
+    if args.time:
+        call()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.repeat):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        print("time_ms %s n=%d %.4f" % (args.op, args.n, e0.elapsed_time(e1) / args.repeat))
+        return
+    for _ in range(args.repeat):
+        call()
     torch.cuda.synchronize()
     print("done", args.op, args.n)
 
