@@ -248,11 +248,12 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     uint64_t *pb_empty = pb_full + MAX_RING;
     uint64_t *v_full = pb_empty + MAX_RING;
     uint64_t *v_empty = v_full + MAX_RING;
-    uint64_t *s_full = v_empty + MAX_RING;  // GEMM1 of a tile landed in S[b]
-    uint64_t *s_free = s_full + 2;          // evaluation warpgroup has read S[b]
-    uint64_t *p_full = s_free + 2;          // kernel values of the tile are in P[b]
-    uint64_t *p_free = p_full + 2;          // GEMM2 has consumed P[b]
-    uint64_t *y_full = p_free + 2;
+    // Three tile buffers in tensor memory, each holding S (fp32) and then, written over
+    // its first 64 columns, the packed fp16 kernel values P of the same tile.
+    uint64_t *t_full = v_empty + MAX_RING;  // GEMM1 of a tile landed in buffer b
+    uint64_t *t_kval = t_full + 3;          // the evaluation warpgroup wrote P into buffer b
+    uint64_t *t_free = t_kval + 3;          // GEMM2 has consumed buffer b
+    uint64_t *y_full = t_free + 3;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -303,11 +304,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             mbar_init(&v_full[s], 1);
             mbar_init(&v_empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&s_full[b], 1);
-            mbar_init(&s_free[b], 128);
-            mbar_init(&p_full[b], 128);
-            mbar_init(&p_free[b], 1);
+        for (int b = 0; b < 3; ++b) {
+            mbar_init(&t_full[b], 1);
+            mbar_init(&t_kval[b], 128);
+            mbar_init(&t_free[b], 1);
         }
         mbar_init(y_full, 1);
         *s_err = 0;
@@ -322,10 +322,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // Tensor memory: S[0..1] fp32 tiles at columns 0 / 128, P[0..1] packed fp16 kernel
-    // values at 256 / 320, the Y accumulator at 384 (R_pad <= 128 columns).
+    // Tensor memory: tile buffers 0..2 at columns 0 / 128 / 256 (S fp32; P packed fp16 over
+    // its first 64 columns), the Y accumulator at 384 (R_pad <= 128 columns).
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tS0 = tmem, tP0 = tmem + 256, tY = tmem + 384;
+    const uint32_t tS0 = tmem, tY = tmem + 384;
 
     if (warp == 0 && lane == 0 && ntiles > 0) {
         // ------------------------------------------------ TMA producer: row operand + PB ring
@@ -362,11 +362,11 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
         const uint32_t b_units = b_bytes >> 4;
         bool ok = mbar_wait(a_full, 0, s_err);
-        // GEMM1 of tile it into S[it % 2], once the warpgroup has read S for tile it - 2.
+        // GEMM1 of tile it into buffer it % 3, once GEMM2 of tile it - 3 has consumed it.
         for (int it = 0; ok && it < ntiles; ++it) {
-            const int s = it % NPB, b = it & 1;
+            const int s = it % NPB, b = it % 3;
             if (!mbar_wait(&pb_full[s], (it / NPB) & 1, s_err)) break;
-            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) break;
+            if (it >= 3 && !mbar_wait(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t db = dPB + (uint64_t)s * b_units;
             const uint32_t dS = tS0 + b * 128;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                 mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
             }
             mma_commit(&pb_empty[s]);
-            mma_commit(&s_full[b]);
+            mma_commit(&t_full[b]);
         }
     } else if (warp == 3 && lane == 0 && ntiles > 0) {
         // ------------------------------------------------ GEMM2 issuer: Y += P V
@@ -386,64 +386,55 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
         bool ok = true;
         for (int it = 0; it < ntiles; ++it) {
-            const int s = it % NV, b = it & 1;
+            const int s = it % NV, b = it % 3;
             if (!mbar_wait(&v_full[s], (it / NV) & 1, s_err)) {
                 ok = false;
                 break;
             }
-            if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) {
+            if (!mbar_wait(&t_kval[b], (it / 3) & 1, s_err)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             const uint64_t dv = dV + (uint64_t)s * v_units;
-            const uint32_t aP = tP0 + b * 64;
+            const uint32_t aP = tS0 + b * 128;
 #pragma unroll
             for (int k = 0; k < TN / 16; ++k) {
                 const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
                 mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
             }
             mma_commit(&v_empty[s]);
-            mma_commit(&p_free[b]);
+            mma_commit(&t_free[b]);
         }
         (void)ok;
         mma_commit(y_full);
     } else if (warp >= 4) {
         // ------------------------------------------------ kernel evaluation + epilogue
-        // Two warpgroups ping-pong: warpgroup wg owns S buffer wg, i.e. the tiles with
-        // it % 2 == wg, so one group evaluates while the other waits on tensor memory.
+        // Two warpgroups ping-pong: warpgroup wg evaluates the tiles with it % 2 == wg (in
+        // buffer it % 3), so one group evaluates while the other waits on tensor memory.
+        // Each thread owns one row: it reads 64 S columns, then writes their 64 kernel
+        // values (32 packed columns) over the columns it has just read, so P needs no
+        // buffer of its own and the warpgroup never waits for GEMM2.
         const int wg = (warp - 4) >> 2;
         const int wq = warp & 3;  // TMEM lane quarter this warp may access
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         const bool unit = (dsc == 1.0f);
         bool ok = true;
         for (int it = wg; it < ntiles; it += 2) {
-            const int b = it & 1;
-            if (!mbar_wait(&s_full[b], (it / 2) & 1, s_err)) {
+            const int b = it % 3;
+            if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             const uint32_t taS = tS0 + b * 128 + lane_off;
-            const uint32_t taP = tP0 + b * 64 + lane_off;
+            const uint32_t taP = taS;
 #pragma unroll 1
             for (int half = 0; half < 2; ++half) {
                 uint32_t r0[32], r1[32];
                 tmem_ld32(taS + half * 64, r0);
                 tmem_ld32(taS + half * 64 + 32, r1);
                 tmem_ld_wait();
-                if (half == 1) {
-                    // S[b] fully read: GEMM1 of tile it + 2 may overwrite it while we compute
-                    tc_fence_before();
-                    mbar_arrive(&s_free[b]);
-                } else if (it >= 2) {
-                    // P[b] must have been consumed by GEMM2 of tile it - 2
-                    if (!mbar_wait(&p_free[b], ((it / 2) - 1) & 1, s_err)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                }
                 uint32_t pk[16];
                 if (unit)
                     eval_chunk<KIND, false>(r0, pk, dsc);
@@ -459,7 +450,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             if (!ok) break;
             tmem_st_wait();
             tc_fence_before();
-            mbar_arrive(&p_full[b]);
+            mbar_arrive(&t_kval[b]);
         }
         // epilogue: Y rows from TMEM lanes, one row per thread; the two warpgroups
         // take alternate 16-column chunks of the right-hand sides
