@@ -41,9 +41,10 @@ namespace {
 
 constexpr int TM = 128;          // output rows per CTA
 constexpr int TN = 128;          // columns per tile
-constexpr int MAX_STAGES = 4;  // gradient kernel ring depth
+constexpr int MAX_STAGES = 6;  // gradient kernel: depth of the PB/W ring
+constexpr int MAX_B3 = 8;      // gradient kernel: depth of the [A | A^2] ring
 constexpr int MAX_RING = 8;    // product kernel: slots per ring (barrier arrays are sized for this)
-constexpr int NTHREADS = 384;     // gradient kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
+constexpr int NTHREADS = 416;     // gradient kernel: producer, 3 MMA issuers, 2 x 4 evaluation warps, producer
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -1180,7 +1181,8 @@ namespace {
 constexpr int GTN = 64;  // gradient column tile
 
 struct GParams {
-    int KD, KM, N3p, d, nstages;
+    int KD, KM, N3p, d, nstages, nb3;
+    int km_steps;  // K = 16 steps of GEMM-M that touch real right-hand sides (ceil(R / 16))
     int64_t n, col_tiles;
     int nsplit;
     const float *dscale;
@@ -1205,23 +1207,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t a_bytes = (uint32_t)TM * p.KD * 2, u_bytes = (uint32_t)TM * p.KM * 2;
     const uint32_t b_bytes = (uint32_t)GTN * p.KD * 2, w_bytes = (uint32_t)GTN * p.KM * 2;
     const uint32_t b3_bytes = (uint32_t)p.N3p * 128;
-    const uint32_t stage_bytes = b_bytes + w_bytes + b3_bytes;
+    const uint32_t stage_bytes = b_bytes + w_bytes;
+    const int NB3 = p.nb3;
+    // Two rings: PB/W tiles (read by GEMM1 and GEMM-M) and [A | A^2] tiles (read by GEMM3,
+    // about two tiles later), each released by its own readers so neither holds the other.
     uint8_t *sA = smem;
     uint8_t *sU = sA + a_bytes;
     uint8_t *sStages = sU + u_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sStages + (size_t)NS * stage_bytes);
+    uint8_t *sB3r = sStages + (size_t)NS * stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB3r + (size_t)NB3 * b3_bytes);
     uint64_t *a_full = bars;
     uint64_t *full = bars + 1;
     uint64_t *empty = full + MAX_STAGES;
-    uint64_t *s_full = empty + MAX_STAGES;  // GEMM1 + GEMM-M of a tile landed in S[b], M[b]
-    uint64_t *s_free = s_full + 2;          // evaluation warpgroup has read S[b] and M[b]
-    uint64_t *p_full = s_free + 2;          // W1 of the tile is in P[b]
-    uint64_t *p_free = p_full + 2;          // GEMM3 has consumed P[b]
-    uint64_t *y_full = p_free + 2;
+    uint64_t *b3_full = empty + MAX_STAGES;
+    uint64_t *b3_empty = b3_full + MAX_B3;
+    // Three tile buffers in tensor memory, each holding S and M of a tile and then, written
+    // over the S columns, the packed fp16 W1 of the same tile.
+    uint64_t *t_full = b3_empty + MAX_B3;   // GEMM1 and GEMM-M of a tile landed (2 commits)
+    uint64_t *t_kval = t_full + 3;          // the evaluation warpgroup wrote W1 into buffer b
+    uint64_t *t_free = t_kval + 3;          // GEMM3 has consumed buffer b
+    uint64_t *y_full = t_free + 3;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red = reinterpret_cast<double *>(smem_raw);  // reused after the pipeline (reduction scratch)
-    double *xch = reinterpret_cast<double *>(bars + 32);   // 256 doubles: per-row sums of warpgroup 1
+    double *xch = reinterpret_cast<double *>(bars + 64);   // 256 doubles: per-row sums of warpgroup 1
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TM;
@@ -1234,13 +1243,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_init(a_full, 1);
         for (int s = 0; s < MAX_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);  // released by the GEMM1 and the GEMM3 issuer
+            mbar_init(&empty[s], 2);  // released by the GEMM1 and GEMM-M issuers
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&s_full[b], 1);
-            mbar_init(&s_free[b], 128);
-            mbar_init(&p_full[b], 128);
-            mbar_init(&p_free[b], 1);
+        for (int q = 0; q < MAX_B3; ++q) {
+            mbar_init(&b3_full[q], 1);
+            mbar_init(&b3_empty[q], 1);
+        }
+        for (int b = 0; b < 3; ++b) {
+            mbar_init(&t_full[b], 2);
+            mbar_init(&t_kval[b], 128);
+            mbar_init(&t_free[b], 1);
         }
         mbar_init(y_full, 1);
         *s_err = 0;
@@ -1255,10 +1267,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // Tensor memory: S[0..1] at columns 0 / 64, M[0..1] at 128 / 192, P[0..1] (packed fp16
-    // W1) at 256 / 288, the D3 accumulator at 320 (N3p <= 192 columns).
+    // Tensor memory: tile buffers 0..2 at columns 0 / 128 / 256, each with S at +0 (W1
+    // packed over its first 32 columns) and M at +64; the D3 accumulator at 384 (N3p <= 128).
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tS = tmem, tM = tmem + 128, tP = tmem + 256, tD = tmem + 320;
+    const uint32_t tS = tmem, tD = tmem + 384;
 
     double g_acc[1];  // silence unused warnings in non-epilogue warps
     (void)g_acc;
@@ -1275,77 +1287,89 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int j0 = (int)((t0 + it) * GTN);
             uint8_t *sB = sStages + (size_t)s * stage_bytes;
             uint8_t *sW = sB + b_bytes;
-            uint8_t *sB3 = sW + w_bytes;
             mbar_expect_tx(&full[s], stage_bytes);
             for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (GTN * 128), &mapB, &full[s], ka * 64, j0);
             for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sW + ka * (GTN * 128), &mapW, &full[s], ka * 64, j0);
-            tma_load_2d(sB3, &mapB3, &full[s], j0, 0);
         }
-    } else if (warp == 1 && lane == 0 && ntiles > 0) {
-        // GEMM1 + GEMM-M issuer (GEMM3 has its own thread, warp 3: see the product kernel).
-        // A stage is released by two commits, one per issuing thread (empty[] counts 2).
+    } else if (warp == 12 && lane == 0 && ntiles > 0) {
+        // ------------------------------------------------ TMA producer: [A | A^2] ring
+        for (int it = 0; it < ntiles; ++it) {
+            const int q = it % NB3;
+            if (it >= NB3 && !mbar_wait(&b3_empty[q], ((it / NB3) - 1) & 1, s_err)) break;
+            const int j0 = (int)((t0 + it) * GTN);
+            mbar_expect_tx(&b3_full[q], b3_bytes);
+            tma_load_2d(sB3r + (size_t)q * b3_bytes, &mapB3, &b3_full[q], j0, 0);
+        }
+    } else if ((warp == 1 || warp == 2) && lane == 0 && ntiles > 0) {
+        // GEMM1 (warp 1) and GEMM-M (warp 2) issuers; GEMM3 has a third thread (warp 3).
+        // Three short issue streams instead of one long one; each stage and each tile buffer
+        // is released by a commit of every thread that read it (empty[] and t_full[] count 2).
         const uint32_t id1 = idesc_f16(TM, GTN);
-        // descriptors built once, advanced in 16-byte units (single-thread issue path)
+        // descriptors built once, advanced in 16-byte units (single-thread issue paths)
         const uint64_t dA = sdesc(sA), dU = sdesc(sU), dSt = sdesc(sStages);
         const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4;
         constexpr uint32_t a_atom = (TM * 128) >> 4, g_atom = (GTN * 128) >> 4;
+        const bool is_g1 = (warp == 1);
         bool ok = mbar_wait(a_full, 0, s_err);
         for (int it = 0; ok && it < ntiles; ++it) {
-            const int s = it % NS, b = it & 1;
+            const int s = it % NS, b = it % 3;
             if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) break;
-            if (it >= 2 && !mbar_wait(&s_free[b], ((it / 2) - 1) & 1, s_err)) break;
+            if (it >= 3 && !mbar_wait(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t dB = dSt + (uint64_t)s * st_units;
-            const uint64_t dW = dB + b_units;
+            if (is_g1) {
 #pragma unroll
-            for (int k = 0; k < 4 * KAT; ++k) {
-                const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                mma_ss(tS + b * GTN, dA + ka * a_atom + ko, dB + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
-            }
-            const int km = p.KM / 16;
-            for (int k = 0; k < km; ++k) {
-                const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                mma_ss(tM + b * GTN, dU + ka * a_atom + ko, dW + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
+                for (int k = 0; k < 4 * KAT; ++k) {
+                    const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                    mma_ss(tS + b * 128, dA + ka * a_atom + ko, dB + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
+                }
+            } else {
+                const uint64_t dW = dB + b_units;
+                const int km = p.km_steps;  // the zero-padded columns beyond R are skipped
+                for (int k = 0; k < km; ++k) {
+                    const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                    mma_ss(tS + b * 128 + 64, dU + ka * a_atom + ko, dW + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
+                }
             }
             mma_commit(&empty[s]);
-            mma_commit(&s_full[b]);
+            mma_commit(&t_full[b]);
         }
     } else if (warp == 3 && lane == 0 && ntiles > 0) {
         // GEMM3 issuer: D3 += W1 [A | A^2]
         const uint32_t id3 = idesc_f16(TM, p.N3p);
-        const uint64_t dSt = sdesc(sStages);
-        const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4, w_units = w_bytes >> 4;
+        const uint64_t dB3r = sdesc(sB3r);
+        const uint32_t b3_units = b3_bytes >> 4;
         for (int it = 0; it < ntiles; ++it) {
-            const int s = it % NS, b = it & 1;
-            // the stage cannot be refilled before this thread's own release, so its phase
-            // is still the one GEMM1 saw
-            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) break;
-            if (!mbar_wait(&p_full[b], (it / 2) & 1, s_err)) break;
+            const int q = it % NB3, b = it % 3;
+            if (!mbar_wait(&b3_full[q], (it / NB3) & 1, s_err)) break;
+            if (!mbar_wait(&t_kval[b], (it / 3) & 1, s_err)) break;
             tc_fence_after();
-            const uint64_t dB3 = dSt + (uint64_t)s * st_units + b_units + w_units;
+            const uint64_t dB3 = dB3r + (uint64_t)q * b3_units;
 #pragma unroll
             for (int k = 0; k < GTN / 16; ++k)
-                mma_ts(tD, tP + b * 32 + k * 8, dB3 + (uint32_t)k * 2, id3, (it > 0 || k > 0) ? 1u : 0u);
-            mma_commit(&empty[s]);
-            mma_commit(&p_free[b]);
+                mma_ts(tD, tS + b * 128 + k * 8, dB3 + (uint32_t)k * 2, id3, (it > 0 || k > 0) ? 1u : 0u);
+            mma_commit(&b3_empty[q]);
+            mma_commit(&t_free[b]);
         }
         mma_commit(y_full);
-    } else if (warp >= 4) {
-        // two evaluation warpgroups; warpgroup wg owns buffers wg (tiles it % 2 == wg)
+    } else if (warp >= 4 && warp < 12) {
+        // two evaluation warpgroups; warpgroup wg takes the tiles with it % 2 == wg (buffer
+        // it % 3).  Each thread owns one row and writes the 32 packed W1 columns of a chunk
+        // over S columns it has already read.
         const int wg = (warp - 4) >> 2;
         const int wq = warp & 3;
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         const float dsc = *p.dscale;
         bool ok = true;
         for (int it = wg; it < ntiles; it += 2) {
-            const int b = it & 1;
-            if (!mbar_wait(&s_full[b], (it / 2) & 1, s_err)) {
+            const int b = it % 3;
+            if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t taS = tS + b * GTN + lane_off, taM = tM + b * GTN + lane_off;
-            const uint32_t taP = tP + b * (GTN / 2) + lane_off;
+            const uint32_t taS = tS + b * 128 + lane_off, taM = taS + 64;
+            const uint32_t taP = taS;
             float rs = 0.0f, sk = 0.0f;
 #pragma unroll 1
             for (int ch = 0; ch < GTN / 32; ++ch) {
@@ -1353,19 +1377,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(taS + ch * 32, rS);
                 tmem_ld32(taM + ch * 32, rM);
                 tmem_ld_wait();
-                if (ch == GTN / 32 - 1) {
-                    // S[b] and M[b] fully read: the next GEMMs into them may start
-                    tc_fence_before();
-                    mbar_arrive(&s_free[b]);
-                }
-                if (ch == 0 && it >= 2) {
-                    // P[b] must have been consumed by GEMM3 of tile it - 2
-                    if (!mbar_wait(&p_free[b], ((it / 2) - 1) & 1, s_err)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                }
                 uint32_t pk[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
@@ -1397,7 +1408,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!ok) break;
             tmem_st_wait();
             tc_fence_before();
-            mbar_arrive(&p_full[b]);
+            mbar_arrive(&t_kval[b]);
             rs_acc += (double)rs;
             s_acc += (double)sk;
         }
@@ -1536,7 +1547,7 @@ __global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int6
 }
 
 struct GradPlanTc {
-    int KD, KM, N3p, ns, nsplit;
+    int KD, KM, N3p, ns, nb3, nsplit;
     int64_t n_pad, row_tiles, col_tiles;
     size_t smem;
 };
@@ -1564,20 +1575,28 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
     g.col_tiles = g.n_pad / GTN;
     g.nsplit = pick_split(g.row_tiles, g.col_tiles);
     const size_t a = (size_t)TM * g.KD * 2 + (size_t)TM * g.KM * 2;
-    const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2 + (size_t)g.N3p * 128;
-    g.ns = (int)std::min<size_t>(MAX_STAGES, (kMaxDynSmem - 4096 - a) / st);
-    g.smem = 1024 + a + (size_t)g.ns * st + 256 + 2048;  // + barriers, + row-sum exchange
+    const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2;
+    const size_t b3 = (size_t)g.N3p * 128;
+    const size_t budget = kMaxDynSmem - 1024 - 512 - 2048 - a;  // alignment, barriers, row-sum exchange
+    g.nb3 = (int)std::min<size_t>(6, std::max<size_t>(2, budget / 3 / b3));
+    g.ns = (int)std::min<size_t>(MAX_STAGES, (budget - (size_t)g.nb3 * b3) / st);
+    g.smem = 1024 + a + (size_t)g.ns * st + (size_t)g.nb3 * b3 + 512 + 2048;
     return g;
 }
 
 }  // namespace
 
-// The tensor-core estimator covers d <= 48 (D3 accumulator of 4d columns in tensor
-// memory) and s + 1 <= 256; wider problems use the CUDA-core FP32 reduction.
-static bool tc_grad_fits(int d, int R) { return d <= 48 && R <= 256; }
+// The tensor-core estimator covers d <= 32 (D3 accumulator of 4d columns next to three
+// 128-column tile buffers in tensor memory) and s + 1 <= 256; wider problems use the
+// CUDA-core FP32 reduction.
+static bool tc_grad_fits(int64_t n, int d, int R) {
+    if (d > 32 || R > 256) return false;
+    const GradPlanTc g = plan_tc_grad(n, d, R);
+    return g.ns >= 2 && g.nb3 >= 2;
+}
 
 size_t tc_grad_workspace(int64_t n, int d, int R) {
-    if (!tc_grad_fits(d, R)) return grad_simt_workspace<float>(n, d, R);
+    if (!tc_grad_fits(n, d, R)) return grad_simt_workspace<float>(n, d, R);
     GradPlanTc g = plan_tc_grad(n, d, R);
     Carver c(nullptr);
     c.take<char>(tc_points_bytes(n, d));
@@ -1594,9 +1613,9 @@ size_t tc_grad_workspace(int64_t n, int d, int R) {
 
 int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int d = a.kp.d;
-    if (!tc_grad_fits(d, a.R)) return grad_simt<float>(a, ws, ws_bytes, st);
+    if (!tc_grad_fits(a.n, d, a.R)) return grad_simt<float>(a, ws, ws_bytes, st);
     GradPlanTc g = plan_tc_grad(a.n, d, a.R);
-    if (g.ns < 2) {
+    if (g.ns < 2 || g.nb3 < 2) {
         set_error("tensor-core gradient tile does not fit shared memory");
         return GP_ERR_UNSUPPORTED;
     }
@@ -1633,9 +1652,11 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     GParams p{};
     p.KD = g.KD;
     p.KM = g.KM;
+    p.km_steps = (int)cdiv(a.R, 16);
     p.N3p = g.N3p;
     p.d = d;
     p.nstages = g.ns;
+    p.nb3 = g.nb3;
     p.n = a.n;
     p.col_tiles = g.col_tiles;
     p.nsplit = g.nsplit;
@@ -1648,7 +1669,7 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     p.partial = partial;
     p.err = err;
     dim3 grid((unsigned)g.row_tiles, (unsigned)g.nsplit);
-    const int kat = g.KD / 64;  // <= 3 since d <= 48
+    const int kat = g.KD / 64;  // <= 2 since d <= 32
     prof_begin(st, 1);
     if (a.kp.kind == GP_RBF) {
         if (kat == 1) GP_TRY(launch_grad_kernel<GP_RBF, 1>(grid, g.smem, mA, mB, mU, mW, mB3, p, st));
