@@ -321,7 +321,13 @@ __global__ void ap_norm_kernel(int R, int P, const double *part, SolverState *st
 
 template <typename T>
 static size_t ap_panel_ws(int64_t n, int64_t bs, int d, int R, int prec) {
-    (void)prec;
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16) {
+        // tensor-core panel: all points prepared once per solve + the product's own scratch
+        Carver c(nullptr);
+        c.take<char>(tc_points_bytes(n, d));
+        c.take<char>(tc_mvm_workspace(n, bs, R));
+        return c.bytes();
+    }
     return mvm_simt_workspace<T>(n, bs, R);
 }
 
@@ -448,6 +454,43 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     pa.ldvd = bs;
     pa.diag_from_col0 = 1;
     pa.done = &sd->done;
+    // Tensor-core panel: K(X, X[col0 : col0 + bs]) over all points prepared once per solve
+    // (after the initial residual, whose product used the same scratch), the block offset
+    // read on the device.
+    bool tc_panel = false;
+    TcMvmArgs ta{};
+    void *tw = nullptr;
+    size_t twb = 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (prec == GP_PREC_TC16) {
+            tc_panel = true;
+            Carver pc(mw);
+            void *pbuf = pc.take<char>(tc_points_bytes(n, kp.d));
+            twb = tc_mvm_workspace(n, bs, R);
+            tw = pc.take<char>(twb);
+            TcPoints pts;
+            GP_TRY(tc_prepare_points(kp, X, n, pbuf, &pts, st));
+            ta.kind = kp.kind;
+            ta.rows = pts;
+            ta.cols = pts;
+            ta.ncols = bs;
+            ta.col0_dev = col0;
+            ta.diag_from_col0 = 1;
+            ta.V = delta;
+            ta.ldv = bs;
+            ta.R = R;
+            ta.Y = r;
+            ta.ldy = n;
+            ta.sf2 = kp.sf2;
+            ta.alpha = -1.0f;
+            ta.beta = 1.0f;
+            ta.diag_coef = -kp.sigma2;
+            ta.Vd = delta;
+            ta.ldvd = bs;
+            ta.ndiag = bs;
+            ta.done = &sd->done;
+        }
+    }
     const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16));
     int64_t t = 0, chunk = 8;
     while (!hs.done && t < max_iters) {
@@ -458,7 +501,15 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             ap_delta_kernel<T><<<gdel, 256, 0, st>>>(Hb, bsp, bs, r, n, R, col0, delta, sd);
             ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, col0, delta, sd);
             GP_TRY(check_launch("ap iteration", 4));
-            GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
+            if constexpr (std::is_same<T, float>::value) {
+                if (tc_panel) {
+                    GP_TRY(tc_mvm(ta, tw, twb, st));
+                } else {
+                    GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
+                }
+            } else {
+                GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
+            }
             coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, &sd->done);
             ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 0);
             GP_TRY(check_launch("ap norms", 2));

@@ -229,8 +229,19 @@ struct TcMvmArgs {
     int64_t ldvd;
     int64_t drow0, ndiag;
     const int *done;
+    // Column panels (alternating projections): the product runs over ncols columns of
+    // `cols` starting at the device-resident point offset *col0_dev (V has ncols entries
+    // per right-hand side); with diag_from_col0 the diagonal rows start there as well
+    // (clipped to cols.n).  ncols = 0 and col0_dev = null: all columns of `cols`.
+    int64_t ncols;
+    const int64_t *col0_dev;
+    int diag_from_col0;
 };
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R);
+// Row operand for points X1 that are a subset of an already prepared set `like` (same
+// scale): the batch rows of the stochastic-gradient panel.
+int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPoints &like, void *buf, TcPoints *out,
+                    cudaStream_t st);
 int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st);
 bool tc_available();
 

@@ -417,6 +417,15 @@ __global__ void sgd_norm_kernel(int R, int nb, const double *dpart, double *rsq,
 
 template <typename T>
 static size_t sgd_panel_ws(int64_t batch, int64_t n, int d, int R, int prec) {
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16) {
+        // tensor-core panel: all points as columns (prepared once per solve), the batch rows
+        // (prepared every iteration with the same scale), the product's own scratch
+        Carver c(nullptr);
+        c.take<char>(tc_points_bytes(n, d));
+        c.take<char>(tc_points_bytes(batch, d));
+        c.take<char>(tc_mvm_workspace(batch, n, R));
+        return c.bytes();
+    }
     return mvm_workspace<T>(batch, n, d, R, prec);
 }
 
@@ -480,6 +489,31 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
 
     SolverState hs{};
     GP_TRY(poll_state(sd, &hs, st));
+    // Tensor-core row panel G = K(X_b, X) V: columns prepared once per solve, rows per iteration.
+    TcMvmArgs ta{};
+    void *rbuf = nullptr, *tw = nullptr;
+    size_t twb = 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (prec == GP_PREC_TC16) {
+            Carver pc(pw);
+            void *cbuf = pc.take<char>(tc_points_bytes(n, d));
+            rbuf = pc.take<char>(tc_points_bytes(batch, d));
+            twb = tc_mvm_workspace(batch, n, R);
+            tw = pc.take<char>(twb);
+            GP_TRY(tc_prepare_points(kp, X, n, cbuf, &ta.cols, st));
+            ta.kind = kp.kind;
+            ta.V = V;
+            ta.ldv = n;
+            ta.R = R;
+            ta.Y = G;
+            ta.ldy = batch;
+            ta.sf2 = kp.sf2;
+            ta.alpha = 1.0f;
+            ta.beta = 0.0f;
+            ta.diag_coef = 0.0f;
+            ta.done = &sd->done;
+        }
+    }
     int64_t t = 0, chunk = 8;
     const T lrb = (T)(lr / (double)batch);
     while (!hs.done && t < max_iters) {
@@ -491,8 +525,8 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
             // G = K(X_b, X) V   (row panel H[i, :] v without the noise term)
             if constexpr (std::is_same<T, float>::value) {
                 if (prec == GP_PREC_TC16) {
-                    // The tensor-core panel re-prepares the batch points each iteration.
-                    GP_TRY(apply_mvm<float>(kp, Xb, batch, X, n, V, n, R, G, batch, 0, prec, pw, pwb, st));
+                    GP_TRY(tc_prepare_rows(kp, Xb, batch, ta.cols, rbuf, &ta.rows, st));
+                    GP_TRY(tc_mvm(ta, tw, twb, st));
                 } else {
                     MvmArgs<T> a{};
                     a.kp = kp; a.X1 = Xb; a.n1 = batch; a.X2 = X; a.n2 = n; a.n2_total = n;

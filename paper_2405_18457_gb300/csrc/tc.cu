@@ -221,6 +221,10 @@ struct KParams {
     const BItem *items;     // null: single problem, grid = row tiles x splits
     const BMember *members;
     const int *mdone;
+    // single mode, column panels: PB rows start at *col0_dev (device-resident offset)
+    const int64_t *col0_dev;
+    int diag_from_col0;     // diagonal rows start at *col0_dev, clipped to ncols_total
+    int64_t ncols_total;
 };
 
 template <int KIND, int KAT>  // KAT: 64-wide atoms of the distance contraction (KD / 64)
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     // Work of this CTA: rows [row0, row0 + 128) of PA against ntiles column tiles of PB
     // starting at tile tb0 (V16 tile tv0); output rows are local rows ioff + lane row
     // of the vectors at Yp.
-    int64_t row0, tb0, tv0, ioff;
+    int64_t row0, tb0, tv0, ioff, pb_off = 0;
     int ntiles;
     int64_t n1 = p.n1, ldy = p.ldy, ldvd = p.ldvd, drow0 = p.drow0, ndiag = p.ndiag;
     float sf2 = p.sf2, diag_coef = p.diag_coef, dsc;
@@ -295,6 +299,13 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         tv0 = tb0;
         ioff = row0;
         dsc = *p.dscale;
+        if (p.col0_dev) {
+            pb_off = *p.col0_dev;
+            if (p.diag_from_col0) {
+                drow0 = pb_off;
+                ndiag = min(ndiag, p.ncols_total - pb_off);
+            }
+        }
     }
 
     if (threadIdx.x == 0) {
@@ -335,7 +346,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NPB;
             if (it >= NPB && !mbar_wait(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
-            const int j0 = (int)((tb0 + it) * TN);
+            const int j0 = (int)((tb0 + it) * TN + pb_off);
             uint8_t *sB = sPB + (size_t)s * b_bytes;
             mbar_expect_tx(&pb_full[s], b_bytes);
             for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
@@ -498,12 +509,17 @@ __global__ void tc_reduce_kernel(KParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (i >= p.n1) return;
+    int64_t drow0 = p.drow0, ndiag = p.ndiag;
+    if (p.col0_dev && p.diag_from_col0) {
+        drow0 = *p.col0_dev;
+        ndiag = min(ndiag, p.ncols_total - drow0);
+    }
     float s = 0.0f;
     for (int sp = 0; sp < p.nsplit; ++sp) s += p.partial[((int64_t)sp * p.R + c) * p.n1 + i];
     float y = p.alpha * s;
     if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
-    if (p.diag_coef != 0.0f && i >= p.drow0 && i < p.drow0 + p.ndiag)
-        y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - p.drow0)];
+    if (p.diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
+        y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - drow0)];
     p.Y[(int64_t)c * p.ldy + i] = y;
 }
 
@@ -826,21 +842,20 @@ int num_sms_tc() {
     return sms;
 }
 
+// Column splits per row tile: minimises (waves of CTAs) x (tiles per CTA + a fixed per-CTA
+// cost of about four tiles: tensor-memory allocation, first loads, epilogue); every split
+// owns at least one tile.  Few row tiles (a stochastic-gradient row panel) get many splits.
 int pick_split(int64_t row_tiles, int64_t col_tiles) {
-    const int sms = num_sms_tc();
+    const int64_t sms = num_sms_tc();
+    const int64_t smax = std::min<int64_t>(256, std::max<int64_t>(1, col_tiles));
     int best = 1;
-    double best_eff = 0.0;
-    for (int s = 1; s <= 8; ++s) {
-        if (col_tiles / s < 4 && s > 1) break;
-        if (cdiv(col_tiles, s) * (s - 1) >= col_tiles) continue;  // every split must own a tile
-        int64_t units = row_tiles * s;
-        double waves = (double)units / sms;
-        double eff = waves / std::ceil(waves);
-        // splitting costs a partial write/read per split: prefer fewer splits
-        eff -= 0.01 * (s - 1);
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
-            best = s;
+    int64_t best_cost = INT64_MAX;
+    for (int64_t s = 1; s <= smax; ++s) {
+        if (s > 1 && cdiv(col_tiles, s) * (s - 1) >= col_tiles) continue;
+        const int64_t cost = cdiv(row_tiles * s, sms) * (cdiv(col_tiles, s) + 4) + (s > 1 ? 1 : 0);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (int)s;
         }
     }
     return best;
@@ -952,6 +967,22 @@ int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const floa
     return GP_OK;
 }
 
+int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPoints &like, void *buf, TcPoints *out,
+                    cudaStream_t st) {
+    const int KD = like.KD;
+    const int64_t p1 = rup(std::max<int64_t>(n1, 1), TM);
+    Carver c(buf);
+    __half *PA = c.take<__half>((size_t)p1 * KD);
+    const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
+    // the bound of the prepared superset fixes the same power-of-two scale
+    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, p1, KD,
+                                                                                          like.bound, PA, nullptr,
+                                                                                          nullptr);
+    GP_TRY(check_launch("tc row preparation"));
+    *out = TcPoints{PA, nullptr, n1, p1, KD, like.dscale, like.bound};
+    return GP_OK;
+}
+
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
     const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
     const int R_pad = rpad_for(std::min(R, kMaxRhsPerPass));
@@ -980,7 +1011,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         }
         return GP_OK;
     }
-    const int64_t n1 = a.rows.n, n2 = a.cols.n;
+    const int64_t n1 = a.rows.n, n2 = a.ncols > 0 ? a.ncols : a.cols.n;
     if (n1 == 0 || a.R == 0) return GP_OK;
     const int KD = a.rows.KD;
     const int R_pad = rpad_for(a.R);
@@ -1034,6 +1065,9 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.partial = partial;
     kp.done = a.done;
     kp.err = err;
+    kp.col0_dev = a.col0_dev;
+    kp.diag_from_col0 = a.diag_from_col0;
+    kp.ncols_total = a.cols.n;
     const size_t smem = smem_for(KD, R_pad, npb, nv);
     dim3 grid((unsigned)row_tiles, (unsigned)nsplit);
     const int kat = KD / 64;

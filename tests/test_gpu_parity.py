@@ -255,6 +255,63 @@ def test_ap_converges_to_dense_solution(dev):
     assert rel(V.cpu().numpy(), np.linalg.solve(H, B.T).T) < 1e-8
 
 
+@pytest.mark.parametrize("n,bs", [(250, 64), (300, 128), (130, 130)])
+def test_tc16_ap_iterates_match_oracle(dev, n, bs):
+    """Tensor-core column panel (device-resident block offset): a few iterations of Alg. 2
+    against the oracle; the fp16 panel error is below 1e-3 per iteration."""
+    if not tc_built():
+        pytest.skip("tensor-core path not built")
+    rng = np.random.default_rng(n + 1)
+    d, R = 5, 4
+    X = rng.standard_normal((n, d))
+    th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.4]])
+    B = rng.standard_normal((R, n))
+    X32 = X.astype(np.float32)
+    iters = 3
+    V, info = gp.gp_solve_ap(oracle.RBF, th, t(X32, dev), t(B, dev), block_size=bs, max_iters=iters, tol=0.0,
+                             prec=gp.GP_PREC_TC16)
+    Vr, ir = oracle.solve_ap(oracle.RBF, th, X32.astype(np.float64), B.astype(np.float32).astype(np.float64),
+                             block_size=bs, max_iters=iters, tol=0.0)
+    assert info.iters == ir["iters"] == iters
+    assert rel(V.double().cpu().numpy(), Vr) < 5e-3
+
+
+def test_tc16_ap_reaches_tolerance_true_residual(dev):
+    """Alg. 2 with the tensor-core panel to tau = 0.01 on the pathwise workload's shape; the true
+    FP64 residual of the returned solution meets tau."""
+    if not tc_built():
+        pytest.skip("tensor-core path not built")
+    p = workloads.pathwise(n=2000, d=8, s=8, m=256, seed=5)
+    X32 = p.X.astype(np.float32)
+    B = np.vstack([p.y_noise, p.Z]).astype(np.float32)
+    V, info = gp.gp_solve_ap(p.kind, p.theta, t(X32, dev), t(B, dev), block_size=256, max_iters=4000, tol=1e-2,
+                             prec=gp.GP_PREC_TC16)
+    assert info.converged
+    Xr, Br = X32.astype(np.float64), B.astype(np.float64)
+    r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
+    rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
+    assert rn[0] <= 1.5e-2 and rn[1:].mean() <= 1.5e-2
+
+
+def test_tc16_sgd_iterates_match_oracle(dev):
+    """Tensor-core row panel (batch rows against all points, many column splits): a few
+    iterations of Alg. 3 against the oracle."""
+    if not tc_built():
+        pytest.skip("tensor-core path not built")
+    rng = np.random.default_rng(19)
+    n, d, R, batch, iters = 3000, 4, 4, 64, 4
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.6]])
+    B = rng.standard_normal((R, n)).astype(np.float32)
+    idx = workloads.sgd_batches(n, batch, iters, seed=6)
+    V, info = gp.gp_solve_sgd(oracle.MATERN32, th, t(X, dev), t(B, dev), torch.tensor(idx, dtype=torch.int32, device=dev),
+                              lr=2.0, momentum=0.9, tol=0.0, prec=gp.GP_PREC_TC16)
+    Vr, ir = oracle.solve_sgd(oracle.MATERN32, th, X.astype(np.float64), B.astype(np.float64), idx, batch=batch,
+                              lr=2.0, momentum=0.9, max_iters=iters, tol=0.0)
+    assert info.iters == ir["iters"] == iters
+    assert rel(V.double().cpu().numpy(), Vr) < 5e-3
+
+
 @pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-9), ("f32", gp.GP_PREC_FP32, 1e-4)])
 def test_sgd_iterates_match_oracle(dev, prec_name, prec, tol):
     rng = np.random.default_rng(9)
