@@ -22,6 +22,8 @@ from ._binding import (  # noqa: F401
     GPError,
     SolveInfo,
     gp_adam_softplus_step,
+    gp_autotune_mvm,
+    gp_autotune_reset,
     gp_bilinear_grad,
     gp_diag_kernel_time,
     gp_diag_launches,

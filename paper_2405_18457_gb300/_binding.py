@@ -96,6 +96,9 @@ _SIGS = {
     "gp_batch_adam_init": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gp_batch_adam_step": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _d, _d, _vp, _vp]),
     "gp_batch_step": (_i, [_vp, _vp, _vp, _vp, _vp, _i64, _d, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp]),
+    "gp_autotune_mvm": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i, ctypes.POINTER(_i), _pd, _vp, _sz, _vp]),
+    "gp_autotune_mvm_workspace": (_sz, [_i64, _i, _i]),
+    "gp_autotune_reset": (None, []),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
@@ -231,6 +234,28 @@ def gp_kernel_mvm(kind, theta, X1, V, X2=None, add_noise=False, prec=GP_PREC_TC1
         _check(lib.gp_kernel_mvm(kind, thp, d, _ptr(X1), n1, _ptr(X2), n2, _ptr(V), n2, R, _ptr(Y), n1,
                                  int(bool(add_noise)), prec, _ptr(ws), wsb, _stream()))
     return Y
+
+
+def gp_autotune_mvm(kind, theta, X, V, reps=3):
+    """Times the tensor-core product H V for a ladder of column-split counts and records the
+    fastest for its shape (used by later products of that shape).  Returns (splits, ms)."""
+    lib = library()
+    _dev(X, torch.float32, "X", 2)
+    _dev(V, torch.float32, "V", 2)
+    n, d = X.shape
+    R = V.shape[0]
+    th, thp = _theta(theta, d)
+    Y = torch.empty_like(V)
+    ws, wsb = _ws(lib.gp_autotune_mvm_workspace(n, d, R), X.device)
+    best = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(lib.gp_autotune_mvm(kind, thp, d, _ptr(X), n, _ptr(V), R, _ptr(Y), int(reps), ctypes.byref(best),
+                               ctypes.byref(ms), _ptr(ws), wsb, _stream()))
+    return int(best.value), float(ms.value)
+
+
+def gp_autotune_reset():
+    library().gp_autotune_reset()
 
 
 def _info(inf: _Info) -> SolveInfo:

@@ -502,6 +502,51 @@ int gp_mll_grad_pathwise_f64(int kind, const double *theta, int d, const double 
     GP_API_END
 }
 
+// ------------------------------------------------------------------ autotuning
+size_t gp_autotune_mvm_workspace(int64_t n, int d, int nrhs) {
+    Carver c(nullptr);
+    c.take<char>(tc_points_bytes(n, d));
+    c.take<char>(tc_autotune_workspace(n, std::min(nrhs, 128)));
+    return c.bytes();
+}
+
+int gp_autotune_mvm(int kind, const double *theta, int d, const float *X, int64_t n, const float *V, int nrhs,
+                    float *Y, int reps, int *best_split, double *best_ms, void *ws, size_t ws_bytes,
+                    cudaStream_t stream) {
+    GP_API_BEGIN
+    KP<float> kp;
+    GP_TRY(make_kp<float>(kind, theta, d, &kp));
+    REQ(n >= 1 && nrhs >= 1 && nrhs <= 128, "need n >= 1 and 1 <= nrhs <= 128");
+    REQ(X && V && Y && best_split && best_ms, "null pointer argument");
+    REQ(reps >= 1 && reps <= 100, "reps must be in [1, 100]");
+    GP_TRY(check_prec(GP_PREC_TC16));
+    Carver c(ws);
+    void *pbuf = c.take<char>(tc_points_bytes(n, d));
+    const size_t twb = tc_autotune_workspace(n, nrhs);
+    void *tw = c.take<char>(twb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    TcMvmArgs a{};
+    a.kind = kind;
+    GP_TRY(tc_prepare_points(kp, X, n, pbuf, &a.rows, stream));
+    a.cols = a.rows;
+    a.V = V;
+    a.ldv = n;
+    a.R = nrhs;
+    a.Y = Y;
+    a.ldy = n;
+    a.sf2 = kp.sf2;
+    a.alpha = 1.0f;
+    a.beta = 0.0f;
+    a.diag_coef = kp.sigma2;
+    a.Vd = V;
+    a.ldvd = n;
+    a.ndiag = n;
+    return tc_autotune(a, reps, tw, twb, stream, best_split, best_ms);
+    GP_API_END
+}
+
+void gp_autotune_reset(void) { tc_autotune_reset(); }
+
 // ------------------------------------------------------------------ bilinear-form derivatives
 }  // extern "C"
 

@@ -244,6 +244,12 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
                     cudaStream_t st);
 int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st);
 bool tc_available();
+// Split-count autotuner of the product (rows == cols): times candidates, records the best
+// for the shape in a process-wide table that later products of that shape use.
+size_t tc_autotune_workspace(int64_t n, int R);
+int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStream_t st, int *best_split,
+                double *best_ms);
+void tc_autotune_reset();
 
 // ---------------------------------------------------------------------------
 // Batches of independent GPs (batched.cu): device tables shared with tc.cu

@@ -33,7 +33,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 namespace gp {
 
@@ -94,6 +96,26 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+// Bounded wait by a whole warp with a warp-uniform result (every lane votes, so the warp
+// never diverges on a time-out).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *err) {
+    const bool ok = mbar_wait(bar, parity, err);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// One lane of a converged warp: the role warps run their loops with the whole warp (so the
+// loop state and the operand descriptors are warp-uniform) and issue the single-thread
+// instructions (TMA, MMA, commit, expect-tx) from the elected lane.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(pred));
+    return pred != 0;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -339,87 +361,96 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t tS0 = tmem, tY = tmem + 384;
 
-    if (warp == 0 && lane == 0 && ntiles > 0) {
+    if (warp == 0 && ntiles > 0) {
         // ------------------------------------------------ TMA producer: row operand + PB ring
-        mbar_expect_tx(a_full, a_bytes);
-        for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
+        const bool leader = elect_one();
+        if (leader) {
+            mbar_expect_tx(a_full, a_bytes);
+            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
+        }
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NPB;
-            if (it >= NPB && !mbar_wait(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
+            if (it >= NPB && !mbar_wait_warp(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
             const int j0 = (int)((tb0 + it) * TN + pb_off);
             uint8_t *sB = sPB + (size_t)s * b_bytes;
-            mbar_expect_tx(&pb_full[s], b_bytes);
-            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
+            if (leader) {
+                mbar_expect_tx(&pb_full[s], b_bytes);
+                for (int ka = 0; ka < katoms; ++ka)
+                    tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
+            }
         }
-    } else if (warp == 2 && lane == 0 && ntiles > 0) {
+    } else if (warp == 2 && ntiles > 0) {
         // ------------------------------------------------ TMA producer: V ring
+        const bool leader = elect_one();
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NV;
-            if (it >= NV && !mbar_wait(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
+            if (it >= NV && !mbar_wait_warp(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
             const int j0 = (int)((tv0 + it) * TN);
             uint8_t *sV = sVr + (size_t)s * v_bytes;
-            mbar_expect_tx(&v_full[s], v_bytes);
-            tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
-            tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
+            if (leader) {
+                mbar_expect_tx(&v_full[s], v_bytes);
+                tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
+                tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
+            }
         }
-    } else if (warp == 1 && lane == 0 && ntiles > 0) {
+    } else if (warp == 1 && ntiles > 0) {
         // ------------------------------------------------ GEMM1 issuer
-        // GEMM1 and GEMM2 are issued by two threads (warps 1 and 3): each thread's stream of
-        // barrier waits, MMAs and commits is then half as long, and the waits of one overlap
-        // the MMAs of the other.  Their MMAs touch disjoint tensor memory (S vs P / Y) and
-        // every dependency between them runs through the evaluation warpgroups' barriers;
-        // a commit tracks the MMAs of its own thread.  Descriptors are built once and
-        // advanced by constant offsets (16-byte units).
+        // GEMM1 and GEMM2 are issued from two warps (1 and 3): each warp's stream of barrier
+        // waits, MMAs and commits is then half as long, and the waits of one overlap the MMAs
+        // of the other.  Their MMAs touch disjoint tensor memory (S vs P / Y) and every
+        // dependency between them runs through the evaluation warpgroups' barriers; a commit
+        // tracks the MMAs of its own thread.  Descriptors are built once and advanced by
+        // constant offsets (16-byte units).
+        const bool leader = elect_one();
         const uint32_t id1 = idesc_f16(TM, TN);
         const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
         const uint32_t b_units = b_bytes >> 4;
-        bool ok = mbar_wait(a_full, 0, s_err);
+        bool ok = mbar_wait_warp(a_full, 0, s_err);
         // GEMM1 of tile it into buffer it % 3, once GEMM2 of tile it - 3 has consumed it.
         for (int it = 0; ok && it < ntiles; ++it) {
             const int s = it % NPB, b = it % 3;
-            if (!mbar_wait(&pb_full[s], (it / NPB) & 1, s_err)) break;
-            if (it >= 3 && !mbar_wait(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
+            if (!mbar_wait_warp(&pb_full[s], (it / NPB) & 1, s_err)) break;
+            if (it >= 3 && !mbar_wait_warp(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t db = dPB + (uint64_t)s * b_units;
             const uint32_t dS = tS0 + b * 128;
+            if (leader) {
 #pragma unroll
-            for (int k = 0; k < 4 * KAT; ++k) {
-                constexpr uint32_t a_atom = (TM * 128) >> 4, b_atom = (TN * 128) >> 4;
-                const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
+                for (int k = 0; k < 4 * KAT; ++k) {
+                    constexpr uint32_t a_atom = (TM * 128) >> 4, b_atom = (TN * 128) >> 4;
+                    const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                    mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
+                }
+                mma_commit(&pb_empty[s]);
+                mma_commit(&t_full[b]);
             }
-            mma_commit(&pb_empty[s]);
-            mma_commit(&t_full[b]);
+            __syncwarp();
         }
-    } else if (warp == 3 && lane == 0 && ntiles > 0) {
+    } else if (warp == 3 && ntiles > 0) {
         // ------------------------------------------------ GEMM2 issuer: Y += P V
+        const bool leader = elect_one();
         const uint32_t id2 = idesc_f16(TM, R_pad);
         const uint64_t dV = sdesc(sVr);
         const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
-        bool ok = true;
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NV, b = it % 3;
-            if (!mbar_wait(&v_full[s], (it / NV) & 1, s_err)) {
-                ok = false;
-                break;
-            }
-            if (!mbar_wait(&t_kval[b], (it / 3) & 1, s_err)) {
-                ok = false;
-                break;
-            }
+            if (!mbar_wait_warp(&v_full[s], (it / NV) & 1, s_err)) break;
+            if (!mbar_wait_warp(&t_kval[b], (it / 3) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t dv = dV + (uint64_t)s * v_units;
             const uint32_t aP = tS0 + b * 128;
+            if (leader) {
 #pragma unroll
-            for (int k = 0; k < TN / 16; ++k) {
-                const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
+                for (int k = 0; k < TN / 16; ++k) {
+                    const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                    mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
+                }
+                mma_commit(&v_empty[s]);
+                mma_commit(&t_free[b]);
             }
-            mma_commit(&v_empty[s]);
-            mma_commit(&t_free[b]);
+            __syncwarp();
         }
-        (void)ok;
-        mma_commit(y_full);
+        if (leader) mma_commit(y_full);
     } else if (warp >= 4) {
         // ------------------------------------------------ kernel evaluation + epilogue
         // Two warpgroups ping-pong: warpgroup wg evaluates the tiles with it % 2 == wg (in
@@ -861,6 +892,32 @@ int pick_split(int64_t row_tiles, int64_t col_tiles) {
     return best;
 }
 
+// Split counts chosen by timing (gp_autotune_mvm), keyed by the product's shape in tiles;
+// they replace the model's choice wherever the caller's workspace holds their partial sums.
+struct TuneTable {
+    std::mutex mu;
+    std::map<std::tuple<int, int64_t, int64_t>, int> best;  // (R_pad, row tiles, col tiles) -> splits
+};
+TuneTable &tune_table() {
+    static TuneTable t;
+    return t;
+}
+thread_local int g_force_split = 0;  // set by the autotuner while it times one candidate
+
+int tuned_split(int R_pad, int64_t row_tiles, int64_t col_tiles) {
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    auto it = t.best.find(std::make_tuple(R_pad, row_tiles, col_tiles));
+    return it == t.best.end() ? 0 : it->second;
+}
+
+// The split a product of this shape uses: forced (autotuner), tuned, or the cost model.
+int split_for(int R_pad, int64_t row_tiles, int64_t col_tiles) {
+    if (g_force_split > 0) return g_force_split;
+    const int t = tuned_split(R_pad, row_tiles, col_tiles);
+    return t > 0 ? t : pick_split(row_tiles, col_tiles);
+}
+
 // Ring depths of the product kernel: up to 4 V slots (GEMM2 runs about two tiles behind
 // GEMM1), the rest of shared memory for PB slots (at most MAX_RING).
 void rings_for(int KD, int R_pad, int *npb, int *nv) {
@@ -983,11 +1040,22 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
     return GP_OK;
 }
 
+size_t tc_mvm_workspace_for(int64_t n1, int64_t p2, int R, int nsplit) {
+    const int R_pad = rpad_for(std::min(R, kMaxRhsPerPass));
+    Carver c(nullptr);
+    c.take<__half>((size_t)R_pad * p2);
+    c.take<float>(256);
+    c.take<float>((size_t)std::min(R, kMaxRhsPerPass) * 64);
+    c.take<int>(1);
+    if (nsplit > 1) c.take<float>((size_t)nsplit * std::min(R, kMaxRhsPerPass) * n1);
+    return c.bytes();
+}
+
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
     const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
     const int R_pad = rpad_for(std::min(R, kMaxRhsPerPass));
     const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM);
-    const int ns = pick_split(row_tiles, cdiv(p2, TN));
+    const int ns = std::max(split_for(R_pad, row_tiles, cdiv(p2, TN)), pick_split(row_tiles, cdiv(p2, TN)));
     Carver c(nullptr);
     c.take<__half>((size_t)R_pad * p2);            // V16
     c.take<float>(256);                            // vinv
@@ -1017,7 +1085,18 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int R_pad = rpad_for(a.R);
     const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
     const int64_t row_tiles = cdiv(n1, TM), col_tiles = cdiv(p2, TN);
-    const int nsplit = pick_split(row_tiles, col_tiles);
+    int nsplit = split_for(R_pad, row_tiles, col_tiles);
+    {
+        // a tuned split whose partial sums do not fit the caller's workspace falls back to
+        // the model's choice
+        Carver probe(nullptr);
+        probe.take<__half>((size_t)R_pad * p2);
+        probe.take<float>(256);
+        probe.take<float>((size_t)a.R * 64);
+        probe.take<int>(1);
+        if (nsplit > 1) probe.take<float>((size_t)nsplit * a.R * n1);
+        if (probe.bytes() > ws_bytes && g_force_split == 0) nsplit = pick_split(row_tiles, col_tiles);
+    }
     Carver c(ws);
     __half *V16 = c.take<__half>((size_t)R_pad * p2);
     float *vinv = c.take<float>(256);
@@ -1092,6 +1171,74 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         GP_TRY(check_launch("tc_reduce_kernel"));
     }
     return GP_OK;
+}
+
+// Times the product H V (a.rows == a.cols) for a ladder of split counts and records the
+// fastest for its shape.  Synchronises `st`; not for use inside a stream capture.
+int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStream_t st, int *best_split,
+                double *best_ms) {
+    const int64_t n1 = a.rows.n;
+    const int64_t p2 = rup(std::max<int64_t>(a.cols.n, 1), TN);
+    const int R_pad = rpad_for(std::min(a.R, kMaxRhsPerPass));
+    const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM), col_tiles = cdiv(p2, TN);
+    static const int ladder[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32, 48, 64, 96, 128};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GP_TRY_CUDA(cudaEventCreate(&e0));
+    GP_TRY_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    double best_t = 1e300;
+    int rc = GP_OK;
+    for (int s : ladder) {
+        if (s > col_tiles || (s > 1 && cdiv(col_tiles, s) * (s - 1) >= col_tiles)) continue;
+        if (tc_mvm_workspace_for(n1, p2, a.R, s) > ws_bytes) continue;
+        g_force_split = s;
+        double t_min = 1e300;
+        for (int r = 0; r <= reps && rc == GP_OK; ++r) {  // the first run is a warm-up
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = GP_ERR_CUDA;
+            if (rc == GP_OK) rc = tc_mvm(a, ws, ws_bytes, st);
+            if (rc == GP_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = GP_ERR_CUDA;
+            if (rc == GP_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = GP_ERR_CUDA;
+            float ms = 0.0f;
+            if (rc == GP_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = GP_ERR_CUDA;
+            if (rc == GP_OK && r > 0) t_min = std::min(t_min, (double)ms);
+        }
+        g_force_split = 0;
+        if (rc != GP_OK) break;
+        if (t_min < best_t) {
+            best_t = t_min;
+            best = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GP_OK) {
+        set_error("autotune: a timed product failed");
+        return rc;
+    }
+    if (best == 0) {
+        set_error("autotune: the workspace holds no candidate");
+        return GP_ERR_WORKSPACE;
+    }
+    {
+        TuneTable &t = tune_table();
+        std::lock_guard<std::mutex> g(t.mu);
+        t.best[std::make_tuple(R_pad, row_tiles, col_tiles)] = best;
+    }
+    *best_split = best;
+    *best_ms = best_t;
+    return GP_OK;
+}
+
+size_t tc_autotune_workspace(int64_t n, int R) {
+    const int64_t p2 = rup(std::max<int64_t>(n, 1), TN);
+    const int64_t col_tiles = p2 / TN;
+    return tc_mvm_workspace_for(n, p2, R, (int)std::min<int64_t>(128, col_tiles));
+}
+
+void tc_autotune_reset() {
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    t.best.clear();
 }
 
 // Grouped product over a batch of independent GPs: one CTA per work item (128 rows of a

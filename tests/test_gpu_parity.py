@@ -372,3 +372,26 @@ def test_pathwise_rhs_and_posterior_samples_match_oracle(dev):
                                   prec=gp.GP_PREC_FP32)
     ref = oracle.posterior_samples(p.kind, p.theta, f(Xs), f(p.X), f(Vsol), f(Fs))
     assert rel(out.double().cpu().numpy(), ref) < 1e-5
+
+
+def test_autotuned_split_is_used_and_keeps_parity(dev):
+    """The autotuner times candidate column splits for one shape and records the fastest;
+    products of that shape (standalone and inside CG) still match the oracle."""
+    if not tc_built():
+        pytest.skip("tensor-core path not built")
+    p = workloads.pathwise(n=2500, d=6, s=8, m=64, seed=7)
+    X32 = p.X.astype(np.float32)
+    V = workloads.vectors(9, 2500, seed=3).astype(np.float32)
+    try:
+        best, ms = gp.gp_autotune_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), reps=2)
+        assert best >= 1 and ms > 0.0
+        Y = gp.gp_kernel_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), add_noise=True, prec=gp.GP_PREC_TC16)
+        Xr = X32.astype(np.float64)
+        ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float64), add_noise=True)
+        assert rel(Y.cpu().numpy(), ref) < 1e-3
+        B = np.vstack([p.y_noise, p.Z]).astype(np.float32)
+        Vs, info = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), max_iters=300, tol=1e-2,
+                                  prec=gp.GP_PREC_TC16)
+        assert info.converged
+    finally:
+        gp.gp_autotune_reset()
