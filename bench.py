@@ -200,6 +200,20 @@ def recorded_traffic(n, prec_tc16):
     return rec["traffic_bytes_per_launch"] if digest == rec["source_sha256"] else None
 
 
+def combine_ranks(dist, device, seconds, work):
+    """Whole-job figures of the replicas: the slowest rank's time and the summed work
+    (weak scaling; no data-path collective, only this reduction of two scalars)."""
+    import torch
+
+    if dist is None:
+        return seconds, work
+    tt = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ww = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(ww)
+    return float(tt.item()), float(ww.item())
+
+
 def flush_l2(torch, buf):
     buf.add_(1.0)
 
@@ -283,13 +297,7 @@ def run_ours(args):
     rep.step()
     phases = {k: round(v, 3) for k, v in rep.phase_ms.items()}
     rep.phase_ms = None
-    if dist is not None:
-        tt = torch.tensor([total_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
-        ww = torch.tensor([work], dtype=torch.float64, device=dev)
-        dist.all_reduce(ww)
-        work = float(ww.item())
+    total_s, work = combine_ranks(dist, dev, total_s, work)
     value = work / total_s / 1e9
 
     # ---- end-to-end: inputs copied from pinned host memory every step, gradient read back
@@ -307,13 +315,7 @@ def run_ours(args):
     e_end.record()
     barrier()
     e_s = e_start.elapsed_time(e_end) / 1e3
-    if dist is not None:
-        tt = torch.tensor([e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_s = float(tt.item())
-        ww = torch.tensor([e_work], dtype=torch.float64, device=dev)
-        dist.all_reduce(ww)
-        e_work = float(ww.item())
+    e_s, e_work = combine_ranks(dist, dev, e_s, e_work)
 
     # ---- plain FP64 GPU form of the same step, same tolerance (equal final residual norm)
     fp64 = None
