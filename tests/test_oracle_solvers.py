@@ -150,3 +150,28 @@ def test_adam_softplus_matches_torch():
         theta = oracle.adam_softplus(nu, m, v, t, g_theta, lr=0.1)
         np.testing.assert_allclose(nu, t_nu.detach().numpy(), rtol=1e-12, atol=1e-14)
         np.testing.assert_allclose(theta, np.log1p(np.exp(nu)), rtol=1e-14)
+
+
+@pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
+def test_warm_start_first_order_identity(kind):
+    """App. A.2 "Taylor Approximation View of Warm Start": for theta' = theta + eps * delta with the same right-hand side,
+    v(theta') = v(theta) - H(theta)^-1 (H(theta') - H(theta)) v(theta) + O(eps^2), so the previous
+    solution is an O(eps) warm start and the first-order correction leaves an O(eps^2) error."""
+    rng = np.random.default_rng(31 + kind)
+    n, d = 40, 3
+    X = rng.standard_normal((n, d))
+    th = np.concatenate([rng.uniform(0.8, 1.4, size=d), [1.1, 0.5]])
+    delta = rng.uniform(-1.0, 1.0, size=d + 2) * th
+    y = rng.standard_normal(n)
+    H0 = oracle.H_matrix(kind, th, X)
+    v0 = np.linalg.solve(H0, y)
+    errs, dists = [], []
+    for eps in (1e-2, 5e-3, 2.5e-3):
+        H1 = oracle.H_matrix(kind, th + eps * delta, X)
+        v1 = np.linalg.solve(H1, y)
+        taylor = v0 - np.linalg.solve(H0, (H1 - H0) @ v0)
+        errs.append(np.linalg.norm(v1 - taylor))
+        dists.append(np.linalg.norm(v1 - v0))
+    # first-order distance, second-order remainder
+    assert 1.8 < dists[0] / dists[1] < 2.2 and 1.8 < dists[1] / dists[2] < 2.2
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
