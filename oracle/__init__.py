@@ -83,6 +83,7 @@ def _load():
                                        _i64, _d, _i, ctypes.POINTER(_Info)]),
                 "gpo_rff_prior": (None, [_i, _i, _pd, _pd, _i64, _i, _pd, _pd, _pd, _i, _pd]),
                 "gpo_posterior_samples": (None, [_i, _i, _pd, _pd, _i64, _pd, _i64, _pd, _i, _pd, _pd]),
+                "gpo_predict": (None, [_i, _i, _pd, _pd, _i64, _pd, _i64, _pd, _i, _pd, _pd, _pd, _pd, _pd]),
                 "gpo_adam_softplus": (None, [_i, _pd, _pd, _pd, _i64, _pd, _d, _d, _d, _d, _pd]),
             }
             for name, (res, args) in sig.items():
@@ -345,6 +346,24 @@ def posterior_samples(kind, theta, Xstar, X, Vsol, Fstar):
     _load().gpo_posterior_samples(kind, d, _p(theta), _p(Xstar), Xstar.shape[0], _p(X), X.shape[0],
                                   _p(Vsol), s, _p(Fstar), _p(out))
     return out
+
+
+def predict(kind, theta, Xstar, X, Vsol, Fstar, ystar=None):
+    """Predictive mean and variance at Xstar from the pathwise solutions, and (RMSE, mean test
+    log-likelihood) when ystar is given."""
+    X, theta, d = _dims(X, theta)
+    Xstar = _a(Xstar).reshape(-1, d)
+    Vsol = _a(Vsol)
+    Fstar = _a(Fstar)
+    s = Vsol.shape[0] - 1
+    ns = Xstar.shape[0]
+    mean = np.empty(ns)
+    var = np.empty(ns)
+    metrics = np.full(2, np.nan)
+    ys = None if ystar is None else _a(ystar)
+    _load().gpo_predict(kind, d, _p(theta), _p(Xstar), ns, _p(X), X.shape[0], _p(Vsol), s, _p(Fstar),
+                        None if ys is None else _p(ys), _p(mean), _p(var), _p(metrics))
+    return mean, var, (None if ys is None else (float(metrics[0]), float(metrics[1])))
 
 
 def adam_softplus(nu, m, v, t, grad_theta, lr, b1=0.9, b2=0.999, eps=1e-8):

@@ -796,6 +796,48 @@ void gpo_posterior_samples(int kind, int d, const double *theta, const double *X
 /* ------------------------------------------------------------------------- */
 
 /*
+ * Predictions from the pathwise solutions (Sec. 3 "Amortising Linear Solves for Optimisation
+ * and Prediction"; App. B reports test RMSE and test log-likelihood).  At the test points x*:
+ *   mean_i = k(x*_i, X) v_y                                  (the posterior mean)
+ *   var_i  = (1/s) sum_j ((f|y)_j(x*_i) - mean_i)^2 + sigma^2, where
+ *            (f|y)_j(x*) - mean(x*) = f_j(x*) - k(x*, X) zhat_j  (pathwise conditioning)
+ * i.e. the predictive variance of y* from the s posterior samples around the exact mean plus
+ * the noise.  With test targets ystar (may be NULL): metrics[0] = RMSE =
+ * sqrt(mean_i (ystar_i - mean_i)^2), metrics[1] = mean_i log N(ystar_i; mean_i, var_i).
+ * The paper does not print these formulas; this is the reading used throughout.
+ * Vsol: (s+1) x n = [v_y, zhat_1..zhat_s]; Fstar: s x nstar prior samples at x*.
+ */
+void gpo_predict(int kind, int d, const double *theta, const double *Xstar, int64_t nstar,
+                 const double *X, int64_t n, const double *Vsol, int s, const double *Fstar,
+                 const double *ystar, double *mean, double *var, double *metrics)
+{
+    int R = s + 1;
+    double *M = (double *)malloc(sizeof(double) * (size_t)R * (size_t)nstar);
+    gpo_kernel_mvm(kind, d, theta, Xstar, nstar, X, n, Vsol, R, 0, NULL, 0, M);
+    double s2 = theta[d + 1] * theta[d + 1];
+    double se = 0.0, ll = 0.0;
+    for (int64_t i = 0; i < nstar; ++i) {
+        mean[i] = M[i];
+        double acc = 0.0;
+        for (int j = 0; j < s; ++j) {
+            double dev = Fstar[(int64_t)j * nstar + i] - M[(int64_t)(j + 1) * nstar + i];
+            acc += dev * dev;
+        }
+        var[i] = acc / (double)s + s2;
+        if (ystar) {
+            double e = ystar[i] - mean[i];
+            se += e * e;
+            ll += -0.5 * log(2.0 * M_PI * var[i]) - 0.5 * e * e / var[i];
+        }
+    }
+    if (metrics && ystar && nstar > 0) {
+        metrics[0] = sqrt(se / (double)nstar);
+        metrics[1] = ll / (double)nstar;
+    }
+    free(M);
+}
+
+/*
  * One Adam ascent step on nu with theta = softplus(nu) = log(1 + e^nu):
  *   g_nu = g_theta * sigmoid(nu)
  *   m = b1 m + (1-b1) g_nu ;  v = b2 v + (1-b2) g_nu^2

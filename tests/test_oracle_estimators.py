@@ -182,3 +182,44 @@ def test_posterior_samples_mean_and_covariance():
     # and that random-feature posterior is close to the exact one of Eq. gp_posterior
     K_post = oracle.kernel_matrix(kind, th, Xs, Xs) - Ksx @ np.linalg.solve(H, Ksx.T)
     assert np.abs(cov_ref - K_post).max() < 0.05
+
+
+def test_predictions_from_pathwise_solutions():
+    """Predictions (Sec. 3, amortised through pathwise conditioning): the mean is the exact
+    posterior mean k(x*, X) H^-1 y; the predictive variance from s samples converges to the
+    exact posterior variance of the random-feature prior plus sigma^2; RMSE and test
+    log-likelihood equal numpy / scipy evaluations of their definitions on that mean and
+    variance."""
+    from scipy.stats import norm
+
+    rng = np.random.default_rng(8)
+    kind = oracle.MATERN32
+    d, n, ns, s, m = 2, 25, 6, 4000, 4000
+    th = np.array([0.9, 1.2, 1.1, 0.3])
+    X = rng.uniform(-1, 1, size=(n, d))
+    Xs = rng.uniform(-1, 1, size=(ns, d))
+    y = rng.standard_normal(n)
+    ys = rng.standard_normal(ns)
+    omega_hat = rng.standard_normal((m // 2, d))
+    chi2 = rng.chisquare(3.0, size=m // 2)
+    W = rng.standard_normal((s, m))
+    Xall = np.vstack([X, Xs])
+    Fall = oracle.rff_prior(kind, th, Xall, omega_hat, chi2, W)
+    F, Fs = Fall[:, :n], Fall[:, n:]
+    xi = F + th[-1] * rng.standard_normal((s, n))
+    H = oracle.H_matrix(kind, th, X)
+    Vsol = np.linalg.solve(H, np.vstack([y, xi]).T).T
+    mean, var, (rmse, llh) = oracle.predict(kind, th, Xs, X, Vsol, Fs, ys)
+    Ksx = oracle.kernel_matrix(kind, th, Xs, X)
+    np.testing.assert_allclose(mean, Ksx @ np.linalg.solve(H, y), rtol=1e-9, atol=1e-12)
+    # exact posterior variance under the random-feature prior covariance C = Phi Phi^T
+    Phi = oracle.rff_prior(kind, th, Xall, omega_hat, chi2, np.eye(m))
+    C = Phi.T @ Phi
+    Cs, Csx = C[n:, n:], C[n:, :n]
+    A = np.linalg.solve(H, Ksx.T)
+    cov = Cs - Csx @ A - A.T @ Csx.T + A.T @ (C[:n, :n] + th[-1] ** 2 * np.eye(n)) @ A
+    v_ref = np.diag(cov) + th[-1] ** 2
+    # sample variance of s draws: relative standard error sqrt(2/s)
+    assert np.all(np.abs(var / v_ref - 1) < 5 * np.sqrt(2.0 / s))
+    np.testing.assert_allclose(rmse, np.sqrt(np.mean((ys - mean) ** 2)), rtol=1e-12)
+    np.testing.assert_allclose(llh, np.mean(norm.logpdf(ys, loc=mean, scale=np.sqrt(var))), rtol=1e-12)
