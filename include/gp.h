@@ -38,7 +38,10 @@
  *       GP_PREC_TC16 : tcgen05 tensor cores, IEEE fp16 operands with FP32
  *                      accumulation; the squared distance uses a three-term
  *                      hi/lo split so that cancellation stays below 1e-6;
- *                      FP32 vectors, FP64 solver scalars.
+ *                      FP32 vectors, FP64 solver scalars.  Products support
+ *                      d <= 62 (GP_ERR_UNSUPPORTED beyond); the gradient
+ *                      estimators use CUDA-core FP32 tiles when d > 32 or
+ *                      s + 1 > 256 (or the tile plan does not fit).
  *     The *_f64 entry points are the plain FP64 GPU form (CUDA-core FP64 tiles
  *     and FP64 vectors) used as the comparison baseline.
  */
@@ -335,6 +338,21 @@ int gp_posterior_samples(int kind, const double *theta, int d, const float *Xsta
                          const float *X, int64_t n, const float *Vsol, int s, const float *Fstar,
                          float *out, int prec, void *ws, size_t ws_bytes, cudaStream_t stream);
 size_t gp_posterior_samples_workspace(int64_t nstar, int64_t n, int d, int s, int prec);
+/* Predictions from the pathwise solutions (Sec. 3 "Amortising Linear Solves for
+ * Optimisation and Prediction"; App. B reports test RMSE and test log-likelihood):
+ *   mean_i = k(x*_i, X) v_y,
+ *   var_i  = (1/s) sum_j (f_j(x*_i) - k(x*_i, X) zhat_j)^2 + sigma^2
+ * (the spread of the s pathwise posterior samples around the exact mean, plus the noise:
+ * the predictive variance of y*).  Vsol = [v_y, zhat_1..zhat_s] ((s+1) x n), Fstar: s x nstar
+ * prior samples at Xstar (gp_rff_prior_sample with the probes' features).  mean, var:
+ * DEVICE nstar floats.  With ystar (DEVICE nstar floats, or NULL) and metrics (DEVICE 2
+ * doubles, or NULL): metrics[0] = RMSE, metrics[1] = mean_i log N(ystar_i; mean_i, var_i).
+ * Sums in FP64.  Errors as gp_posterior_samples. */
+int gp_predict(int kind, const double *theta, int d, const float *Xstar, int64_t nstar,
+               const float *X, int64_t n, const float *Vsol, int s, const float *Fstar,
+               const float *ystar, float *mean, float *var, double *metrics, int prec,
+               void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_predict_workspace(int64_t nstar, int64_t n, int d, int s, int prec);
 
 /* ------------------------------------------------------------------------ */
 /* Outer loop (Sec. 2.1 "Outer-Loop Optimiser"; App. B "Iterative Optimiser") */

@@ -99,6 +99,8 @@ _SIGS = {
     "gp_autotune_mvm": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i, ctypes.POINTER(_i), _pd, _vp, _sz, _vp]),
     "gp_autotune_mvm_workspace": (_sz, [_i64, _i, _i]),
     "gp_autotune_reset": (None, []),
+    "gp_predict": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp]),
+    "gp_predict_workspace": (_sz, [_i64, _i64, _i, _i, _i]),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
@@ -461,6 +463,27 @@ def gp_posterior_samples(kind, theta, Xstar, X, Vsol, Fstar, prec=GP_PREC_TC16):
     _check(lib.gp_posterior_samples(kind, thp, d, _ptr(Xstar), nstar, _ptr(X), n, _ptr(Vsol), s, _ptr(Fstar),
                                     _ptr(out), prec, _ptr(ws), wsb, _stream()))
     return out
+
+
+def gp_predict(kind, theta, Xstar, X, Vsol, Fstar, ystar=None, prec=GP_PREC_TC16):
+    """Predictive mean and variance (nstar each) from the pathwise solutions; with ystar also
+    a CUDA float64 tensor (RMSE, mean test log-likelihood)."""
+    lib = library()
+    for t_, nm in ((Xstar, "Xstar"), (X, "X"), (Vsol, "Vsol"), (Fstar, "Fstar")):
+        _dev(t_, torch.float32, nm, 2)
+    if ystar is not None:
+        _dev(ystar, torch.float32, "ystar", 1)
+    nstar, d = Xstar.shape
+    n = X.shape[0]
+    s = Vsol.shape[0] - 1
+    th, thp = _theta(theta, d)
+    mean = torch.empty(nstar, dtype=torch.float32, device=X.device)
+    var = torch.empty(nstar, dtype=torch.float32, device=X.device)
+    metrics = torch.empty(2, dtype=torch.float64, device=X.device) if ystar is not None else None
+    ws, wsb = _ws(lib.gp_predict_workspace(nstar, n, d, s, prec), X.device)
+    _check(lib.gp_predict(kind, thp, d, _ptr(Xstar), nstar, _ptr(X), n, _ptr(Vsol), s, _ptr(Fstar), _ptr(ystar),
+                          _ptr(mean), _ptr(var), _ptr(metrics), prec, _ptr(ws), wsb, _stream()))
+    return mean, var, metrics
 
 
 def gp_adam_softplus_step(nu, m, v, t, grad_theta, lr, beta1=0.9, beta2=0.999, eps=1e-8):

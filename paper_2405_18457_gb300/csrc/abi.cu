@@ -502,6 +502,25 @@ int gp_mll_grad_pathwise_f64(int kind, const double *theta, int d, const double 
     GP_API_END
 }
 
+// ------------------------------------------------------------------ predictions
+size_t gp_predict_workspace(int64_t nstar, int64_t n, int d, int s, int prec) {
+    return predict_workspace(nstar, n, d, s, prec);
+}
+
+int gp_predict(int kind, const double *theta, int d, const float *Xstar, int64_t nstar, const float *X, int64_t n,
+               const float *Vsol, int s, const float *Fstar, const float *ystar, float *mean, float *var,
+               double *metrics, int prec, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    KP<float> kp;
+    GP_TRY(make_kp<float>(kind, theta, d, &kp));
+    REQ(nstar >= 0 && n >= 1 && s >= 1, "need nstar >= 0, n >= 1 and s >= 1");
+    if (nstar == 0) return GP_OK;
+    REQ(Xstar && X && Vsol && Fstar && mean && var, "null pointer argument");
+    GP_TRY(check_prec(prec));
+    return predict(kp, Xstar, nstar, X, n, Vsol, s, Fstar, ystar, mean, var, metrics, prec, ws, ws_bytes, stream);
+    GP_API_END
+}
+
 // ------------------------------------------------------------------ autotuning
 size_t gp_autotune_mvm_workspace(int64_t n, int d, int nrhs) {
     Carver c(nullptr);

@@ -321,4 +321,98 @@ int posterior_samples(const KP<float> &kp, const float *Xstar, int64_t nstar, co
     return check_launch("add_prior_kernel");
 }
 
+// ===========================================================================
+// Predictions from the pathwise solutions (Sec. 3 "Amortising Linear Solves for
+// Optimisation and Prediction"): mean = k(x*, X) v_y, predictive variance = the s
+// posterior samples' spread around that mean plus sigma^2, RMSE and mean test
+// log-likelihood of ystar.
+// ===========================================================================
+namespace {
+
+constexpr int PRED_BLOCKS = 256;
+
+// M = K(X*, X) [v_y, zhat_1..] (R x nstar); per point: mean, variance; per block:
+// partial sums of squared errors and log-densities (FP64) when ystar is given.
+__global__ void predict_kernel(const float *M, const float *Fstar, const float *ystar, int64_t nstar, int s,
+                               double sigma2, float *mean, float *var, double *part) {
+    double se = 0.0, ll = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nstar; i += (int64_t)gridDim.x * blockDim.x) {
+        const double mu = (double)M[i];
+        double acc = 0.0;
+        for (int j = 0; j < s; ++j) {
+            const double dev = (double)Fstar[(int64_t)j * nstar + i] - (double)M[(int64_t)(j + 1) * nstar + i];
+            acc += dev * dev;
+        }
+        const double v = acc / (double)s + sigma2;
+        mean[i] = (float)mu;
+        var[i] = (float)v;
+        if (ystar) {
+            const double e = (double)ystar[i] - mu;
+            se += e * e;
+            ll += -0.5 * log(2.0 * 3.14159265358979323846 * v) - 0.5 * e * e / v;
+        }
+    }
+    if (!part) return;
+    __shared__ double r1[32], r2[32];
+    se = warp_sum(se);
+    ll = warp_sum(ll);
+    if ((threadIdx.x & 31) == 0) {
+        r1[threadIdx.x >> 5] = se;
+        r2[threadIdx.x >> 5] = ll;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += r1[w];
+            b += r2[w];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void predict_metrics_kernel(const double *part, int nblocks, int64_t nstar, double *metrics) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblocks; ++k) {
+        a += part[2 * k];
+        b += part[2 * k + 1];
+    }
+    metrics[0] = sqrt(a / (double)nstar);
+    metrics[1] = b / (double)nstar;
+}
+
+}  // namespace
+
+size_t predict_workspace(int64_t nstar, int64_t n, int d, int s, int prec) {
+    Carver c(nullptr);
+    c.take<float>((size_t)(s + 1) * (size_t)nstar);
+    c.take<double>(2 * PRED_BLOCKS);
+    c.take<char>(mvm_workspace<float>(nstar, n, d, s + 1, prec));
+    return c.bytes();
+}
+
+int predict(const KP<float> &kp, const float *Xstar, int64_t nstar, const float *X, int64_t n, const float *Vsol,
+            int s, const float *Fstar, const float *ystar, float *mean, float *var, double *metrics, int prec,
+            void *ws, size_t ws_bytes, cudaStream_t st) {
+    Carver c(ws);
+    float *M = c.take<float>((size_t)(s + 1) * (size_t)nstar);
+    double *part = c.take<double>(2 * PRED_BLOCKS);
+    const size_t mw = mvm_workspace<float>(nstar, n, kp.d, s + 1, prec);
+    void *mws = c.take<char>(mw);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    GP_TRY(apply_mvm<float>(kp, Xstar, nstar, X, n, Vsol, n, s + 1, M, nstar, 0, prec, mws, mw, st));
+    const bool metr = ystar && metrics;
+    const int nb = (int)std::min<int64_t>(PRED_BLOCKS, cdiv(nstar, 256));
+    predict_kernel<<<nb, 256, 0, st>>>(M, Fstar, ystar, nstar, s, (double)kp.sigma2, mean, var,
+                                       metr ? part : nullptr);
+    GP_TRY(check_launch("predict_kernel"));
+    if (metr) {
+        predict_metrics_kernel<<<1, 32, 0, st>>>(part, nb, nstar, metrics);
+        GP_TRY(check_launch("predict_metrics_kernel"));
+    }
+    return GP_OK;
+}
+
 }  // namespace gp

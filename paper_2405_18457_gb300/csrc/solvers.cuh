@@ -37,6 +37,11 @@ int posterior_samples(const KP<float> &kp, const float *Xstar, int64_t nstar, co
                       const float *Vsol, int s, const float *Fstar, float *out, int prec, void *ws,
                       size_t ws_bytes, cudaStream_t st);
 
+size_t predict_workspace(int64_t nstar, int64_t n, int d, int s, int prec);
+int predict(const KP<float> &kp, const float *Xstar, int64_t nstar, const float *X, int64_t n, const float *Vsol,
+            int s, const float *Fstar, const float *ystar, float *mean, float *var, double *metrics, int prec,
+            void *ws, size_t ws_bytes, cudaStream_t st);
+
 // Solvers (App. B, Alg. 1-3).
 template <typename T>
 size_t cg_workspace(int64_t n, int d, int R, int prec);

@@ -395,3 +395,25 @@ def test_autotuned_split_is_used_and_keeps_parity(dev):
         assert info.converged
     finally:
         gp.gp_autotune_reset()
+
+
+@pytest.mark.parametrize("prec_name,prec,tol", [("f32", gp.GP_PREC_FP32, 1e-5), ("tc16", gp.GP_PREC_TC16, 2e-3)])
+def test_predictions_match_oracle(dev, prec_name, prec, tol):
+    """Predictive mean/variance and test RMSE/log-likelihood from the pathwise solutions."""
+    if prec_name == "tc16" and not tc_built():
+        pytest.skip("tensor-core path not built")
+    p = workloads.pathwise(n=1500, d=6, s=12, m=256, seed=9)
+    rng = np.random.default_rng(10)
+    Xs = rng.standard_normal((700, 6)).astype(np.float32)
+    X32 = p.X.astype(np.float32)
+    Vsol = (0.3 * rng.standard_normal((13, 1500))).astype(np.float32)
+    Fs = rng.standard_normal((12, 700)).astype(np.float32)
+    ys = rng.standard_normal(700).astype(np.float32)
+    mean, var, met = gp.gp_predict(p.kind, p.theta, t(Xs, dev), t(X32, dev), t(Vsol, dev), t(Fs, dev), t(ys, dev),
+                                   prec=prec)
+    m_ref, v_ref, (rmse, llh) = oracle.predict(p.kind, p.theta, Xs.astype(np.float64), X32.astype(np.float64),
+                                               Vsol.astype(np.float64), Fs.astype(np.float64), ys.astype(np.float64))
+    assert rel(mean.cpu().numpy(), m_ref) < tol
+    assert rel(var.cpu().numpy(), v_ref) < tol
+    met = met.cpu().numpy()
+    assert abs(met[0] - rmse) <= tol * rmse and abs(met[1] - llh) <= 10 * tol * abs(llh)
