@@ -77,6 +77,9 @@ def _load():
                 "gpo_grad_pathwise": (None, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd]),
                 "gpo_solve_cg": (_i, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd, _i64, _d, _i,
                                       ctypes.POINTER(_Info)]),
+                "gpo_pivoted_cholesky": (_i, [_i, _i, _pd, _pd, _i64, _i, _pd, _pi64]),
+                "gpo_solve_pcg": (_i, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd, _i, _i64, _d, _i,
+                                       ctypes.POINTER(_Info)]),
                 "gpo_solve_ap": (_i, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd, _i64, _i64, _d, _i,
                                       ctypes.POINTER(_Info)]),
                 "gpo_solve_sgd": (_i, [_i, _i, _pd, _pd, _i64, _pd, _i, _pd, _i64, _pi64, _d, _d,
@@ -292,6 +295,30 @@ def solve_cg(kind, theta, X, B, V0=None, max_iters=1000, tol=1e-2, stop_rule=0):
     inf = _Info()
     _load().gpo_solve_cg(kind, d, _p(theta), _p(X), X.shape[0], _p(B), B.shape[0], _p(V),
                          int(max_iters), float(tol), int(stop_rule), ctypes.byref(inf))
+    return V, _info(inf)
+
+
+def pivoted_cholesky(kind, theta, X, k):
+    """Rank-k pivoted Cholesky factor L (rank x n, K ~ L^T L) and its pivots."""
+    X, theta, d = _dims(X, theta)
+    n = X.shape[0]
+    L = np.zeros((k, n))
+    piv = np.zeros(k, dtype=np.int64)
+    rank = _load().gpo_pivoted_cholesky(kind, d, _p(theta), _p(X), n, k, _p(L),
+                                        piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return L[:rank], piv[:rank]
+
+
+def solve_pcg(kind, theta, X, B, rank, V0=None, max_iters=1000, tol=1e-2, stop_rule=0):
+    """Alg. 1 with the rank-`rank` pivoted Cholesky preconditioner (rank 0: plain CG)."""
+    X, theta, d = _dims(X, theta)
+    B = _a(B)
+    V = np.zeros_like(B) if V0 is None else _a(V0).copy()
+    inf = _Info()
+    st = _load().gpo_solve_pcg(kind, d, _p(theta), _p(X), X.shape[0], _p(B), B.shape[0], _p(V), int(rank),
+                               int(max_iters), float(tol), int(stop_rule), ctypes.byref(inf))
+    if st != 0:
+        raise np.linalg.LinAlgError("preconditioner not positive definite")
     return V, _info(inf)
 
 

@@ -587,6 +587,138 @@ int gpo_solve_cg(int kind, int d, const double *theta, const double *X, int64_t 
 }
 
 /*
+ * Rank-k pivoted Cholesky factor of K (App. B "Conjugate Gradients": rank-100 pivoted
+ * Cholesky preconditioner, following Wang et al. 2019 / Gardner et al. 2018; the greedy
+ * algorithm of Harbrecht, Peters and Schneider 2012).  Starting from the diagonal of K, step m
+ * picks the not yet chosen point p with the largest remaining diagonal (ties: lowest index),
+ * sets row m of L to (k(x_j, x_p) - sum_{l<m} L[l][j] L[l][p]) / sqrt(diag_p) for every j and
+ * subtracts its square from the remaining diagonal.  L is k x n (row m = m-th factor column),
+ * K ~ L^T L.  Returns the rank reached (< k if the remaining diagonal vanishes); pivots in piv.
+ */
+int gpo_pivoted_cholesky(int kind, int d, const double *theta, const double *X, int64_t n, int k,
+                         double *L, int64_t *piv)
+{
+    double *dg = malloc(sizeof(double) * (size_t)n);
+    char *used = calloc((size_t)n, 1);
+    for (int64_t j = 0; j < n; ++j)
+        dg[j] = gpo_kernel(kind, d, theta, X + j * d, X + j * d);
+    int m = 0;
+    for (; m < k; ++m) {
+        int64_t p = -1;
+        for (int64_t j = 0; j < n; ++j)
+            if (!used[j] && (p < 0 || dg[j] > dg[p]))
+                p = j;
+        if (p < 0 || !(dg[p] > 0.0))
+            break;
+        used[p] = 1;
+        piv[m] = p;
+        double lpp = sqrt(dg[p]);
+        for (int64_t j = 0; j < n; ++j) {
+            double v = gpo_kernel(kind, d, theta, X + j * d, X + p * d);
+            for (int l = 0; l < m; ++l)
+                v -= L[(int64_t)l * n + j] * L[(int64_t)l * n + p];
+            L[(int64_t)m * n + j] = v / lpp;
+        }
+        for (int64_t j = 0; j < n; ++j)
+            dg[j] -= L[(int64_t)m * n + j] * L[(int64_t)m * n + j];
+    }
+    free(dg);
+    free(used);
+    return m;
+}
+
+/*
+ * Alg. 1 with a preconditioner P (App. B "Conjugate Gradients"): P = L^T L + sigma^2 I from the
+ * rank-k pivoted Cholesky factor above (k = 0: P = I, plain CG).  The loop follows the listing:
+ * p = P^-1 r, d = p, gamma = r^T p; alpha = gamma / d^T H d; v += alpha d; r -= alpha H d;
+ * p = P^-1 r; beta = r^T p / gamma; gamma = r^T p; d = p + beta d.  P^-1 is applied through a
+ * dense Cholesky factor of P.  Normalisation, split norms (of r), stop rule and the frozen-column
+ * rule as gpo_solve_cg.
+ */
+int gpo_solve_pcg(int kind, int d, const double *theta, const double *X, int64_t n,
+                  const double *B, int R, double *V, int k, int64_t max_iters, double tol, int stop_rule,
+                  gpo_info_t *info)
+{
+    size_t nn = (size_t)n, nr = (size_t)R * nn;
+    double *H = malloc(sizeof(double) * nn * nn), *P = malloc(sizeof(double) * nn * nn);
+    double *bt = malloc(sizeof(double) * nr), *r = malloc(sizeof(double) * nr), *pz = malloc(sizeof(double) * nr);
+    double *dd = malloc(sizeof(double) * nr), *Hd = malloc(sizeof(double) * nr);
+    double *scale = malloc(sizeof(double) * (size_t)R), *gamma = malloc(sizeof(double) * (size_t)R);
+    double *L = malloc(sizeof(double) * (size_t)(k > 0 ? k : 1) * nn);
+    int64_t *piv = malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    gpo_H_matrix(kind, d, theta, X, n, H);
+    int rank = k > 0 ? gpo_pivoted_cholesky(kind, d, theta, X, n, k, L, piv) : 0;
+    double s2 = theta[d + 1] * theta[d + 1];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double v = (i == j) ? s2 : 0.0;
+            for (int l = 0; l < rank; ++l)
+                v += L[(int64_t)l * n + i] * L[(int64_t)l * n + j];
+            P[i * n + j] = v;
+        }
+    if (gpo_cholesky(n, P) != 0) {
+        free(H); free(P); free(bt); free(r); free(pz); free(dd); free(Hd); free(scale); free(gamma); free(L);
+        free(piv);
+        return -1;
+    }
+    normalise(B, V, n, R, bt, scale);
+    dense_apply(H, n, V, Hd, R);
+    for (size_t e = 0; e < nr; ++e)
+        r[e] = bt[e] - Hd[e];
+    memcpy(pz, r, sizeof(double) * nr);
+    gpo_chol_solve(n, P, pz, R); /* p = P^-1 r */
+    memcpy(dd, pz, sizeof(double) * nr);
+    for (int c = 0; c < R; ++c) {
+        double g = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            g += r[(int64_t)c * n + i] * pz[(int64_t)c * n + i];
+        gamma[c] = g;
+    }
+    int64_t t = 0;
+    double ry, rz;
+    split_norms(r, n, R, &ry, &rz);
+    while (keep_going(t, max_iters, ry, rz, tol, stop_rule)) {
+        dense_apply(H, n, dd, Hd, R);
+        double *alpha = malloc(sizeof(double) * (size_t)R);
+        for (int c = 0; c < R; ++c) {
+            double *vc = V + (int64_t)c * n, *rc = r + (int64_t)c * n;
+            double *dc = dd + (int64_t)c * n, *hc = Hd + (int64_t)c * n;
+            double dHd = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                dHd += dc[i] * hc[i];
+            alpha[c] = (gamma[c] > 1e-30 && dHd > 0.0) ? gamma[c] / dHd : 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                vc[i] += alpha[c] * dc[i];
+                rc[i] -= alpha[c] * hc[i];
+            }
+        }
+        memcpy(pz, r, sizeof(double) * nr);
+        gpo_chol_solve(n, P, pz, R);
+        for (int c = 0; c < R; ++c) {
+            double *rc = r + (int64_t)c * n, *pc = pz + (int64_t)c * n, *dc = dd + (int64_t)c * n;
+            double gnew = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                gnew += rc[i] * pc[i];
+            double beta = (alpha[c] != 0.0) ? gnew / gamma[c] : 0.0;
+            if (alpha[c] != 0.0)
+                gamma[c] = gnew;
+            for (int64_t i = 0; i < n; ++i)
+                dc[i] = pc[i] + beta * dc[i];
+        }
+        free(alpha);
+        t += 1;
+        split_norms(r, n, R, &ry, &rz);
+    }
+    denormalise(V, n, R, scale);
+    info->iters = t;
+    info->res_y = ry;
+    info->res_z = rz;
+    info->converged = !(ry > tol || rz > tol) || (stop_rule == 1 && (ry <= tol || rz <= tol));
+    free(H); free(P); free(bt); free(r); free(pz); free(dd); free(Hd); free(scale); free(gamma); free(L); free(piv);
+    return 0;
+}
+
+/*
  * Alg. 2, alternating projections with block size bs.  Each iteration picks the
  * block with the largest ||sum_c r_c[i]||, solves its diagonal block exactly by
  * the cached Cholesky factor, updates v on that block and r everywhere.

@@ -175,3 +175,72 @@ def test_warm_start_first_order_identity(kind):
     # first-order distance, second-order remainder
     assert 1.8 < dists[0] / dists[1] < 2.2 and 1.8 < dists[1] / dists[2] < 2.2
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+@pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
+def test_pivoted_cholesky_full_rank_reproduces_K(kind):
+    rng = np.random.default_rng(40 + kind)
+    n, d = 30, 2
+    X = rng.standard_normal((n, d))
+    th = np.array([0.9, 1.3, 1.1, 0.2])
+    L, piv = oracle.pivoted_cholesky(kind, th, X, n)
+    K = oracle.kernel_matrix(kind, th, X, X)
+    assert L.shape[0] >= n - 2  # numerically full rank (the remaining diagonal may vanish a step early)
+    np.testing.assert_allclose(L.T @ L, K, atol=1e-9)
+    assert piv[0] == 0 and len(set(piv.tolist())) == len(piv)  # equal diagonals: ties to index 0
+    # each pivot column is interpolated exactly from the first step that picks it on
+    for m, p in enumerate(piv):
+        np.testing.assert_allclose(L[: m + 1].T @ L[: m + 1, p], K[:, p], atol=1e-9)
+
+
+def test_pivoted_cholesky_trace_error_decreases():
+    rng = np.random.default_rng(41)
+    n = 80
+    X = rng.uniform(-1, 1, size=(n, 2))
+    th = np.array([0.5, 0.5, 1.0, 0.1])
+    K = oracle.kernel_matrix(oracle.RBF, th, X, X)
+    errs = []
+    for k in (2, 5, 10, 20):
+        L, _ = oracle.pivoted_cholesky(oracle.RBF, th, X, k)
+        E = K - L.T @ L
+        assert np.min(np.linalg.eigvalsh(E)) > -1e-10  # the remainder is PSD
+        errs.append(np.trace(E))
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+
+
+def test_pcg_rank_zero_is_plain_cg():
+    rng = np.random.default_rng(42)
+    n, R = 60, 3
+    X = rng.standard_normal((n, 3))
+    th = np.array([1.0, 0.8, 1.2, 1.0, 0.3])
+    B = rng.standard_normal((R, n))
+    Va, ia = oracle.solve_cg(oracle.MATERN32, th, X, B, max_iters=6, tol=0.0)
+    Vb, ib = oracle.solve_pcg(oracle.MATERN32, th, X, B, 0, max_iters=6, tol=0.0)
+    np.testing.assert_allclose(Vb, Va, rtol=1e-12, atol=1e-14)
+    assert ia["iters"] == ib["iters"] == 6
+
+
+def test_pcg_with_the_exact_preconditioner_needs_one_iteration():
+    """Full rank: P = K + sigma^2 I = H, so the first step lands on the solution."""
+    rng = np.random.default_rng(43)
+    n, R = 40, 2
+    X = rng.standard_normal((n, 2))
+    th = np.array([0.7, 1.1, 1.0, 0.5])
+    B = rng.standard_normal((R, n))
+    V, info = oracle.solve_pcg(oracle.RBF, th, X, B, n, max_iters=5, tol=1e-9)
+    assert info["iters"] == 1 and info["converged"]
+    H = oracle.H_matrix(oracle.RBF, th, X)
+    np.testing.assert_allclose(V, np.linalg.solve(H, B.T).T, rtol=1e-7, atol=1e-9)
+
+
+def test_pcg_matches_dense_solve_and_needs_fewer_iterations():
+    p_rng = np.random.default_rng(44)
+    n, R = 300, 3
+    X = p_rng.uniform(0, 1, size=(n, 4))
+    th = np.array([0.5, 0.5, 0.5, 0.5, 1.0, 0.1])  # the small workload's hyperparameters
+    B = p_rng.standard_normal((R, n))
+    V, info = oracle.solve_pcg(oracle.RBF, th, X, B, 20, max_iters=2000, tol=1e-8)
+    _, info_cg = oracle.solve_cg(oracle.RBF, th, X, B, max_iters=2000, tol=1e-8)
+    H = oracle.H_matrix(oracle.RBF, th, X)
+    np.testing.assert_allclose(V, np.linalg.solve(H, B.T).T, rtol=1e-5, atol=1e-6)
+    assert info["converged"] and info["iters"] < info_cg["iters"]
