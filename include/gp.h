@@ -176,6 +176,25 @@ int gp_solve_cg_f64(int kind, const double *theta, int d, const double *X, int64
                     cudaStream_t stream);
 size_t gp_solve_cg_f64_workspace(int64_t n, int d, int nrhs);
 
+/* Alg. 1 with the preconditioner of App. B "Conjugate Gradients": P = L^T L + sigma^2 I
+ * from a rank-`rank` pivoted Cholesky factor of K (greedy pivots on the largest remaining
+ * diagonal, ties to the lowest index; the paper uses rank 100), applied through the
+ * Woodbury identity with a k x k Cholesky factor in FP64.  The loop is the listing's:
+ * p = P^-1 r, gamma = r^T p, d = p + beta d; split norms and the stop rule use ||r|| as in
+ * gp_solve_cg.  rank = 0 is gp_solve_cg; 0 <= rank <= 128 (clamped to n).  The factor is
+ * built once per call (2 rank + 3 small launches) and its arithmetic, like the solver's
+ * vectors, is FP32 (FP64 in the _f64 form) with FP64 sums across tiles. */
+int gp_solve_pcg(int kind, const double *theta, int d, const float *X, int64_t n,
+                 const float *B, int nrhs, float *V_inout, int64_t max_iters, double tol,
+                 int stop_rule, int prec, int rank, gp_solve_info_t *info,
+                 void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_pcg_workspace(int64_t n, int d, int nrhs, int prec, int rank);
+int gp_solve_pcg_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                     const double *B, int nrhs, double *V_inout, int64_t max_iters, double tol,
+                     int stop_rule, int rank, gp_solve_info_t *info,
+                     void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_solve_pcg_f64_workspace(int64_t n, int d, int nrhs, int rank);
+
 /* Alternating projections, Alg. 2.  Blocks are contiguous row ranges
  * [i*block_size, min((i+1)*block_size, n)); each iteration selects the block
  * with the largest ||sum_c r_c[i]|| (ties: lowest index), adds

@@ -64,6 +64,12 @@ _SIGS = {
     "gp_solve_cg_workspace": (_sz, [_i64, _i, _i, _i]),
     "gp_solve_cg_f64": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i64, _d, _i, ctypes.POINTER(_Info), _vp, _sz, _vp]),
     "gp_solve_cg_f64_workspace": (_sz, [_i64, _i, _i]),
+    "gp_solve_pcg": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i64, _d, _i, _i, _i, ctypes.POINTER(_Info), _vp,
+                          _sz, _vp]),
+    "gp_solve_pcg_workspace": (_sz, [_i64, _i, _i, _i, _i]),
+    "gp_solve_pcg_f64": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i64, _d, _i, _i, ctypes.POINTER(_Info), _vp,
+                              _sz, _vp]),
+    "gp_solve_pcg_f64_workspace": (_sz, [_i64, _i, _i, _i]),
     "gp_solve_ap": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i64, _i64, _d, _i, _i, ctypes.POINTER(_Info), _vp, _sz,
                          _vp]),
     "gp_solve_ap_workspace": (_sz, [_i64, _i, _i, _i64, _i]),
@@ -278,12 +284,25 @@ def _solver_prep(X, B, V0):
     return dt, n, d, R, V
 
 
-def gp_solve_cg(kind, theta, X, B, V0=None, max_iters=1000, tol=1e-2, stop_rule=GP_STOP_BOTH, prec=GP_PREC_TC16):
-    """Alg. 1 (CG).  V0 (R, n) is the warm start and is overwritten with the solution."""
+def gp_solve_cg(kind, theta, X, B, V0=None, max_iters=1000, tol=1e-2, stop_rule=GP_STOP_BOTH, prec=GP_PREC_TC16,
+                precond_rank=0):
+    """Alg. 1 (CG).  V0 (R, n) is the warm start and is overwritten with the solution.
+    precond_rank > 0: the rank-k pivoted Cholesky preconditioner of App. B (gp_solve_pcg)."""
     lib = library()
     dt, n, d, R, V = _solver_prep(X, B, V0)
     th, thp = _theta(theta, d)
     inf = _Info()
+    if precond_rank > 0:
+        k = int(precond_rank)
+        if _f64(X):
+            ws, wsb = _ws(lib.gp_solve_pcg_f64_workspace(n, d, R, k), X.device)
+            _check(lib.gp_solve_pcg_f64(kind, thp, d, _ptr(X), n, _ptr(B), R, _ptr(V), int(max_iters), float(tol),
+                                        stop_rule, k, ctypes.byref(inf), _ptr(ws), wsb, _stream()))
+        else:
+            ws, wsb = _ws(lib.gp_solve_pcg_workspace(n, d, R, prec, k), X.device)
+            _check(lib.gp_solve_pcg(kind, thp, d, _ptr(X), n, _ptr(B), R, _ptr(V), int(max_iters), float(tol),
+                                    stop_rule, prec, k, ctypes.byref(inf), _ptr(ws), wsb, _stream()))
+        return V, _info(inf)
     if _f64(X):
         ws, wsb = _ws(lib.gp_solve_cg_f64_workspace(n, d, R), X.device)
         _check(lib.gp_solve_cg_f64(kind, thp, d, _ptr(X), n, _ptr(B), R, _ptr(V), int(max_iters), float(tol),

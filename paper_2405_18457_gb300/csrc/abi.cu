@@ -2,6 +2,7 @@
 #include "gp_internal.cuh"
 #include "solvers.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -313,6 +314,42 @@ int gp_solve_cg_f64(int kind, const double *theta, int d, const double *X, int64
     GP_TRY(solver_args<double>(kind, theta, d, X, n, B, nrhs, V_inout, max_iters, tol, stop_rule, info, &kp));
     return cg_solve<double>(kp, X, n, B, nrhs, V_inout, max_iters, tol, stop_rule, GP_PREC_FP32, info, ws,
                             ws_bytes, stream);
+    GP_API_END
+}
+
+// ------------------------------------------------------------------ preconditioned CG
+size_t gp_solve_pcg_workspace(int64_t n, int d, int nrhs, int prec, int rank) {
+    return cg_workspace<float>(n, d, nrhs, prec, std::max(0, std::min<int>(rank, (int)std::min<int64_t>(n, 128))));
+}
+size_t gp_solve_pcg_f64_workspace(int64_t n, int d, int nrhs, int rank) {
+    return cg_workspace<double>(n, d, nrhs, GP_PREC_FP32,
+                                std::max(0, std::min<int>(rank, (int)std::min<int64_t>(n, 128))));
+}
+
+int gp_solve_pcg(int kind, const double *theta, int d, const float *X, int64_t n, const float *B, int nrhs,
+                 float *V_inout, int64_t max_iters, double tol, int stop_rule, int prec, int rank,
+                 gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    KP<float> kp;
+    GP_TRY(solver_args<float>(kind, theta, d, X, n, B, nrhs, V_inout, max_iters, tol, stop_rule, info, &kp));
+    GP_TRY(check_prec(prec));
+    REQ(rank >= 0 && rank <= 128, "rank must be in [0, 128]");
+    const int k = (int)std::min<int64_t>(rank, n);
+    return cg_solve<float>(kp, X, n, B, nrhs, V_inout, max_iters, tol, stop_rule, prec, info, ws, ws_bytes,
+                           stream, k);
+    GP_API_END
+}
+
+int gp_solve_pcg_f64(int kind, const double *theta, int d, const double *X, int64_t n, const double *B,
+                     int nrhs, double *V_inout, int64_t max_iters, double tol, int stop_rule, int rank,
+                     gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    KP<double> kp;
+    GP_TRY(solver_args<double>(kind, theta, d, X, n, B, nrhs, V_inout, max_iters, tol, stop_rule, info, &kp));
+    REQ(rank >= 0 && rank <= 128, "rank must be in [0, 128]");
+    const int k = (int)std::min<int64_t>(rank, n);
+    return cg_solve<double>(kp, X, n, B, nrhs, V_inout, max_iters, tol, stop_rule, GP_PREC_FP32, info, ws,
+                            ws_bytes, stream, k);
     GP_API_END
 }
 

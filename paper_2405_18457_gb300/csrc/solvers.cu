@@ -17,14 +17,15 @@ namespace gp {
 namespace {
 
 // ---------------------------------------------------------------- CG kernels
-// gamma = ||r||^2 after the initial residual; sets done if already converged.
+// gamma = r^T P^-1 r (partG; = ||r||^2 without a preconditioner) after the initial residual,
+// split norms from ||r||^2 (partN); sets done if already converged.
 // One block, one thread per column (R <= 512).
-__global__ void cg_start_kernel(int R, int P, const double *part, double *gamma, SolverState *st,
-                                long long max_iters, double tol, int stop_rule) {
+__global__ void cg_start_kernel(int R, int P, const double *partG, const double *partN, double *gamma,
+                                SolverState *st, long long max_iters, double tol, int stop_rule) {
     __shared__ double sq[512];
     for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        sq[c] = sum_parts(part, c, P);
-        gamma[c] = sq[c];
+        sq[c] = sum_parts(partN, c, P);
+        gamma[c] = sum_parts(partG, c, P);
     }
     if (threadIdx.x == 0) {
         st->done = 0;
@@ -73,18 +74,20 @@ __global__ void cg_update_kernel(T *v, T *r, const T *d, const T *Hd, int64_t n,
     }
 }
 
-// beta = gamma_new / gamma ; gamma = gamma_new ; norms ; t++ ; loop condition.
-// One block, one thread per column.
-__global__ void cg_beta_kernel(int R, int P, const double *part, double *gamma, const double *alpha, double *beta,
-                               SolverState *st, long long max_iters, double tol, int stop_rule) {
+// beta = gamma_new / gamma ; gamma = gamma_new (partG: r^T P^-1 r) ; split norms from ||r||^2
+// (partN, current for frozen columns too) ; t++ ; loop condition.  One block, one thread per
+// column.  Without a preconditioner partG == partN.
+__global__ void cg_beta_kernel(int R, int P, const double *partG, const double *partN, double *gamma,
+                               const double *alpha, double *beta, SolverState *st, long long max_iters, double tol,
+                               int stop_rule) {
     if (st->done) return;
     __shared__ double sq[512];
     for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        double gn = sum_parts(part, c, P);
+        double gn = sum_parts(partG, c, P);
         bool active = alpha[c] != 0.0;
         beta[c] = active ? gn / gamma[c] : 0.0;
         if (active) gamma[c] = gn;
-        sq[c] = active ? gn : gamma[c];
+        sq[c] = sum_parts(partN, c, P);
     }
     const long long t = st->iter + 1;
     __syncthreads();
@@ -203,7 +206,7 @@ struct HOp {
 // Conjugate gradients, Alg. 1 (P = identity)
 // ===========================================================================
 template <typename T>
-size_t cg_workspace(int64_t n, int d, int R, int prec) {
+size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank) {
     const int P = nparts_for(n);
     Carver c(nullptr);
     for (int k = 0; k < 3; ++k) c.take<T>((size_t)R * n);  // r, d, Hd
@@ -211,16 +214,23 @@ size_t cg_workspace(int64_t n, int d, int R, int prec) {
     for (int k = 0; k < 4; ++k) c.take<double>(R);          // scale, gamma, alpha, beta
     c.take<SolverState>(1);
     c.take<char>(HOp<T>::workspace(n, d, R, prec));
+    if (pc_rank > 0) {
+        c.take<T>((size_t)R * n);                           // p = P^-1 r
+        c.take<double>((size_t)R * P);                      // r^T p partial sums
+        c.take<char>(precond_workspace<T>(n, R, pc_rank));
+    }
     return c.bytes();
 }
 
 template <typename T>
 int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t max_iters, double tol,
-             int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st) {
+             int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st,
+             int pc_rank) {
     if (R > 512) {
         set_error("nrhs must be <= 512");
         return GP_ERR_INVALID_ARG;
     }
+    const bool pc = pc_rank > 0;
     const int P = nparts_for(n);
     Carver c(ws);
     T *r = c.take<T>((size_t)R * n);
@@ -234,10 +244,16 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     SolverState *sd = c.take<SolverState>(1);
     size_t opb = HOp<T>::workspace(n, kp.d, R, prec);
     void *opw = c.take<char>(opb);
+    T *pz = pc ? c.take<T>((size_t)R * n) : nullptr;
+    double *partG = pc ? c.take<double>((size_t)R * P) : part;
+    const size_t pcb = pc ? precond_workspace<T>(n, R, pc_rank) : 0;
+    void *pcw = pc ? c.take<char>(pcb) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
     HOp<T> op;
     GP_TRY(op.init(kp, X, n, R, prec, opw, opb, st));
+    Precond<T> pcd{};
+    if (pc) GP_TRY(precond_build<T>(kp, X, n, R, pc_rank, pcw, pcb, &pcd, st));
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
     const dim3 gp_((unsigned)P, (unsigned)R);
     const int *done = &sd->done;
@@ -247,12 +263,18 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
     GP_TRY(check_launch("cg setup", 3));
-    // r = b~ - H v ; d = r ; gamma = r^T r
+    // r = b~ - H v ; p = P^-1 r ; d = p ; gamma = r^T p
     GP_TRY(op.apply(V, Hd, nullptr, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, Hd, r, dd, n, scale);
+    GP_TRY(check_launch("cg residual"));
+    if (pc) {
+        GP_TRY(precond_apply<T>(pcd, r, pz, nullptr, st));
+        GP_TRY_CUDA(cudaMemcpyAsync(dd, pz, sizeof(T) * (size_t)R * n, cudaMemcpyDeviceToDevice, st));
+        coldot_kernel<T><<<gp_, 256, 0, st>>>(r, pz, n, P, partG, nullptr);
+    }
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
-    cg_start_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, sd, (long long)max_iters, tol, stop_rule);
-    GP_TRY(check_launch("cg start", 3));
+    cg_start_kernel<<<1, 256, 0, st>>>(R, P, partG, part, gamma, sd, (long long)max_iters, tol, stop_rule);
+    GP_TRY(check_launch("cg start", pc ? 3 : 2));
 
     // Iterations are enqueued speculatively in chunks without waiting for the start-up
     // kernels: once the device-side loop condition latches `done`, the remaining kernels
@@ -269,10 +291,14 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
             cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
             cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
-            cg_beta_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, beta, sd, (long long)max_iters, tol,
+            if (pc) {
+                GP_TRY(precond_apply<T>(pcd, r, pz, done, st));
+                coldot_kernel<T><<<gp_, 256, 0, st>>>(r, pz, n, P, partG, done);
+            }
+            cg_beta_kernel<<<1, 256, 0, st>>>(R, P, partG, part, gamma, alpha, beta, sd, (long long)max_iters, tol,
                                               stop_rule);
-            cg_dir_kernel<T><<<gv, 256, 0, st>>>(dd, r, n, beta, sd);
-            GP_TRY(check_launch("cg iteration", 5));
+            cg_dir_kernel<T><<<gv, 256, 0, st>>>(dd, pc ? pz : r, n, beta, sd);
+            GP_TRY(check_launch("cg iteration", pc ? 6 : 5));
         }
         launched += k;
         ++polls;
@@ -291,12 +317,12 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     return GP_OK;
 }
 
-template size_t cg_workspace<float>(int64_t, int, int, int);
-template size_t cg_workspace<double>(int64_t, int, int, int);
+template size_t cg_workspace<float>(int64_t, int, int, int, int);
+template size_t cg_workspace<double>(int64_t, int, int, int, int);
 template int cg_solve<float>(const KP<float> &, const float *, int64_t, const float *, int, float *, int64_t,
-                             double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t);
+                             double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t, int);
 template int cg_solve<double>(const KP<double> &, const double *, int64_t, const double *, int, double *,
-                              int64_t, double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t);
+                              int64_t, double, int, int, gp_solve_info_t *, void *, size_t, cudaStream_t, int);
 
 // ===========================================================================
 // Stochastic gradient descent, Alg. 3

@@ -42,12 +42,33 @@ int predict(const KP<float> &kp, const float *Xstar, int64_t nstar, const float 
             int s, const float *Fstar, const float *ystar, float *mean, float *var, double *metrics, int prec,
             void *ws, size_t ws_bytes, cudaStream_t st);
 
+// Pivoted Cholesky preconditioner (precond.cu): P = L^T L + sigma^2 I, applied by Woodbury.
+template <typename T>
+struct Precond {
+    int k;
+    int64_t n;
+    int R;
+    T *L;            // k x n factor rows
+    double *G;       // k x k Cholesky factor of sigma^2 I + L L^T (lower triangle)
+    double *part;    // per-tile partial sums of L r
+    double *w;       // k x R
+    double inv_sigma2;
+};
+template <typename T>
+size_t precond_workspace(int64_t n, int R, int k);
+template <typename T>
+int precond_build(const KP<T> &kp, const T *X, int64_t n, int R, int k, void *ws, size_t ws_bytes, Precond<T> *out,
+                  cudaStream_t st);
+template <typename T>
+int precond_apply(const Precond<T> &P, const T *r, T *p, const int *done, cudaStream_t st);
+
 // Solvers (App. B, Alg. 1-3).
 template <typename T>
-size_t cg_workspace(int64_t n, int d, int R, int prec);
+size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank = 0);
 template <typename T>
 int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, int64_t max_iters, double tol,
-             int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st);
+             int stop_rule, int prec, gp_solve_info_t *info, void *ws, size_t ws_bytes, cudaStream_t st,
+             int pc_rank = 0);
 
 template <typename T>
 size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec);

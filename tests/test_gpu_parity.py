@@ -417,3 +417,69 @@ def test_predictions_match_oracle(dev, prec_name, prec, tol):
     assert rel(var.cpu().numpy(), v_ref) < tol
     met = met.cpu().numpy()
     assert abs(met[0] - rmse) <= tol * rmse and abs(met[1] - llh) <= 10 * tol * abs(llh)
+
+
+@pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
+def test_pcg_iterates_match_oracle_fp64(dev, kind):
+    """Preconditioned CG (App. B: pivoted Cholesky, here rank 20) iterate by iterate in FP64."""
+    rng = np.random.default_rng(50 + kind)
+    n, d, R = 230, 3, 4
+    X = rng.uniform(0, 1, size=(n, d))
+    th = np.concatenate([rng.uniform(0.4, 0.7, size=d), [1.0, 0.1]])
+    B = rng.standard_normal((R, n))
+    V, info = gp.gp_solve_cg(kind, th, t(X, dev, torch.float64), t(B, dev, torch.float64), max_iters=6, tol=0.0,
+                             precond_rank=20)
+    Vr, ir = oracle.solve_pcg(kind, th, X, B, 20, max_iters=6, tol=0.0)
+    assert info.iters == ir["iters"] == 6
+    assert rel(V.cpu().numpy(), Vr) < 1e-9
+
+
+def test_pcg_full_rank_converges_in_one_iteration(dev):
+    rng = np.random.default_rng(52)
+    n, R = 90, 3
+    X = rng.standard_normal((n, 2))
+    th = np.array([0.8, 1.2, 1.0, 0.4])
+    B = rng.standard_normal((R, n))
+    V, info = gp.gp_solve_cg(oracle.RBF, th, t(X, dev, torch.float64), t(B, dev, torch.float64), max_iters=5,
+                             tol=1e-8, precond_rank=128)
+    assert info.converged and info.iters == 1
+    H = oracle.H_matrix(oracle.RBF, th, X)
+    assert rel(V.cpu().numpy(), np.linalg.solve(H, B.T).T) < 1e-7
+
+
+def test_pcg_reaches_tolerance_in_fewer_iterations_fp32(dev):
+    """The small workload's shape (RBF, l = 0.5, sigma = 0.1, ill-conditioned): with the rank-100
+    preconditioner CG meets the tolerance (true FP64 residual) in fewer iterations."""
+    tol = 1e-4
+    p = workloads.small(n=1500, s=4, seed=2)
+    X32 = p.X.astype(np.float32)
+    B = np.vstack([p.y, p.Z]).astype(np.float32)
+    V0, info0 = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), max_iters=3000, tol=tol,
+                               prec=gp.GP_PREC_FP32)
+    V, info = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), max_iters=3000, tol=tol,
+                             prec=gp.GP_PREC_FP32, precond_rank=100)
+    assert info.converged and info0.converged and info.iters < info0.iters
+    Xr, Br = X32.astype(np.float64), B.astype(np.float64)
+    r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
+    rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
+    assert rn[0] <= 1.5 * tol and rn[1:].mean() <= 1.5 * tol
+
+
+def test_tc16_pcg_at_the_paper_tolerance_true_residual(dev):
+    """Tensor-core products with the rank-100 preconditioner at tau = 0.01 on the pathwise
+    workload's shape (sigma = 0.3; an fp16 product cannot certify tau on the ill-conditioned small
+    workload, see the plain-CG tests): converged and the true FP64 residual meets tau.  In this
+    high-dimensional shape the kernel spectrum is flat, so a rank-100 factor barely changes the
+    iteration count (the FP32 test above shows the reduction on the small workload)."""
+    if not tc_built():
+        pytest.skip("tensor-core path not built")
+    p = workloads.pathwise(n=3000, d=8, s=16, m=256, seed=3)
+    X32 = p.X.astype(np.float32)
+    B = np.vstack([p.y_noise, p.Z]).astype(np.float32)
+    V, info = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), max_iters=500, tol=1e-2,
+                             prec=gp.GP_PREC_TC16, precond_rank=100)
+    assert info.converged
+    Xr, Br = X32.astype(np.float64), B.astype(np.float64)
+    r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
+    rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
+    assert rn[0] <= 1.5e-2 and rn[1:].mean() <= 1.5e-2
