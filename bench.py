@@ -395,6 +395,164 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+SMALL_METRIC = "sec per MLL step, small workload (CG to 1e-6, cold start), plain vs pivoted-Cholesky preconditioned CG"
+
+
+def run_small(args):
+    """The small workload (n = 2048, d = 8, RBF l = 0.5, sigma = 0.1, s = 8 Gaussian probes, CG to
+    relative tolerance 1e-6 from a cold start, standard estimator, Adam lr 0.1): seconds per MLL
+    step with plain CG and with the rank-100 pivoted Cholesky preconditioner of App. B, FP32
+    form, next to the plain FP64 GPU form with the same preconditioner."""
+    import torch
+
+    import paper_2405_18457_gb300 as gp
+    from paper_2405_18457_gb300 import workloads
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    gp.library()
+    p = workloads.small()
+    res = {}
+    for name, dtype, rank in (("fp32_plain", torch.float32, 0), ("fp32_pc100", torch.float32, 100),
+                              ("fp64_pc100", torch.float64, 100)):
+        Xt = torch.tensor(p.X, dtype=dtype, device=dev)
+        B = torch.tensor(np.vstack([p.y, p.Z]), dtype=dtype, device=dev)
+        Zt = B[1:].contiguous()
+        nu = np.log(np.expm1(p.theta))
+        m = np.zeros_like(nu)
+        v = np.zeros_like(nu)
+        theta = p.theta.copy()
+        steps = args.steps if dtype == torch.float32 else max(1, args.fp64_steps)
+        times, iters = [], []
+        for t in range(1, args.warmup + steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            V, info = gp.gp_solve_cg(p.kind, theta, Xt, B, max_iters=20000, tol=1e-6, prec=gp.GP_PREC_FP32,
+                                     precond_rank=rank)
+            g = gp.gp_mll_grad_standard(p.kind, theta, Xt, V, Zt, prec=gp.GP_PREC_FP32).cpu().numpy()
+            theta = gp.gp_adam_softplus_step(nu, m, v, t, g, lr=0.1)
+            torch.cuda.synchronize()
+            if t > args.warmup:
+                times.append(time.perf_counter() - t0)
+                iters.append(info.iters)
+        res[name] = {"sec_per_step": float(np.mean(times)), "cg_iters": iters}
+    out = {"metric": SMALL_METRIC, "value": res["fp32_pc100"]["sec_per_step"], "unit": "s per step",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * res["fp32_pc100"]["sec_per_step"], "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic (seeded)",
+           "config": {"workload": "small: n=2048 d=8 RBF l=0.5 sigma=0.1 s=8, CG tol 1e-6 cold, standard "
+                                  "estimator, Adam lr 0.1"},
+           "forms": res,
+           "speedup_pc_vs_plain": res["fp32_plain"]["sec_per_step"] / res["fp32_pc100"]["sec_per_step"]}
+    print(json.dumps(out))
+
+
+ABL_METRIC = "solver time to tolerance per MLL step: standard vs pathwise x cold vs warm x CG/AP/SGD"
+
+
+def run_ablation(args):
+    """Table 1's design on synthetic data: for each solver (CG, AP with 1024-row blocks, SGD with
+    512-row batches and momentum 0.9) and each of standard / pathwise probes x cold / warm start,
+    run `--abl-steps` marginal-likelihood steps (tensor-core form, Matern-3/2, n = 8192, d = 8,
+    s = 64, tau = 0.01 with budgets of 1000 CG iterations and 40 epochs for AP/SGD, Adam lr 0.1)
+    and report the solver's time and iterations per step and the speed-up over standard-cold."""
+    import torch
+
+    import paper_2405_18457_gb300 as gp
+    from paper_2405_18457_gb300 import workloads
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    gp.library()
+    n, steps, s = 8192, args.abl_steps, 64
+    p = workloads.pathwise(n=n, d=8, s=s, m=1024, seed=11)
+    tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    X = tf(p.X)
+    om, c2, Wp, w = tf(p.omega_hat), tf(p.chi2), tf(p.W_probe), tf(p.Z)
+    fy = gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, tf(p.W_y))[0]
+    y = (fy + p.noise_y * tf(p.y_noise)).contiguous()
+    Zstd = tf(p.Z)
+    prec = gp.GP_PREC_TC16
+    bs_ap, bs_sgd, epochs = 1024, 512, 40
+    rng = np.random.default_rng(12)
+
+    def solve(solver, theta, B, V0, lr_sgd):
+        if solver == "cg":
+            return gp.gp_solve_cg(p.kind, theta, X, B, V0=V0, max_iters=1000, tol=0.01, prec=prec)
+        if solver == "ap":
+            return gp.gp_solve_ap(p.kind, theta, X, B, V0=V0, block_size=bs_ap, max_iters=epochs * n // bs_ap,
+                                  tol=0.01, prec=prec)
+        iters = epochs * n // bs_sgd
+        idx = torch.tensor(workloads.sgd_batches(n, bs_sgd, iters, seed=int(rng.integers(1 << 30))),
+                           dtype=torch.int32, device=dev)
+        return gp.gp_solve_sgd(p.kind, theta, X, B, idx, lr=lr_sgd, momentum=0.9, V0=V0, tol=0.01, prec=prec)
+
+    # SGD step size: the largest of a grid that does not diverge on the first system (the paper's rule)
+    lr_sgd = None
+    B0 = torch.cat([y[None], Zstd], 0).contiguous()
+    for lr in (50.0, 20.0, 10.0, 5.0, 2.0, 1.0, 0.5):
+        try:
+            solve("sgd", p.theta, B0, None, lr)
+            lr_sgd = lr
+            break
+        except gp.GPError:
+            continue
+    rows = {}
+    for solver in ("cg", "ap", "sgd"):
+        for pathwise in (False, True):
+            for warm in (False, True):
+                theta = p.theta.copy()
+                nu = np.log(np.expm1(theta))
+                m_ = np.zeros_like(nu)
+                v_ = np.zeros_like(nu)
+                V = None
+                t_tot, its, conv = 0.0, [], 0
+                for t in range(1, steps + 1):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    if pathwise:
+                        F = gp.gp_rff_prior_sample(p.kind, theta, X, om, c2, Wp)
+                        B = gp.gp_pathwise_rhs(theta, p.d, y, F, w)
+                    else:
+                        B = B0
+                    V0 = V.clone() if (warm and V is not None) else None
+                    try:
+                        V, info = solve(solver, theta, B, V0, lr_sgd)
+                    except gp.GPError:
+                        V, info = None, None
+                    torch.cuda.synchronize()
+                    t_tot += time.perf_counter() - t0
+                    if info is None:
+                        its.append(-1)
+                        V = None
+                        continue
+                    its.append(int(info.iters))
+                    conv += int(info.converged)
+                    if pathwise:
+                        g = gp.gp_mll_grad_pathwise(p.kind, theta, X, V, prec=prec)
+                    else:
+                        g = gp.gp_mll_grad_standard(p.kind, theta, X, V, Zstd, prec=prec)
+                    theta = gp.gp_adam_softplus_step(nu, m_, v_, t, g.cpu().numpy(), lr=0.1)
+                rows["%s/%s/%s" % (solver, "pathwise" if pathwise else "standard", "warm" if warm else "cold")] = {
+                    "solver_sec_per_step": t_tot / steps, "iters": its, "converged_steps": conv}
+    for solver in ("cg", "ap", "sgd"):
+        base = rows["%s/standard/cold" % solver]["solver_sec_per_step"]
+        for k, r in rows.items():
+            if k.startswith(solver + "/"):
+                r["speedup_vs_standard_cold"] = base / r["solver_sec_per_step"]
+    out = {"metric": ABL_METRIC, "value": rows["cg/pathwise/warm"]["speedup_vs_standard_cold"],
+           "unit": "x speed-up of CG pathwise+warm over standard+cold", "n_gpus": 1, "steps": steps, "warmup": 0,
+           "ms_per_step": 1e3 * rows["cg/pathwise/warm"]["solver_sec_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f16-tensor/f32/f64", "data": "synthetic (seeded)",
+           "config": {"workload": "ablation: n=%d d=8 Matern-3/2 sigma=0.3 s=%d, tau 0.01, CG <= 1000 iters, AP b=%d "
+                                  "and SGD b=%d (lr %s, momentum 0.9) <= %d epochs, Adam lr 0.1, %d steps"
+                                  % (n, s, bs_ap, bs_sgd, lr_sgd, epochs, steps)},
+           "grid": rows}
+    print(json.dumps(out))
+
+
 BATCH_METRIC = "batched MLL step time (256 independent uneven RBF GPs, one captured CUDA graph per step)"
 
 
@@ -618,7 +776,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--kernel-reps", type=int, default=10)
-    ap.add_argument("--workload", choices=["pathwise", "batched"], default="pathwise")
+    ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation"], default="pathwise")
+    ap.add_argument("--abl-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-gps", type=int, default=256)
     args = ap.parse_args()
@@ -629,6 +788,12 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "small":
+        run_small(args)
+        return
+    if args.workload == "ablation":
+        run_ablation(args)
         return
     if args.prec is None:
         args.prec = "tc16" if _tc_ok() else "fp32"
