@@ -71,6 +71,7 @@ def _load():
                 "gpo_mll_grad_exact": (_i, [_i, _i, _pd, _pd, _i64, _pd, _pd]),
                 "gpo_grad_bilinear": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _pd, _i, _pd]),
                 "gpo_bilinear_value": (_d, [_i, _i, _pd, _pd, _i64, _pd, _pd, _pd, _i]),
+                "gpo_rkhs_sqdist": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _i, _pd]),
                 "gpo_dkernel_dx": (None, [_i, _i, _pd, _pd, _pd, _pd]),
                 "gpo_grad_bilinear_X": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _pd, _i, _pd]),
                 "gpo_grad_standard": (None, [_i, _i, _pd, _pd, _i64, _pd, _pd, _i, _pd]),
@@ -239,6 +240,28 @@ def bilinear_value(kind, theta, X, U, W, lam):
     lam = _a(lam)
     return float(_load().gpo_bilinear_value(kind, d, _p(theta), _p(X), X.shape[0], _p(U), _p(W), _p(lam),
                                             U.shape[0]))
+
+
+def rkhs_sqdist(kind, theta, X, U, Uinit=None):
+    """Per column, ||Uinit[c] - U[c]||_H^2 = (Uinit[c] - U[c])^T H (Uinit[c] - U[c]) (Sec. 3,
+    Eq. RKHS_distance); Uinit None is the zero initialisation."""
+    X, theta, d = _dims(X, theta)
+    U = np.ascontiguousarray(_a(U).reshape(-1, X.shape[0]))
+    R = U.shape[0]
+    U0 = None if Uinit is None else np.ascontiguousarray(_a(Uinit).reshape(R, X.shape[0]))
+    out = np.empty(R)
+    _load().gpo_rkhs_sqdist(kind, d, _p(theta), _p(X), X.shape[0], None if U0 is None else _p(U0), _p(U), R,
+                            _p(out))
+    return out
+
+
+def trace_H_inv(kind, theta, X):
+    """tr(H^-1), the expected initial RKHS distance of the standard estimator's systems
+    (Sec. 3, Eq. standard_dist), from the dense H and its Cholesky factor (numpy)."""
+    H = H_matrix(kind, theta, X)
+    L = np.linalg.cholesky(H)
+    Linv = np.linalg.solve(L, np.eye(H.shape[0]))
+    return float(np.sum(Linv * Linv))
 
 
 def dkernel_dx(kind, theta, x, xp):

@@ -362,6 +362,33 @@ double gpo_bilinear_value(int kind, int d, const double *theta, const double *X,
 }
 
 /*
+ * RKHS squared distance between a solver initialisation and a solution (Sec. 3,
+ * "Initial Distance to the Linear System Solution", Eq. RKHS_distance), one value
+ * per column c:  dist[c] = (Uinit[c] - U[c])^T H (Uinit[c] - U[c]).
+ * Uinit == NULL means the zero initialisation, so dist[c] = U[c]^T H U[c].
+ */
+void gpo_rkhs_sqdist(int kind, int d, const double *theta, const double *X, int64_t n,
+                     const double *Uinit, const double *U, int R, double *dist)
+{
+    double s2 = theta[d + 1] * theta[d + 1];
+    double *e = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int c = 0; c < R; ++c) {
+        for (int64_t i = 0; i < n; ++i)
+            e[i] = (Uinit ? Uinit[(int64_t)c * n + i] : 0.0) - U[(int64_t)c * n + i];
+        double total = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : total)
+        for (int64_t i = 0; i < n; ++i) {
+            double row = 0.0;
+            for (int64_t j = 0; j < n; ++j)
+                row += (gpo_kernel(kind, d, theta, X + i * d, X + j * d) + (i == j ? s2 : 0.0)) * e[j];
+            total += e[i] * row;
+        }
+        dist[c] = total;
+    }
+    free(e);
+}
+
+/*
  * Gradient of k(x, x') with respect to its first argument, g (d values).
  * By the chain rule through r (r^2 = sum_p (x_p - x'_p)^2 / l_p^2):
  *   RBF:      dk/dx_p = -k (x_p - x'_p) / l_p^2
