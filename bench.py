@@ -174,6 +174,7 @@ class Replica:
         if self.phase_ms is not None:
             for (_, e0), (name, e1) in zip(self._events[:-1], self._events[1:]):
                 self.phase_ms[name] = self.phase_ms.get(name, 0.0) + e0.elapsed_time(e1)
+        self.last_theta = th
         self.theta = gp.gp_adam_softplus_step(self.nu, self.m, self.v, self.t, gh, lr=0.1)
         self.t += 1
         self.last = info
@@ -451,12 +452,100 @@ def run_small(args):
 ABL_METRIC = "solver time to tolerance per MLL step: standard vs pathwise x cold vs warm x CG/AP/SGD"
 
 
-def run_ablation(args):
-    """Table 1's design on synthetic data: for each solver (CG, AP with 1024-row blocks, SGD with
-    512-row batches and momentum 0.9) and each of standard / pathwise probes x cold / warm start,
-    run `--abl-steps` marginal-likelihood steps (tensor-core form, Matern-3/2, n = 8192, d = 8,
-    s = 64, tau = 0.01 with budgets of 1000 CG iterations and 40 epochs for AP/SGD, Adam lr 0.1)
-    and report the solver's time and iterations per step and the speed-up over standard-cold."""
+class SolverGrid:
+    """Shared set-up of the solver ablations (Table 1's design, Sec. 5's budgets) on synthetic data:
+    Matern-3/2, n = 8192, d = 8, s = 64, sigma = 0.3, targets an RFF prior draw plus noise, the
+    tensor-core form, tau = 0.01, AP with 1024-row blocks, SGD with 512-row batches and momentum 0.9
+    (step size: the largest of a grid that does not diverge on the first system), Adam lr 0.1."""
+
+    def __init__(self, torch, gp, workloads, dev, n=8192, s=64):
+        self.torch, self.gp, self.wl, self.dev = torch, gp, workloads, dev
+        self.n, self.s = n, s
+        p = self.p = workloads.pathwise(n=n, d=8, s=s, m=1024, seed=11)
+        tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+        self.X = tf(p.X)
+        self.om, self.c2, self.Wp, self.w = tf(p.omega_hat), tf(p.chi2), tf(p.W_probe), tf(p.Z)
+        fy = gp.gp_rff_prior_sample(p.kind, p.theta, self.X, self.om, self.c2, tf(p.W_y))[0]
+        self.y = (fy + p.noise_y * tf(p.y_noise)).contiguous()
+        self.B_std = torch.cat([self.y[None], self.w], 0).contiguous()
+        self.prec = gp.GP_PREC_TC16
+        self.bs_ap, self.bs_sgd = 1024, 512
+        self.rng = np.random.default_rng(12)
+        self.lr_sgd = None
+        for lr in (50.0, 20.0, 10.0, 5.0, 2.0, 1.0, 0.5):
+            try:
+                self.solve("sgd", p.theta, self.B_std, None, 40, lr=lr)
+                self.lr_sgd = lr
+                break
+            except gp.GPError:
+                continue
+
+    def solve(self, solver, theta, B, V0, epochs, lr=None):
+        gp, p, n = self.gp, self.p, self.n
+        if solver == "cg":
+            return gp.gp_solve_cg(p.kind, theta, self.X, B, V0=V0, max_iters=epochs, tol=0.01, prec=self.prec)
+        if solver == "ap":
+            return gp.gp_solve_ap(p.kind, theta, self.X, B, V0=V0, block_size=self.bs_ap,
+                                  max_iters=epochs * n // self.bs_ap, tol=0.01, prec=self.prec)
+        iters = epochs * n // self.bs_sgd
+        idx = self.torch.tensor(self.wl.sgd_batches(n, self.bs_sgd, iters, seed=int(self.rng.integers(1 << 30))),
+                                dtype=self.torch.int32, device=self.dev)
+        return gp.gp_solve_sgd(p.kind, theta, self.X, B, idx, lr=self.lr_sgd if lr is None else lr, momentum=0.9,
+                               V0=V0, tol=0.01, prec=self.prec)
+
+    def rhs(self, theta, pathwise):
+        gp, p = self.gp, self.p
+        if not pathwise:
+            return self.B_std
+        F = gp.gp_rff_prior_sample(p.kind, theta, self.X, self.om, self.c2, self.Wp)
+        return gp.gp_pathwise_rhs(theta, p.d, self.y, F, self.w)
+
+    def true_residuals(self, theta, B, V):
+        """Relative residual norms ||b - H v|| / ||b|| of the y system and the mean over the probes'
+        systems, from one product (measurement only)."""
+        HV = self.gp.gp_kernel_mvm(self.p.kind, theta, self.X, V, add_noise=True, prec=self.prec)
+        rel = ((B - HV).norm(dim=1) / B.norm(dim=1)).double().cpu().numpy()
+        return float(rel[0]), float(rel[1:].mean())
+
+    def run(self, solver, pathwise, warm, steps, epochs, residuals=False):
+        """`steps` marginal-likelihood steps; per step the solver's wall time, iterations, convergence
+        flag and (optionally) the true residual norms reached."""
+        torch, gp, p = self.torch, self.gp, self.p
+        theta = p.theta.copy()
+        nu = np.log(np.expm1(theta))
+        m_, v_ = np.zeros_like(nu), np.zeros_like(nu)
+        V = None
+        out = {"sec": [], "iters": [], "converged": [], "res_y": [], "res_z": []}
+        for t in range(1, steps + 1):
+            B = self.rhs(theta, pathwise)
+            V0 = V.clone() if (warm and V is not None) else None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                V, info = self.solve(solver, theta, B, V0, epochs)
+            except gp.GPError:
+                V, info = None, None
+            torch.cuda.synchronize()
+            out["sec"].append(time.perf_counter() - t0)
+            if info is None:
+                out["iters"].append(-1)
+                out["converged"].append(False)
+                continue
+            out["iters"].append(int(info.iters))
+            out["converged"].append(bool(info.converged))
+            if residuals:
+                ry, rz = self.true_residuals(theta, B, V)
+                out["res_y"].append(ry)
+                out["res_z"].append(rz)
+            if pathwise:
+                g = gp.gp_mll_grad_pathwise(p.kind, theta, self.X, V, prec=self.prec)
+            else:
+                g = gp.gp_mll_grad_standard(p.kind, theta, self.X, V, self.w, prec=self.prec)
+            theta = gp.gp_adam_softplus_step(nu, m_, v_, t, g.cpu().numpy(), lr=0.1)
+        return out
+
+
+def _gpu_setup():
     import torch
 
     import paper_2405_18457_gb300 as gp
@@ -466,77 +555,25 @@ def run_ablation(args):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     gp.library()
-    n, steps, s = 8192, args.abl_steps, 64
-    p = workloads.pathwise(n=n, d=8, s=s, m=1024, seed=11)
-    tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
-    X = tf(p.X)
-    om, c2, Wp, w = tf(p.omega_hat), tf(p.chi2), tf(p.W_probe), tf(p.Z)
-    fy = gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, tf(p.W_y))[0]
-    y = (fy + p.noise_y * tf(p.y_noise)).contiguous()
-    Zstd = tf(p.Z)
-    prec = gp.GP_PREC_TC16
-    bs_ap, bs_sgd, epochs = 1024, 512, 40
-    rng = np.random.default_rng(12)
+    return torch, gp, workloads, dev
 
-    def solve(solver, theta, B, V0, lr_sgd):
-        if solver == "cg":
-            return gp.gp_solve_cg(p.kind, theta, X, B, V0=V0, max_iters=1000, tol=0.01, prec=prec)
-        if solver == "ap":
-            return gp.gp_solve_ap(p.kind, theta, X, B, V0=V0, block_size=bs_ap, max_iters=epochs * n // bs_ap,
-                                  tol=0.01, prec=prec)
-        iters = epochs * n // bs_sgd
-        idx = torch.tensor(workloads.sgd_batches(n, bs_sgd, iters, seed=int(rng.integers(1 << 30))),
-                           dtype=torch.int32, device=dev)
-        return gp.gp_solve_sgd(p.kind, theta, X, B, idx, lr=lr_sgd, momentum=0.9, V0=V0, tol=0.01, prec=prec)
 
-    # SGD step size: the largest of a grid that does not diverge on the first system (the paper's rule)
-    lr_sgd = None
-    B0 = torch.cat([y[None], Zstd], 0).contiguous()
-    for lr in (50.0, 20.0, 10.0, 5.0, 2.0, 1.0, 0.5):
-        try:
-            solve("sgd", p.theta, B0, None, lr)
-            lr_sgd = lr
-            break
-        except gp.GPError:
-            continue
+def run_ablation(args):
+    """Table 1's design on synthetic data: for each solver (CG, AP, SGD) and each of standard /
+    pathwise probes x cold / warm start, `--abl-steps` marginal-likelihood steps solved to
+    tau = 0.01 (budgets: 1000 CG iterations, 40 epochs of AP / SGD); reports the solver's time
+    and iterations per step and the speed-up over standard-cold (SolverGrid has the workload)."""
+    torch, gp, workloads, dev = _gpu_setup()
+    grid = SolverGrid(torch, gp, workloads, dev)
+    steps = args.abl_steps
     rows = {}
     for solver in ("cg", "ap", "sgd"):
         for pathwise in (False, True):
             for warm in (False, True):
-                theta = p.theta.copy()
-                nu = np.log(np.expm1(theta))
-                m_ = np.zeros_like(nu)
-                v_ = np.zeros_like(nu)
-                V = None
-                t_tot, its, conv = 0.0, [], 0
-                for t in range(1, steps + 1):
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    if pathwise:
-                        F = gp.gp_rff_prior_sample(p.kind, theta, X, om, c2, Wp)
-                        B = gp.gp_pathwise_rhs(theta, p.d, y, F, w)
-                    else:
-                        B = B0
-                    V0 = V.clone() if (warm and V is not None) else None
-                    try:
-                        V, info = solve(solver, theta, B, V0, lr_sgd)
-                    except gp.GPError:
-                        V, info = None, None
-                    torch.cuda.synchronize()
-                    t_tot += time.perf_counter() - t0
-                    if info is None:
-                        its.append(-1)
-                        V = None
-                        continue
-                    its.append(int(info.iters))
-                    conv += int(info.converged)
-                    if pathwise:
-                        g = gp.gp_mll_grad_pathwise(p.kind, theta, X, V, prec=prec)
-                    else:
-                        g = gp.gp_mll_grad_standard(p.kind, theta, X, V, Zstd, prec=prec)
-                    theta = gp.gp_adam_softplus_step(nu, m_, v_, t, g.cpu().numpy(), lr=0.1)
+                r = grid.run(solver, pathwise, warm, steps, 1000 if solver == "cg" else 40)
                 rows["%s/%s/%s" % (solver, "pathwise" if pathwise else "standard", "warm" if warm else "cold")] = {
-                    "solver_sec_per_step": t_tot / steps, "iters": its, "converged_steps": conv}
+                    "solver_sec_per_step": float(np.mean(r["sec"])), "iters": r["iters"],
+                    "converged_steps": int(sum(r["converged"]))}
     for solver in ("cg", "ap", "sgd"):
         base = rows["%s/standard/cold" % solver]["solver_sec_per_step"]
         for k, r in rows.items():
@@ -547,9 +584,81 @@ def run_ablation(args):
            "ms_per_step": 1e3 * rows["cg/pathwise/warm"]["solver_sec_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f16-tensor/f32/f64", "data": "synthetic (seeded)",
            "config": {"workload": "ablation: n=%d d=8 Matern-3/2 sigma=0.3 s=%d, tau 0.01, CG <= 1000 iters, AP b=%d "
-                                  "and SGD b=%d (lr %s, momentum 0.9) <= %d epochs, Adam lr 0.1, %d steps"
-                                  % (n, s, bs_ap, bs_sgd, lr_sgd, epochs, steps)},
+                                  "and SGD b=%d (lr %s, momentum 0.9) <= 40 epochs, Adam lr 0.1, %d steps"
+                                  % (grid.n, grid.s, grid.bs_ap, grid.bs_sgd, grid.lr_sgd, steps)},
            "grid": rows}
+    print(json.dumps(out))
+
+
+DIAG_METRIC = "solver diagnostics: initial RKHS distance, probe-count cost, residual norm under epoch budgets"
+
+
+def run_diagnostics(args):
+    """Sec. 3-5 diagnostics on the GPU path.
+    (1) Initial RKHS distance (Eq. RKHS_distance) along a pathwise warm-started optimisation of the
+        pathwise workload (n = 32768): per step the mean over the probes' systems of ||u||_H^2 for the
+        standard systems (expectation tr(H^-1), Eq. standard_dist), for the pathwise systems (n, Eq.
+        pathwise_dist) and ||u_prev - u||_H^2 for the warm start.
+    (2) Cost of the probe count (Sec. 3, "How Many Probe Vectors"): seconds per warm pathwise step and
+        per solver iteration at s = 16, 32, 64 on the pathwise workload.
+    (3) Epoch budgets (Sec. 5, "The Effects of Early Stopping"): true relative residual norms reached
+        with 10-50 epochs by CG / AP / SGD, standard-cold against pathwise-warm (SolverGrid's workload)."""
+    torch, gp, workloads, dev = _gpu_setup()
+    steps = args.abl_steps
+    # (1) RKHS distances
+    p = workloads.pathwise()
+    rep = Replica(gp, torch, p, dev, torch.float32, gp.GP_PREC_TC16, 1000)
+    Bstd = torch.cat([rep.y[None], rep.w], 0).contiguous()
+    rk = {"std_cold": [], "pathwise_cold": [], "pathwise_warm": [], "n": p.n, "pathwise_iters": []}
+    for t in range(steps):
+        V_prev = rep.V.clone()
+        info, _ = rep.step()  # warm pathwise solve into rep.V, gradient, Adam (advances rep.theta)
+        th = rep.last_theta
+        rk["pathwise_iters"].append(int(info.iters))
+        rk["pathwise_cold"].append(float(gp.gp_rkhs_sqdist(p.kind, th, rep.X, rep.V[1:]).mean()))
+        if t > 0:
+            rk["pathwise_warm"].append(float(gp.gp_rkhs_sqdist(p.kind, th, rep.X, rep.V[1:], V_prev[1:]).mean()))
+        Vs, _ = gp.gp_solve_cg(p.kind, th, rep.X, Bstd, max_iters=1000, tol=0.01, prec=gp.GP_PREC_TC16)
+        rk["std_cold"].append(float(gp.gp_rkhs_sqdist(p.kind, th, rep.X, Vs[1:]).mean()))
+    # (2) probe count
+    probe = {}
+    for s in (16, 32, 64):
+        ps = workloads.pathwise(s=s)
+        r = Replica(gp, torch, ps, dev, torch.float32, gp.GP_PREC_TC16, 1000)
+        for _ in range(3):
+            r.step()
+        secs, its = [], []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info, _ = r.step()
+            torch.cuda.synchronize()
+            secs.append(time.perf_counter() - t0)
+            its.append(int(info.iters))
+        probe["s=%d" % s] = {"sec_per_step": float(np.mean(secs)), "cg_iters": its,
+                             "sec_per_product": float(np.sum(secs) / (np.sum(its) + 2 * steps))}
+    base = probe["s=16"]["sec_per_product"]
+    for v in probe.values():
+        v["product_cost_vs_s16"] = v["sec_per_product"] / base
+    # (3) epoch budgets
+    grid = SolverGrid(torch, gp, workloads, dev)
+    budget = {}
+    for solver in ("cg", "ap", "sgd"):
+        for epochs in (10, 20, 30, 40, 50):
+            for pathwise, warm in ((False, False), (True, True)):
+                r = grid.run(solver, pathwise, warm, steps, epochs, residuals=True)
+                budget["%s/%d/%s" % (solver, epochs, "pathwise-warm" if pathwise else "standard-cold")] = {
+                    "res_y_last": r["res_y"][-1] if r["res_y"] else None,
+                    "res_z_last": r["res_z"][-1] if r["res_z"] else None,
+                    "res_z_mean": float(np.mean(r["res_z"])) if r["res_z"] else None,
+                    "iters": r["iters"]}
+    out = {"metric": DIAG_METRIC, "value": probe["s=64"]["product_cost_vs_s16"],
+           "unit": "x cost per solver product at s=64 vs s=16", "n_gpus": 1, "steps": steps, "warmup": 3,
+           "ms_per_step": 1e3 * probe["s=64"]["sec_per_step"], "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16-tensor/f32/f64", "data": "synthetic (seeded)",
+           "config": {"workload": "pathwise n=32768 d=16 Matern-3/2 (RKHS distances, probe counts); "
+                                  "n=8192 d=8 Matern-3/2 s=64 (epoch budgets 10-50)"},
+           "rkhs_distance": rk, "probe_count": probe, "epoch_budget": budget}
     print(json.dumps(out))
 
 
@@ -776,7 +885,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--kernel-reps", type=int, default=10)
-    ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation"], default="pathwise")
+    ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation", "diagnostics"],
+                    default="pathwise")
     ap.add_argument("--abl-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-gps", type=int, default=256)
@@ -794,6 +904,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args)
+        return
+    if args.workload == "diagnostics":
+        run_diagnostics(args)
         return
     if args.prec is None:
         args.prec = "tc16" if _tc_ok() else "fp32"

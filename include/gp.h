@@ -374,6 +374,29 @@ int gp_predict(int kind, const double *theta, int d, const float *Xstar, int64_t
 size_t gp_predict_workspace(int64_t nstar, int64_t n, int d, int s, int prec);
 
 /* ------------------------------------------------------------------------ */
+/* Solver diagnostic: initial RKHS distance (Sec. 3, "Initial Distance to the  */
+/* Linear System Solution", Eq. RKHS_distance)                               */
+/* ------------------------------------------------------------------------ */
+
+/* dist[c] = (Uinit[c] - U[c])^T H (Uinit[c] - U[c]), c < R, H = K(X, X) + sigma^2 I:
+ * the squared RKHS distance between a solver's initialisation and a solution.  With
+ * Uinit = NULL (the zero initialisation) it is U[c]^T H U[c] = b^T H^-1 b when U[c] solves
+ * H u = b; its expectation is tr(H^-1) for the standard estimator's probes (Eq.
+ * standard_dist) and n for the pathwise targets (Eq. pathwise_dist).
+ *   X : n x d, U and Uinit : R x n (stride n), DEVICE; dist : DEVICE R doubles.
+ * One product H E in the requested form (prec), then FP64 dot products summed in a fixed
+ * order (deterministic).  Errors: GP_ERR_INVALID_ARG (sizes, null X/U/dist, theta, prec),
+ * GP_ERR_WORKSPACE, GP_ERR_UNSUPPORTED (GP_PREC_TC16 without tcgen05). */
+int gp_rkhs_sqdist(int kind, const double *theta, int d, const float *X, int64_t n, const float *Uinit,
+                   const float *U, int R, double *dist, int prec, void *ws, size_t ws_bytes,
+                   cudaStream_t stream);
+size_t gp_rkhs_sqdist_workspace(int64_t n, int d, int R, int prec);
+int gp_rkhs_sqdist_f64(int kind, const double *theta, int d, const double *X, int64_t n,
+                       const double *Uinit, const double *U, int R, double *dist, void *ws,
+                       size_t ws_bytes, cudaStream_t stream);
+size_t gp_rkhs_sqdist_f64_workspace(int64_t n, int d, int R);
+
+/* ------------------------------------------------------------------------ */
 /* Outer loop (Sec. 2.1 "Outer-Loop Optimiser"; App. B "Iterative Optimiser") */
 /* ------------------------------------------------------------------------ */
 

@@ -35,6 +35,7 @@ from ._binding import (  # noqa: F401
     gp_pathwise_rhs,
     gp_posterior_samples,
     gp_predict,
+    gp_rkhs_sqdist,
     gp_rff_prior_sample,
     gp_solve_ap,
     gp_solve_cg,

@@ -107,6 +107,10 @@ _SIGS = {
     "gp_autotune_reset": (None, []),
     "gp_predict": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp]),
     "gp_predict_workspace": (_sz, [_i64, _i64, _i, _i, _i]),
+    "gp_rkhs_sqdist": (_i, [_i, _pd, _i, _vp, _i64, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp]),
+    "gp_rkhs_sqdist_workspace": (_sz, [_i64, _i, _i, _i]),
+    "gp_rkhs_sqdist_f64": (_i, [_i, _pd, _i, _vp, _i64, _vp, _vp, _i, _vp, _vp, _sz, _vp]),
+    "gp_rkhs_sqdist_f64_workspace": (_sz, [_i64, _i, _i]),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
@@ -503,6 +507,34 @@ def gp_predict(kind, theta, Xstar, X, Vsol, Fstar, ystar=None, prec=GP_PREC_TC16
     _check(lib.gp_predict(kind, thp, d, _ptr(Xstar), nstar, _ptr(X), n, _ptr(Vsol), s, _ptr(Fstar), _ptr(ystar),
                           _ptr(mean), _ptr(var), _ptr(metrics), prec, _ptr(ws), wsb, _stream()))
     return mean, var, metrics
+
+
+def gp_rkhs_sqdist(kind, theta, X, U, Uinit=None, prec=GP_PREC_TC16):
+    """Per column, the squared RKHS distance (Uinit[c] - U[c])^T H (Uinit[c] - U[c]) (Sec. 3,
+    Eq. RKHS_distance); Uinit None is the zero initialisation.  CUDA float64 tensor of R."""
+    lib = library()
+    dt = X.dtype
+    _dev(X, dt, "X", 2)
+    _dev(U, dt, "U", 2)
+    n, d = X.shape
+    R = U.shape[0]
+    if U.shape[1] != n:
+        raise ValueError("U must be (R, n)")
+    if Uinit is not None:
+        _dev(Uinit, dt, "Uinit", 2)
+        if Uinit.shape != U.shape:
+            raise ValueError("Uinit must have U's shape")
+    th, thp = _theta(theta, d)
+    dist = torch.empty(R, dtype=torch.float64, device=X.device)
+    if _f64(X):
+        ws, wsb = _ws(lib.gp_rkhs_sqdist_f64_workspace(n, d, R), X.device)
+        _check(lib.gp_rkhs_sqdist_f64(kind, thp, d, _ptr(X), n, _ptr(Uinit), _ptr(U), R, _ptr(dist), _ptr(ws), wsb,
+                                      _stream()))
+    else:
+        ws, wsb = _ws(lib.gp_rkhs_sqdist_workspace(n, d, R, prec), X.device)
+        _check(lib.gp_rkhs_sqdist(kind, thp, d, _ptr(X), n, _ptr(Uinit), _ptr(U), R, _ptr(dist), prec, _ptr(ws),
+                                  wsb, _stream()))
+    return dist
 
 
 def gp_adam_softplus_step(nu, m, v, t, grad_theta, lr, beta1=0.9, beta2=0.999, eps=1e-8):

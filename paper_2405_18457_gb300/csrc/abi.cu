@@ -214,6 +214,18 @@ int solver_args(int kind, const double *theta, int d, const T *X, int64_t n, con
     return make_kp<T>(kind, theta, d, kp);
 }
 
+template <typename T>
+int rkhs_common(int kind, const double *theta, int d, const T *X, int64_t n, const T *Uinit, const T *U, int R,
+                double *dist, int prec, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    KP<T> kp;
+    GP_TRY(make_kp<T>(kind, theta, d, &kp));
+    REQ(n >= 1 && R >= 0, "need n >= 1 and R >= 0");
+    if (R == 0) return GP_OK;
+    REQ(X && U && dist, "null pointer argument");
+    if (sizeof(T) == sizeof(float)) GP_TRY(check_prec(prec));
+    return rkhs_sqdist<T>(kp, X, n, Uinit, U, R, dist, prec, ws, ws_bytes, stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -555,6 +567,27 @@ int gp_predict(int kind, const double *theta, int d, const float *Xstar, int64_t
     REQ(Xstar && X && Vsol && Fstar && mean && var, "null pointer argument");
     GP_TRY(check_prec(prec));
     return predict(kp, Xstar, nstar, X, n, Vsol, s, Fstar, ystar, mean, var, metrics, prec, ws, ws_bytes, stream);
+    GP_API_END
+}
+
+// ------------------------------------------------------------------ solver diagnostics
+size_t gp_rkhs_sqdist_workspace(int64_t n, int d, int R, int prec) { return rkhs_workspace<float>(n, d, R, prec); }
+size_t gp_rkhs_sqdist_f64_workspace(int64_t n, int d, int R) {
+    return rkhs_workspace<double>(n, d, R, GP_PREC_FP32);
+}
+
+
+int gp_rkhs_sqdist(int kind, const double *theta, int d, const float *X, int64_t n, const float *Uinit,
+                   const float *U, int R, double *dist, int prec, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    return rkhs_common<float>(kind, theta, d, X, n, Uinit, U, R, dist, prec, ws, ws_bytes, stream);
+    GP_API_END
+}
+
+int gp_rkhs_sqdist_f64(int kind, const double *theta, int d, const double *X, int64_t n, const double *Uinit,
+                       const double *U, int R, double *dist, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    return rkhs_common<double>(kind, theta, d, X, n, Uinit, U, R, dist, GP_PREC_FP32, ws, ws_bytes, stream);
     GP_API_END
 }
 

@@ -415,4 +415,92 @@ int predict(const KP<float> &kp, const float *Xstar, int64_t nstar, const float 
     return GP_OK;
 }
 
+// ===========================================================================
+// Solver diagnostic: RKHS squared distance between an initialisation and a
+// solution (Sec. 3, "Initial Distance to the Linear System Solution", Eq.
+// RKHS_distance): dist[c] = e_c^T H e_c with e_c = U[c] - Uinit[c] (the sign of e
+// does not matter).  One product H E in the requested form, then per-column FP64
+// dot products summed over fixed blocks in a fixed order.
+// ===========================================================================
+namespace {
+
+constexpr int RK_PARTS = 64;
+
+template <typename T>
+__global__ void rkhs_diff_kernel(const T *U, const T *U0, T *E, int64_t cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        E[i] = U[i] - U0[i];
+}
+
+// grid (RK_PARTS, R): block p of column c sums e_i y_i over rows i = p*256 + t (mod RK_PARTS*256).
+template <typename T>
+__global__ void rkhs_dot_kernel(const T *E, const T *Y, int64_t n, double *part) {
+    const int c = blockIdx.y;
+    const T *e = E + (int64_t)c * n;
+    const T *y = Y + (int64_t)c * n;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)e[i] * (double)y[i];
+    __shared__ double red[8];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[(int64_t)c * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void rkhs_finish_kernel(const double *part, int nparts, int R, double *dist) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= R) return;
+    double t = 0.0;
+    for (int p = 0; p < nparts; ++p) t += part[(int64_t)c * nparts + p];
+    dist[c] = t;
+}
+
+}  // namespace
+
+template <typename T>
+size_t rkhs_workspace(int64_t n, int d, int R, int prec) {
+    Carver c(nullptr);
+    c.take<T>((size_t)R * (size_t)n);  // E
+    c.take<T>((size_t)R * (size_t)n);  // H E
+    c.take<double>((size_t)R * RK_PARTS);
+    c.take<char>(mvm_workspace<T>(n, n, d, R, prec));
+    return c.bytes();
+}
+
+template <typename T>
+int rkhs_sqdist(const KP<T> &kp, const T *X, int64_t n, const T *U0, const T *U, int R, double *dist, int prec,
+                void *ws, size_t ws_bytes, cudaStream_t st) {
+    Carver c(ws);
+    T *E = c.take<T>((size_t)R * (size_t)n);
+    T *Y = c.take<T>((size_t)R * (size_t)n);
+    double *part = c.take<double>((size_t)R * RK_PARTS);
+    const size_t mw = mvm_workspace<T>(n, n, kp.d, R, prec);
+    void *mws = c.take<char>(mw);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    const T *Ed = U;
+    if (U0) {
+        const int64_t cnt = (int64_t)R * n;
+        rkhs_diff_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(cnt, 256), 4096), 256, 0, st>>>(U, U0, E, cnt);
+        GP_TRY(check_launch("rkhs_diff_kernel"));
+        Ed = E;
+    }
+    GP_TRY(apply_mvm<T>(kp, X, n, X, n, Ed, n, R, Y, n, 1, prec, mws, mw, st));
+    rkhs_dot_kernel<T><<<dim3(RK_PARTS, (unsigned)R), 256, 0, st>>>(Ed, Y, n, part);
+    GP_TRY(check_launch("rkhs_dot_kernel"));
+    rkhs_finish_kernel<<<(unsigned)cdiv(R, 128), 128, 0, st>>>(part, RK_PARTS, R, dist);
+    return check_launch("rkhs_finish_kernel");
+}
+
+template size_t rkhs_workspace<float>(int64_t, int, int, int);
+template size_t rkhs_workspace<double>(int64_t, int, int, int);
+template int rkhs_sqdist<float>(const KP<float> &, const float *, int64_t, const float *, const float *, int,
+                                double *, int, void *, size_t, cudaStream_t);
+template int rkhs_sqdist<double>(const KP<double> &, const double *, int64_t, const double *, const double *, int,
+                                 double *, int, void *, size_t, cudaStream_t);
+
 }  // namespace gp

@@ -42,6 +42,13 @@ int predict(const KP<float> &kp, const float *Xstar, int64_t nstar, const float 
             int s, const float *Fstar, const float *ystar, float *mean, float *var, double *metrics, int prec,
             void *ws, size_t ws_bytes, cudaStream_t st);
 
+// RKHS squared distance e_c^T H e_c, e_c = U[c] - U0[c] (U0 may be null), into dist (R doubles).
+template <typename T>
+size_t rkhs_workspace(int64_t n, int d, int R, int prec);
+template <typename T>
+int rkhs_sqdist(const KP<T> &kp, const T *X, int64_t n, const T *U0, const T *U, int R, double *dist, int prec,
+                void *ws, size_t ws_bytes, cudaStream_t st);
+
 // Pivoted Cholesky preconditioner (precond.cu): P = L^T L + sigma^2 I, applied by Woodbury.
 template <typename T>
 struct Precond {
