@@ -127,13 +127,15 @@ int gp_kernel_mvm(int kind, const double *theta, int d,
 size_t gp_kernel_mvm_workspace(int64_t n1, int64_t n2, int d, int nrhs, int prec);
 
 /* Autotuner of the tensor-core product's schedule (the paper has no counterpart).
- * Times H V = (K(X, X) + sigma^2 I) V for a ladder of column-split counts (1 .. 128 splits
- * of each 128-row tile's column range; `reps` timed runs each after one warm-up, CUDA
- * events on `stream`) and records the fastest for the product's shape (rows, columns and
+ * Times H V = (K(X, X) + sigma^2 I) V for the persistent schedule (one CTA per SM over
+ * equal runs of (row tile, column tile) pairs) and a ladder of column-split counts (1 .. 128
+ * splits of each 128-row tile's column range); `reps` timed runs each after one warm-up,
+ * CUDA events on `stream`; records the fastest for the product's shape (rows, columns and
  * padded right-hand sides in tiles) in a process-wide table.  Every later tensor-core
- * product of that shape, including the solvers' operators, uses the recorded split when
- * its workspace holds the partial sums (else the built-in cost model's split).  Y receives
- * H V.  best_split, best_ms: HOST outputs.  1 <= nrhs <= 128.  Synchronises `stream`, so
+ * product of that shape, including the solvers' operators, uses the recorded schedule when
+ * its workspace holds the partial sums (else the built-in cost model's choice).  Y receives
+ * H V.  best_split, best_ms: HOST outputs; best_split = -1 is the persistent schedule, k >= 1
+ * k column splits.  1 <= nrhs <= 128.  Synchronises `stream`, so
  * it must not be called inside a stream capture.  Because the split fixes the order of the
  * column sums, results after tuning may differ from untuned ones by rounding.
  * gp_autotune_reset() forgets every recorded choice. */

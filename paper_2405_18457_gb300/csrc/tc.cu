@@ -47,6 +47,7 @@ constexpr int MAX_STAGES = 6;  // gradient kernel: depth of the PB/W ring
 constexpr int MAX_B3 = 8;      // gradient kernel: depth of the [A | A^2] ring
 constexpr int MAX_RING = 8;    // product kernel: slots per ring (barrier arrays are sized for this)
 constexpr int NTHREADS = 416;     // gradient kernel: producer, 3 MMA issuers, 2 x 4 evaluation warps, producer
+constexpr int kPersist = -1;       // split code of the persistent product schedule
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -254,9 +255,17 @@ struct KParams {
     int64_t ldvd, drow0, ndiag;
     float *Y;
     int64_t ldy;
-    float *partial;      // nsplit > 1: partial[split][c][i]
+    float *partial;      // nsplit > 1: partial[split][c][i]; persistent: partial[slot][c][row in tile]
     const int *done;
     int *err;
+    // persistent schedule (single problem): CTA b takes the (row tile, column tile) pairs
+    // [T b / G, T (b+1) / G) in row-major order, T = ptotal, G = pgrid = gridDim.x; a run of
+    // pairs in one row tile is a segment.  Only a CTA's first and last segments can miss part
+    // of their row tile; such a segment writes its sums to slot 2 b (first) or 2 b + 1 (last)
+    // and tc_reduce_persist_kernel combines the slots of each row tile.
+    int persist;
+    int64_t ptotal;
+    int pgrid;
     // grouped mode (a batch of independent GPs): one work item per CTA
     const BItem *items;     // null: single problem, grid = row tiles x splits
     const BMember *members;
@@ -267,7 +276,9 @@ struct KParams {
     int64_t ncols_total;
 };
 
-template <int KIND, int KAT>  // KAT: 64-wide atoms of the distance contraction (KD / 64)
+// KAT: 64-wide atoms of the distance contraction (KD / 64); PERSIST: the persistent schedule
+// (single problem; a separate instantiation so that the other schedules keep their code).
+template <int KIND, int KAT, bool PERSIST = false>
 __global__ void __launch_bounds__(MVM_THREADS, 1)
     tc_mvm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapV, const KParams p) {
@@ -299,7 +310,9 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     uint64_t *t_kval = t_full + 3;          // the evaluation warpgroup wrote P into buffer b
     uint64_t *t_free = t_kval + 3;          // GEMM2 has consumed buffer b
     uint64_t *y_full = t_free + 3;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y_full + 1);
+    uint64_t *y_empty = y_full + 1;  // persistent: the evaluation threads have read Y
+    uint64_t *a_empty = y_empty + 1; // persistent: GEMM1 is done with the row operand
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_empty + 1);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -312,7 +325,22 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     float sf2 = p.sf2, diag_coef = p.diag_coef, dsc;
     const float *vinv = p.vinv, *Vd = p.Vd;
     float *Yp = p.Y;
-    if (p.items) {
+    if constexpr (PERSIST) {
+        const int64_t g0 = p.ptotal * blockIdx.x / gridDim.x, g1 = p.ptotal * (blockIdx.x + 1) / gridDim.x;
+        row0 = (g0 / p.col_tiles) * TM;  // first segment's rows; later segments follow row by row
+        tb0 = g0;                        // global pair index of local tile 0
+        tv0 = 0;
+        ntiles = (int)(g1 - g0);
+        ioff = row0;
+        dsc = *p.dscale;
+        if (p.col0_dev) {
+            pb_off = *p.col0_dev;
+            if (p.diag_from_col0) {
+                drow0 = pb_off;
+                ndiag = min(ndiag, p.ncols_total - pb_off);
+            }
+        }
+    } else if (p.items) {
         const BItem itm = p.items[blockIdx.x];
         if (p.mdone && p.mdone[itm.member]) return;
         const BMember &m = p.members[itm.member];
@@ -362,6 +390,8 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             mbar_init(&t_free[b], 1);
         }
         mbar_init(y_full, 1);
+        mbar_init(y_empty, 256);
+        mbar_init(a_empty, 1);
         *s_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -378,164 +408,386 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     // its first 64 columns), the Y accumulator at 384 (R_pad <= 128 columns).
     const uint32_t tmem = *tmem_slot;
     const uint32_t tS0 = tmem, tY = tmem + 384;
-
-    if (warp == 0 && ntiles > 0) {
-        // ------------------------------------------------ TMA producer: row operand + PB ring
-        const bool leader = elect_one();
-        if (leader) {
-            mbar_expect_tx(a_full, a_bytes);
-            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
-        }
-        for (int it = 0; it < ntiles; ++it) {
-            const int s = it % NPB;
-            if (it >= NPB && !mbar_wait_warp(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
-            const int j0 = (int)((tb0 + it) * TN + pb_off);
-            uint8_t *sB = sPB + (size_t)s * b_bytes;
+    if constexpr (!PERSIST) {
+        if (warp == 0 && ntiles > 0) {
+            // ------------------------------------------------ TMA producer: row operand + PB ring
+            const bool leader = elect_one();
             if (leader) {
-                mbar_expect_tx(&pb_full[s], b_bytes);
-                for (int ka = 0; ka < katoms; ++ka)
-                    tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
+                mbar_expect_tx(a_full, a_bytes);
+                for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
             }
-        }
-    } else if (warp == 2 && ntiles > 0) {
-        // ------------------------------------------------ TMA producer: V ring
-        const bool leader = elect_one();
-        for (int it = 0; it < ntiles; ++it) {
-            const int s = it % NV;
-            if (it >= NV && !mbar_wait_warp(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
-            const int j0 = (int)((tv0 + it) * TN);
-            uint8_t *sV = sVr + (size_t)s * v_bytes;
-            if (leader) {
-                mbar_expect_tx(&v_full[s], v_bytes);
-                tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
-                tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
-            }
-        }
-    } else if (warp == 1 && ntiles > 0) {
-        // ------------------------------------------------ GEMM1 issuer
-        // GEMM1 and GEMM2 are issued from two warps (1 and 3): each warp's stream of barrier
-        // waits, MMAs and commits is then half as long, and the waits of one overlap the MMAs
-        // of the other.  Their MMAs touch disjoint tensor memory (S vs P / Y) and every
-        // dependency between them runs through the evaluation warpgroups' barriers; a commit
-        // tracks the MMAs of its own thread.  Descriptors are built once and advanced by
-        // constant offsets (16-byte units).
-        const bool leader = elect_one();
-        const uint32_t id1 = idesc_f16(TM, TN);
-        const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
-        const uint32_t b_units = b_bytes >> 4;
-        bool ok = mbar_wait_warp(a_full, 0, s_err);
-        // GEMM1 of tile it into buffer it % 3, once GEMM2 of tile it - 3 has consumed it.
-        for (int it = 0; ok && it < ntiles; ++it) {
-            const int s = it % NPB, b = it % 3;
-            if (!mbar_wait_warp(&pb_full[s], (it / NPB) & 1, s_err)) break;
-            if (it >= 3 && !mbar_wait_warp(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
-            tc_fence_after();
-            const uint64_t db = dPB + (uint64_t)s * b_units;
-            const uint32_t dS = tS0 + b * 128;
-            if (leader) {
-#pragma unroll
-                for (int k = 0; k < 4 * KAT; ++k) {
-                    constexpr uint32_t a_atom = (TM * 128) >> 4, b_atom = (TN * 128) >> 4;
-                    const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                    mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
+            for (int it = 0; it < ntiles; ++it) {
+                const int s = it % NPB;
+                if (it >= NPB && !mbar_wait_warp(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
+                const int j0 = (int)((tb0 + it) * TN + pb_off);
+                uint8_t *sB = sPB + (size_t)s * b_bytes;
+                if (leader) {
+                    mbar_expect_tx(&pb_full[s], b_bytes);
+                    for (int ka = 0; ka < katoms; ++ka)
+                        tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
                 }
-                mma_commit(&pb_empty[s]);
-                mma_commit(&t_full[b]);
             }
-            __syncwarp();
-        }
-    } else if (warp == 3 && ntiles > 0) {
-        // ------------------------------------------------ GEMM2 issuer: Y += P V
-        const bool leader = elect_one();
-        const uint32_t id2 = idesc_f16(TM, R_pad);
-        const uint64_t dV = sdesc(sVr);
-        const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
-        for (int it = 0; it < ntiles; ++it) {
-            const int s = it % NV, b = it % 3;
-            if (!mbar_wait_warp(&v_full[s], (it / NV) & 1, s_err)) break;
-            if (!mbar_wait_warp(&t_kval[b], (it / 3) & 1, s_err)) break;
-            tc_fence_after();
-            const uint64_t dv = dV + (uint64_t)s * v_units;
-            const uint32_t aP = tS0 + b * 128;
-            if (leader) {
-#pragma unroll
-                for (int k = 0; k < TN / 16; ++k) {
-                    const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                    mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
+        } else if (warp == 2 && ntiles > 0) {
+            // ------------------------------------------------ TMA producer: V ring
+            const bool leader = elect_one();
+            for (int it = 0; it < ntiles; ++it) {
+                const int s = it % NV;
+                if (it >= NV && !mbar_wait_warp(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
+                const int j0 = (int)((tv0 + it) * TN);
+                uint8_t *sV = sVr + (size_t)s * v_bytes;
+                if (leader) {
+                    mbar_expect_tx(&v_full[s], v_bytes);
+                    tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
+                    tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
                 }
-                mma_commit(&v_empty[s]);
-                mma_commit(&t_free[b]);
             }
-            __syncwarp();
-        }
-        if (leader) mma_commit(y_full);
-    } else if (warp >= 4) {
-        // ------------------------------------------------ kernel evaluation + epilogue
-        // Two warpgroups ping-pong: warpgroup wg evaluates the tiles with it % 2 == wg (in
-        // buffer it % 3), so one group evaluates while the other waits on tensor memory.
-        // Each thread owns one row: it reads 64 S columns, then writes their 64 kernel
-        // values (32 packed columns) over the columns it has just read, so P needs no
-        // buffer of its own and the warpgroup never waits for GEMM2.
-        const int wg = (warp - 4) >> 2;
-        const int wq = warp & 3;  // TMEM lane quarter this warp may access
-        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
-        const bool unit = (dsc == 1.0f);
-        bool ok = true;
-        for (int it = wg; it < ntiles; it += 2) {
-            const int b = it % 3;
-            if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
-                ok = false;
-                break;
+        } else if (warp == 1 && ntiles > 0) {
+            // ------------------------------------------------ GEMM1 issuer
+            // GEMM1 and GEMM2 are issued from two warps (1 and 3): each warp's stream of barrier
+            // waits, MMAs and commits is then half as long, and the waits of one overlap the MMAs
+            // of the other.  Their MMAs touch disjoint tensor memory (S vs P / Y) and every
+            // dependency between them runs through the evaluation warpgroups' barriers; a commit
+            // tracks the MMAs of its own thread.  Descriptors are built once and advanced by
+            // constant offsets (16-byte units).
+            const bool leader = elect_one();
+            const uint32_t id1 = idesc_f16(TM, TN);
+            const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
+            const uint32_t b_units = b_bytes >> 4;
+            bool ok = mbar_wait_warp(a_full, 0, s_err);
+            // GEMM1 of tile it into buffer it % 3, once GEMM2 of tile it - 3 has consumed it.
+            for (int it = 0; ok && it < ntiles; ++it) {
+                const int s = it % NPB, b = it % 3;
+                if (!mbar_wait_warp(&pb_full[s], (it / NPB) & 1, s_err)) break;
+                if (it >= 3 && !mbar_wait_warp(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
+                tc_fence_after();
+                const uint64_t db = dPB + (uint64_t)s * b_units;
+                const uint32_t dS = tS0 + b * 128;
+                if (leader) {
+#pragma unroll
+                    for (int k = 0; k < 4 * KAT; ++k) {
+                        constexpr uint32_t a_atom = (TM * 128) >> 4, b_atom = (TN * 128) >> 4;
+                        const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                        mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&pb_empty[s]);
+                    mma_commit(&t_full[b]);
+                }
+                __syncwarp();
             }
-            tc_fence_after();
-            const uint32_t taS = tS0 + b * 128 + lane_off;
-            const uint32_t taP = taS;
+        } else if (warp == 3 && ntiles > 0) {
+            // ------------------------------------------------ GEMM2 issuer: Y += P V
+            const bool leader = elect_one();
+            const uint32_t id2 = idesc_f16(TM, R_pad);
+            const uint64_t dV = sdesc(sVr);
+            const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
+            for (int it = 0; it < ntiles; ++it) {
+                const int s = it % NV, b = it % 3;
+                if (!mbar_wait_warp(&v_full[s], (it / NV) & 1, s_err)) break;
+                if (!mbar_wait_warp(&t_kval[b], (it / 3) & 1, s_err)) break;
+                tc_fence_after();
+                const uint64_t dv = dV + (uint64_t)s * v_units;
+                const uint32_t aP = tS0 + b * 128;
+                if (leader) {
+#pragma unroll
+                    for (int k = 0; k < TN / 16; ++k) {
+                        const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                        mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&v_empty[s]);
+                    mma_commit(&t_free[b]);
+                }
+                __syncwarp();
+            }
+            if (leader) mma_commit(y_full);
+        } else if (warp >= 4) {
+            // ------------------------------------------------ kernel evaluation + epilogue
+            // Two warpgroups ping-pong: warpgroup wg evaluates the tiles with it % 2 == wg (in
+            // buffer it % 3), so one group evaluates while the other waits on tensor memory.
+            // Each thread owns one row: it reads 64 S columns, then writes their 64 kernel
+            // values (32 packed columns) over the columns it has just read, so P needs no
+            // buffer of its own and the warpgroup never waits for GEMM2.
+            const int wg = (warp - 4) >> 2;
+            const int wq = warp & 3;  // TMEM lane quarter this warp may access
+            const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+            const bool unit = (dsc == 1.0f);
+            bool ok = true;
+            for (int it = wg; it < ntiles; it += 2) {
+                const int b = it % 3;
+                if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taS = tS0 + b * 128 + lane_off;
+                const uint32_t taP = taS;
 #pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-                // one 64-column load and one 32-column store per half: fewer tensor-memory
-                // instructions competing with the MMA issue for the same queue
-                uint32_t r[64];
-                tmem_ld64(taS + half * 64, r);
-                tmem_ld_wait();
-                uint32_t pk[32];
-                if (unit)
-                    eval_chunk64<KIND, false>(r, pk, dsc);
-                else
-                    eval_chunk64<KIND, true>(r, pk, dsc);
-                tmem_st32(taP + half * 32, pk);
+                for (int half = 0; half < 2; ++half) {
+                    // one 64-column load and one 32-column store per half: fewer tensor-memory
+                    // instructions competing with the MMA issue for the same queue
+                    uint32_t r[64];
+                    tmem_ld64(taS + half * 64, r);
+                    tmem_ld_wait();
+                    uint32_t pk[32];
+                    if (unit)
+                        eval_chunk64<KIND, false>(r, pk, dsc);
+                    else
+                        eval_chunk64<KIND, true>(r, pk, dsc);
+                    tmem_st32(taP + half * 32, pk);
+                }
+                if (!ok) break;
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(&t_kval[b]);
             }
-            if (!ok) break;
-            tmem_st_wait();
-            tc_fence_before();
-            mbar_arrive(&t_kval[b]);
-        }
-        // epilogue: Y rows from TMEM lanes, one row per thread; the two warpgroups
-        // take alternate 16-column chunks of the right-hand sides
-        if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
-        if (ok && ntiles > 0) {
-            tc_fence_after();
-            const int64_t i = ioff + wq * 32 + lane;
-            for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
-                uint32_t r[16];
-                tmem_ld16(tY + lane_off + c0, r);
-                tmem_ld_wait();
-                if (i < n1) {
+            // epilogue: Y rows from TMEM lanes, one row per thread; the two warpgroups
+            // take alternate 16-column chunks of the right-hand sides
+            if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
+            if (ok && ntiles > 0) {
+                tc_fence_after();
+                const int64_t i = ioff + wq * 32 + lane;
+                for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
+                    uint32_t r[16];
+                    tmem_ld16(tY + lane_off + c0, r);
+                    tmem_ld_wait();
+                    if (i < n1) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int c = c0 + e;
-                        if (c >= p.R) break;
-                        float v = sf2 * vinv[c] * __uint_as_float(r[e]);
-                        if (p.nsplit > 1) {
-                            p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v;
-                        } else {
-                            float y = p.alpha * v;
-                            if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
-                            if (diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
-                                y += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
-                            Yp[(int64_t)c * ldy + i] = y;
+                        for (int e = 0; e < 16; ++e) {
+                            const int c = c0 + e;
+                            if (c >= p.R) break;
+                            float v = sf2 * vinv[c] * __uint_as_float(r[e]);
+                            if (p.nsplit > 1) {
+                                p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v;
+                            } else {
+                                float y = p.alpha * v;
+                                if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
+                                if (diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
+                                    y += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
+                                Yp[(int64_t)c * ldy + i] = y;
+                            }
                         }
                     }
                 }
+            }
+        }
+    } else {
+        // Walk over the CTA's tiles: the PB / V tile of local tile it, its segment (row tile
+        // relative to the first) and whether it opens or closes the segment, advanced one tile
+        // at a time.  Without the persistent schedule a CTA has one segment.
+        const int64_t ctiles = p.col_tiles, r_first = row0 / TM;
+        struct Walk {
+            int64_t ct;  // column tile (persistent) or local offset
+            int seg;
+        };
+        auto walk0 = [&]() { return Walk{PERSIST ? tb0 - r_first * ctiles : 0, 0}; };
+        auto walk_next = [&](Walk &w) {
+            if (++w.ct == ctiles && PERSIST) {
+                w.ct = 0;
+                ++w.seg;
+            }
+        };
+        auto tile_pb = [&](const Walk &w, int it) { return PERSIST ? w.ct : tb0 + it; };
+        auto tile_v = [&](const Walk &w, int it) { return PERSIST ? w.ct : tv0 + it; };
+        auto tile_first = [&](const Walk &w, int it) { return it == 0 || (PERSIST && w.ct == 0); };
+        auto tile_last = [&](const Walk &w, int it) { return it == ntiles - 1 || (PERSIST && w.ct == ctiles - 1); };
+
+        if (warp == 0 && ntiles > 0) {
+            // ------------------------------------------------ TMA producer: row operand + PB ring
+            const bool leader = elect_one();
+            Walk w = walk0();
+            for (int it = 0; it < ntiles; ++it, walk_next(w)) {
+                const int seg = w.seg;
+                const int64_t pbt = tile_pb(w, it);
+                if (tile_first(w, it)) {
+                    // row operand of this segment, once GEMM1 has finished with the previous one
+                    if (seg > 0 && !mbar_wait_warp(a_empty, (seg - 1) & 1, s_err)) break;
+                    if (leader) {
+                        mbar_expect_tx(a_full, a_bytes);
+                        const int ra = (int)((r_first + seg) * TM);
+                        for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, ra);
+                    }
+                }
+                const int s = it % NPB;
+                if (it >= NPB && !mbar_wait_warp(&pb_empty[s], ((it / NPB) - 1) & 1, s_err)) break;
+                const int j0 = (int)(pbt * TN + pb_off);
+                uint8_t *sB = sPB + (size_t)s * b_bytes;
+                if (leader) {
+                    mbar_expect_tx(&pb_full[s], b_bytes);
+                    for (int ka = 0; ka < katoms; ++ka)
+                        tma_load_2d(sB + ka * (TN * 128), &mapB, &pb_full[s], ka * 64, j0);
+                }
+            }
+        } else if (warp == 2 && ntiles > 0) {
+            // ------------------------------------------------ TMA producer: V ring
+            const bool leader = elect_one();
+            Walk w = walk0();
+            for (int it = 0; it < ntiles; ++it, walk_next(w)) {
+                const int s = it % NV;
+                if (it >= NV && !mbar_wait_warp(&v_empty[s], ((it / NV) - 1) & 1, s_err)) break;
+                const int j0 = (int)(tile_v(w, it) * TN);
+                uint8_t *sV = sVr + (size_t)s * v_bytes;
+                if (leader) {
+                    mbar_expect_tx(&v_full[s], v_bytes);
+                    tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
+                    tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
+                }
+            }
+        } else if (warp == 1 && ntiles > 0) {
+            // ------------------------------------------------ GEMM1 issuer
+            // GEMM1 and GEMM2 are issued from two warps (1 and 3): each warp's stream of barrier
+            // waits, MMAs and commits is then half as long, and the waits of one overlap the MMAs
+            // of the other.  Their MMAs touch disjoint tensor memory (S vs P / Y) and every
+            // dependency between them runs through the evaluation warpgroups' barriers; a commit
+            // tracks the MMAs of its own thread.  Descriptors are built once and advanced by
+            // constant offsets (16-byte units).
+            const bool leader = elect_one();
+            const uint32_t id1 = idesc_f16(TM, TN);
+            const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
+            const uint32_t b_units = b_bytes >> 4;
+            // GEMM1 of tile it into buffer it % 3, once GEMM2 of tile it - 3 has consumed it.
+            Walk w = walk0();
+            for (int it = 0; it < ntiles; ++it, walk_next(w)) {
+                const bool last = tile_last(w, it);
+                if (tile_first(w, it) && !mbar_wait_warp(a_full, w.seg & 1, s_err)) break;
+                const int s = it % NPB, b = it % 3;
+                if (!mbar_wait_warp(&pb_full[s], (it / NPB) & 1, s_err)) break;
+                if (it >= 3 && !mbar_wait_warp(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
+                tc_fence_after();
+                const uint64_t db = dPB + (uint64_t)s * b_units;
+                const uint32_t dS = tS0 + b * 128;
+                if (leader) {
+#pragma unroll
+                    for (int k = 0; k < 4 * KAT; ++k) {
+                        constexpr uint32_t a_atom = (TM * 128) >> 4, b_atom = (TN * 128) >> 4;
+                        const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                        mma_ss(dS, dA + ka * a_atom + ko, db + ka * b_atom + ko, id1, k > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&pb_empty[s]);
+                    mma_commit(&t_full[b]);
+                    if (last) mma_commit(a_empty);
+                }
+                __syncwarp();
+            }
+        } else if (warp == 3 && ntiles > 0) {
+            // ------------------------------------------------ GEMM2 issuer: Y += P V
+            const bool leader = elect_one();
+            const uint32_t id2 = idesc_f16(TM, R_pad);
+            const uint64_t dV = sdesc(sVr);
+            const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
+            Walk w = walk0();
+            for (int it = 0; it < ntiles; ++it, walk_next(w)) {
+                const int seg = w.seg;
+                const bool first = tile_first(w, it), last = tile_last(w, it);
+                const int s = it % NV, b = it % 3;
+                // a new segment restarts the accumulator once the previous one has been read out
+                if (first && seg > 0 && !mbar_wait_warp(y_empty, (seg - 1) & 1, s_err)) break;
+                if (!mbar_wait_warp(&v_full[s], (it / NV) & 1, s_err)) break;
+                if (!mbar_wait_warp(&t_kval[b], (it / 3) & 1, s_err)) break;
+                tc_fence_after();
+                const uint64_t dv = dV + (uint64_t)s * v_units;
+                const uint32_t aP = tS0 + b * 128;
+                if (leader) {
+#pragma unroll
+                    for (int k = 0; k < TN / 16; ++k) {
+                        const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+                        mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (!first || k > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&v_empty[s]);
+                    mma_commit(&t_free[b]);
+                    if (last) mma_commit(y_full);
+                }
+                __syncwarp();
+            }
+        } else if (warp >= 4) {
+            // ------------------------------------------------ kernel evaluation + epilogue
+            // Two warpgroups ping-pong: warpgroup wg evaluates the tiles with it % 2 == wg (in
+            // buffer it % 3), so one group evaluates while the other waits on tensor memory.
+            // Each thread owns one row: it reads 64 S columns, then writes their 64 kernel
+            // values (32 packed columns) over the columns it has just read, so P needs no
+            // buffer of its own and the warpgroup never waits for GEMM2.
+            const int wg = (warp - 4) >> 2;
+            const int wq = warp & 3;  // TMEM lane quarter this warp may access
+            const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+            const bool unit = (dsc == 1.0f);
+            bool ok = true;
+            // Read-out of segment sg's accumulator: final rows when the segment is a whole row
+            // tile of an unsplit product, else partial sums (split slice or persistent slot).
+            // Both warpgroups take alternate 16-column chunks, then release Y to GEMM2.
+            auto epilogue = [&](int sg) {
+                if (!ok) return;
+                ok = mbar_wait(y_full, sg & 1, s_err);
+                if (!ok) return;
+                tc_fence_after();
+                bool whole = p.nsplit <= 1;
+                int64_t io = ioff;
+                if (PERSIST) {
+                    const int64_t r = r_first + sg;
+                    const int64_t s0 = max(tb0, r * ctiles), s1 = min(tb0 + ntiles, (r + 1) * ctiles);
+                    whole = (s0 == r * ctiles) && (s1 == (r + 1) * ctiles);
+                    io = r * TM;
+                }
+                const int64_t i = io + wq * 32 + lane;
+                for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
+                    uint32_t r[16];
+                    tmem_ld16(tY + lane_off + c0, r);
+                    tmem_ld_wait();
+                    if (i < n1) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int c = c0 + e;
+                            if (c >= p.R) break;
+                            float v = sf2 * vinv[c] * __uint_as_float(r[e]);
+                            if (PERSIST && !whole) {
+                                p.partial[(((int64_t)blockIdx.x * 2 + (sg > 0)) * p.R + c) * TM + (wq * 32 + lane)] = v;
+                            } else if (!whole) {
+                                p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v;
+                            } else {
+                                float y = p.alpha * v;
+                                if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
+                                if (diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
+                                    y += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
+                                Yp[(int64_t)c * ldy + i] = y;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(y_empty);
+            };
+            const int nseg = ntiles <= 0 ? 0 : (PERSIST ? (int)((tb0 + ntiles - 1) / ctiles - r_first) + 1 : 1);
+            int it = wg;
+            for (int sg = 0; sg < nseg; ++sg) {
+                // this warpgroup's tiles of segment sg, then the segment's read-out
+                const int seg_end =
+                    PERSIST ? (int)min((int64_t)ntiles, (r_first + sg + 1) * ctiles - tb0) : ntiles;
+                for (; ok && it < seg_end; it += 2) {
+                    const int b = it % 3;
+                    if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t taS = tS0 + b * 128 + lane_off;
+                    const uint32_t taP = taS;
+#pragma unroll 1
+                    for (int half = 0; half < 2; ++half) {
+                        // one 64-column load and one 32-column store per half: fewer tensor-memory
+                        // instructions competing with the MMA issue for the same queue
+                        uint32_t r[64];
+                        tmem_ld64(taS + half * 64, r);
+                        tmem_ld_wait();
+                        uint32_t pk[32];
+                        if (unit)
+                            eval_chunk64<KIND, false>(r, pk, dsc);
+                        else
+                            eval_chunk64<KIND, true>(r, pk, dsc);
+                        tmem_st32(taP + half * 32, pk);
+                    }
+                    if (!ok) break;
+                    tmem_st_wait();
+                    tc_fence_before();
+                    mbar_arrive(&t_kval[b]);
+                }
+                epilogue(sg);
             }
         }
     }
@@ -562,6 +814,40 @@ __global__ void tc_reduce_kernel(KParams p) {
     float s = 0.0f;
     for (int sp = 0; sp < p.nsplit; ++sp) s += p.partial[((int64_t)sp * p.R + c) * p.n1 + i];
     float y = p.alpha * s;
+    if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
+    if (p.diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
+        y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - drow0)];
+    p.Y[(int64_t)c * p.ldy + i] = y;
+}
+
+// Row tiles of a persistent product that several CTAs share, listed by the host: entry e is
+// row tile r[e], computed by the CTAs bf[e] .. bf[e] + nb[e] - 1; the first of them holds it
+// in slot s0[e] (its last segment), the others in slot 0 (their first segment).
+constexpr int kPTabMax = 256;  // >= the persistent grid (one CTA per SM)
+struct PTable {
+    int n;
+    int r[kPTabMax];
+    short bf[kPTabMax];
+    unsigned short nb[kPTabMax];
+    unsigned char s0[kPTabMax];
+};
+
+// Sums the slots of each shared row tile in CTA order (deterministic), then the epilogue;
+// grid (table entries, right-hand sides), one thread per row.
+__global__ void tc_reduce_persist_kernel(KParams p, const PTable tab) {
+    if (p.done && *p.done) return;
+    const int e = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+    const int64_t i = (int64_t)tab.r[e] * TM + t;
+    if (i >= p.n1) return;
+    int64_t drow0 = p.drow0, ndiag = p.ndiag;
+    if (p.col0_dev && p.diag_from_col0) {
+        drow0 = *p.col0_dev;
+        ndiag = min(ndiag, p.ncols_total - drow0);
+    }
+    const int64_t b0 = tab.bf[e];
+    float sum = p.partial[((b0 * 2 + tab.s0[e]) * p.R + c) * TM + t];
+    for (int k = 1; k < tab.nb[e]; ++k) sum += p.partial[(((b0 + k) * 2) * p.R + c) * TM + t];
+    float y = p.alpha * sum;
     if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
     if (p.diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
         y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - drow0)];
@@ -887,10 +1173,19 @@ int num_sms_tc() {
     return sms;
 }
 
+// The persistent schedule (split code kPersist): one CTA per SM over equal runs of
+// (row tile, column tile) pairs; nseg = the most row segments one CTA can meet.
+void persist_geom(int64_t row_tiles, int64_t col_tiles, int *G, int *nseg) {
+    const int64_t T = row_tiles * col_tiles;
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(std::min(num_sms_tc(), kPTabMax), T));
+    *G = (int)g;
+    *nseg = (int)(cdiv(cdiv(T, g), col_tiles) + 1);
+}
+
 // Column splits per row tile: minimises (waves of CTAs) x (tiles per CTA + a fixed per-CTA
 // cost of about four tiles: tensor-memory allocation, first loads, epilogue); every split
 // owns at least one tile.  Few row tiles (a stochastic-gradient row panel) get many splits.
-int pick_split(int64_t row_tiles, int64_t col_tiles) {
+int pick_uniform_split(int64_t row_tiles, int64_t col_tiles, int64_t *cost_out) {
     const int64_t sms = num_sms_tc();
     const int64_t smax = std::min<int64_t>(256, std::max<int64_t>(1, col_tiles));
     int best = 1;
@@ -903,7 +1198,32 @@ int pick_split(int64_t row_tiles, int64_t col_tiles) {
             best = (int)s;
         }
     }
+    if (cost_out) *cost_out = best_cost;
     return best;
+}
+
+// The product's schedule: the best uniform split, or the persistent one when the model
+// prices it lower: no partial last wave and one start-up per SM, against about two tiles per
+// extra row segment (row-operand reload, accumulator read-out), the straddling rows'
+// reduction, and a tile period about 2% longer than the uniform split's (measured at
+// n = 32768 to 131072).
+int pick_split(int64_t row_tiles, int64_t col_tiles) {
+    int64_t ucost = 0;
+    const int best = pick_uniform_split(row_tiles, col_tiles, &ucost);
+    int G = 0, sg = 0;
+    persist_geom(row_tiles, col_tiles, &G, &sg);
+    const int64_t pcost = (cdiv(row_tiles * col_tiles, G) * 102 + 99) / 100 + 4 + 2 * (int64_t)(sg - 1) + 1;
+    return pcost < ucost ? kPersist : best;
+}
+
+// Floats of partial sums a product with this split code needs.
+size_t partial_floats(int split, int64_t n1, int R, int64_t row_tiles, int64_t col_tiles) {
+    if (split == kPersist) {
+        int G = 0, sg = 0;
+        persist_geom(row_tiles, col_tiles, &G, &sg);
+        return (size_t)G * 2 * R * TM;  // two slots per CTA
+    }
+    return split > 1 ? (size_t)split * R * n1 : 0;
 }
 
 // Split counts chosen by timing (gp_autotune_mvm), keyed by the product's shape in tiles;
@@ -927,9 +1247,9 @@ int tuned_split(int R_pad, int64_t row_tiles, int64_t col_tiles) {
 
 // The split a product of this shape uses: forced (autotuner), tuned, or the cost model.
 int split_for(int R_pad, int64_t row_tiles, int64_t col_tiles) {
-    if (g_force_split > 0) return g_force_split;
+    if (g_force_split != 0) return g_force_split;
     const int t = tuned_split(R_pad, row_tiles, col_tiles);
-    return t > 0 ? t : pick_split(row_tiles, col_tiles);
+    return t != 0 ? t : pick_split(row_tiles, col_tiles);
 }
 
 // Ring depths of the product kernel: up to 4 V slots (GEMM2 runs about two tiles behind
@@ -948,17 +1268,24 @@ size_t smem_for(int KD, int R_pad, int npb, int nv) {
     return 1024 + (size_t)TM * KD * 2 + (size_t)npb * TN * KD * 2 + (size_t)nv * 2 * R_pad * 128 + 512;
 }
 
-template <int KIND, int KAT>
+template <int KIND, int KAT, bool PERSIST>
 int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mV,
                       const KParams &kp, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<KIND, KAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxDynSmem));
+        GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<KIND, KAT, PERSIST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
         attr = true;
     }
-    tc_mvm_kernel<KIND, KAT><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+    tc_mvm_kernel<KIND, KAT, PERSIST><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
     return GP_OK;
+}
+
+template <int KIND, int KAT>
+int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mV,
+                      const KParams &kp, cudaStream_t st) {
+    return kp.persist ? launch_mvm_kernel<KIND, KAT, true>(grid, smem, mA, mB, mV, kp, st)
+                      : launch_mvm_kernel<KIND, KAT, false>(grid, smem, mA, mB, mV, kp, st);
 }
 
 }  // namespace
@@ -1061,21 +1388,26 @@ size_t tc_mvm_workspace_for(int64_t n1, int64_t p2, int R, int nsplit) {
     c.take<float>(256);
     c.take<float>((size_t)std::min(R, kMaxRhsPerPass) * 64);
     c.take<int>(1);
-    if (nsplit > 1) c.take<float>((size_t)nsplit * std::min(R, kMaxRhsPerPass) * n1);
+    const size_t pf = partial_floats(nsplit, n1, std::min(R, kMaxRhsPerPass), cdiv(std::max<int64_t>(n1, 1), TM),
+                                     cdiv(p2, TN));
+    if (pf > 0) c.take<float>(pf);
     return c.bytes();
 }
 
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
     const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
     const int R_pad = rpad_for(std::min(R, kMaxRhsPerPass));
-    const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM);
-    const int ns = std::max(split_for(R_pad, row_tiles, cdiv(p2, TN)), pick_split(row_tiles, cdiv(p2, TN)));
+    const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM), col_tiles = cdiv(p2, TN);
+    // room for the partial sums of both the tuned and the model's choice
+    const int s1 = split_for(R_pad, row_tiles, col_tiles), s2 = pick_split(row_tiles, col_tiles);
+    const size_t pf = std::max(partial_floats(s1, n1, R, row_tiles, col_tiles),
+                               partial_floats(s2, n1, R, row_tiles, col_tiles));
     Carver c(nullptr);
     c.take<__half>((size_t)R_pad * p2);            // V16
     c.take<float>(256);                            // vinv
     c.take<float>((size_t)R * 64);                 // column max partials
     c.take<int>(1);                                // error flag
-    if (ns > 1) c.take<float>((size_t)ns * R * n1);
+    if (pf > 0) c.take<float>(pf);                 // partial sums
     return c.bytes();
 }
 
@@ -1108,15 +1440,20 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         probe.take<float>(256);
         probe.take<float>((size_t)a.R * 64);
         probe.take<int>(1);
-        if (nsplit > 1) probe.take<float>((size_t)nsplit * a.R * n1);
+        const size_t pf = partial_floats(nsplit, n1, a.R, row_tiles, col_tiles);
+        if (pf > 0) probe.take<float>(pf);
         if (probe.bytes() > ws_bytes && g_force_split == 0) nsplit = pick_split(row_tiles, col_tiles);
     }
+    const bool persist = (nsplit == kPersist);
+    int pgrid = 0, pseg = 0;
+    if (persist) persist_geom(row_tiles, col_tiles, &pgrid, &pseg);
+    const size_t pfl = partial_floats(nsplit, n1, a.R, row_tiles, col_tiles);
     Carver c(ws);
     __half *V16 = c.take<__half>((size_t)R_pad * p2);
     float *vinv = c.take<float>(256);
     float *cm = c.take<float>((size_t)a.R * 64);
     int *err = c.take<int>(1);
-    float *partial = nsplit > 1 ? c.take<float>((size_t)nsplit * a.R * n1) : nullptr;
+    float *partial = pfl > 0 ? c.take<float>(pfl) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
     const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
     tc_colmax_kernel<<<dim3(P, a.R), 256, 0, st>>>(a.V, a.ldv, n2, P, cm, a.done);
@@ -1142,7 +1479,10 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.nv = nv;
     kp.n1 = n1;
     kp.col_tiles = col_tiles;
-    kp.nsplit = nsplit;
+    kp.nsplit = persist ? 1 : nsplit;
+    kp.persist = persist ? 1 : 0;
+    kp.ptotal = row_tiles * col_tiles;
+    kp.pgrid = pgrid;
     kp.sf2 = a.sf2;
     kp.alpha = a.alpha;
     kp.beta = a.beta;
@@ -1162,7 +1502,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.diag_from_col0 = a.diag_from_col0;
     kp.ncols_total = a.cols.n;
     const size_t smem = smem_for(KD, R_pad, npb, nv);
-    dim3 grid((unsigned)row_tiles, (unsigned)nsplit);
+    dim3 grid = persist ? dim3((unsigned)pgrid, 1) : dim3((unsigned)row_tiles, (unsigned)nsplit);
     const int kat = KD / 64;
     if (kat > 3) {
         set_error("tensor-core product supports d <= 62 (got KD=%d)", KD);
@@ -1180,7 +1520,31 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     }
     prof_end(st);
     GP_TRY(check_launch("tc_mvm_kernel"));
-    if (nsplit > 1) {
+    if (persist) {
+        // row tiles that straddle a CTA boundary (a boundary inside a row tile)
+        PTable tab;
+        tab.n = 0;
+        const int64_t T = kp.ptotal, C = col_tiles;
+        for (int64_t bb = 1; bb < pgrid; ++bb) {
+            const int64_t gb = T * bb / pgrid;
+            if (gb % C == 0) continue;
+            const int r = (int)(gb / C);
+            if (tab.n > 0 && tab.r[tab.n - 1] == r) {
+                ++tab.nb[tab.n - 1];
+                continue;
+            }
+            const int e = tab.n++;
+            const int64_t gprev = T * (bb - 1) / pgrid;
+            tab.r[e] = r;
+            tab.bf[e] = (short)(bb - 1);
+            tab.nb[e] = 2;
+            tab.s0[e] = (unsigned char)(r > gprev / C ? 1 : 0);
+        }
+        if (tab.n > 0) {
+            tc_reduce_persist_kernel<<<dim3((unsigned)tab.n, (unsigned)a.R), TM, 0, st>>>(kp, tab);
+            GP_TRY(check_launch("tc_reduce_persist_kernel"));
+        }
+    } else if (nsplit > 1) {
         tc_reduce_kernel<<<dim3((unsigned)cdiv(n1, 256), a.R), 256, 0, st>>>(kp);
         GP_TRY(check_launch("tc_reduce_kernel"));
     }
@@ -1195,7 +1559,7 @@ int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStr
     const int64_t p2 = rup(std::max<int64_t>(a.cols.n, 1), TN);
     const int R_pad = rpad_for(std::min(a.R, kMaxRhsPerPass));
     const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM), col_tiles = cdiv(p2, TN);
-    static const int ladder[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32, 48, 64, 96, 128};
+    static const int ladder[] = {kPersist, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32, 48, 64, 96, 128};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GP_TRY_CUDA(cudaEventCreate(&e0));
     GP_TRY_CUDA(cudaEventCreate(&e1));
@@ -1203,7 +1567,7 @@ int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStr
     double best_t = 1e300;
     int rc = GP_OK;
     for (int s : ladder) {
-        if (s > col_tiles || (s > 1 && cdiv(col_tiles, s) * (s - 1) >= col_tiles)) continue;
+        if (s != kPersist && (s > col_tiles || (s > 1 && cdiv(col_tiles, s) * (s - 1) >= col_tiles))) continue;
         if (tc_mvm_workspace_for(n1, p2, a.R, s) > ws_bytes) continue;
         g_force_split = s;
         double t_min = 1e300;
@@ -1246,7 +1610,8 @@ int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStr
 size_t tc_autotune_workspace(int64_t n, int R) {
     const int64_t p2 = rup(std::max<int64_t>(n, 1), TN);
     const int64_t col_tiles = p2 / TN;
-    return tc_mvm_workspace_for(n, p2, R, (int)std::min<int64_t>(128, col_tiles));
+    return std::max(tc_mvm_workspace_for(n, p2, R, (int)std::min<int64_t>(128, col_tiles)),
+                    tc_mvm_workspace_for(n, p2, R, kPersist));
 }
 
 void tc_autotune_reset() {
@@ -1768,7 +2133,7 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
     g.n_pad = rup(std::max<int64_t>(n, 1), TM);
     g.row_tiles = g.n_pad / TM;
     g.col_tiles = g.n_pad / GTN;
-    g.nsplit = pick_split(g.row_tiles, g.col_tiles);
+    g.nsplit = pick_uniform_split(g.row_tiles, g.col_tiles, nullptr);
     const size_t a = (size_t)TM * g.KD * 2 + (size_t)TM * g.KM * 2;
     const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2;
     const size_t b3 = (size_t)g.N3p * 128;
