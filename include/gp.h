@@ -254,6 +254,18 @@ size_t gp_solve_sgd_f64_workspace(int64_t n, int d, int nrhs, int64_t batch);
 int gp_rff_prior_sample(int kind, const double *theta, int d, const float *X, int64_t n,
                         int m, const float *omega_hat, const float *chi2, const float *W,
                         int s, float *F, int64_t ldf, cudaStream_t stream);
+/* Same, in a precision form with a caller workspace (gp_rff_prior_sample_workspace bytes):
+ * GP_PREC_FP32 is the CUDA-core form above; GP_PREC_TC16 takes F^T = Phi W^T on the tensor
+ * cores, with the features Phi (cos / sin of w_l . x, range-reduced by 2 pi, on the MUFU) and
+ * the weights each split into fp16 hi + lo parts and the product summed as hi.hi + hi.lo +
+ * lo.hi in FP32 (error ~1e-6 relative, the FP32 form's order), for d <= 32 and s <= 128
+ * (larger problems run the CUDA-core form).  Errors: as gp_rff_prior_sample, plus
+ * GP_ERR_WORKSPACE and GP_ERR_UNSUPPORTED (GP_PREC_TC16 without tcgen05). */
+int gp_rff_prior_sample_ws(int kind, const double *theta, int d, const float *X, int64_t n,
+                           int m, const float *omega_hat, const float *chi2, const float *W,
+                           int s, float *F, int64_t ldf, int prec, void *ws, size_t ws_bytes,
+                           cudaStream_t stream);
+size_t gp_rff_prior_sample_workspace(int d, int m, int s, int prec);
 int gp_rff_prior_sample_f64(int kind, const double *theta, int d, const double *X, int64_t n,
                             int m, const double *omega_hat, const double *chi2, const double *W,
                             int s, double *F, int64_t ldf, cudaStream_t stream);

@@ -113,6 +113,8 @@ _SIGS = {
     "gp_rkhs_sqdist_f64_workspace": (_sz, [_i64, _i, _i]),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
+    "gp_rff_prior_sample_ws": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _i, _vp, _sz, _vp]),
+    "gp_rff_prior_sample_workspace": (_sz, [_i, _i, _i, _i]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
     "gp_mll_grad_standard": (_i, [_i, _pd, _i, _vp, _i64, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp]),
     "gp_mll_grad_pathwise": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i, _vp, _sz, _vp]),
@@ -361,8 +363,9 @@ def gp_solve_sgd(kind, theta, X, B, batch_idx, lr, momentum=0.9, V0=None, max_it
     return V, _info(inf)
 
 
-def gp_rff_prior_sample(kind, theta, X, omega_hat, chi2, W, out=None):
-    """Prior samples F (s, n) at X from fixed random-feature parameters."""
+def gp_rff_prior_sample(kind, theta, X, omega_hat, chi2, W, out=None, prec=GP_PREC_TC16):
+    """Prior samples F (s, n) at X from fixed random-feature parameters.  float32: prec selects
+    the tensor-core form (GP_PREC_TC16) or the CUDA-core form (GP_PREC_FP32)."""
     lib = library()
     dt = X.dtype
     _dev(X, dt, "X", 2)
@@ -376,9 +379,13 @@ def gp_rff_prior_sample(kind, theta, X, omega_hat, chi2, W, out=None):
         raise ValueError("omega_hat must be (m/2, d)")
     th, thp = _theta(theta, d)
     F = torch.empty((s, n), dtype=dt, device=X.device) if out is None else out
-    fn = lib.gp_rff_prior_sample_f64 if _f64(X) else lib.gp_rff_prior_sample
-    _check(fn(kind, thp, d, _ptr(X), n, m, _ptr(omega_hat), _ptr(chi2), _ptr(W), s, _ptr(F), F.stride(0),
-              _stream()))
+    if _f64(X):
+        _check(lib.gp_rff_prior_sample_f64(kind, thp, d, _ptr(X), n, m, _ptr(omega_hat), _ptr(chi2), _ptr(W), s,
+                                           _ptr(F), F.stride(0), _stream()))
+    else:
+        ws, wsb = _ws(lib.gp_rff_prior_sample_workspace(d, m, s, prec), X.device)
+        _check(lib.gp_rff_prior_sample_ws(kind, thp, d, _ptr(X), n, m, _ptr(omega_hat), _ptr(chi2), _ptr(W), s,
+                                          _ptr(F), F.stride(0), prec, _ptr(ws), wsb, _stream()))
     return F
 
 

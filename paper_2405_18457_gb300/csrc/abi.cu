@@ -456,6 +456,25 @@ int gp_rff_prior_sample(int kind, const double *theta, int d, const float *X, in
     GP_API_END
 }
 
+size_t gp_rff_prior_sample_workspace(int d, int m, int s, int prec) { return rff_workspace(d, m, s, prec); }
+
+int gp_rff_prior_sample_ws(int kind, const double *theta, int d, const float *X, int64_t n, int m,
+                           const float *omega_hat, const float *chi2, const float *W, int s, float *F, int64_t ldf,
+                           int prec, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    GP_API_BEGIN
+    KP<float> kp;
+    GP_TRY(make_kp<float>(kind, theta, d, &kp));
+    REQ(n >= 0 && s >= 0, "sizes must be non-negative");
+    REQ(m >= 2 && m % 2 == 0, "m must be even and >= 2");
+    if (n == 0 || s == 0) return GP_OK;
+    REQ(X && omega_hat && W && F, "null pointer argument");
+    REQ(kind == GP_RBF || chi2 != nullptr, "chi2 is required for Matern-3/2");
+    REQ(ldf >= n, "ldf must be >= n");
+    GP_TRY(check_prec(prec));
+    return rff_prior_ws(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, prec, ws, ws_bytes, stream);
+    GP_API_END
+}
+
 int gp_rff_prior_sample_f64(int kind, const double *theta, int d, const double *X, int64_t n, int m,
                             const double *omega_hat, const double *chi2, const double *W, int s, double *F,
                             int64_t ldf, cudaStream_t stream) {

@@ -244,6 +244,12 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
                     cudaStream_t st);
 int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st);
 bool tc_available();
+// Random Fourier features on the tensor cores (fp16 hi/lo split of features and weights):
+// d <= 32 and s <= 128; the workspace holds the scaled frequencies and the split weights.
+bool tc_rff_fits(int d, int m, int s);
+size_t tc_rff_workspace(int d, int m, int s);
+int tc_rff(const KP<float> &kp, const float *X, int64_t n, int m, const float *omega_hat, const float *chi2,
+           const float *W, int s, float *F, int64_t ldf, void *ws, size_t ws_bytes, cudaStream_t st);
 // Split-count autotuner of the product (rows == cols): times candidates, records the best
 // for the shape in a process-wide table that later products of that shape use.
 size_t tc_autotune_workspace(int64_t n, int R);

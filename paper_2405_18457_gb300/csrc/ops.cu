@@ -258,6 +258,17 @@ int rff_prior(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat,
 }
 template int rff_prior<float>(const KP<float> &, const float *, int64_t, int, const float *, const float *,
                               const float *, int, float *, int64_t, cudaStream_t);
+
+size_t rff_workspace(int d, int m, int s, int prec) {
+    return (prec == GP_PREC_TC16 && tc_rff_fits(d, m, s)) ? tc_rff_workspace(d, m, s) : 0;
+}
+
+int rff_prior_ws(const KP<float> &kp, const float *X, int64_t n, int m, const float *omega_hat, const float *chi2,
+                 const float *W, int s, float *F, int64_t ldf, int prec, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (prec == GP_PREC_TC16 && tc_rff_fits(kp.d, m, s))
+        return tc_rff(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, ws, ws_bytes, st);
+    return launch_rff<float>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf, st);
+}
 template int rff_prior<double>(const KP<double> &, const double *, int64_t, int, const double *, const double *,
                                const double *, int, double *, int64_t, cudaStream_t);
 

@@ -29,6 +29,11 @@ int bilinear_value(const KP<T> &kp, const double *g, double *value, cudaStream_t
 template <typename T>
 int rff_prior(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat, const T *chi2, const T *W,
               int s, T *F, int64_t ldf, cudaStream_t st);
+// Same, with a precision form (GP_PREC_TC16: tensor cores within tc_rff_fits, else CUDA cores)
+// and a caller workspace.
+size_t rff_workspace(int d, int m, int s, int prec);
+int rff_prior_ws(const KP<float> &kp, const float *X, int64_t n, int m, const float *omega_hat, const float *chi2,
+                 const float *W, int s, float *F, int64_t ldf, int prec, void *ws, size_t ws_bytes, cudaStream_t st);
 int pathwise_rhs(float sigma, const float *y, const float *F, const float *w, int64_t n, int s, float *B,
                  cudaStream_t st);
 

@@ -43,7 +43,7 @@ def main():
         elif args.op == "grad":
             gp.gp_mll_grad_pathwise(p.kind, p.theta, X, V, prec=prec)
         elif args.op == "rff":
-            gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, Wp)
+            gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, Wp, prec=prec)
         else:
             gp.gp_solve_cg(p.kind, p.theta, X, V, max_iters=10, tol=0.0, prec=prec)
 

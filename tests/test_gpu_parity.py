@@ -345,15 +345,43 @@ def test_sgd_reports_divergence(dev):
 
 
 # --------------------------------------------------------------------------- random features, posterior
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 2e-5)])
+@pytest.mark.parametrize("dtype,prec,tol", [(torch.float64, gp.GP_PREC_FP32, 1e-11),
+                                            (torch.float32, gp.GP_PREC_FP32, 2e-5),
+                                            (torch.float32, gp.GP_PREC_TC16, 2e-5)])
 @pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
-def test_rff_prior_sample_matches_oracle(dev, dtype, tol, kind):
+def test_rff_prior_sample_matches_oracle(dev, dtype, prec, tol, kind):
+    """Ragged n, s not a multiple of 16, m/2 not a multiple of the 32-frequency chunk."""
     p = workloads.pathwise(n=517, d=9, s=33, m=130, seed=2)
     F = gp.gp_rff_prior_sample(kind, p.theta, t(p.X, dev, dtype), t(p.omega_hat, dev, dtype),
-                               t(p.chi2, dev, dtype), t(p.W_probe, dev, dtype))
+                               t(p.chi2, dev, dtype), t(p.W_probe, dev, dtype), prec=prec)
     cast = (lambda a: a) if dtype == torch.float64 else (lambda a: a.astype(np.float32).astype(np.float64))
     ref = oracle.rff_prior(kind, p.theta, cast(p.X), cast(p.omega_hat), cast(p.chi2), cast(p.W_probe))
     assert rel(F.double().cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("n,d,s,m", [(300, 32, 128, 64), (260, 4, 129, 96), (128, 1, 1, 2)])
+def test_rff_tensor_core_limits(dev, n, d, s, m):
+    """The largest tensor-core shape (d = 32, s = 128), the CUDA-core fallback past it
+    (s = 129) and the smallest case (one point row tile, one sample, one frequency)."""
+    p = workloads.pathwise(n=n, d=d, s=s, m=m, seed=4)
+    F = gp.gp_rff_prior_sample(p.kind, p.theta, t(p.X, dev), t(p.omega_hat, dev), t(p.chi2, dev),
+                               t(p.W_probe, dev), prec=gp.GP_PREC_TC16)
+    f = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    ref = oracle.rff_prior(p.kind, p.theta, f(p.X), f(p.omega_hat), f(p.chi2), f(p.W_probe))
+    assert rel(F.double().cpu().numpy(), ref) < 2e-5
+
+
+def test_rff_full_size_sampled_points(dev):
+    """The pathwise workload's prior samples (n = 32768, d = 16, m = 2048, s = 64, Matern-3/2)
+    in both forms, checked on sampled points (a point's features do not depend on the others)."""
+    p = workloads.pathwise()
+    f = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    rows = np.random.default_rng(31).choice(p.n, size=200, replace=False)
+    ref = oracle.rff_prior(p.kind, p.theta, f(p.X)[rows], f(p.omega_hat), f(p.chi2), f(p.W_probe))
+    for prec in (gp.GP_PREC_TC16, gp.GP_PREC_FP32):
+        F = gp.gp_rff_prior_sample(p.kind, p.theta, t(p.X, dev), t(p.omega_hat, dev), t(p.chi2, dev),
+                                   t(p.W_probe, dev), prec=prec)
+        assert rel(F.double().cpu().numpy()[:, rows], ref) < 2e-5
 
 
 def test_pathwise_rhs_and_posterior_samples_match_oracle(dev):
