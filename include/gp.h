@@ -109,6 +109,16 @@ long long gp_diag_launches(void);
 int gp_diag_kernel_time(int which, double *total_ms, long long *count);
 int gp_diag_product_time(double *total_ms, long long *count);
 
+/* Device status.  Every wait of the tensor-core kernels on a barrier is bounded (about 2 s);
+ * a wait that gives up makes its kernel skip the rest of its work, release its tensor memory,
+ * return, and set a device status word.  gp_device_check() synchronises `stream`, reads and
+ * clears the word: GP_ERR_TIMEOUT when a wait gave up since the last check (the results of
+ * the calls in between are not valid), else GP_OK.  CG in the tensor-core form checks it
+ * before returning.  gp_diag_timeout_probe() launches one wait that nothing completes,
+ * bounded by wait_cycles (<= 4e9) SM cycles, to exercise that path. */
+int gp_device_check(cudaStream_t stream);
+int gp_diag_timeout_probe(long long wait_cycles, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Kernel matrix-vector products (Sec. 2 H_theta; Eq. standard_system,        */
 /* Eq. pathwise_system; every solver's "linear operator H(.)", Alg. 1-3)     */

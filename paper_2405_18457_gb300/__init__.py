@@ -35,6 +35,8 @@ from ._binding import (  # noqa: F401
     gp_pathwise_rhs,
     gp_posterior_samples,
     gp_predict,
+    gp_device_check,
+    gp_diag_timeout_probe,
     gp_rkhs_sqdist,
     gp_rff_prior_sample,
     gp_solve_ap,

@@ -113,6 +113,8 @@ _SIGS = {
     "gp_rkhs_sqdist_f64_workspace": (_sz, [_i64, _i, _i]),
     "gp_rff_prior_sample": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
+    "gp_device_check": (_i, [_vp]),
+    "gp_diag_timeout_probe": (_i, [ctypes.c_longlong, _vp]),
     "gp_rff_prior_sample_ws": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _i, _vp, _sz, _vp]),
     "gp_rff_prior_sample_workspace": (_sz, [_i, _i, _i, _i]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
@@ -148,6 +150,16 @@ def gp_diag_reset(time_products: bool = False) -> None:
 
 def gp_diag_launches() -> int:
     return int(library().gp_diag_launches())
+
+
+def gp_device_check():
+    """Raise GPError(GP_ERR_TIMEOUT) if a bounded device wait gave up since the last check."""
+    _check(library().gp_device_check(_stream()))
+
+
+def gp_diag_timeout_probe(wait_cycles):
+    """Launch one bounded wait that nothing completes (exercises the time-out status)."""
+    _check(library().gp_diag_timeout_probe(int(wait_cycles), _stream()))
 
 
 def gp_diag_product_time():

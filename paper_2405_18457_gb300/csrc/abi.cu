@@ -248,6 +248,19 @@ void gp_diag_reset(int time_products) {
 
 long long gp_diag_launches(void) { return g_launches.load(); }
 
+int gp_device_check(cudaStream_t stream) {
+    GP_API_BEGIN
+    return tc_timeout_status(stream);
+    GP_API_END
+}
+
+int gp_diag_timeout_probe(long long wait_cycles, cudaStream_t stream) {
+    GP_API_BEGIN
+    REQ(wait_cycles >= 0 && wait_cycles <= 4000000000LL, "wait_cycles must be in [0, 4e9]");
+    return tc_timeout_probe(wait_cycles, stream);
+    GP_API_END
+}
+
 int gp_diag_kernel_time(int which, double *total_ms, long long *count) {
     GP_API_BEGIN
     REQ(total_ms && count, "null pointer argument");

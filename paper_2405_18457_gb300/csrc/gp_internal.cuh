@@ -244,6 +244,12 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
                     cudaStream_t st);
 int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st);
 bool tc_available();
+// Device word that a tensor-core kernel sets when one of its bounded waits gives up;
+// tc_timeout_status synchronises the stream, reads and clears it (GP_ERR_TIMEOUT if set);
+// tc_timeout_probe launches a wait that nothing completes, bounded by `limit` cycles.
+int *tc_timeout_word();
+int tc_timeout_status(cudaStream_t st);
+int tc_timeout_probe(long long limit, cudaStream_t st);
 // Random Fourier features on the tensor cores (fp16 hi/lo split of features and weights):
 // d <= 32 and s <= 128; the workspace holds the scaled frequencies and the split weights.
 bool tc_rff_fits(int d, int m, int s);

@@ -310,6 +310,7 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(check_launch("cg rescale"));
     GP_TRY(poll_state(sd, &hs, st));
     fill_info(hs, info);
+    if (op.tc) GP_TRY(tc_timeout_status(st));
     if (hs.status != GP_OK) {
         set_error("CG breakdown: residual became non-finite at iteration %lld", hs.iter);
         return hs.status;

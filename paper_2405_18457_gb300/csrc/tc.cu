@@ -79,18 +79,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait; false when this or another thread of the CTA timed out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, volatile int *err, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (*err) return false;
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *err = 1;
             return false;
         }
     }
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *err) {
+    return mbar_wait_for(bar, parity, err, kWaitCycles);
+}
+
+// Set (to 1) by any tensor-core kernel whose bounded wait gave up; read and cleared by the
+// host (tc_timeout_status).
+__device__ int g_tc_timeout = 0;
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(
@@ -797,7 +804,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
-    if (threadIdx.x == 0 && *s_err) atomicExch(p.err, 1);
+    if (threadIdx.x == 0 && *s_err && p.err) atomicExch(p.err, 1);
 }
 
 // Empty column set or split partial reduction + epilogue.
@@ -1290,6 +1297,56 @@ int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUten
 
 }  // namespace
 
+int *tc_timeout_word() {
+    static int *w = nullptr;
+    if (!w) {
+        void *a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_tc_timeout) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        w = static_cast<int *>(a);
+    }
+    return w;
+}
+
+int tc_timeout_status(cudaStream_t st) {
+    int *w = tc_timeout_word();
+    if (!w) return GP_OK;
+    int h = 0;
+    GP_TRY_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        GP_TRY_CUDA(cudaMemsetAsync(w, 0, sizeof(int), st));
+        GP_TRY_CUDA(cudaStreamSynchronize(st));
+        set_error("a bounded wait in a tensor-core kernel gave up (its results are not valid)");
+        return GP_ERR_TIMEOUT;
+    }
+    return GP_OK;
+}
+
+namespace {
+// A wait that nothing completes, bounded by `limit` cycles: exercises the time-out path.
+__global__ void tc_timeout_probe_kernel(long long limit, int *word) {
+    __shared__ uint64_t bar;
+    __shared__ int err;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_for(&bar, 0, &err, limit);
+    __syncthreads();
+    if (threadIdx.x == 0 && !ok && word) atomicExch(word, 1);
+}
+}  // namespace
+
+int tc_timeout_probe(long long limit, cudaStream_t st) {
+    tc_timeout_probe_kernel<<<1, 32, 0, st>>>(limit, tc_timeout_word());
+    return check_launch("tc_timeout_probe_kernel");
+}
+
 bool tc_available() {
     static int ok = -1;
     if (ok < 0) {
@@ -1452,7 +1509,8 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     __half *V16 = c.take<__half>((size_t)R_pad * p2);
     float *vinv = c.take<float>(256);
     float *cm = c.take<float>((size_t)a.R * 64);
-    int *err = c.take<int>(1);
+    c.take<int>(1);  // (kept for the workspace layout)
+    int *err = tc_timeout_word();
     float *partial = pfl > 0 ? c.take<float>(pfl) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
     const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
@@ -2036,7 +2094,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncthreads();
         if (threadIdx.x == 0) out[k] = red[4] + red[5] + red[6] + red[7];
     }
-    if (threadIdx.x == 0 && *s_err) atomicExch(p.err, 1);
+    if (threadIdx.x == 0 && *s_err && p.err) atomicExch(p.err, 1);
 }
 
 // max |lambda_c U_ci| and max |W_cj| over i < n, c < R (float bits).
@@ -2186,7 +2244,8 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     __half *B3 = c.take<__half>((size_t)g.N3p * g.n_pad);
     unsigned int *bnd = c.take<unsigned int>(2);
     float *guw = c.take<float>(1);
-    int *err = c.take<int>(1);
+    c.take<int>(1);  // (kept for the workspace layout)
+    int *err = tc_timeout_word();
     const int nblocks = (int)(g.row_tiles * g.nsplit);
     double *partial = c.take<double>((size_t)nblocks * (d + 1));
     double *dpart = c.take<double>(256);
@@ -2511,7 +2570,7 @@ __global__ void __launch_bounds__(RF_THREADS, 1) tc_rff_kernel(const __grid_cons
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tD), "r"(p.tcols) : "memory");
     }
-    if (threadIdx.x == 0 && *s_err) atomicExch(p.err, 1);
+    if (threadIdx.x == 0 && *s_err && p.err) atomicExch(p.err, 1);
 }
 
 struct RfPlan {
@@ -2557,13 +2616,13 @@ int tc_rff(const KP<float> &kp, const float *X, int64_t n, int m, const float *o
     Carver c(ws);
     float *Om = c.take<float>((size_t)g.h_pad * ((d + 3) & ~3));
     __half *Wt = c.take<__half>((size_t)2 * g.s_pad * 2 * g.h_pad);
-    int *err = c.take<int>(1);
+    c.take<int>(1);  // (kept for the workspace layout)
+    int *err = tc_timeout_word();
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
     const int64_t prep = (int64_t)g.h_pad * ((d + 3) & ~3) + (int64_t)g.s_pad * 2 * g.h_pad;
     tc_rff_prep_kernel<<<(unsigned)std::min<int64_t>(cdiv(prep, 256), 2048), 256, 0, st>>>(
         kp, m, omega_hat, chi2, W, s, g.s_pad, g.h_pad, Om, Wt);
     GP_TRY(check_launch("tc_rff_prep_kernel"));
-    GP_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     CUtensorMap mW;
     GP_TRY(make_map(&mW, Wt, (uint64_t)2 * g.h_pad, (uint64_t)2 * g.s_pad, 64, (uint32_t)g.s_pad));
     RfParams p{};
