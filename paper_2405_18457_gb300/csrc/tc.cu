@@ -2357,8 +2357,8 @@ __device__ __forceinline__ void rf_split(float v, __half *hi, __half *lo) {
 // Wt[r][k], r < s_pad: hi part of w(r, k); r >= s_pad: lo part of w(r - s_pad, k), with
 // w(j, 2l + e) = W[j][e m/2 + l] (zero for j >= s or l >= m/2).
 __global__ void tc_rff_prep_kernel(const KP<float> kp, int m, const float *omega_hat, const float *chi2,
-                                   const float *W, int s, int s_pad, int h_pad, float *Om, __half *Wt) {
-    const int d = kp.d, dp = (d + 3) & ~3, h = m / 2;
+                                   const float *W, int s, int s_pad, int h_pad, int dp, float *Om, __half *Wt) {
+    const int d = kp.d, h = m / 2;
     const int64_t nom = (int64_t)h_pad * dp, mp = 2 * (int64_t)h_pad, nw = (int64_t)s_pad * mp;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nom + nw;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -2391,6 +2391,9 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// DQ: float4 groups per frequency row (d <= 4 DQ; 1, 2, 4 or 8), fixed so that the dot
+// products are fully unrolled without predicated-off steps.
+template <int DQ>
 __global__ void __launch_bounds__(RF_THREADS, 1) tc_rff_kernel(const __grid_constant__ CUtensorMap mapW,
                                                                 const RfParams p) {
     extern __shared__ uint8_t smem_raw[];
@@ -2399,8 +2402,8 @@ __global__ void __launch_bounds__(RF_THREADS, 1) tc_rff_kernel(const __grid_cons
     const uint32_t w_bytes = (uint32_t)p.s_pad * 128;
     uint8_t *sA = smem;                              // RF_NA stages x {hi, lo}
     uint8_t *sW = sA + RF_NA * 2 * a_bytes;          // nb stages x {hi, lo}
-    // each weight stage also carries its chunk's frequencies (RF_FREQ rows of dp floats)
-    const int dpd = (p.d + 3) & ~3;
+    // each weight stage also carries its chunk's frequencies (RF_FREQ rows of 4 DQ floats)
+    constexpr int dpd = 4 * DQ;
     const uint32_t om_bytes = (uint32_t)RF_FREQ * dpd * 4;
     float *sOm = reinterpret_cast<float *>(sW + (size_t)p.nb * 2 * w_bytes);
     uint64_t *a_full = reinterpret_cast<uint64_t *>(sOm + (size_t)p.nb * RF_FREQ * RF_MAXD);
@@ -2486,10 +2489,10 @@ __global__ void __launch_bounds__(RF_THREADS, 1) tc_rff_kernel(const __grid_cons
         const int ft = threadIdx.x - 128;
         const int row = ft & 127, half = ft >> 7;
         const int64_t ip = row0 + row;
-        const int d = p.d, dq = dpd >> 2;
-        float x[RF_MAXD];
+        const int d = p.d;
+        float x[4 * DQ];
 #pragma unroll
-        for (int k = 0; k < RF_MAXD; ++k) x[k] = (k < d && ip < p.n) ? p.X[ip * d + k] : 0.0f;
+        for (int k = 0; k < 4 * DQ; ++k) x[k] = (k < d && ip < p.n) ? p.X[ip * d + k] : 0.0f;
         bool ok = true;
         for (int c = 0; c < nch; ++c) {
             // the chunk's frequencies arrive with its weight tiles; the stage stays until the
@@ -2511,16 +2514,14 @@ __global__ void __launch_bounds__(RF_THREADS, 1) tc_rff_kernel(const __grid_cons
                 // four frequencies at a time: independent dot products, then sin / cos
                 float arg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                for (int k4 = 0; k4 < RF_MAXD / 4; ++k4) {
-                    if (k4 < dq) {
+                for (int k4 = 0; k4 < DQ; ++k4) {
 #pragma unroll
-                        for (int f4 = 0; f4 < 4; ++f4) {
-                            const float4 w = om4[(q * 4 + f4) * dq + k4];
-                            arg[f4] = fmaf(w.x, x[4 * k4], arg[f4]);
-                            arg[f4] = fmaf(w.y, x[4 * k4 + 1], arg[f4]);
-                            arg[f4] = fmaf(w.z, x[4 * k4 + 2], arg[f4]);
-                            arg[f4] = fmaf(w.w, x[4 * k4 + 3], arg[f4]);
-                        }
+                    for (int f4 = 0; f4 < 4; ++f4) {
+                        const float4 w = om4[(q * 4 + f4) * DQ + k4];
+                        arg[f4] = fmaf(w.x, x[4 * k4], arg[f4]);
+                        arg[f4] = fmaf(w.y, x[4 * k4 + 1], arg[f4]);
+                        arg[f4] = fmaf(w.z, x[4 * k4 + 2], arg[f4]);
+                        arg[f4] = fmaf(w.w, x[4 * k4 + 3], arg[f4]);
                     }
                 }
                 uint32_t hv[4], lv[4];
@@ -2573,6 +2574,20 @@ __global__ void __launch_bounds__(RF_THREADS, 1) tc_rff_kernel(const __grid_cons
     if (threadIdx.x == 0 && *s_err && p.err) atomicExch(p.err, 1);
 }
 
+// float4 groups per frequency row of the instantiation that serves d
+int rf_dq(int d) { return d <= 4 ? 1 : d <= 8 ? 2 : d <= 16 ? 4 : 8; }
+
+template <int DQ>
+int launch_rff_kernel(const CUtensorMap &mW, const RfParams &p, size_t smem, int64_t grid, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        GP_TRY_CUDA(cudaFuncSetAttribute(tc_rff_kernel<DQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+        attr = true;
+    }
+    tc_rff_kernel<DQ><<<(unsigned)grid, RF_THREADS, smem, st>>>(mW, p);
+    return GP_OK;
+}
+
 struct RfPlan {
     int s_pad, h_pad, nb;
     uint32_t tcols;
@@ -2603,7 +2618,7 @@ bool tc_rff_fits(int d, int m, int s) {
 size_t tc_rff_workspace(int d, int m, int s) {
     const RfPlan g = plan_rff(m, s);
     Carver c(nullptr);
-    c.take<float>((size_t)g.h_pad * ((d + 3) & ~3));
+    c.take<float>((size_t)g.h_pad * 4 * rf_dq(d));
     c.take<__half>((size_t)2 * g.s_pad * 2 * g.h_pad);
     c.take<int>(1);
     return c.bytes();
@@ -2614,14 +2629,15 @@ int tc_rff(const KP<float> &kp, const float *X, int64_t n, int m, const float *o
     const int d = kp.d;
     const RfPlan g = plan_rff(m, s);
     Carver c(ws);
-    float *Om = c.take<float>((size_t)g.h_pad * ((d + 3) & ~3));
+    float *Om = c.take<float>((size_t)g.h_pad * 4 * rf_dq(d));
     __half *Wt = c.take<__half>((size_t)2 * g.s_pad * 2 * g.h_pad);
     c.take<int>(1);  // (kept for the workspace layout)
     int *err = tc_timeout_word();
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
-    const int64_t prep = (int64_t)g.h_pad * ((d + 3) & ~3) + (int64_t)g.s_pad * 2 * g.h_pad;
+    const int dp = 4 * rf_dq(d);
+    const int64_t prep = (int64_t)g.h_pad * dp + (int64_t)g.s_pad * 2 * g.h_pad;
     tc_rff_prep_kernel<<<(unsigned)std::min<int64_t>(cdiv(prep, 256), 2048), 256, 0, st>>>(
-        kp, m, omega_hat, chi2, W, s, g.s_pad, g.h_pad, Om, Wt);
+        kp, m, omega_hat, chi2, W, s, g.s_pad, g.h_pad, dp, Om, Wt);
     GP_TRY(check_launch("tc_rff_prep_kernel"));
     CUtensorMap mW;
     GP_TRY(make_map(&mW, Wt, (uint64_t)2 * g.h_pad, (uint64_t)2 * g.s_pad, 64, (uint32_t)g.s_pad));
@@ -2639,12 +2655,11 @@ int tc_rff(const KP<float> &kp, const float *X, int64_t n, int m, const float *o
     p.F = F;
     p.ldf = ldf;
     p.err = err;
-    static bool attr = false;
-    if (!attr) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(tc_rff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr = true;
-    }
-    tc_rff_kernel<<<(unsigned)cdiv(n, 128), RF_THREADS, g.smem, st>>>(mW, p);
+    const int dq = rf_dq(d);
+    if (dq == 1) GP_TRY(launch_rff_kernel<1>(mW, p, g.smem, cdiv(n, 128), st));
+    else if (dq == 2) GP_TRY(launch_rff_kernel<2>(mW, p, g.smem, cdiv(n, 128), st));
+    else if (dq == 4) GP_TRY(launch_rff_kernel<4>(mW, p, g.smem, cdiv(n, 128), st));
+    else GP_TRY(launch_rff_kernel<8>(mW, p, g.smem, cdiv(n, 128), st));
     return check_launch("tc_rff_kernel");
 }
 
