@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/gp.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -253,6 +254,10 @@ int tc_timeout_probe(long long limit, cudaStream_t st);
 // Random Fourier features on the tensor cores (fp16 hi/lo split of features and weights):
 // d <= 32 and s <= 128; the workspace holds the scaled frequencies and the split weights.
 bool tc_rff_fits(int d, int m, int s);
+// 2-D fp16 tensor map (128-byte swizzle) of an inner x outer row-major array, box_inner x
+// box_outer tiles (tc.cu).
+int tc_make_map16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                  uint32_t box_outer);
 size_t tc_rff_workspace(int d, int m, int s);
 int tc_rff(const KP<float> &kp, const float *X, int64_t n, int m, const float *omega_hat, const float *chi2,
            const float *W, int s, float *F, int64_t ldf, void *ws, size_t ws_bytes, cudaStream_t st);
