@@ -106,6 +106,79 @@ __global__ void cg_dir_kernel(T *d, const T *r, int64_t n, const double *beta, c
     }
 }
 
+// Fused forms of one iteration without a preconditioner (two launches instead of four).
+// alpha_c = gamma_c / d_c^T H d_c from the d^T H d partials (summed in a fixed order by every
+// block; block 0 of column c records alpha_c), then v += alpha d, r -= alpha Hd and the
+// partial sums of ||r||^2 into partN.  grid P x R
+template <typename T>
+__global__ void cg_update_fused_kernel(T *v, T *r, const T *d, const T *Hd, int64_t n, int P, const double *partD,
+                                       const double *gcur, double *alpha, double *partN, const SolverState *st) {
+    if (st->done) return;
+    const int p = blockIdx.x, c = blockIdx.y;
+    __shared__ double s_al;
+    if (threadIdx.x == 0) {
+        const double dHd = sum_parts(partD, c, P);
+        const double g = gcur[c];
+        const double al = (g > kFreeze && dHd > 0.0 && isfinite(dHd)) ? g / dHd : 0.0;
+        s_al = al;
+        if (p == 0) alpha[c] = al;
+    }
+    __syncthreads();
+    const int64_t per = cdiv(n, P);
+    const int64_t i0 = (int64_t)p * per, i1 = min(n, i0 + per);
+    const T a = (T)s_al;
+    const int64_t off = (int64_t)c * n;
+    double sum = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        v[off + i] += a * d[off + i];
+        T rv = r[off + i] - a * Hd[off + i];
+        r[off + i] = rv;
+        sum += (double)rv * (double)rv;
+    }
+    __shared__ double red[32];
+    sum = warp_sum(sum);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        partN[(int64_t)c * P + p] = t;
+    }
+}
+
+// beta_c = gamma_new / gamma_c (0 for a frozen column) from the ||r||^2 partials, d = r + beta d.
+// gamma alternates between two arrays by iteration parity: block (0, c) writes the next one,
+// every block reads the current one.  Block (0, 0) also takes the split norms, the iteration
+// count and the loop condition; a block that starts after `done` is latched skips its part of
+// d, which the finished solve no longer needs.  grid G x R
+template <typename T>
+__global__ void cg_dir_fused_kernel(T *d, const T *r, int64_t n, int P, const double *partN, const double *gcur,
+                                    double *gnext, const double *alpha, SolverState *st, long long max_iters,
+                                    double tol, int stop_rule, int R) {
+    if (st->done) return;
+    const int c = blockIdx.y;
+    __shared__ double s_b;
+    if (threadIdx.x == 0) {
+        const double gn = sum_parts(partN, c, P);
+        const bool active = alpha[c] != 0.0;
+        s_b = active ? gn / gcur[c] : 0.0;
+        if (blockIdx.x == 0) gnext[c] = active ? gn : gcur[c];
+    }
+    __syncthreads();
+    const T b = (T)s_b;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = (int64_t)c * n + i;
+        d[e] = r[e] + b * d[e];
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
+        __shared__ double sq[512];
+        for (int cc = threadIdx.x; cc < R; cc += blockDim.x) sq[cc] = sum_parts(partN, cc, P);
+        const long long t = st->iter + 1;
+        __syncthreads();
+        finish_norms_block(st, sq, R, t, max_iters, tol, stop_rule);
+    }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -211,7 +284,8 @@ size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank) {
     Carver c(nullptr);
     for (int k = 0; k < 3; ++k) c.take<T>((size_t)R * n);  // r, d, Hd
     c.take<double>((size_t)R * P);                          // partial sums
-    for (int k = 0; k < 4; ++k) c.take<double>(R);          // scale, gamma, alpha, beta
+    c.take<double>((size_t)R * P);                          // ||r||^2 partial sums
+    for (int k = 0; k < 5; ++k) c.take<double>(R);          // scale, gamma (x2), alpha, beta
     c.take<SolverState>(1);
     c.take<char>(HOp<T>::workspace(n, d, R, prec));
     if (pc_rank > 0) {
@@ -237,8 +311,9 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     T *dd = c.take<T>((size_t)R * n);
     T *Hd = c.take<T>((size_t)R * n);
     double *part = c.take<double>((size_t)R * P);
+    double *partN = c.take<double>((size_t)R * P);
     double *scale = c.take<double>(R);
-    double *gamma = c.take<double>(R);
+    double *gamma = c.take<double>(2 * (size_t)R);  // two arrays, alternating by iteration parity
     double *alpha = c.take<double>(R);
     double *beta = c.take<double>(R);
     SolverState *sd = c.take<SolverState>(1);
@@ -289,6 +364,16 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         for (int64_t it = 0; it < k; ++it) {
             GP_TRY(op.apply(dd, Hd, done, st));
             coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
+            if (!pc) {
+                const int64_t ti = launched + it;
+                const double *gcur = gamma + (ti & 1) * R;
+                double *gnext = gamma + ((ti + 1) & 1) * R;
+                cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, part, gcur, alpha, partN, sd);
+                cg_dir_fused_kernel<T><<<gv, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
+                                                           (long long)max_iters, tol, stop_rule, R);
+                GP_TRY(check_launch("cg iteration", 3));
+                continue;
+            }
             cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
             cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
             if (pc) {
