@@ -4,6 +4,7 @@
 #include "solvers.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace gp {
 
@@ -13,19 +14,41 @@ constexpr double kNormEps = 1e-12;   // eps of the normalisation b / (||b|| + ep
 constexpr double kFreeze = 1e-30;    // CG column frozen once gamma <= this
 
 // Row partitions of the per-column partial sums: enough blocks (partitions x columns)
-// to fill the GPU for the vector updates, at most 64 partials per column.
+// to fill the GPU for the vector updates, at most 64 partials per column.  A partition
+// covers a multiple of 4 rows, so that float vectors can be read as float4 when n % 4 == 0.
 int nparts_for(int64_t n) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n, 2048))); }
+__host__ __device__ inline int64_t part_len(int64_t n, int P) { return rup(cdiv(n, P), 4); }
+
+// Sum of a[i] b[i] over [i0, i1) by the threads of a block, FP64 accumulation.  For float
+// with 16-byte aligned rows (n % 4 == 0) four products are summed in FP32 (FMA) before each
+// FP64 addition: FP64 runs at a small fraction of the FP32 rate on this GPU, and the FP32
+// rounding of a four-term sum is below that of the FP32 inputs themselves.
+template <typename T>
+__device__ __forceinline__ double block_dot(const T *a, const T *b, int64_t i0, int64_t i1, bool vec4) {
+    double s = 0.0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (vec4) {
+            const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
+            for (int64_t q = (i0 >> 2) + threadIdx.x; q < (i1 >> 2); q += blockDim.x) {
+                const float4 x = a4[q], y = b4[q];
+                s += (double)fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+            }
+            return s;
+        }
+    }
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += (double)a[i] * (double)b[i];
+    return s;
+}
 
 // part[c*P + p] = sum_{i in chunk p} A[c][i] * B[c][i]   (grid P x R)
 template <typename T>
 __global__ void coldot_kernel(const T *A, const T *B, int64_t n, int P, double *part, const int *done) {
     if (done && *done) return;
     const int p = blockIdx.x, c = blockIdx.y;
-    const int64_t per = cdiv(n, P);
-    const int64_t i0 = (int64_t)p * per, i1 = min(n, i0 + per);
+    const int64_t per = part_len(n, P);
+    const int64_t i0 = min(n, (int64_t)p * per), i1 = min(n, i0 + per);
     const T *a = A + (int64_t)c * n, *b = B + (int64_t)c * n;
-    double s = 0.0;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += (double)a[i] * (double)b[i];
+    double s = block_dot<T>(a, b, i0, i1, (n & 3) == 0);
     __shared__ double red[32];
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -35,6 +58,14 @@ __global__ void coldot_kernel(const T *A, const T *B, int64_t n, int P, double *
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         part[(int64_t)c * P + p] = t;
     }
+}
+
+// The same sum taken by one whole warp (lane l adds partials l, l + 32, ... in order, then a
+// fixed butterfly): one round of loads instead of P dependent ones; deterministic.
+__device__ __forceinline__ double sum_parts_warp(const double *part, int c, int P) {
+    double s = 0.0;
+    for (int p = (int)(threadIdx.x & 31); p < P; p += 32) s += part[(int64_t)c * P + p];
+    return warp_sum(s);
 }
 
 __device__ __forceinline__ double sum_parts(const double *part, int c, int P) {

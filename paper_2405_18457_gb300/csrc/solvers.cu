@@ -116,24 +116,52 @@ __global__ void cg_update_fused_kernel(T *v, T *r, const T *d, const T *Hd, int6
     if (st->done) return;
     const int p = blockIdx.x, c = blockIdx.y;
     __shared__ double s_al;
-    if (threadIdx.x == 0) {
-        const double dHd = sum_parts(partD, c, P);
-        const double g = gcur[c];
-        const double al = (g > kFreeze && dHd > 0.0 && isfinite(dHd)) ? g / dHd : 0.0;
-        s_al = al;
-        if (p == 0) alpha[c] = al;
+    if (threadIdx.x < 32) {
+        const double dHd = sum_parts_warp(partD, c, P);
+        if (threadIdx.x == 0) {
+            const double g = gcur[c];
+            const double al = (g > kFreeze && dHd > 0.0 && isfinite(dHd)) ? g / dHd : 0.0;
+            s_al = al;
+            if (p == 0) alpha[c] = al;
+        }
     }
     __syncthreads();
-    const int64_t per = cdiv(n, P);
-    const int64_t i0 = (int64_t)p * per, i1 = min(n, i0 + per);
+    const int64_t per = part_len(n, P);
+    const int64_t i0 = min(n, (int64_t)p * per), i1 = min(n, i0 + per);
     const T a = (T)s_al;
     const int64_t off = (int64_t)c * n;
     double sum = 0.0;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        v[off + i] += a * d[off + i];
-        T rv = r[off + i] - a * Hd[off + i];
-        r[off + i] = rv;
-        sum += (double)rv * (double)rv;
+    bool done4 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if ((n & 3) == 0) {
+            // float4 rows; the squares of four residual entries summed in FP32 per FP64 add
+            float4 *v4 = reinterpret_cast<float4 *>(v + off), *r4 = reinterpret_cast<float4 *>(r + off);
+            const float4 *d4 = reinterpret_cast<const float4 *>(d + off), *h4 = reinterpret_cast<const float4 *>(Hd + off);
+            for (int64_t q = (i0 >> 2) + threadIdx.x; q < (i1 >> 2); q += blockDim.x) {
+                float4 vv = v4[q], rr = r4[q];
+                const float4 dv = d4[q], hv = h4[q];
+                vv.x += a * dv.x;
+                vv.y += a * dv.y;
+                vv.z += a * dv.z;
+                vv.w += a * dv.w;
+                rr.x -= a * hv.x;
+                rr.y -= a * hv.y;
+                rr.z -= a * hv.z;
+                rr.w -= a * hv.w;
+                v4[q] = vv;
+                r4[q] = rr;
+                sum += (double)fmaf(rr.w, rr.w, fmaf(rr.z, rr.z, fmaf(rr.y, rr.y, rr.x * rr.x)));
+            }
+            done4 = true;
+        }
+    }
+    if (!done4) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            v[off + i] += a * d[off + i];
+            T rv = r[off + i] - a * Hd[off + i];
+            r[off + i] = rv;
+            sum += (double)rv * (double)rv;
+        }
     }
     __shared__ double red[32];
     sum = warp_sum(sum);
@@ -148,34 +176,71 @@ __global__ void cg_update_fused_kernel(T *v, T *r, const T *d, const T *Hd, int6
 
 // beta_c = gamma_new / gamma_c (0 for a frozen column) from the ||r||^2 partials, d = r + beta d.
 // gamma alternates between two arrays by iteration parity: block (0, c) writes the next one,
-// every block reads the current one.  Block (0, 0) also takes the split norms, the iteration
-// count and the loop condition; a block that starts after `done` is latched skips its part of
-// d, which the finished solve no longer needs.  grid G x R
+// every block reads the current one.  Block (0, c) also records ||r_c||^2 in sq[c]; the last of
+// the R blocks (0, .) to do so (a counter, reset by that block) takes the split norms, the
+// iteration count and the loop condition.  A block that starts after `done` is latched skips
+// its part of d, which the finished solve no longer needs.  grid G x R
 template <typename T>
 __global__ void cg_dir_fused_kernel(T *d, const T *r, int64_t n, int P, const double *partN, const double *gcur,
                                     double *gnext, const double *alpha, SolverState *st, long long max_iters,
-                                    double tol, int stop_rule, int R) {
+                                    double tol, int stop_rule, int R, double *sq, int *counter) {
     if (st->done) return;
     const int c = blockIdx.y;
     __shared__ double s_b;
-    if (threadIdx.x == 0) {
-        const double gn = sum_parts(partN, c, P);
-        const bool active = alpha[c] != 0.0;
-        s_b = active ? gn / gcur[c] : 0.0;
-        if (blockIdx.x == 0) gnext[c] = active ? gn : gcur[c];
+    __shared__ int s_last;
+    if (threadIdx.x < 32) {
+        const double gn = sum_parts_warp(partN, c, P);
+        if (threadIdx.x == 0) {
+            const bool active = alpha[c] != 0.0;
+            s_b = active ? gn / gcur[c] : 0.0;
+            s_last = 0;
+            if (blockIdx.x == 0) {
+                gnext[c] = active ? gn : gcur[c];
+                sq[c] = gn;
+                __threadfence();
+                s_last = (atomicAdd(counter, 1) == R - 1) ? 1 : 0;
+            }
+        }
     }
     __syncthreads();
-    const T b = (T)s_b;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = (int64_t)c * n + i;
-        d[e] = r[e] + b * d[e];
-    }
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
-        __shared__ double sq[512];
-        for (int cc = threadIdx.x; cc < R; cc += blockDim.x) sq[cc] = sum_parts(partN, cc, P);
-        const long long t = st->iter + 1;
+    if (s_last) {
+        // every column's ||r||^2 is in sq: norms (the block in parallel), then the iteration
+        // count and the loop condition
+        __shared__ double rt[512];
+        __threadfence();
+        const volatile double *vs = sq;
+        for (int cc = threadIdx.x; cc < R; cc += blockDim.x) rt[cc] = sqrt(vs[cc]);
         __syncthreads();
-        finish_norms_block(st, sq, R, t, max_iters, tol, stop_rule);
+        if (threadIdx.x == 0) {
+            *counter = 0;
+            finish_state(st, rt, R, st->iter + 1, max_iters, tol, stop_rule);
+        }
+    }
+    const T b = (T)s_b;
+    bool done4 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if ((n & 3) == 0) {
+            float4 *d4 = reinterpret_cast<float4 *>(d + (int64_t)c * n);
+            const float4 *r4 = reinterpret_cast<const float4 *>(r + (int64_t)c * n);
+            for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (n >> 2);
+                 q += (int64_t)gridDim.x * blockDim.x) {
+                float4 dv = d4[q];
+                const float4 rv = r4[q];
+                dv.x = rv.x + b * dv.x;
+                dv.y = rv.y + b * dv.y;
+                dv.z = rv.z + b * dv.z;
+                dv.w = rv.w + b * dv.w;
+                d4[q] = dv;
+            }
+            done4 = true;
+        }
+    }
+    if (!done4) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t e = (int64_t)c * n + i;
+            d[e] = r[e] + b * d[e];
+        }
     }
 }
 
@@ -285,7 +350,8 @@ size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank) {
     for (int k = 0; k < 3; ++k) c.take<T>((size_t)R * n);  // r, d, Hd
     c.take<double>((size_t)R * P);                          // partial sums
     c.take<double>((size_t)R * P);                          // ||r||^2 partial sums
-    for (int k = 0; k < 5; ++k) c.take<double>(R);          // scale, gamma (x2), alpha, beta
+    for (int k = 0; k < 6; ++k) c.take<double>(R);          // scale, gamma (x2), alpha, beta, ||r||^2
+    c.take<int>(1);                                         // block counter of the direction kernel
     c.take<SolverState>(1);
     c.take<char>(HOp<T>::workspace(n, d, R, prec));
     if (pc_rank > 0) {
@@ -315,6 +381,8 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     double *scale = c.take<double>(R);
     double *gamma = c.take<double>(2 * (size_t)R);  // two arrays, alternating by iteration parity
     double *alpha = c.take<double>(R);
+    double *sqn = c.take<double>(R);
+    int *dcount = c.take<int>(1);
     double *beta = c.take<double>(R);
     SolverState *sd = c.take<SolverState>(1);
     size_t opb = HOp<T>::workspace(n, kp.d, R, prec);
@@ -331,8 +399,11 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     if (pc) GP_TRY(precond_build<T>(kp, X, n, R, pc_rank, pcw, pcb, &pcd, st));
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
     const dim3 gp_((unsigned)P, (unsigned)R);
+    // direction update: about four float4 per thread
+    const dim3 gd((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 4096), 1024)), (unsigned)R);
     const int *done = &sd->done;
 
+    GP_TRY_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int), st));
     // normalisation (App. B): scale_c = ||b_c|| + eps, v <- v / scale
     coldot_kernel<T><<<gp_, 256, 0, st>>>(B, B, n, P, part, nullptr);
     norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
@@ -369,8 +440,8 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
                 const double *gcur = gamma + (ti & 1) * R;
                 double *gnext = gamma + ((ti + 1) & 1) * R;
                 cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, part, gcur, alpha, partN, sd);
-                cg_dir_fused_kernel<T><<<gv, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
-                                                           (long long)max_iters, tol, stop_rule, R);
+                cg_dir_fused_kernel<T><<<gd, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
+                                                           (long long)max_iters, tol, stop_rule, R, sqn, dcount);
                 GP_TRY(check_launch("cg iteration", 3));
                 continue;
             }

@@ -963,9 +963,16 @@ __global__ void tc_convert_kernel(const float *V, int64_t ldv, int64_t n, int64_
     if (done && *done) return;
     const int c = blockIdx.y;
     float scale = 0.0f, inv = 1.0f;
+    __shared__ float s_m;
+    if (c < R && threadIdx.x < 32) {
+        float mw = 0.0f;
+        for (int q = threadIdx.x; q < P; q += 32) mw = fmaxf(mw, part[(int64_t)c * P + q]);
+        for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+        if (threadIdx.x == 0) s_m = mw;
+    }
+    __syncthreads();
     if (c < R) {
-        float m = 0.0f;
-        for (int q = 0; q < P; ++q) m = fmaxf(m, part[(int64_t)c * P + q]);
+        const float m = s_m;
         int e = 0;
         if (m > 0.0f && isfinite(m)) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
         scale = ldexpf(1.0f, 1 - e);                  // m * scale in [1, 2)
@@ -976,8 +983,23 @@ __global__ void tc_convert_kernel(const float *V, int64_t ldv, int64_t n, int64_
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) vinv[c] = inv;
     }
+    const float *vc = V + (int64_t)c * ldv;
+    if ((n & 3) == 0 && (ldv & 3) == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {
+        // four values per thread: one float4 load, one 8-byte store (n_pad is a multiple of 128)
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (n_pad >> 2);
+             q += (int64_t)gridDim.x * blockDim.x) {
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (c < R && 4 * q < n) v = reinterpret_cast<const float4 *>(vc)[q];
+            __half2 lo = __floats2half2_rn(v.x * scale, v.y * scale), hi = __floats2half2_rn(v.z * scale, v.w * scale);
+            uint2 u;
+            u.x = *reinterpret_cast<uint32_t *>(&lo);
+            u.y = *reinterpret_cast<uint32_t *>(&hi);
+            reinterpret_cast<uint2 *>(V16 + (int64_t)c * n_pad)[q] = u;
+        }
+        return;
+    }
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += (int64_t)gridDim.x * blockDim.x) {
-        float v = (c < R && j < n) ? V[(int64_t)c * ldv + j] * scale : 0.0f;
+        float v = (c < R && j < n) ? vc[j] * scale : 0.0f;
         V16[(int64_t)c * n_pad + j] = __float2half_rn(v);
     }
 }
@@ -1376,7 +1398,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
     const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
     tc_colmax_kernel<<<dim3(P, a.R), 256, 0, st>>>(a.V, a.ldv, n2, P, cm, a.done);
-    tc_convert_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(p2, 256), 256), R_pad), 256, 0, st>>>(
+    tc_convert_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(p2, 1024), 256), R_pad), 256, 0, st>>>(
         a.V, a.ldv, n2, p2, a.R, P, cm, V16, vinv, a.done);
     GP_TRY(check_launch("tc rhs conversion", 2));
 
