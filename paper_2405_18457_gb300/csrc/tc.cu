@@ -799,20 +799,101 @@ __device__ __forceinline__ float operand_scale(float bnd) {
     return s;
 }
 
-// Writes PA (if PA) and PB (if PB) rows for the point set X (n points, n_pad rows).
+// Writes PA (if PA) and PB (if PB) rows for the point set X (n points, n_pad rows): one warp
+// per row, the same values as operand_row.  Lane l splits the coordinates l and l + 32 (d <= 64);
+// the row's KD halves are then written as half2 pairs by consecutive lanes (coalesced), each
+// lane fetching the split parts of the coordinate a position needs by a shuffle.
+__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
+    __half2 h = __halves2half2(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ __half lo_half(uint32_t u) { return __ushort_as_half((unsigned short)(u & 0xFFFFu)); }
+__device__ __forceinline__ __half hi_half(uint32_t u) { return __ushort_as_half((unsigned short)(u >> 16)); }
+
 __global__ void tc_operands_kernel(const KP<float> kp, float c, const float *X, int64_t n, int64_t n_pad, int KD,
                                    const unsigned int *bound, __half *PA, __half *PB, float *dscale_out) {
     const float s = operand_scale(__uint_as_float(*bound));
     if (blockIdx.x == 0 && threadIdx.x == 0 && dscale_out) *dscale_out = s;
     const float inv_s = 1.0f / s;
-    const int d = kp.d;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
-        __half *pa = PA ? PA + i * KD : nullptr;
-        __half *pb = PB ? PB + i * KD : nullptr;
-        if (i >= n)
-            zero_row(KD, pa, pb);
-        else
-            operand_row(X + i * d, kp.inv_ell, d, c, inv_s, KD, pa, pb);
+    const int d = kp.d, lane = threadIdx.x & 31;
+    const __half z = __float2half_rn(0.0f), one = __float2half_rn(1.0f);
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n_pad; i += nw) {
+        // split parts of coordinates lane (A) and lane + 32 (B): (h, l) for PB, (h2, l2) for PA
+        uint32_t bA = 0, aA = 0, bB = 0, aB = 0;
+        float sq = 0.0f;
+        if (i < n) {
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * h;
+                if (k >= d) break;
+                const float a = X[i * d + k] * kp.inv_ell[k];
+                __half hh, ll, h2, l2;
+                split16(a, &hh, &ll);
+                const float ar = __half2float(hh) + __half2float(ll);  // the value the tensor cores see
+                sq = fmaf(ar, ar, sq);
+                split16(-2.0f * c * inv_s * ar, &h2, &l2);
+                if (h == 0) {
+                    bA = pack2(hh, ll);
+                    aA = pack2(h2, l2);
+                } else {
+                    bB = pack2(hh, ll);
+                    aB = pack2(h2, l2);
+                }
+            }
+        }
+        float nrm = sq;
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        __half nh, nl;
+        split16(c * inv_s * nrm, &nh, &nl);
+        const int o3 = 3 * d;
+        for (int p0 = 2 * lane; p0 < KD; p0 += 64) {
+            __half va[2], vb[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int pos = p0 + e;
+                // coordinate and segment of this position: [h(a) | l(a) | h(a)] in PB,
+                // [h(-2ca/s) | h(-2ca/s) | l(-2ca/s)] in PA
+                const int seg = pos < o3 ? pos / d : 3, k = pos < o3 ? pos - seg * d : 0;
+                // every lane passes the same variable to a shuffle; lane src holds coordinate k
+                const int src = k & 31;
+                uint32_t b32 = __shfl_sync(0xffffffffu, bA, src);
+                uint32_t a32 = __shfl_sync(0xffffffffu, aA, src);
+                if (d > 32) {  // uniform: coordinates 32 .. d-1 live in the second pair
+                    const uint32_t b2 = __shfl_sync(0xffffffffu, bB, src);
+                    const uint32_t a2 = __shfl_sync(0xffffffffu, aB, src);
+                    if (k >= 32) {
+                        b32 = b2;
+                        a32 = a2;
+                    }
+                }
+                __half pa, pb;
+                if (i >= n) {
+                    pa = pb = z;
+                } else if (pos < o3) {
+                    pb = (seg == 1) ? hi_half(b32) : lo_half(b32);
+                    pa = (seg == 2) ? hi_half(a32) : lo_half(a32);
+                } else if (pos == o3) {
+                    pa = nh;
+                    pb = one;
+                } else if (pos == o3 + 1) {
+                    pa = nl;
+                    pb = one;
+                } else if (pos == o3 + 2) {
+                    pa = one;
+                    pb = nh;
+                } else if (pos == o3 + 3) {
+                    pa = one;
+                    pb = nl;
+                } else {
+                    pa = pb = z;
+                }
+                va[e] = pa;
+                vb[e] = pb;
+            }
+            if (PA) *reinterpret_cast<__half2 *>(PA + i * KD + p0) = __halves2half2(va[0], va[1]);
+            if (PB) *reinterpret_cast<__half2 *>(PB + i * KD + p0) = __halves2half2(vb[0], vb[1]);
+        }
     }
 }
 
@@ -1981,16 +2062,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // max |lambda_c U_ci| and max |W_cj| over i < n, c < R (float bits).
+// grid (blocks over points, R): column c = blockIdx.y
 __global__ void tc_uw_bound_kernel(GradArgs<float> a, unsigned int *bnd) {
     float mu = 0.0f, mw = 0.0f;
     const int64_t n = a.n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * a.R; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / n);
-        const int64_t i = e - (int64_t)c * n;
-        const float u = (c == 0) ? a.U0[i] * (float)a.lam0 : a.U[(int64_t)(c - 1) * a.ldu + i] * (float)a.lam_rest;
-        const float w = (c == 0) ? a.W0[i] : a.W[(int64_t)(c - 1) * a.ldw + i];
-        mu = fmaxf(mu, fabsf(u));
-        mw = fmaxf(mw, fabsf(w));
+    const int c = blockIdx.y;
+    const float *uc = (c == 0) ? a.U0 : a.U + (int64_t)(c - 1) * a.ldu;
+    const float *wc = (c == 0) ? a.W0 : a.W + (int64_t)(c - 1) * a.ldw;
+    const float lam = (float)((c == 0) ? a.lam0 : a.lam_rest);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        mu = fmaxf(mu, fabsf(uc[i] * lam));
+        mw = fmaxf(mw, fabsf(wc[i]));
     }
     for (int o = 16; o > 0; o >>= 1) {
         mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
@@ -2010,40 +2092,54 @@ __device__ __forceinline__ float pow2_norm(float m) {  // 2^-e with m 2^-e in [1
 }
 
 // U16[i][c] = fp16(lambda_c U_ci G_u), W16[j][c] = fp16(W_cj G_w), [n_pad x KM]; guw = 1/(G_u G_w).
+// A block transposes 64 points x 64 columns at a time through shared memory: reads along the
+// points of a column, writes along the columns of a point (both coalesced).  grid: point tiles.
 __global__ void tc_uw_convert_kernel(GradArgs<float> a, int64_t n_pad, int KM, const unsigned int *bnd, __half *U16,
                                      __half *W16, float *guw) {
+    __shared__ float tu[64][65], tw[64][65];
     const float gu = pow2_norm(__uint_as_float(bnd[0]));
     const float gw = pow2_norm(__uint_as_float(bnd[1]));
     if (blockIdx.x == 0 && threadIdx.x == 0) *guw = 1.0f / (gu * gw);
     const int64_t n = a.n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_pad * KM; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / KM;
-        const int c = (int)(e - i * KM);
-        float u = 0.0f, w = 0.0f;
-        if (i < n && c < a.R) {
-            u = (c == 0) ? a.U0[i] * (float)a.lam0 : a.U[(int64_t)(c - 1) * a.ldu + i] * (float)a.lam_rest;
-            w = (c == 0) ? a.W0[i] : a.W[(int64_t)(c - 1) * a.ldw + i];
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 256 threads: 64 x 4
+    for (int64_t i0 = (int64_t)blockIdx.x * 64; i0 < n_pad; i0 += (int64_t)gridDim.x * 64) {
+        for (int c0 = 0; c0 < KM; c0 += 64) {
+            __syncthreads();
+            for (int cc = ty; cc < 64; cc += 4) {  // read: point i0 + tx of column c0 + cc
+                const int c = c0 + cc;
+                const int64_t i = i0 + tx;
+                float u = 0.0f, w = 0.0f;
+                if (i < n && c < a.R) {
+                    u = (c == 0) ? a.U0[i] * (float)a.lam0 : a.U[(int64_t)(c - 1) * a.ldu + i] * (float)a.lam_rest;
+                    w = (c == 0) ? a.W0[i] : a.W[(int64_t)(c - 1) * a.ldw + i];
+                }
+                tu[cc][tx] = u;
+                tw[cc][tx] = w;
+            }
+            __syncthreads();
+            for (int ii = ty; ii < 64; ii += 4) {  // write: column c0 + tx of point i0 + ii
+                const int64_t e = (i0 + ii) * KM + c0 + tx;
+                U16[e] = __float2half_rn(tu[tx][ii] * gu);
+                W16[e] = __float2half_rn(tw[tx][ii] * gw);
+            }
         }
-        U16[e] = __float2half_rn(u * gu);
-        W16[e] = __float2half_rn(w * gw);
     }
 }
 
 // B3[f][j] (N3p x n_pad): f = part * d + k, parts hi(a), lo(a), hi(a^2), lo(a^2) of a_jk = x_jk / l_k.
+// grid (blocks over points, N3p): row f = blockIdx.y.
 __global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int64_t n_pad, int N3p, __half *B3) {
-    const int d = kp.d;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)N3p * n_pad; e += (int64_t)gridDim.x * blockDim.x) {
-        const int f = (int)(e / n_pad);
-        const int64_t j = e - (int64_t)f * n_pad;
+    const int d = kp.d, f = blockIdx.y;
+    const int part = f / d, k = f - part * d;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += (int64_t)gridDim.x * blockDim.x) {
         float v = 0.0f;
         if (j < n && f < 4 * d) {
-            const int part = f / d, k = f - part * d;
             const float a = X[j * d + k] * kp.inv_ell[k];
             const float x = (part < 2) ? a : a * a;
             const __half h = __float2half_rn(x);
             v = (part & 1) ? (x - __half2float(h)) : __half2float(h);
         }
-        B3[e] = __float2half_rn(v);
+        B3[(int64_t)f * n_pad + j] = __float2half_rn(v);
     }
 }
 
@@ -2137,11 +2233,10 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     TcPoints pts;
     GP_TRY(tc_prepare_points(a.kp, a.X, a.n, pbuf, &pts, st));
     GP_TRY_CUDA(cudaMemsetAsync(bnd, 0, 2 * sizeof(unsigned int), st));
-    const unsigned nb1 = (unsigned)std::min<int64_t>(cdiv(a.n * a.R, 256), 2048);
-    tc_uw_bound_kernel<<<nb1, 256, 0, st>>>(a, bnd);
-    tc_uw_convert_kernel<<<(unsigned)std::min<int64_t>(cdiv(g.n_pad * g.KM, 256), 4096), 256, 0, st>>>(
-        a, g.n_pad, g.KM, bnd, U16, W16, guw);
-    tc_b3_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)g.N3p * g.n_pad, 256), 4096), 256, 0, st>>>(
+    tc_uw_bound_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(a.n, 1024), 256), (unsigned)a.R), 256, 0, st>>>(a, bnd);
+    tc_uw_convert_kernel<<<(unsigned)std::min<int64_t>(cdiv(g.n_pad, 64), 1024), 256, 0, st>>>(a, g.n_pad, g.KM, bnd,
+                                                                                             U16, W16, guw);
+    tc_b3_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(g.n_pad, 1024), 256), (unsigned)g.N3p), 256, 0, st>>>(
         a.kp, a.X, a.n, g.n_pad, g.N3p, B3);
     GP_TRY(check_launch("tc gradient operand preparation", 3));
 
