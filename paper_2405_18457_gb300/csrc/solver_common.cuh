@@ -149,6 +149,21 @@ static inline int poll_state(const SolverState *dev, SolverState *host, cudaStre
     return GP_OK;
 }
 
+// The same poll, also reading the tensor-core kernels' time-out word (cleared when set, so the
+// caller reports GP_ERR_TIMEOUT once): one synchronisation for both.
+static inline int poll_state_tc(const SolverState *dev, SolverState *host, int *timed_out, cudaStream_t st) {
+    int *w = tc_timeout_word();
+    int h = 0;
+    GP_TRY_CUDA(cudaMemcpyAsync(host, dev, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+    if (w) GP_TRY_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        *timed_out = 1;
+        GP_TRY_CUDA(cudaMemsetAsync(w, 0, sizeof(int), st));
+    }
+    return GP_OK;
+}
+
 static inline void fill_info(const SolverState &s, gp_solve_info_t *info) {
     info->iters = s.iter;
     info->converged = s.converged;

@@ -428,8 +428,11 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // Chunks of 8, 4, 4, 4, 8, 16, 32, 32, ... iterations between polls: a warm-started solve
     // typically needs about ten, so few empty iterations are enqueued past convergence.
     SolverState hs{};
-    int64_t launched = 0, chunk = 8;
-    int polls = 0;
+    // The first chunk follows the previous solve on this thread (warm-started solves of one
+    // optimisation take similar counts), so that most solves poll once.
+    static thread_local int64_t last_iters = 0;
+    int64_t launched = 0, chunk = last_iters > 0 ? std::min<int64_t>(std::max<int64_t>(last_iters + 1, 4), 64) : 8;
+    int polls = 0, timed_out = 0;
     while (launched < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - launched);
         for (int64_t it = 0; it < k; ++it) {
@@ -459,14 +462,19 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         launched += k;
         ++polls;
         chunk = polls < 4 ? 4 : std::min<int64_t>(polls == 4 ? 8 : chunk * 2, 32);
-        GP_TRY(poll_state(sd, &hs, st));
+        GP_TRY(op.tc ? poll_state_tc(sd, &hs, &timed_out, st) : poll_state(sd, &hs, st));
         if (hs.done) break;
     }
+    // the loop ends on a poll (the state no longer changes), so the rescale is not waited for
+    if (launched == 0) GP_TRY(poll_state(sd, &hs, st));
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
     GP_TRY(check_launch("cg rescale"));
-    GP_TRY(poll_state(sd, &hs, st));
     fill_info(hs, info);
-    if (op.tc) GP_TRY(tc_timeout_status(st));
+    last_iters = hs.iter;
+    if (timed_out) {
+        set_error("a bounded wait in a tensor-core kernel gave up (its results are not valid)");
+        return GP_ERR_TIMEOUT;
+    }
     if (hs.status != GP_OK) {
         set_error("CG breakdown: residual became non-finite at iteration %lld", hs.iter);
         return hs.status;
