@@ -321,20 +321,21 @@ __global__ void bt_cg_info_kernel(int G, const SolverState *state, gp_solve_info
 //   gpart[d]  = sum_ij k_ij M_ij                     (before the 2/s_f factor)
 // with M_ij = sum_c lam_c U_ci W_cj, U = the solutions, W = [v_y, probes] (standard,
 // Eq. trace) or the solutions again (pathwise, Eq. pathwise_estimator).
-__global__ void __launch_bounds__(256) bt_grad_kernel(const BMember *mem, const BGItem *gitems, int ngi,
-                                                      const float *X, const float *Vs, const float *B, int R,
-                                                      int pathwise, double lam0, double lamr, double *gpart) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int gi = blockIdx.x;
-    if (gi >= ngi) return;
-    const BGItem it = gitems[gi];
-    const BMember &m = mem[it.member];
-    const int d = m.d, dp = d + 1, rp = R | 1;
-    float *As = reinterpret_cast<float *>(smem_raw);
-    float *Bs = As + GT * (kBatchMaxD + 1);
-    float *Us = Bs + GT * (kBatchMaxD + 1);
-    float *Ws = Us + GT * rp;
-    float *Ms = Ws + GT * rp;
+// One work item with the coordinates padded to DM (4, 8, 16 or 32; zero beyond d).  Shared
+// memory holds the tile's operands transposed (coordinate- and column-major: At[k][r],
+// Bt[k][r], Ut[c][r], Wt[c][r]), and every thread keeps a 4 x 4 block of pairs (rows
+// ty + 16p, columns tx + 16q) in registers: M by R outer-product steps, r^2 by DM steps, then
+// w = phi M and the DM coordinate sums w (a_ik - a_jk)^2, so that each shared-memory value
+// read feeds four FMAs.
+template <int DM>
+__device__ __forceinline__ void bt_grad_item(const BMember &m, const BGItem it, const float *X, const float *Vs,
+                                             const float *B, int R, int pathwise, double lam0, double lamr,
+                                             float *smem, double (&gacc)[kBatchMaxD], double &sacc) {
+    const int d = m.d;
+    float *At = smem;
+    float *Bt = At + DM * GT;
+    float *Ut = Bt + DM * GT;
+    float *Wt = Ut + R * GT;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t n = m.n;
     const float *Xm = X + m.xo;
@@ -343,85 +344,129 @@ __global__ void __launch_bounds__(256) bt_grad_kernel(const BMember *mem, const 
     const int64_t row0 = (int64_t)it.row_tile * GT;
     const float sf2 = m.sf2;
     const int kind = m.kind;
-
-    for (int e = tid; e < GT * d; e += 256) {
-        const int r = e / d, k = e - r * d;
+    for (int e = tid; e < GT * DM; e += 256) {
+        const int k = e / GT, r = e - k * GT;
         const int64_t i = row0 + r;
-        As[r * dp + k] = i < n ? Xm[i * d + k] * m.inv_ell[k] : 0.0f;
+        At[e] = (i < n && k < d) ? Xm[i * d + k] * m.inv_ell[k] : 0.0f;
     }
     for (int e = tid; e < GT * R; e += 256) {
         const int c = e / GT, r = e - c * GT;
         const int64_t i = row0 + r;
-        Us[r * rp + c] = i < n ? Vm[(int64_t)c * n + i] * (float)(c == 0 ? lam0 : lamr) : 0.0f;
+        Ut[e] = i < n ? Vm[(int64_t)c * n + i] * (float)(c == 0 ? lam0 : lamr) : 0.0f;
     }
-    double gacc[kBatchMaxD];
+    bool rin[4];
 #pragma unroll
-    for (int k = 0; k < kBatchMaxD; ++k) gacc[k] = 0.0;
-    double sacc = 0.0;
-
+    for (int p = 0; p < 4; ++p) rin[p] = row0 + ty + 16 * p < n;
     for (int jt = it.ct0; jt < it.ct1; ++jt) {
         const int64_t col0 = (int64_t)jt * GT;
         __syncthreads();
-        for (int e = tid; e < GT * d; e += 256) {
-            const int r = e / d, k = e - r * d;
+        for (int e = tid; e < GT * DM; e += 256) {
+            const int k = e / GT, r = e - k * GT;
             const int64_t j = col0 + r;
-            Bs[r * dp + k] = j < n ? Xm[j * d + k] * m.inv_ell[k] : 0.0f;
+            Bt[e] = (j < n && k < d) ? Xm[j * d + k] * m.inv_ell[k] : 0.0f;
         }
         for (int e = tid; e < GT * R; e += 256) {
             const int c = e / GT, r = e - c * GT;
             const int64_t j = col0 + r;
             // W = [v_y, w_1..]: column 0 is always the y-solution
-            Ws[r * rp + c] = j < n ? (c == 0 ? Vm[j] : Wm[(int64_t)c * n + j]) : 0.0f;
+            Wt[e] = j < n ? (c == 0 ? Vm[j] : Wm[(int64_t)c * n + j]) : 0.0f;
         }
         __syncthreads();
+        float M[4][4], r2[4][4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = ty + 16 * p;
+        for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = tx + 16 * q;
-                float acc = 0.0f;
-                for (int c = 0; c < R; ++c) acc += Us[i * rp + c] * Ws[j * rp + c];
-                Ms[i * (GT + 1) + j] = acc;
-            }
+            for (int q = 0; q < 4; ++q) M[p][q] = r2[p][q] = 0.0f;
+#pragma unroll 4
+        for (int c = 0; c < R; ++c) {
+            float u[4], w[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) u[p] = Ut[c * GT + ty + 16 * p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = Wt[c * GT + tx + 16 * q];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) M[p][q] = fmaf(u[p], w[q], M[p][q]);
         }
-        __syncthreads();
-        float gl[kBatchMaxD];
+#pragma unroll 4
+        for (int k = 0; k < DM; ++k) {
+            float a[4], b[4];
 #pragma unroll
-        for (int k = 0; k < kBatchMaxD; ++k) gl[k] = 0.0f;
+            for (int p = 0; p < 4; ++p) a[p] = At[k * GT + ty + 16 * p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = Bt[k * GT + tx + 16 * q];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float t = a[p] - b[q];
+                    r2[p][q] = fmaf(t, t, r2[p][q]);
+                }
+        }
         float sl = 0.0f;
-        for (int p = 0; p < 4; ++p) {
-            const int i = ty + 16 * p;
-            if (row0 + i >= n) continue;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int j = tx + 16 * q;
-                if (col0 + j >= n) continue;
-                float r2 = 0.0f;
-                for (int k = 0; k < d; ++k) {
-                    const float t = As[i * dp + k] - Bs[j * dp + k];
-                    r2 += t * t;
-                }
                 float kv;
-                const float phi = kphi(kind, sf2, r2, &kv);
-                const float mm = Ms[i * (GT + 1) + j];
-                const float w = phi * mm;
-                sl += kv * mm;
-#pragma unroll
-                for (int k = 0; k < kBatchMaxD; ++k) {
-                    if (k < d) {
-                        const float t = As[i * dp + k] - Bs[j * dp + k];
-                        gl[k] += w * t * t;
-                    }
-                }
+                const float phi = kphi(kind, sf2, r2[p][q], &kv);
+                const bool in = rin[p] && (col0 + tx + 16 * q < n);
+                const float mm = in ? M[p][q] : 0.0f;
+                sl = fmaf(kv, mm, sl);
+                M[p][q] = phi * mm;  // w_ij, reusing M
             }
-        }
-#pragma unroll
-        for (int k = 0; k < kBatchMaxD; ++k) gacc[k] += (double)gl[k];
         sacc += (double)sl;
+#pragma unroll 2
+        for (int k = 0; k < DM; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) a[p] = At[k * GT + ty + 16 * p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = Bt[k * GT + tx + 16 * q];
+            float g = 0.0f;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float t = a[p] - b[q];
+                    g = fmaf(M[p][q] * t, t, g);
+                }
+            gacc[k] += (double)g;
+        }
     }
+}
+
+// Per work item (64 rows of a member x up to GL column tiles of 64):
+//   gpart[k]  = sum_ij phi_ij M_ij (a_ik - a_jk)^2   (k < d, before the 1/l_k factor)
+//   gpart[d]  = sum_ij k_ij M_ij                     (before the 2/s_f factor)
+// with M_ij = sum_c lam_c U_ci W_cj, U = the solutions, W = [v_y, probes] (standard,
+// Eq. trace) or the solutions again (pathwise, Eq. pathwise_estimator).
+__global__ void __launch_bounds__(256) bt_grad_kernel(const BMember *mem, const BGItem *gitems, int ngi,
+                                                      const float *X, const float *Vs, const float *B, int R,
+                                                      int pathwise, double lam0, double lamr, double *gpart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = blockIdx.x;
+    if (gi >= ngi) return;
+    const BGItem it = gitems[gi];
+    const BMember &m = mem[it.member];
+    const int d = m.d;
+    float *smem = reinterpret_cast<float *>(smem_raw);
+    double gacc[kBatchMaxD];
+#pragma unroll
+    for (int k = 0; k < kBatchMaxD; ++k) gacc[k] = 0.0;
+    double sacc = 0.0;
+    if (d <= 4)
+        bt_grad_item<4>(m, it, X, Vs, B, R, pathwise, lam0, lamr, smem, gacc, sacc);
+    else if (d <= 8)
+        bt_grad_item<8>(m, it, X, Vs, B, R, pathwise, lam0, lamr, smem, gacc, sacc);
+    else if (d <= 16)
+        bt_grad_item<16>(m, it, X, Vs, B, R, pathwise, lam0, lamr, smem, gacc, sacc);
+    else
+        bt_grad_item<32>(m, it, X, Vs, B, R, pathwise, lam0, lamr, smem, gacc, sacc);
     // block reduction in a fixed order
     __shared__ double red[8];
-    const int lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *out = gpart + (int64_t)gi * GSTRIDE;
     for (int k = 0; k <= d; ++k) {
         double v = (k < d) ? 0.0 : sacc;
@@ -534,10 +579,7 @@ dim3 chunk_grid(const gp_batch *b, int cols) {
     return dim3((unsigned)std::max(1, std::min(nch, 4 * nsms())), (unsigned)cols);
 }
 
-size_t grad_smem(int R) {
-    const int rp = R | 1;
-    return sizeof(float) * (size_t)(2 * GT * (kBatchMaxD + 1) + 2 * GT * rp + GT * (GT + 1));
-}
+size_t grad_smem(int R) { return sizeof(float) * (size_t)(2 * GT * kBatchMaxD + 2 * GT * R); }
 
 // Y = H V (diag = 1) or K V (diag = 0) for every member not flagged in mdone.
 int batch_apply(gp_batch *b, const float *V, float *Y, float diag, const int *mdone, cudaStream_t st) {
