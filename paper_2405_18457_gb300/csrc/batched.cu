@@ -151,12 +151,15 @@ __global__ void bt_dot_kernel(const BMember *mem, const BChunk *chunks, int nch,
         if (mdone && mdone[k.member]) continue;
         const BMember &m = mem[k.member];
         const int64_t base = m.vo + (int64_t)c * m.n;
-        double s = 0.0;
+        // a thread's few products of the chunk summed in FP32 (FMA), one FP64 addition per
+        // chunk and thread: FP64 is slow on this GPU
+        float sf = 0.0f;
         for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
             const int64_t i = (int64_t)k.start + r;
             if (i >= m.n) break;
-            s += (double)A[base + i] * (double)B[base + i];
+            sf = fmaf(A[base + i], B[base + i], sf);
         }
+        double s = (double)sf;
         s = block_sum(s, red);
         if (threadIdx.x == 0) part[(int64_t)c * nch + q] = s;
     }
@@ -166,6 +169,13 @@ __device__ __forceinline__ double member_sum(const double *part, int nch, int c,
     double s = 0.0;
     for (int q = m.ch0; q < m.ch0 + m.nch; ++q) s += part[(int64_t)c * nch + q];
     return s;
+}
+// The same sum by a whole warp (lane l adds chunks l, l + 32, ... in order, then a fixed
+// butterfly): one round of loads instead of one per chunk.
+__device__ __forceinline__ double member_sum_warp(const double *part, int nch, int c, const BMember &m) {
+    double s = 0.0;
+    for (int q = m.ch0 + (int)(threadIdx.x & 31); q < m.ch0 + m.nch; q += 32) s += part[(int64_t)c * nch + q];
+    return warp_sum(s);
 }
 
 // scale[g][c] = ||b_gc|| + eps  (App. B normalisation)
@@ -214,32 +224,43 @@ __global__ void bt_init_residual_kernel(const BMember *mem, const BChunk *chunks
 }
 
 // ---------------------------------------------------------------- CG (Alg. 1) per member
+// one block per member: warps over the columns, lanes over the member's chunks
 __global__ void bt_cg_start_kernel(const BMember *mem, int G, int R, int nch, const double *part, double *gamma,
                                    SolverState *state, int *done, long long max_iters, double tol, int stop_rule) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x;
     if (g >= G) return;
-    double sq[kMaxBatchR];
-    for (int c = 0; c < R; ++c) {
-        sq[c] = member_sum(part, nch, c, mem[g]);
-        gamma[(int64_t)g * R + c] = sq[c];
+    __shared__ double sq[kMaxBatchR];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = w; c < R; c += nw) {
+        const double v = member_sum_warp(part, nch, c, mem[g]);
+        if ((threadIdx.x & 31) == 0) {
+            sq[c] = v;
+            gamma[(int64_t)g * R + c] = v;
+        }
     }
-    SolverState *st = state + g;
-    st->done = 0;
-    st->status = GP_OK;
-    st->res0 = 0.0;
-    finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
-    done[g] = st->done;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SolverState *st = state + g;
+        st->done = 0;
+        st->status = GP_OK;
+        st->res0 = 0.0;
+        finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
+        done[g] = st->done;
+    }
 }
 
+// one warp per (member, column)
 __global__ void bt_cg_alpha_kernel(const BMember *mem, int G, int R, int nch, const double *part,
                                    const double *gamma, double *alpha, const int *done) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= G * R) return;
-    const int g = e / R, c = e - g * R;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e >= (int64_t)G * R) return;
+    const int g = (int)(e / R), c = (int)(e - (int64_t)g * R);
     if (done[g]) return;
-    const double dHd = member_sum(part, nch, c, mem[g]);
-    const double gm = gamma[e];
-    alpha[e] = (gm > kFreeze && dHd > 0.0 && isfinite(dHd)) ? gm / dHd : 0.0;
+    const double dHd = member_sum_warp(part, nch, c, mem[g]);
+    if ((threadIdx.x & 31) == 0) {
+        const double gm = gamma[e];
+        alpha[e] = (gm > kFreeze && dHd > 0.0 && isfinite(dHd)) ? gm / dHd : 0.0;
+    }
 }
 
 // v += alpha d ; r -= alpha Hd ; part = ||r||^2 partial sums
@@ -254,37 +275,45 @@ __global__ void bt_cg_update_kernel(const BMember *mem, const BChunk *chunks, in
         const BMember &m = mem[k.member];
         const float a = (float)alpha[(int64_t)k.member * R + c];
         const int64_t base = m.vo + (int64_t)c * m.n;
-        double s = 0.0;
+        float sf = 0.0f;
         for (int rr = threadIdx.x; rr < kBatchChunk; rr += blockDim.x) {
             const int64_t i = (int64_t)k.start + rr;
             if (i >= m.n) break;
             V[base + i] += a * d[base + i];
             const float rv = r[base + i] - a * Hd[base + i];
             r[base + i] = rv;
-            s += (double)rv * (double)rv;
+            sf = fmaf(rv, rv, sf);
         }
+        double s = (double)sf;
         s = block_sum(s, red);
         if (threadIdx.x == 0) part[(int64_t)c * nch + q] = s;
     }
 }
 
+// one block per member: warps over the columns, lanes over the member's chunks
 __global__ void bt_cg_beta_kernel(const BMember *mem, int G, int R, int nch, const double *part, double *gamma,
                                   const double *alpha, double *beta, SolverState *state, int *done,
                                   long long max_iters, double tol, int stop_rule) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x;
     if (g >= G || done[g]) return;
-    double sq[kMaxBatchR];
-    for (int c = 0; c < R; ++c) {
-        const int64_t e = (int64_t)g * R + c;
-        const double gn = member_sum(part, nch, c, mem[g]);
-        const bool active = alpha[e] != 0.0;
-        beta[e] = active ? gn / gamma[e] : 0.0;
-        if (active) gamma[e] = gn;
-        sq[c] = active ? gn : gamma[e];
+    __shared__ double sq[kMaxBatchR];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = w; c < R; c += nw) {
+        const double gn = member_sum_warp(part, nch, c, mem[g]);
+        if ((threadIdx.x & 31) == 0) {
+            const int64_t e = (int64_t)g * R + c;
+            const bool active = alpha[e] != 0.0;
+            beta[e] = active ? gn / gamma[e] : 0.0;
+            if (active) gamma[e] = gn;
+            sq[c] = active ? gn : gamma[e];
+        }
     }
-    SolverState *st = state + g;
-    finish_norms(st, sq, R, st->iter + 1, max_iters, tol, stop_rule);
-    done[g] = st->done;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SolverState *st = state + g;
+        finish_norms(st, sq, R, st->iter + 1, max_iters, tol, stop_rule);
+        done[g] = st->done;
+    }
 }
 
 // d = r + beta d
@@ -625,7 +654,7 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     auto &p = b->p;
     const int G = b->G, R = b->R, nch = (int)b->chunks.size();
     const dim3 gc = chunk_grid(b, R);
-    const unsigned gm = (unsigned)cdiv(G, 128), gmr = (unsigned)cdiv((int64_t)G * R, 128);
+    const unsigned gmr = (unsigned)cdiv((int64_t)G * R, 128), gmw = (unsigned)cdiv((int64_t)G * R * 32, 256);
     // normalisation (App. B): scale = ||b|| + eps per member and column, v <- v / scale
     bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, B, p.part, nullptr);
     bt_norm_scale_kernel<<<gmr, 128, 0, st>>>(p.mem, G, R, nch, p.part, p.scale);
@@ -635,16 +664,16 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     GP_TRY(batch_apply(b, V, p.Hd, 1.0f, nullptr, st));
     bt_init_residual_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, p.Hd, p.r, p.dd, R, p.scale);
     bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.r, p.r, p.part, nullptr);
-    bt_cg_start_kernel<<<gm, 128, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, (long long)iters,
+    bt_cg_start_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, (long long)iters,
                                           tol, stop_rule);
     GP_TRY(check_launch("batched cg start", 3));
     for (int64_t it = 0; it < iters; ++it) {
         GP_TRY(batch_apply(b, p.dd, p.Hd, 1.0f, p.done, st));
         bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.dd, p.Hd, p.part, p.done);
-        bt_cg_alpha_kernel<<<gmr, 128, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.alpha, p.done);
+        bt_cg_alpha_kernel<<<gmw, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.alpha, p.done);
         bt_cg_update_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, V, p.r, p.dd, p.Hd, R, p.alpha, p.part,
                                                 p.done);
-        bt_cg_beta_kernel<<<gm, 128, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.alpha, p.beta, p.state, p.done,
+        bt_cg_beta_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.alpha, p.beta, p.state, p.done,
                                              (long long)iters, tol, stop_rule);
         bt_cg_dir_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.dd, p.r, R, p.beta, p.done);
         GP_TRY(check_launch("batched cg iteration", 5));
@@ -652,7 +681,7 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     bt_scale_cols_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, V, R, p.scale, 0);
     GP_TRY(check_launch("batched cg rescale"));
     if (info) {
-        bt_cg_info_kernel<<<gm, 128, 0, st>>>(G, p.state, info);
+        bt_cg_info_kernel<<<(unsigned)cdiv(G, 128), 128, 0, st>>>(G, p.state, info);
         GP_TRY(check_launch("bt_cg_info_kernel"));
     }
     return GP_OK;
