@@ -20,7 +20,7 @@
  *            vector c occupies V + c*n.  Vector 0 is the y system.
  *   kind   : 0 = RBF-ARD, 1 = Matern-3/2 ARD
  *
- * Readings of the paper taken here (each is also listed in the design doc):
+ * Readings of the paper taken here (where it is silent, ambiguous or garbled):
  *   - Matern-3/2 with "a scalar signal scale" (Sec. 2, App. B) is
  *     k = s_f^2 (1 + sqrt(3) r) exp(-sqrt(3) r), r^2 = sum_k (x_k-x'_k)^2 / l_k^2,
  *     s_f an amplitude, gradients taken with respect to s_f.
