@@ -26,6 +26,9 @@ constexpr int GT = 64;          // gradient tile edge
 constexpr int GL = 32;          // gradient column tiles per work item
 constexpr int GSTRIDE = kBatchMaxD + 1;  // partial sums per gradient item
 constexpr int kMaxBatchR = 128;
+// Members with at least this many points take the tensor-core gradient (16-bit operands; with
+// fewer points the CUDA-core FP32 estimator is both cheap and tighter).
+constexpr int64_t kTcGradMinN = 1024;
 
 struct BGItem {
     int member, row_tile, ct0, ct1;
@@ -60,6 +63,8 @@ struct gp_batch {
         int *done;
         double *gpart, *spart;
         int *err;
+        void *tcg;         // workspace of the tensor-core gradient, reused member by member
+        size_t tcg_bytes;  // 0: the batch's gradient runs on the CUDA cores
     } p{};
     void *ws = nullptr;
     bool bound = false;
@@ -92,7 +97,16 @@ struct gp_batch {
         o->gpart = c.take<double>((size_t)gp::bt::GSTRIDE * std::max<size_t>(gitems.size(), 1));
         o->spart = c.take<double>(std::max<size_t>(nch, 1));
         o->err = c.take<int>(1);
+        o->tcg_bytes = tc_grad_bytes();
+        o->tcg = o->tcg_bytes ? c.take<char>(o->tcg_bytes) : nullptr;
         return c.bytes();
+    }
+    // Largest tensor-core gradient workspace over the members that take that estimator.
+    size_t tc_grad_bytes() const {
+        size_t mx = 0;
+        for (const BMember &m : mem)
+            if (m.tcg) mx = std::max(mx, gp::tc_grad_workspace(m.n, m.d, R));
+        return mx;
     }
 };
 
@@ -521,6 +535,7 @@ __global__ void bt_sigma_dot_kernel(const BMember *mem, const BChunk *chunks, in
     for (int q = blockIdx.x; q < nch; q += gridDim.x) {
         const BChunk k = chunks[q];
         const BMember &m = mem[k.member];
+        if (m.tcg) continue;  // block-uniform
         const float *Vm = Vs + m.vo;
         const float *Wm = pathwise ? Vm : B + m.vo;
         double s = 0.0;
@@ -542,6 +557,7 @@ __global__ void bt_sigma_dot_kernel(const BMember *mem, const BChunk *chunks, in
 __global__ void bt_grad_finalize_kernel(const BMember *mem, const double *gpart, const double *spart,
                                         const double *theta, double *grad) {
     const BMember &m = mem[blockIdx.x];
+    if (m.tcg) return;  // written by the tensor-core estimator
     const int k = threadIdx.x;
     if (k > m.d + 1) return;
     double s = 0.0;
@@ -692,6 +708,38 @@ int batch_grad(gp_batch *b, const double *theta, const float *X, const float *Vs
     auto &p = b->p;
     const int ngi = (int)b->gitems.size(), nch = (int)b->chunks.size();
     const double lam0 = 0.5, lamr = -0.5 / (double)b->s;
+    // Members with tcg set: the fused tensor-core estimator member by member (stream-ordered,
+    // one workspace), with the hyperparameters read from the device (set from theta by the
+    // preparation): no host copy of theta, so the step stays one CUDA graph.  The others: the
+    // CUDA-core kernels below, which skip the tcg members.
+    if (p.tcg) {
+        for (int g = 0; g < b->G; ++g) {
+            const BMember &hm = b->mem[g];
+            if (!hm.tcg) continue;
+            GradArgs<float> a{};
+            a.kp.kind = b->kind;
+            a.kp.d = hm.d;
+            for (int k = 0; k < hm.d; ++k) a.kp.inv_ell[k] = a.kp.ell[k] = 1.0f;  // replaced on the device
+            a.kp.sf = a.kp.sf2 = a.kp.sigma = a.kp.sigma2 = 1.0f;
+            a.X = X + hm.xo;
+            a.n = hm.n;
+            a.U0 = Vs + hm.vo;
+            a.U = Vs + hm.vo + hm.n;
+            a.ldu = hm.n;
+            a.W0 = Vs + hm.vo;  // column 0 is always the y-solution
+            a.W = pathwise ? Vs + hm.vo + hm.n : B + hm.vo + hm.n;
+            a.ldw = hm.n;
+            a.R = b->R;
+            a.lam0 = lam0;
+            a.lam_rest = lamr;
+            a.grad = grad + hm.to;
+            a.dev_inv_ell = p.mem[g].inv_ell;
+            a.dev_sf2 = &p.mem[g].sf2;
+            a.dev_theta = theta + hm.to;
+            GP_TRY(tc_grad(a, p.tcg, p.tcg_bytes, st));
+        }
+    }
+    if (ngi == 0) return GP_OK;
     bt_grad_kernel<<<(unsigned)ngi, 256, grad_smem(b->R), st>>>(p.mem, p.gitems, ngi, X, Vs, B, b->R, pathwise,
                                                                 lam0, lamr, p.gpart);
     bt_sigma_dot_kernel<<<chunk_grid(b, 1), 256, 0, st>>>(p.mem, p.chunks, nch, Vs, B, b->R, pathwise, lam0, lamr,
@@ -781,10 +829,12 @@ int gp_batch_create(int kind, int G, const int64_t *n, const int *d, int s, gp_b
         for (int rt = 0; rt < tiles; ++rt)
             b->items[m.cls].push_back(
                 BItem{(int)(m.rb / 128) + rt, (int)(m.rb / 128), (int)(m.cb / 128), tiles, g, 0, 0, 0});
+        m.tcg = (n[g] >= kTcGradMinN && tc_available() && tc_grad_fits(n[g], d[g], b->R)) ? 1 : 0;
         m.gi0 = (int)b->gitems.size();
         const int gt = (int)cdiv(n[g], GT);
-        for (int rt = 0; rt < gt; ++rt)
-            for (int c0 = 0; c0 < gt; c0 += GL) b->gitems.push_back(BGItem{g, rt, c0, std::min(gt, c0 + GL)});
+        if (!m.tcg)
+            for (int rt = 0; rt < gt; ++rt)
+                for (int c0 = 0; c0 < gt; c0 += GL) b->gitems.push_back(BGItem{g, rt, c0, std::min(gt, c0 + GL)});
         m.ngi = (int)b->gitems.size() - m.gi0;
     }
     b->N = nacc;

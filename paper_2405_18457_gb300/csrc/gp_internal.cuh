@@ -186,6 +186,12 @@ struct GradArgs {
     int R;
     double lam0, lam_rest;  // lambda_0 and lambda_c for c >= 1
     double *grad;           // device, d+2
+    // Optional device-resident hyperparameters (a batch member whose theta lives on the device;
+    // tensor-core form only): 1/l (d floats), s_f^2, and theta = [l, s_f, sigma] (d+2 doubles).
+    // When set they replace kp's inv_ell, sf2, ell, sf and sigma.
+    const float *dev_inv_ell = nullptr;
+    const float *dev_sf2 = nullptr;
+    const double *dev_theta = nullptr;
 };
 // The sigma term (dH/dsigma = 2 sigma I, an O(n R) dot product) and the final
 // assembly of grad from per-block partial sums (256 doubles of scratch in dpart).
@@ -212,6 +218,13 @@ size_t tc_points_bytes(int64_t n, int d);
 // Rows and columns from one point set (H V).
 int tc_prepare_points(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out,
                       cudaStream_t st);
+int tc_prepare_points_dev(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out,
+                          const float *inv_dev, cudaStream_t st);
+// Fused tensor-core estimator (d <= 32, R <= 256; tc_grad falls back to the CUDA-core form
+// outside tc_grad_fits).
+bool tc_grad_fits(int64_t n, int d, int R);
+size_t tc_grad_workspace(int64_t n, int d, int R);
+int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st);
 // Rows from X1 and columns from X2 with one shared scale (cross products).
 int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const float *X2, int64_t n2, void *buf1,
                     void *buf2, TcPoints *rows, TcPoints *cols, cudaStream_t st);
@@ -285,7 +298,8 @@ struct BMember {
     int64_t rb;     // first row of its points in its class's PA/PB (multiple of 128)
     int d, cls, kind;
     int ch0, nch;   // its point chunks in the batch's chunk table
-    int gi0, ngi;   // its gradient work items
+    int gi0, ngi;   // its gradient work items (CUDA-core estimator)
+    int tcg;        // 1: its gradient is taken by the tensor-core estimator instead
     // set from theta on the device before every use
     float inv_ell[kBatchMaxD];
     float sf, sf2, sigma, sigma2;

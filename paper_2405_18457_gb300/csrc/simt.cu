@@ -432,7 +432,7 @@ __global__ void diag_dot_kernel(const GradArgs<T> a, double *partial) {
 // grad[d+1] = 2 sigma * sum_b dpart[b].
 template <typename T>
 __global__ void grad_finalize_kernel(const KP<T> kp, int nblocks, const double *partial, int ndiag,
-                                     const double *dpart, double *grad) {
+                                     const double *dpart, double *grad, const double *theta_dev) {
     const int d = kp.d;
     const int k = blockIdx.x;  // one block per output
     double s = 0.0;
@@ -448,9 +448,12 @@ __global__ void grad_finalize_kernel(const KP<T> kp, int nblocks, const double *
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        if (k < d) grad[k] = t / (double)kp.ell[k];
-        else if (k == d) grad[k] = 2.0 * t / (double)kp.sf;
-        else grad[k] = 2.0 * (double)kp.sigma * t;
+        const double ell = theta_dev ? theta_dev[k < d ? k : 0] : (k < d ? (double)kp.ell[k] : 0.0);
+        const double sf = theta_dev ? theta_dev[d] : (double)kp.sf;
+        const double sigma = theta_dev ? theta_dev[d + 1] : (double)kp.sigma;
+        if (k < d) grad[k] = t / ell;
+        else if (k == d) grad[k] = 2.0 * t / sf;
+        else grad[k] = 2.0 * sigma * t;
     }
 }
 
@@ -472,7 +475,7 @@ int launch_grad(const GradArgs<T> &a, const GradPlan<T> &pl, double *partial, do
     diag_dot_kernel<T><<<DIAG_BLOCKS, 256, 0, st>>>(a, dpart);
     GP_TRY(check_launch("diag_dot_kernel"));
     grad_finalize_kernel<T><<<a.kp.d + 2, 256, 0, st>>>(a.kp, pl.nblocks, partial, DIAG_BLOCKS, dpart,
-                                                        a.grad);
+                                                        a.grad, nullptr);
     GP_TRY(check_launch("grad_finalize_kernel"));
     return GP_OK;
 }
@@ -486,7 +489,8 @@ template <typename T>
 int grad_tail(const GradArgs<T> &a, int nblocks, const double *partial, double *dpart, cudaStream_t st) {
     diag_dot_kernel<T><<<DIAG_BLOCKS, 256, 0, st>>>(a, dpart);
     GP_TRY(check_launch("diag_dot_kernel"));
-    grad_finalize_kernel<T><<<a.kp.d + 2, 256, 0, st>>>(a.kp, nblocks, partial, DIAG_BLOCKS, dpart, a.grad);
+    grad_finalize_kernel<T><<<a.kp.d + 2, 256, 0, st>>>(a.kp, nblocks, partial, DIAG_BLOCKS, dpart, a.grad,
+                                                        a.dev_theta);
     return check_launch("grad_finalize_kernel");
 }
 template int grad_tail<float>(const GradArgs<float> &, int, const double *, double *, cudaStream_t);

@@ -725,12 +725,13 @@ __device__ __forceinline__ void split16(float x, __half *hi, __half *lo) {
 }
 
 // max over points of c*||a||^2 and of |2 c a_k|  (as float bits, atomicMax on ints)
-__global__ void tc_bound_kernel(const KP<float> kp, float c, const float *X, int64_t n, unsigned int *bound) {
+__global__ void tc_bound_kernel(const KP<float> kp, float c, const float *X, int64_t n, unsigned int *bound,
+                                const float *inv_dev) {
     float m = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float nrm = 0.0f, amax = 0.0f;
         for (int k = 0; k < kp.d; ++k) {
-            float a = X[i * kp.d + k] * kp.inv_ell[k];
+            float a = X[i * kp.d + k] * (inv_dev ? inv_dev[k] : kp.inv_ell[k]);
             nrm += a * a;
             amax = fmaxf(amax, fabsf(a));
         }
@@ -811,7 +812,8 @@ __device__ __forceinline__ __half lo_half(uint32_t u) { return __ushort_as_half(
 __device__ __forceinline__ __half hi_half(uint32_t u) { return __ushort_as_half((unsigned short)(u >> 16)); }
 
 __global__ void tc_operands_kernel(const KP<float> kp, float c, const float *X, int64_t n, int64_t n_pad, int KD,
-                                   const unsigned int *bound, __half *PA, __half *PB, float *dscale_out) {
+                                   const unsigned int *bound, __half *PA, __half *PB, float *dscale_out,
+                                   const float *inv_dev) {
     const float s = operand_scale(__uint_as_float(*bound));
     if (blockIdx.x == 0 && threadIdx.x == 0 && dscale_out) *dscale_out = s;
     const float inv_s = 1.0f / s;
@@ -827,7 +829,7 @@ __global__ void tc_operands_kernel(const KP<float> kp, float c, const float *X, 
             for (int h = 0; h < 2; ++h) {
                 const int k = lane + 32 * h;
                 if (k >= d) break;
-                const float a = X[i * d + k] * kp.inv_ell[k];
+                const float a = X[i * d + k] * (inv_dev ? inv_dev[k] : kp.inv_ell[k]);
                 __half hh, ll, h2, l2;
                 split16(a, &hh, &ll);
                 const float ar = __half2float(hh) + __half2float(ll);  // the value the tensor cores see
@@ -1337,6 +1339,12 @@ size_t tc_points_bytes(int64_t n, int d) {
 }
 
 int tc_prepare_points(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out, cudaStream_t st) {
+    return tc_prepare_points_dev(kp, X, n, buf, out, nullptr, st);
+}
+
+// Same, with the length-scales read from device memory when inv_dev is set.
+int tc_prepare_points_dev(const KP<float> &kp, const float *X, int64_t n, void *buf, TcPoints *out,
+                          const float *inv_dev, cudaStream_t st) {
     const int KD = kd_for(kp.d);
     const int64_t n_pad = rup(std::max<int64_t>(n, 1), TM);
     Carver c(buf);
@@ -1347,8 +1355,8 @@ int tc_prepare_points(const KP<float> &kp, const float *X, int64_t n, void *buf,
     const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
     GP_TRY_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned int), st));
     const unsigned nb = (unsigned)std::min<int64_t>(cdiv(n_pad, 256), 1024);
-    tc_bound_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, bound);
-    tc_operands_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, n_pad, KD, bound, PA, PB, dscale);
+    tc_bound_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, bound, inv_dev);
+    tc_operands_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, n_pad, KD, bound, PA, PB, dscale, inv_dev);
     GP_TRY(check_launch("tc operand preparation", 2));
     out->PA = PA;
     out->PB = PB;
@@ -1374,12 +1382,14 @@ int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const floa
     __half *PB = c2.take<__half>((size_t)p2 * KD);
     const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
     GP_TRY_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned int), st));
-    tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, bound);
-    tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(kp, cf, X2, n2, bound);
-    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, p1, KD,
-                                                                                          bound, PA, nullptr, dscale);
-    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(kp, cf, X2, n2, p2, KD,
-                                                                                          bound, nullptr, PB, nullptr);
+    tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, bound,
+                                                                                       nullptr);
+    tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(kp, cf, X2, n2, bound,
+                                                                                       nullptr);
+    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(
+        kp, cf, X1, n1, p1, KD, bound, PA, nullptr, dscale, nullptr);
+    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(
+        kp, cf, X2, n2, p2, KD, bound, nullptr, PB, nullptr, nullptr);
     GP_TRY(check_launch("tc pair preparation", 4));
     *rows = TcPoints{PA, nullptr, n1, p1, KD, dscale, bound};
     *cols = TcPoints{nullptr, PB, n2, p2, KD, dscale, bound};
@@ -1394,9 +1404,8 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
     __half *PA = c.take<__half>((size_t)p1 * KD);
     const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
     // the bound of the prepared superset fixes the same power-of-two scale
-    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(kp, cf, X1, n1, p1, KD,
-                                                                                          like.bound, PA, nullptr,
-                                                                                          nullptr);
+    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(
+        kp, cf, X1, n1, p1, KD, like.bound, PA, nullptr, nullptr, nullptr);
     GP_TRY(check_launch("tc row preparation"));
     *out = TcPoints{PA, nullptr, n1, p1, KD, like.dscale, like.bound};
     return GP_OK;
@@ -1773,6 +1782,8 @@ struct GParams {
     float inv_ell[GP_MAX_D];
     float cphi_sf2;  // phi = cphi_sf2 * phi'  (3 s_f^2 Matern, s_f^2 RBF)
     float sf2;
+    const float *inv_dev;  // device-resident 1/l and s_f^2 (replace inv_ell, sf2 when set)
+    const float *sf2_dev;
     double *partial;
     int *err;
 };
@@ -2016,7 +2027,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (ok && ntiles > 0) {
             tc_fence_after();
             float a[64];
-            for (int k = 0; k < d; ++k) a[k] = (i < p.n) ? p.X[i * d + k] * p.inv_ell[k] : 0.0f;
+            for (int k = 0; k < d; ++k)
+                a[k] = (i < p.n) ? p.X[i * d + k] * (p.inv_dev ? p.inv_dev[k] : p.inv_ell[k]) : 0.0f;
             for (int k = 0; k < d; ++k) gk[k] = a[k] * a[k] * (float)rs_acc;
             for (int f0 = 0; f0 < p.N3p; f0 += 16) {
                 uint32_t r[16];
@@ -2047,8 +2059,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     // block reduction over the 128 epilogue threads, fixed order
     double *out = p.partial + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * (p.d + 1);
-    const double gscale = (double)p.cphi_sf2 * (double)(*p.guw);
-    const double sscale = (double)p.sf2 * (double)(*p.guw);
+    const double sf2v = p.sf2_dev ? (double)*p.sf2_dev : (double)p.sf2;
+    const double cphi = p.sf2_dev ? (KIND == GP_RBF ? 1.0 : 3.0) * sf2v : (double)p.cphi_sf2;
+    const double gscale = cphi * (double)(*p.guw);
+    const double sscale = sf2v * (double)(*p.guw);
     for (int k = 0; k <= p.d; ++k) {
         double v = 0.0;
         if (warp >= 4 && warp < 8) v = (k < p.d) ? (double)gk[k] * gscale : s_acc * sscale;
@@ -2128,13 +2142,14 @@ __global__ void tc_uw_convert_kernel(GradArgs<float> a, int64_t n_pad, int KM, c
 
 // B3[f][j] (N3p x n_pad): f = part * d + k, parts hi(a), lo(a), hi(a^2), lo(a^2) of a_jk = x_jk / l_k.
 // grid (blocks over points, N3p): row f = blockIdx.y.
-__global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int64_t n_pad, int N3p, __half *B3) {
+__global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int64_t n_pad, int N3p, __half *B3,
+                             const float *inv_dev) {
     const int d = kp.d, f = blockIdx.y;
     const int part = f / d, k = f - part * d;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += (int64_t)gridDim.x * blockDim.x) {
         float v = 0.0f;
         if (j < n && f < 4 * d) {
-            const float a = X[j * d + k] * kp.inv_ell[k];
+            const float a = X[j * d + k] * (inv_dev ? inv_dev[k] : kp.inv_ell[k]);
             const float x = (part < 2) ? a : a * a;
             const __half h = __float2half_rn(x);
             v = (part & 1) ? (x - __half2float(h)) : __half2float(h);
@@ -2186,7 +2201,7 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
 // The tensor-core estimator covers d <= 32 (D3 accumulator of 4d columns next to three
 // 128-column tile buffers in tensor memory) and s + 1 <= 256; wider problems use the
 // CUDA-core FP32 reduction.
-static bool tc_grad_fits(int64_t n, int d, int R) {
+bool tc_grad_fits(int64_t n, int d, int R) {
     if (d > 32 || R > 256) return false;
     const GradPlanTc g = plan_tc_grad(n, d, R);
     return g.ns >= 2 && g.nb3 >= 2;
@@ -2231,13 +2246,13 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
     TcPoints pts;
-    GP_TRY(tc_prepare_points(a.kp, a.X, a.n, pbuf, &pts, st));
+    GP_TRY(tc_prepare_points_dev(a.kp, a.X, a.n, pbuf, &pts, a.dev_inv_ell, st));
     GP_TRY_CUDA(cudaMemsetAsync(bnd, 0, 2 * sizeof(unsigned int), st));
     tc_uw_bound_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(a.n, 1024), 256), (unsigned)a.R), 256, 0, st>>>(a, bnd);
     tc_uw_convert_kernel<<<(unsigned)std::min<int64_t>(cdiv(g.n_pad, 64), 1024), 256, 0, st>>>(a, g.n_pad, g.KM, bnd,
                                                                                              U16, W16, guw);
     tc_b3_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(g.n_pad, 1024), 256), (unsigned)g.N3p), 256, 0, st>>>(
-        a.kp, a.X, a.n, g.n_pad, g.N3p, B3);
+        a.kp, a.X, a.n, g.n_pad, g.N3p, B3, a.dev_inv_ell);
     GP_TRY(check_launch("tc gradient operand preparation", 3));
 
     CUtensorMap mA, mB, mU, mW, mB3;
@@ -2262,6 +2277,8 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     p.X = a.X;
     for (int k = 0; k < d; ++k) p.inv_ell[k] = a.kp.inv_ell[k];
     p.cphi_sf2 = (a.kp.kind == GP_RBF ? 1.0f : 3.0f) * a.kp.sf2;
+    p.inv_dev = a.dev_inv_ell;
+    p.sf2_dev = a.dev_sf2;
     p.sf2 = a.kp.sf2;
     p.partial = partial;
     p.err = err;

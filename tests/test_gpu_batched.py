@@ -159,6 +159,30 @@ def test_batch_gradient_matches_oracle(dev, kind, pathwise):
         assert rel(gg.cpu().numpy(), ref) < 1e-4
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("pathwise", [False, True])
+def test_batch_gradient_tensor_core_members_match_oracle(dev, kind, pathwise):
+    """Members of 1024 points or more take the fused tensor-core estimator (hyperparameters
+    read on the device), the others the CUDA-core one; tolerance of the 16-bit form (1e-3)."""
+    s = 3
+    shapes = [(1100, 4), (300, 8), (2048, 16), (1500, 32)]
+    b, ms, X, th = make_batch(kind, shapes, s, dev)
+    rng = np.random.default_rng(15)
+    Vs = [rng.standard_normal((s + 1, n)).astype(np.float32) for n, _ in shapes]
+    Bs = [rng.standard_normal((s + 1, n)).astype(np.float32) for n, _ in shapes]
+    V = b.pack_vectors(Vs)
+    B = b.pack_vectors(Bs)
+    b.prepare(th, X)
+    g = b.mll_grad(th, X, V, B=None if pathwise else B, pathwise=pathwise)
+    for (Xg, thg, _), Vg, Bg, gg, (n, _) in zip(ms, Vs, Bs, b.unpack_theta(g), shapes):
+        Xr, Vr = Xg.astype(np.float64), Vg.astype(np.float64)
+        if pathwise:
+            ref = oracle.grad_pathwise(kind, thg, Xr, Vr)
+        else:
+            ref = oracle.grad_standard(kind, thg, Xr, Vr, Bg[1:].astype(np.float64))
+        assert rel(gg.cpu().numpy(), ref) < (1e-3 if n >= 1024 else 1e-4), n
+
+
 def test_batch_adam_matches_oracle(dev):
     b, ms, X, th = make_batch(0, SHAPES, 2, dev)
     st = b.adam_init(th)
