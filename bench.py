@@ -67,8 +67,14 @@ class Clocks:
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                      "--format=csv,noheader,nounits", "-lms", "50"],
                                      stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        # the sampler is running (first row written) before the timed region starts
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -87,6 +93,8 @@ class Clocks:
         os.unlink(self.path)
         if not rows:
             return None
+        if len(rows) > 1:
+            rows = rows[1:]  # the first row was taken before the region started
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         reasons = set()
@@ -273,7 +281,6 @@ def run_ours(args):
         work += rep.work(info)
         iters.append(info.iters)
     barrier()
-    clk = clocks.stop()
     launches = gp.gp_diag_launches()
     gp.gp_diag_reset(False)
     # Dominant-kernel timing: CUDA events around each launch of the product kernel (and the
@@ -308,13 +315,18 @@ def run_ours(args):
     e_end = torch.cuda.Event(enable_timing=True)
     e_work = 0.0
     h2d = 0
+    e_iters = []
     e_start.record()
     for k in range(args.steps):
         h2d = rep.load_inputs(pinned)
         info, gh = rep.step()
         e_work += rep.work(info)
+        e_iters.append(info.iters)
     e_end.record()
     barrier()
+    clk = clocks.stop()  # sampled from the first timed step to the last end-to-end step
+    if clk:
+        clk["region"] = "timed steps, kernel timing and end-to-end steps"
     e_s = e_start.elapsed_time(e_end) / 1e3
     e_s, e_work = combine_ranks(dist, dev, e_s, e_work)
 
@@ -384,7 +396,7 @@ def run_ours(args):
         "fp64_form": fp64,
         "speedup_vs_fp64_form": (fp64["sec_per_step"] / (total_s / args.steps)) if fp64 else None,
         "e2e": {"value": e_work / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": 8 * (d + 2)},
+                "d2h_bytes_per_step": 8 * (d + 2), "ms_per_step": 1e3 * e_s / args.steps, "cg_iters_per_step": e_iters},
         "gpu_launches": launches,
         "roofline": roof,
         "gradient_kernel": grad_kernel,
