@@ -1870,47 +1870,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float gk[64];
     double rs_acc = 0.0, s_acc = 0.0;
 
-    if (warp == 0 && lane == 0 && ntiles > 0) {
-        mbar_expect_tx(a_full, a_bytes + u_bytes);
-        for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
-        for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sU + ka * (TM * 128), &mapU, a_full, ka * 64, (int)row0);
+    // The role warps (0, 1, 2, 3, 12) run their loops with the whole warp (warp-uniform waits
+    // and loop state) and issue TMA, MMA and commit instructions from one elected lane.
+    if (warp == 0 && ntiles > 0) {
+        const bool leader = elect_one();
+        if (leader) {
+            mbar_expect_tx(a_full, a_bytes + u_bytes);
+            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sA + ka * (TM * 128), &mapA, a_full, ka * 64, (int)row0);
+            for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sU + ka * (TM * 128), &mapU, a_full, ka * 64, (int)row0);
+        }
+        __syncwarp();
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % NS, use = it / NS;
-            if (it >= NS && !mbar_wait(&empty[s], (use - 1) & 1, s_err)) break;
+            if (it >= NS && !mbar_wait_warp(&empty[s], (use - 1) & 1, s_err)) break;
             const int j0 = (int)((t0 + it) * GTN);
             uint8_t *sB = sStages + (size_t)s * stage_bytes;
             uint8_t *sW = sB + b_bytes;
-            mbar_expect_tx(&full[s], stage_bytes);
-            for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (GTN * 128), &mapB, &full[s], ka * 64, j0);
-            for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sW + ka * (GTN * 128), &mapW, &full[s], ka * 64, j0);
+            if (leader) {
+                mbar_expect_tx(&full[s], stage_bytes);
+                for (int ka = 0; ka < katoms; ++ka) tma_load_2d(sB + ka * (GTN * 128), &mapB, &full[s], ka * 64, j0);
+                for (int ka = 0; ka < matoms; ++ka) tma_load_2d(sW + ka * (GTN * 128), &mapW, &full[s], ka * 64, j0);
+            }
+            __syncwarp();
         }
-    } else if (warp == 12 && lane == 0 && ntiles > 0) {
+    } else if (warp == 12 && ntiles > 0) {
         // ------------------------------------------------ TMA producer: [A | A^2] ring
+        const bool leader = elect_one();
         for (int it = 0; it < ntiles; ++it) {
             const int q = it % NB3;
-            if (it >= NB3 && !mbar_wait(&b3_empty[q], ((it / NB3) - 1) & 1, s_err)) break;
+            if (it >= NB3 && !mbar_wait_warp(&b3_empty[q], ((it / NB3) - 1) & 1, s_err)) break;
             const int j0 = (int)((t0 + it) * GTN);
-            mbar_expect_tx(&b3_full[q], b3_bytes);
-            tma_load_2d(sB3r + (size_t)q * b3_bytes, &mapB3, &b3_full[q], j0, 0);
+            if (leader) {
+                mbar_expect_tx(&b3_full[q], b3_bytes);
+                tma_load_2d(sB3r + (size_t)q * b3_bytes, &mapB3, &b3_full[q], j0, 0);
+            }
+            __syncwarp();
         }
-    } else if ((warp == 1 || warp == 2) && lane == 0 && ntiles > 0) {
-        // GEMM1 (warp 1) and GEMM-M (warp 2) issuers; GEMM3 has a third thread (warp 3).
+    } else if ((warp == 1 || warp == 2) && ntiles > 0) {
+        // GEMM1 (warp 1) and GEMM-M (warp 2) issuers; GEMM3 has a third warp (3).
         // Three short issue streams instead of one long one; each stage and each tile buffer
-        // is released by a commit of every thread that read it (empty[] and t_full[] count 2).
+        // is released by a commit of every warp that read it (empty[] and t_full[] count 2).
+        const bool leader = elect_one();
         const uint32_t id1 = idesc_f16(TM, GTN);
         // descriptors built once, advanced in 16-byte units (single-thread issue paths)
         const uint64_t dA = sdesc(sA), dU = sdesc(sU), dSt = sdesc(sStages);
         const uint32_t st_units = stage_bytes >> 4, b_units = b_bytes >> 4;
         constexpr uint32_t a_atom = (TM * 128) >> 4, g_atom = (GTN * 128) >> 4;
         const bool is_g1 = (warp == 1);
-        bool ok = mbar_wait(a_full, 0, s_err);
+        bool ok = mbar_wait_warp(a_full, 0, s_err);
         for (int it = 0; ok && it < ntiles; ++it) {
             const int s = it % NS, b = it % 3;
-            if (!mbar_wait(&full[s], (it / NS) & 1, s_err)) break;
-            if (it >= 3 && !mbar_wait(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
+            if (!mbar_wait_warp(&full[s], (it / NS) & 1, s_err)) break;
+            if (it >= 3 && !mbar_wait_warp(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t dB = dSt + (uint64_t)s * st_units;
-            if (is_g1) {
+            if (!leader) {
+            } else if (is_g1) {
 #pragma unroll
                 for (int k = 0; k < 4 * KAT; ++k) {
                     const uint32_t ka = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
@@ -1924,27 +1939,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_ss(tS + b * 128 + 64, dU + ka * a_atom + ko, dW + ka * g_atom + ko, id1, k > 0 ? 1u : 0u);
                 }
             }
-            mma_commit(&empty[s]);
-            mma_commit(&t_full[b]);
+            if (leader) {
+                mma_commit(&empty[s]);
+                mma_commit(&t_full[b]);
+            }
+            __syncwarp();
         }
-    } else if (warp == 3 && lane == 0 && ntiles > 0) {
+    } else if (warp == 3 && ntiles > 0) {
         // GEMM3 issuer: D3 += W1 [A | A^2]
+        const bool leader = elect_one();
         const uint32_t id3 = idesc_f16(TM, p.N3p);
         const uint64_t dB3r = sdesc(sB3r);
         const uint32_t b3_units = b3_bytes >> 4;
         for (int it = 0; it < ntiles; ++it) {
             const int q = it % NB3, b = it % 3;
-            if (!mbar_wait(&b3_full[q], (it / NB3) & 1, s_err)) break;
-            if (!mbar_wait(&t_kval[b], (it / 3) & 1, s_err)) break;
+            if (!mbar_wait_warp(&b3_full[q], (it / NB3) & 1, s_err)) break;
+            if (!mbar_wait_warp(&t_kval[b], (it / 3) & 1, s_err)) break;
             tc_fence_after();
             const uint64_t dB3 = dB3r + (uint64_t)q * b3_units;
+            if (leader) {
 #pragma unroll
-            for (int k = 0; k < GTN / 16; ++k)
-                mma_ts(tD, tS + b * 128 + k * 8, dB3 + (uint32_t)k * 2, id3, (it > 0 || k > 0) ? 1u : 0u);
-            mma_commit(&b3_empty[q]);
-            mma_commit(&t_free[b]);
+                for (int k = 0; k < GTN / 16; ++k)
+                    mma_ts(tD, tS + b * 128 + k * 8, dB3 + (uint32_t)k * 2, id3, (it > 0 || k > 0) ? 1u : 0u);
+                mma_commit(&b3_empty[q]);
+                mma_commit(&t_free[b]);
+            }
+            __syncwarp();
         }
-        mma_commit(y_full);
+        if (leader) mma_commit(y_full);
+        __syncwarp();
     } else if (warp >= 4 && warp < 12) {
         // two evaluation warpgroups; warpgroup wg takes the tiles with it % 2 == wg (buffer
         // it % 3).  Each thread owns one row and writes the 32 packed W1 columns of a chunk
