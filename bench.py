@@ -146,9 +146,8 @@ class Replica:
         return (self.theta.copy(), self.nu.copy(), self.m.copy(), self.v.copy(), self.t, self.V.clone())
 
     def restore(self, snap):
-        self.theta, nu, m, v, self.t, V = snap
-        self.theta = self.theta.copy()
-        self.nu, self.m, self.v = nu.copy(), m.copy(), v.copy()
+        theta, nu, m, v, self.t, V = snap
+        self.theta, self.nu, self.m, self.v = theta.copy(), nu.copy(), m.copy(), v.copy()
         self.V.copy_(V)
 
     def pinned_inputs(self):
