@@ -38,6 +38,8 @@ if ROOT not in sys.path:
 METRIC = "kernel-MVM Gpair*RHS/s (whole warm-started pathwise MLL step; sec per step vs plain FP64 GPU form)"
 UNIT = "Gpair*RHS/s"
 L2_BYTES = 129 * 1024 * 1024
+# Sec. 5 "The Effects of Early Stopping": solver budgets of 10 to 50 epochs per step
+EPOCH_BUDGETS = (10, 20, 30, 40, 50)
 
 
 def _peaks():
@@ -671,7 +673,7 @@ def run_diagnostics(args):
     grid = SolverGrid(torch, gp, workloads, dev)
     budget = {}
     for solver in ("cg", "ap", "sgd"):
-        for epochs in (10, 20, 30, 40, 50):
+        for epochs in EPOCH_BUDGETS:
             for pathwise, warm in ((False, False), (True, True)):
                 r = grid.run(solver, pathwise, warm, steps, epochs, residuals=True)
                 budget["%s/%d/%s" % (solver, epochs, "pathwise-warm" if pathwise else "standard-cold")] = {
