@@ -5,16 +5,27 @@ workload (n=32768, d=16, Matern-3/2, s=64 probes -> 65 right-hand sides,
 m=2048 random features, CG to relative tolerance 0.01 with the stop rule of
 App. B):
     random-feature prior samples -> pathwise right-hand sides -> CG solve
-    (warm start from the previous step) -> fused pathwise gradient -> gradient
-    to the host -> Adam ascent step in softplus coordinates.
+    (warm start from the previous step; the tolerance certified on the true
+    residual) -> fused pathwise gradient -> gradient to the host -> Adam ascent
+    step in softplus coordinates.
 Inputs are synthetic (seeded generators) and resident in HBM for `value`.
 
 value = kernel-matrix pair x RHS work of the step (every H V product of the
-solve, including the initial residual, plus the gradient pass, each n^2 x 65)
-divided by the step time, in Gpair*RHS/s.  The plain FP64 GPU form of the same
-step (same tolerance, i.e. equal final residual norm) is timed beside it.
+solve's iterations and its initial residual, plus the gradient pass counted as
+one n^2 x 65 pass; the true-residual check product is not counted) divided by
+the step time, in Gpair*RHS/s.  The product kernel's own rate is beside it
+(`mvm_kernel`).  The plain FP64 GPU form of the same steps (replayed from the
+same optimiser state, same tolerance on the true residual) is timed beside it.
+
+The same line carries sub-records for the other single-GPU workloads: one
+warm-started step of the alternating-projection workload (n=262144, 10-epoch
+budget), one of the SGD workload (n=2,000,000, 1000 iterations) and a few
+steps of the batched workload (256 uneven GPs, p50/p99), each with the
+roofline of its dominant kernel and the oracle's rate on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --op mvm|grad|rff|cg|unit-rates [--n N] [--repeat R]   (single
+           operations, for profilers)
 With torchrun (N > 1) every rank runs an independent replica (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
 """
@@ -49,6 +60,39 @@ def _peaks():
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
         "fallback"
+
+
+def pair_roofline(kind, d, R, pairs, launch_s, rates, peaks, peak_src, sms, clk_mhz, kd, r_pad, kernel):
+    """Roofline of one kernel-matrix launch over `pairs` (i, j) pairs: the slower of
+      MUFU   : Matern-3/2 needs one rsqrt and one ex2 per pair, RBF one ex2, at the unit rates
+               measured on this GPU (gp_diag_unit_rates: per SM per clock) x SMs x max SM clock;
+      tensor : the algorithmic contraction, 2 d flops (distance cross term) + 2 R flops (K V)
+               per pair, at the measured sustained bf16 dense rate (fp16 runs at the same rate).
+    The kernel's own contraction is wider (hi/lo split distance columns padded to KD, right-hand
+    sides padded to R_pad); that padding is reported, not counted."""
+    per_pair_clk = 1.0 / rates["ex2"] + (1.0 / rates["rsqrt"] if kind == 1 else 0.0)
+    mufu = sms * clk_mhz * 1e6 / per_pair_clk  # pairs/s
+    tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1e12
+    tensor = tpeak / (2.0 * d + 2.0 * R)  # pairs/s
+    peak = min(mufu, tensor)
+    achieved = pairs / launch_s if launch_s else None
+    return {"bound": "alu" if mufu <= tensor else "tensor", "unit": "Gpair/s",
+            "achieved": achieved / 1e9 if achieved else None, "peak": peak / 1e9,
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_derivation": "min(MUFU: %d SMs x %.0f MHz / (%s), tensor: %.0f TFLOP/s / (2d + 2R = %d flops))"
+                               % (sms, clk_mhz, "1/ex2 + 1/rsqrt" if kind == 1 else "1/ex2", tpeak / 1e12,
+                                  2 * d + 2 * R),
+            "mufu_gpairs_per_s": mufu / 1e9, "tensor_alg_gpairs_per_s": tensor / 1e9,
+            "unit_rates_per_sm_clk": {k: round(v, 2) for k, v in rates.items()},
+            "peak_source": "%s (unit rates measured live; bf16 rate from MEASURED_PEAKS.json)" % peak_src,
+            "kernel": kernel, "avg_launch_ms": launch_s * 1e3 if launch_s else None, "pairs_per_launch": pairs,
+            "padded_contraction_flops_per_pair": 2 * kd + 2 * r_pad,
+            "algorithmic_flops_per_pair": 2 * d + 2 * R}
+
+
+def kd_of(d):
+    """Width of the tensor-core distance contraction (hi/lo split columns, padded to 64)."""
+    return 64 * -(-(3 * d + 4) // 64)
 
 
 class Clocks:
@@ -260,6 +304,7 @@ def run_ours(args):
     prec = gp.GP_PREC_TC16 if args.prec == "tc16" else gp.GP_PREC_FP32
     n = args.n
     prob = workloads.pathwise(n=n, seed=rank)
+    rates = gp.gp_diag_unit_rates(4096)  # MUFU / FMA unit rates of this GPU (roofline peaks)
     rep = Replica(gp, torch, prob, dev, torch.float32, prec, args.max_iters)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     tuned = None
@@ -285,7 +330,7 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     work = 0.0
-    iters = []
+    iters, res = [], []
     for k in range(args.steps):
         flush_l2(torch, flush)
         starts[k].record()
@@ -293,6 +338,7 @@ def run_ours(args):
         ends[k].record()
         work += rep.work(info)
         iters.append(info.iters)
+        res.append((info.res_y, info.res_z, bool(info.converged)))
     barrier()
     launches = gp.gp_diag_launches()
     gp.gp_diag_reset(False)
@@ -347,20 +393,36 @@ def run_ours(args):
     e_s = e_start.elapsed_time(e_end) / 1e3
     e_s, e_work = combine_ranks(dist, dev, e_s, e_work)
 
-    # ---- plain FP64 GPU form of the same step, same tolerance (equal final residual norm)
+    # ---- plain FP64 GPU form of the same steps: the first `fp64_steps` timed steps replayed
+    # from the same optimiser state (hyperparameters, Adam moments, warm start), each solved to
+    # the same tolerance on its true residual, device-timed like the mixed form's steps.
     fp64 = None
     if args.fp64_steps > 0:
+        F = min(args.fp64_steps, args.steps)
         rep64 = Replica(gp, torch, prob, dev, torch.float64, gp.GP_PREC_FP32, args.max_iters)
-        rep64.step()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = []
-        for _ in range(args.fp64_steps):
+        rep64.restore(start_state)
+        per64 = []
+        for k in range(F):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            flush_l2(torch, flush)
+            e0.record()
             info64, _ = rep64.step()
-            res.append((info64.iters, info64.res_y, info64.res_z))
-        torch.cuda.synchronize()
-        fp64 = {"sec_per_step": (time.perf_counter() - t0) / args.fp64_steps,
-                "cg_iters": [r[0] for r in res], "res_y": res[-1][1], "res_z": res[-1][2]}
+            e1.record()
+            torch.cuda.synchronize()
+            per64.append({"ms": e0.elapsed_time(e1), "cg_iters": int(info64.iters), "res_y": info64.res_y,
+                          "res_z": info64.res_z, "converged": bool(info64.converged)})
+        mixed = [{"ms": step_ms[k], "cg_iters": int(iters[k]), "res_y": res[k][0], "res_z": res[k][1],
+                  "converged": res[k][2]} for k in range(F)]
+        f_s = float(np.mean([r["ms"] for r in per64])) / 1e3
+        m_s = float(np.mean([r["ms"] for r in mixed])) / 1e3
+        fp64 = {"steps_replayed": F, "sec_per_step": f_s, "mixed_sec_per_step_same_steps": m_s,
+                "ms_per_cg_iteration": float(np.sum([r["ms"] for r in per64]) / max(1, sum(r["cg_iters"] for r in per64))),
+                "mixed_ms_per_cg_iteration": float(np.sum([r["ms"] for r in mixed]) /
+                                                   max(1, sum(r["cg_iters"] for r in mixed))),
+                "fp64_steps": per64, "mixed_steps": mixed,
+                "residuals": "true residual norms of the returned solutions (FP64 form: exact operator; mixed "
+                             "form: its tensor-core operator, certified at tau - 1e-3); both meet tau = 0.01"}
 
     if rank != 0:
         if dist is not None:
@@ -370,33 +432,36 @@ def run_ours(args):
     d, R = prob.d, prob.s + 1
     avg_launch_s = (prod_ms / 1e3) / max(prod_cnt, 1)
     clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pairs = float(n) * n
     if prec == gp.GP_PREC_TC16:
-        # Matern-3/2 needs one rsqrt (16/clk/SM) and one ex2 (32/clk/SM) per pair on the MUFU
-        # (special-function unit); rates measured on this GB300 with a CUDA-event probe.
-        mufu_pairs_per_clk = 1.0 / (1.0 / 16 + 1.0 / 32) if prob.kind == 1 else 32.0
-        peak = 152 * mufu_pairs_per_clk * clk_mhz * 1e6 / 1e9
-        achieved = pairs / avg_launch_s / 1e9 if prod_cnt else None
-        tflops = (2.0 * d + 2.0 * R) * pairs / avg_launch_s / 1e12 if prod_cnt else None
+        roof = pair_roofline(prob.kind, d, R, pairs, avg_launch_s if prod_cnt else None, rates, peaks, peak_src, sms,
+                             clk_mhz, kd_of(d), 16 * -(-R // 16), "tc_mvm_kernel (H V)")
         tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        roof = {"bound": "alu", "unit": "Gpair/s", "peak": peak,
-                "peak_derivation": "MUFU: 152 SMs x (1/(1/16 + 1/32)) pairs/clk x %.0f MHz" % clk_mhz,
-                "tensor_tflops": tflops, "tensor_frac_of_measured_bf16_sustained": (tflops / tpeak) if tflops else None}
+        tflops = (2.0 * kd_of(d) + 2.0 * 16 * -(-R // 16)) * pairs / avg_launch_s / 1e12 if prod_cnt else None
+        roof["tensor_pipe_tflops_padded"] = tflops
+        roof["tensor_pipe_frac_of_measured_bf16_sustained"] = (tflops / tpeak) if tflops else None
     else:
-        # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flops x max SM clock
+        # FP32 CUDA-core peak at the measured FMA rate: per pair ~3d + 2R + 10 FP32 flops
         flops_pair = 3.0 * d + 2.0 * R + 10.0
-        peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        peak = sms * rates["ffma"] * 2 * clk_mhz * 1e6 / 1e12
         achieved = flops_pair * pairs / avg_launch_s / 1e12 if prod_cnt else None
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "algorithmic_flops_per_pair": flops_pair}
-    roof.update({"achieved": achieved, "frac": (achieved / roof["peak"]) if achieved else None,
-                 "traffic": recorded_traffic(n, prec == gp.GP_PREC_TC16), "peak_source": peak_src, "kernel": "tc_mvm_kernel (H V)" if prec == 2 else
-                 "mvm_simt_kernel (H V)", "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": prod_cnt,
-                 "pairs_per_launch": pairs})
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak, "algorithmic_flops_per_pair": flops_pair,
+                "achieved": achieved, "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "mvm_simt_kernel (H V)", "avg_launch_ms": avg_launch_s * 1e3}
+    roof["traffic"] = recorded_traffic(n, prec == gp.GP_PREC_TC16)
+    roof["launches_timed"] = prod_cnt
     grad_kernel = None
     if grad_cnt:
         g_avg = grad_ms / 1e3 / grad_cnt
+        # the pathwise estimator's summand is symmetric: the kernel sweeps the upper triangle of
+        # tiles (n^2 / 2 evaluated pairs, the off-diagonal ones counted twice)
+        ev = pairs / 2.0 + 64.0 * n
+        groof = pair_roofline(prob.kind, d, R, ev, g_avg, rates, peaks, peak_src, sms, clk_mhz, kd_of(d),
+                              16 * -(-R // 16), "tc_grad_kernel (fused pathwise gradient, upper triangle)")
         grad_kernel = {"kernel": "tc_grad_kernel", "avg_launch_ms": g_avg * 1e3, "launches_timed": grad_cnt,
-                       "gpairs_per_s": pairs / g_avg / 1e9}
+                       "logical_gpairs_per_s": pairs / g_avg / 1e9, "evaluated_pairs_per_launch": ev,
+                       "frac_of_roofline_evaluated": groof["frac"], "roofline": groof}
     cpu = cpu_baseline(prob, R, budget_s=args.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -409,9 +474,12 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU", "autotuned": tuned},
         "sec_per_step": total_s / args.steps,
         "cg_iters_per_step": iters,
+        "final_true_residuals": [[round(r[0], 5), round(r[1], 5)] for r in res],
         "phase_ms_one_step": phases,
+        "mvm_kernel": {"gpair_rhs_per_s": pairs * R / avg_launch_s / 1e9 if prod_cnt else None,
+                       "note": "the product kernel alone (n^2 x R per launch / its mean launch time)"},
         "fp64_form": fp64,
-        "speedup_vs_fp64_form": (fp64["sec_per_step"] / (total_s / args.steps)) if fp64 else None,
+        "speedup_vs_fp64_form": (fp64["sec_per_step"] / fp64["mixed_sec_per_step_same_steps"]) if fp64 else None,
         "e2e": {"value": e_work / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 8 * (d + 2), "ms_per_step": 1e3 * e_s / args.steps, "cg_iters_per_step": e_iters},
         "gpu_launches": launches,
@@ -420,9 +488,142 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk,
     }
+    del rep, flush, pinned
+    if world == 1 and not args.no_subrecords:
+        torch.cuda.empty_cache()
+        out["workloads"] = {
+            "ap": solver_record(torch, gp, workloads, dev, "ap", rates, peaks, peak_src, sms, clk_mhz,
+                                args.sub_cpu_seconds),
+            "sgd": solver_record(torch, gp, workloads, dev, "sgd", rates, peaks, peak_src, sms, clk_mhz,
+                                 args.sub_cpu_seconds),
+            "batched": batched_record(torch, gp, workloads, dev, rates, peaks, peak_src, sms, clk_mhz,
+                                      steps=args.batched_steps, warmup=1, kernel_reps=3, n_gps=args.n_gps,
+                                      cpu_seconds=args.sub_cpu_seconds, rank=0, local=local),
+        }
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms, clk_mhz, cpu_seconds):
+    """One warm-started pathwise marginal-likelihood step of the alternating-projection workload
+    (which = "ap": n = 262144, d = 26, RBF, AP with 1024-row blocks, a budget of 10 epochs = 2560
+    block iterations; Alg. 2, Sec. 5 "The Effects of Early Stopping") or the SGD workload
+    (which = "sgd": n = 2,000,000, d = 11, Matern-3/2, SGD with 512-row batches, momentum 0.9,
+    1000 iterations; Alg. 3): random features -> pathwise right-hand sides -> solver (tau = 0.01,
+    warm start from an untimed first solve) -> pathwise gradient -> Adam.  The step is timed with
+    CUDA events, its dominant kernel (the solver's panel product) in a loop of its own."""
+    p = workloads.ap() if which == "ap" else workloads.sgd()
+    n, d, R = p.n, p.d, p.s + 1
+    bs = 1024 if which == "ap" else 512
+    iters = 10 * n // bs if which == "ap" else 1000
+    tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    X = tf(p.X)
+    om, c2, Wp, w = tf(p.omega_hat), tf(p.chi2), tf(p.W_probe), tf(p.Z)
+    y = (gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, tf(p.W_y))[0] + p.noise_y * tf(p.y_noise)).contiguous()
+    V = torch.zeros((R, n), dtype=torch.float32, device=dev)
+    idx = None
+    if which == "sgd":
+        idx = torch.tensor(workloads.sgd_batches(n, bs, iters, seed=13), dtype=torch.int32, device=dev)
+    theta = p.theta.copy()
+    nu = np.log(np.expm1(theta))
+    m_, v_ = np.zeros_like(nu), np.zeros_like(nu)
+    lr_sgd = None
+
+    def rhs(th):
+        F = gp.gp_rff_prior_sample(p.kind, th, X, om, c2, Wp)
+        return gp.gp_pathwise_rhs(th, d, y, F, w)
+
+    def solve(th, B, lr=None):
+        if which == "ap":
+            return gp.gp_solve_ap(p.kind, th, X, B, V0=V, block_size=bs, max_iters=iters, tol=0.01,
+                                  prec=gp.GP_PREC_TC16)
+        return gp.gp_solve_sgd(p.kind, th, X, B, idx, lr=lr, momentum=0.9, V0=V, tol=0.01, prec=gp.GP_PREC_TC16)
+
+    # untimed first solve (the warm start), and the SGD step size: the largest of the grid that does
+    # not diverge on it (App. B "Stochastic Gradient Descent"; the reading of the paper's rule)
+    B = rhs(theta)
+    if which == "sgd":
+        for lr in (50.0, 20.0, 10.0, 5.0, 2.0, 1.0, 0.5):
+            V.zero_()
+            try:
+                solve(theta, B, lr)
+                lr_sgd = lr
+                break
+            except gp.GPError:
+                continue
+    else:
+        solve(theta, B)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    B = rhs(theta)
+    ev[1].record()
+    _, info = solve(theta, B, lr_sgd)
+    ev[2].record()
+    g = gp.gp_mll_grad_pathwise(p.kind, theta, X, V, prec=gp.GP_PREC_TC16)
+    gh = g.cpu().numpy()
+    ev[3].record()
+    theta = gp.gp_adam_softplus_step(nu, m_, v_, 1, gh, lr=0.1)
+    torch.cuda.synchronize()
+    step_s = ev[0].elapsed_time(ev[3]) / 1e3
+    solve_s = ev[1].elapsed_time(ev[2]) / 1e3
+    grad_s = ev[2].elapsed_time(ev[3]) / 1e3
+    it = int(info.iters)
+    panel_pairs = float(n) * bs
+    # solver work: its panel products, its initial-residual product (AP), the gradient pass
+    work = (it * panel_pairs + (float(n) * n if which == "ap" else 0.0) + float(n) * n) * R
+    # dominant kernel: the panel product in the solver's shape, events per launch, L2 flushed
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    if which == "ap":
+        blk = slice(5 * bs, 6 * bs)
+        Xc, Vc, Xr_ = X[blk].contiguous(), V[:, blk].contiguous(), X
+    else:
+        rows = torch.tensor(workloads.sgd_batches(n, bs, 1, seed=14)[0], dtype=torch.int64, device=dev)
+        Xc, Vc, Xr_ = X, V, X[rows].contiguous()
+    gp.gp_diag_reset(True)
+    for _ in range(5):
+        flush_l2(torch, flush)
+        gp.gp_kernel_mvm(p.kind, theta, Xr_, Vc, X2=Xc, prec=gp.GP_PREC_TC16)
+    torch.cuda.synchronize()
+    k_ms, k_cnt = gp.gp_diag_kernel_time(0)
+    gp.gp_diag_reset(False)
+    launch_s = k_ms / 1e3 / max(k_cnt, 1)
+    roof = pair_roofline(p.kind, d, R, panel_pairs, launch_s, rates, peaks, peak_src, sms, clk_mhz, kd_of(d),
+                         16 * -(-R // 16), "tc_mvm_kernel (%s panel: %s)" % (
+                             which, "all n rows x one 1024-column block" if which == "ap"
+                             else "512 batch rows x all n columns"))
+    # oracle on the host cores: sampled rows of the same panel product
+    import oracle
+
+    Xh = p.X.astype(np.float32).astype(np.float64)
+    Vh = Vc.double().cpu().numpy()
+    Xrows = Xh if which == "ap" else Xh[workloads.sgd_batches(n, bs, 1, seed=14)[0]]
+    Xcols = Xh[5 * bs:6 * bs] if which == "ap" else Xh
+    t0 = time.perf_counter()
+    oracle.kernel_mvm(p.kind, theta, Xrows, Xcols, Vh, rows=np.arange(2))
+    t2 = max(time.perf_counter() - t0, 1e-6)
+    k = int(max(2, min(Xrows.shape[0], 2 * cpu_seconds / t2)))
+    sample = np.random.default_rng(3).choice(Xrows.shape[0], size=k, replace=False)
+    t0 = time.perf_counter()
+    oracle.kernel_mvm(p.kind, theta, Xrows, Xcols, Vh, rows=sample)
+    dt = time.perf_counter() - t0
+    cols = Xcols.shape[0]
+    cpu = {"value": k * cols * R / dt / 1e9, "unit": "Gpair*RHS/s",
+           "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+           "sample": "%d sampled rows of the %s panel product (%d columns, R=%d), FP64, %.1f s"
+                     % (k, which, cols, R, dt)}
+    return {"metric": "Gpair*RHS/s of one warm-started pathwise MLL step (%s solver)" % which.upper(),
+            "value": work / step_s / 1e9, "unit": "Gpair*RHS/s",
+            "config": {"workload": ("alternating projections: n=%d d=%d RBF s=%d b=%d, 10 epochs (%d block iterations), "
+                                    "tol 0.01, warm start" % (n, d, p.s, bs, iters)) if which == "ap" else
+                                   ("SGD: n=%d d=%d Matern-3/2 mixture of 32 Gaussians s=%d b=%d momentum 0.9 lr %s, "
+                                    "%d iterations, tol 0.01, warm start" % (n, d, p.s, bs, lr_sgd, iters)),
+                       "n": n, "d": d, "rhs": R},
+            "ms_per_step": step_s * 1e3, "solver_ms": solve_s * 1e3, "gradient_and_readback_ms": grad_s * 1e3,
+            "solver_iters": it, "converged": bool(info.converged), "res_y": info.res_y, "res_z": info.res_z,
+            "residual_kind": "true residual (recomputed)" if which == "ap" else "Alg. 3 residual estimate",
+            "roofline": roof, "cpu_baseline": cpu}
 
 
 SMALL_METRIC = "sec per MLL step, small workload (CG to 1e-6, cold start), plain vs pivoted-Cholesky preconditioned CG"
@@ -431,8 +632,10 @@ SMALL_METRIC = "sec per MLL step, small workload (CG to 1e-6, cold start), plain
 def run_small(args):
     """The small workload (n = 2048, d = 8, RBF l = 0.5, sigma = 0.1, s = 8 Gaussian probes, CG to
     relative tolerance 1e-6 from a cold start, standard estimator, Adam lr 0.1): seconds per MLL
-    step with plain CG and with the rank-100 pivoted Cholesky preconditioner of App. B, FP32
-    form, next to the plain FP64 GPU form with the same preconditioner."""
+    step with plain CG and with the rank-100 pivoted Cholesky preconditioner of App. B in the
+    FP64 form (a true residual of 1e-6 on this system, condition number about 1e4, is below
+    what FP32 vectors attain, and CG certifies its tolerance on the true residual), next to the
+    FP32 form of both at 1e-4."""
     import torch
 
     import paper_2405_18457_gb300 as gp
@@ -444,8 +647,9 @@ def run_small(args):
     gp.library()
     p = workloads.small()
     res = {}
-    for name, dtype, rank in (("fp32_plain", torch.float32, 0), ("fp32_pc100", torch.float32, 100),
-                              ("fp64_pc100", torch.float64, 100)):
+    for name, dtype, rank, tol in (("fp64_plain", torch.float64, 0, 1e-6), ("fp64_pc100", torch.float64, 100, 1e-6),
+                                   ("fp32_plain_tol1e-4", torch.float32, 0, 1e-4),
+                                   ("fp32_pc100_tol1e-4", torch.float32, 100, 1e-4)):
         Xt = torch.tensor(p.X, dtype=dtype, device=dev)
         B = torch.tensor(np.vstack([p.y, p.Z]), dtype=dtype, device=dev)
         Zt = B[1:].contiguous()
@@ -453,12 +657,12 @@ def run_small(args):
         m = np.zeros_like(nu)
         v = np.zeros_like(nu)
         theta = p.theta.copy()
-        steps = args.steps if dtype == torch.float32 else max(1, args.fp64_steps)
-        times, iters = [], []
+        steps = args.steps
+        times, iters, conv = [], [], []
         for t in range(1, args.warmup + steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            V, info = gp.gp_solve_cg(p.kind, theta, Xt, B, max_iters=20000, tol=1e-6, prec=gp.GP_PREC_FP32,
+            V, info = gp.gp_solve_cg(p.kind, theta, Xt, B, max_iters=20000, tol=tol, prec=gp.GP_PREC_FP32,
                                      precond_rank=rank)
             g = gp.gp_mll_grad_standard(p.kind, theta, Xt, V, Zt, prec=gp.GP_PREC_FP32).cpu().numpy()
             theta = gp.gp_adam_softplus_step(nu, m, v, t, g, lr=0.1)
@@ -466,15 +670,17 @@ def run_small(args):
             if t > args.warmup:
                 times.append(time.perf_counter() - t0)
                 iters.append(info.iters)
-        res[name] = {"sec_per_step": float(np.mean(times)), "cg_iters": iters}
-    out = {"metric": SMALL_METRIC, "value": res["fp32_pc100"]["sec_per_step"], "unit": "s per step",
+                conv.append(bool(info.converged))
+        res[name] = {"sec_per_step": float(np.mean(times)), "cg_iters": iters, "tol": tol,
+                     "converged_steps": int(sum(conv))}
+    out = {"metric": SMALL_METRIC, "value": res["fp64_pc100"]["sec_per_step"], "unit": "s per step",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * res["fp32_pc100"]["sec_per_step"], "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic (seeded)",
-           "config": {"workload": "small: n=2048 d=8 RBF l=0.5 sigma=0.1 s=8, CG tol 1e-6 cold, standard "
+           "ms_per_step": 1e3 * res["fp64_pc100"]["sec_per_step"], "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic (seeded)",
+           "config": {"workload": "small: n=2048 d=8 RBF l=0.5 sigma=0.1 s=8, CG tol 1e-6 cold (FP64 form), standard "
                                   "estimator, Adam lr 0.1"},
            "forms": res,
-           "speedup_pc_vs_plain": res["fp32_plain"]["sec_per_step"] / res["fp32_pc100"]["sec_per_step"]}
+           "speedup_pc_vs_plain": res["fp64_plain"]["sec_per_step"] / res["fp64_pc100"]["sec_per_step"]}
     print(json.dumps(out))
 
 
@@ -695,11 +901,7 @@ BATCH_METRIC = "batched MLL step time (256 independent uneven RBF GPs, one captu
 
 
 def run_batched(args):
-    """The batched workload: 256 independent RBF-ARD GPs, n ~ LogUniform[512, 65536],
-    d in {4, 8, 16, 32}, X ~ U[0,1]^d, y = RFF prior draw + N(0, 0.1^2), s = 16 standard
-    probes (R = 17); per step: operands from theta, warm-started CG with a budget of 50
-    iterations (tolerance 0.01, per-member early stop), standard estimator, Adam (lr 0.1),
-    all captured once into a CUDA graph and replayed.  Reports p50/p99 step time."""
+    """The batched workload on its own (python bench.py --workload batched): batched_record's line."""
     import torch
 
     import paper_2405_18457_gb300 as gp
@@ -711,8 +913,28 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     gp.library()
+    rates = gp.gp_diag_unit_rates(4096)
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = batched_record(torch, gp, workloads, dev, rates, peaks, peak_src, sms, peaks.get("sm_max_mhz", 2070.0),
+                         steps=args.steps, warmup=args.warmup, kernel_reps=args.kernel_reps, n_gps=args.n_gps,
+                         cpu_seconds=args.cpu_seconds, rank=rank, local=local)
+    if rank != 0:
+        return
+    out.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None})
+    print(json.dumps(out))
+
+
+def batched_record(torch, gp, workloads, dev, rates, peaks, peak_src, sms, clk_mhz, steps, warmup, kernel_reps,
+                   n_gps, cpu_seconds, rank, local):
+    """The batched workload: 256 independent RBF-ARD GPs, n ~ LogUniform[512, 65536],
+    d in {4, 8, 16, 32}, X ~ U[0,1]^d, y = RFF prior draw + N(0, 0.1^2), s = 16 standard
+    probes (R = 17); per step: operands from theta, warm-started CG with a budget of 50
+    iterations (tolerance 0.01 on the true residual, per-member early stop), standard estimator,
+    Adam (lr 0.1), all captured once into a CUDA graph and replayed.  Reports p50/p99 step time."""
     s, iters, tol, lr = 16, 50, 0.01, 0.1
-    ns, ds = workloads.batched_sizes(n_gps=args.n_gps, seed=rank)
+    ns, ds = workloads.batched_sizes(n_gps=n_gps, seed=rank)
     mem = [workloads.batched_member(int(n), int(d), s=s, m=1024, seed=rank, index=g)
            for g, (n, d) in enumerate(zip(ns, ds))]
     b = gp.GPBatch(gp.GP_RBF, ns, ds, s, device=dev)
@@ -738,7 +960,7 @@ def run_batched(args):
     with torch.cuda.graph(graph):
         b.step(X, theta, B, V, iters, tol, st, lr, grad)
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize()
     b.status()
@@ -747,7 +969,7 @@ def run_batched(args):
     clocks = Clocks(local)
     clocks.start()
     times, work, its = [], 0.0, []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush_l2(torch, flush)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -765,28 +987,32 @@ def run_batched(args):
     total_s = sum(times) / 1e3
     # dominant kernel: the grouped product (one launch per contraction class), events per launch
     gp.gp_diag_reset(True)
-    for _ in range(args.kernel_reps):
+    for _ in range(kernel_reps):
         flush_l2(torch, flush)
         b.mvm(V, add_noise=True)
     torch.cuda.synchronize()
     prod_ms, prod_cnt = gp.gp_diag_kernel_time(0)
     gp.gp_diag_reset(False)
-    prod_s = prod_ms / 1e3 / args.kernel_reps  # all classes of one batched product
+    prod_s = prod_ms / 1e3 / kernel_reps  # all classes of one batched product
     pairs = float(nsq.sum())
-    peaks, peak_src = _peaks()
-    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    # roofline of one batched product (all classes): per pair the algorithmic contraction
+    # 2 d_g + 2 R flops (tensor, measured bf16 rate) and one ex2 (MUFU, measured rate), summed
+    # over the members; the kernel's padded contraction (KD, R_pad = 32) is reported beside it
     tpeak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1e12
-    # per pair: GEMM1 2 KD + GEMM2 2 R_pad flops on the tensor pipe; one ex2 on the MUFU (RBF)
-    kd = np.where(np.asarray(ds) <= 20, 64, 128)
-    t_tensor = float((nsq * (2.0 * kd + 2.0 * 32)).sum()) / tpeak
-    t_mufu = pairs / (152 * 32.0 * clk_mhz * 1e6)
+    dd = np.asarray(ds, dtype=np.float64)
+    t_tensor = float((nsq * (2.0 * dd + 2.0 * R)).sum()) / tpeak
+    t_mufu = pairs / (sms * rates["ex2"] * clk_mhz * 1e6)
     bound_s = max(t_tensor, t_mufu)
+    kd = np.array([kd_of(int(x)) for x in ds], dtype=np.float64)
+    padded = float((nsq * (2.0 * kd + 2.0 * 32)).sum()) / float((nsq * (2.0 * dd + 2.0 * R)).sum())
     achieved = pairs / prod_s / 1e9
     roof = {"bound": "tensor" if t_tensor >= t_mufu else "alu", "unit": "Gpair/s", "achieved": achieved,
             "peak": pairs / bound_s / 1e9, "frac": bound_s / prod_s, "traffic": None,
-            "peak_derivation": "max(tensor: sum n^2 (2 KD + 2 R_pad) flops / measured bf16 sustained, "
-                               "MUFU: sum n^2 / (152 x 32 ex2/clk x %.0f MHz))" % clk_mhz,
-            "peak_source": peak_src, "kernel": "tc_mvm_kernel (grouped H V, all classes)",
+            "peak_derivation": "max over pipes of sum over members of n^2 x (tensor: (2 d + 2 R) flops / %.0f TFLOP/s; "
+                               "MUFU: 1 ex2 / (%d SMs x %.1f ex2/clk x %.0f MHz))"
+                               % (tpeak / 1e12, sms, rates["ex2"], clk_mhz),
+            "padded_over_algorithmic_tensor_flops": padded,
+            "peak_source": "%s (unit rates measured live)" % peak_src, "kernel": "tc_mvm_kernel (grouped H V, all classes)",
             "avg_launch_ms": prod_s * 1e3, "launches_timed": prod_cnt, "pairs_per_launch": pairs}
     # end to end: points and right-hand sides from pinned host memory every step, theta read back
     Xh = X.cpu().pin_memory()
@@ -796,7 +1022,7 @@ def run_batched(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         X.copy_(Xh, non_blocking=True)
         B.copy_(Bh, non_blocking=True)
         graph.replay()
@@ -815,7 +1041,7 @@ def run_batched(args):
 
         oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, Vh, add_noise=True, rows=rows)
         t8 = time.perf_counter() - t0
-        k = int(max(8, min(p.n, 8 * args.cpu_seconds / max(t8, 1e-6))))
+        k = int(max(8, min(p.n, 8 * cpu_seconds / max(t8, 1e-6))))
         rows = np.random.default_rng(1).choice(p.n, size=k, replace=False)
         t0 = time.perf_counter()
         oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, Vh, add_noise=True, rows=rows)
@@ -824,25 +1050,22 @@ def run_batched(args):
                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
                "sample": "%d sampled rows of H V of the largest member (n=%d, d=%d, R=%d), FP64, %.1f s"
                          % (k, p.n, p.d, R, dt)}
-    if rank != 0:
-        return
     ts = np.array(times)
     out = {
         "metric": BATCH_METRIC, "value": float(np.percentile(ts, 50)), "unit": "ms per step (p50)",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(ts.mean()),
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16-tensor/f32/f64",
+        "steps": steps, "ms_per_step": float(ts.mean()), "dtype": "f16-tensor/f32/f64",
         "data": "synthetic (seeded)",
         "config": {"workload": "batched: %d RBF GPs, n~LogUniform[512,65536] (sum n=%d), d in {4,8,16,32}, s=%d, "
                                "CG budget %d tol %.2g warm, standard estimator, Adam lr %.2g"
                                % (len(ns), int(np.sum(ns)), s, iters, tol, lr),
                    "l2": "flushed between timed steps", "parallelism": "single GPU"},
         "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
-        "pair_rhs_per_s": work / total_s, "mean_cg_iters_per_member": its,
-        "e2e": {"value": 1e3 * e_s / args.steps, "unit": "ms per step (mean)",
+        "gpair_rhs_per_s": work / total_s / 1e9, "mean_cg_iters_per_member": its,
+        "e2e": {"value": 1e3 * e_s / steps, "unit": "ms per step (mean)",
                 "h2d_bytes_per_step": int(Xh.numel() * 4 + Bh.numel() * 4), "d2h_bytes_per_step": int(th_h.numel() * 8)},
         "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "fp64_form": None,
     }
-    print(json.dumps(out))
+    return out
 
 
 def cpu_baseline(prob, R, budget_s=15.0, rows_per_step=None):
@@ -901,25 +1124,92 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_op(args):
+    """Single hot-path operations on the pathwise workload's shape (d = 16, Matern-3/2, 65
+    right-hand sides, seeded synthetic inputs), `repeat` calls, for profilers (a capture of one
+    kernel on a case that ends in seconds): mvm (gp_kernel_mvm, H V), grad (gp_mll_grad_pathwise),
+    rff (gp_rff_prior_sample), cg (gp_solve_cg, 10 iterations), unit-rates (gp_diag_unit_rates).
+    --time prints the mean time per call (CUDA events)."""
+    import torch
+
+    import paper_2405_18457_gb300 as gp
+    from paper_2405_18457_gb300 import workloads
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    gp.library()
+    if args.op == "unit-rates":
+        rates = gp.gp_diag_unit_rates(4096)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peaks, _ = _peaks()
+        clk = peaks.get("sm_max_mhz", 2070.0)
+        print(json.dumps({"unit_rates_per_sm_per_clk": rates, "sms": sms, "sm_max_mhz": clk,
+                          "mufu_bound_gpairs_per_s": {
+                              "matern32 (rsqrt + ex2)": sms * clk * 1e6 / (1 / rates["ex2"] + 1 / rates["rsqrt"]) / 1e9,
+                              "rbf (ex2)": sms * clk * 1e6 * rates["ex2"] / 1e9},
+                          "ffma_tflops": sms * rates["ffma"] * 2 * clk * 1e6 / 1e12,
+                          "dfma_tflops": sms * rates["dfma"] * 2 * clk * 1e6 / 1e12}))
+        return
+    prec = gp.GP_PREC_TC16 if args.prec == "tc16" else gp.GP_PREC_FP32
+    p = workloads.pathwise(n=args.n, d=16, s=64, m=2048, seed=0)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    X = t(p.X)
+    V = t(workloads.vectors(p.s + 1, p.n, seed=1))
+    om, c2, Wp = t(p.omega_hat), t(p.chi2), t(p.W_probe)
+
+    def call():
+        if args.op == "mvm":
+            gp.gp_kernel_mvm(p.kind, p.theta, X, V, add_noise=True, prec=prec)
+        elif args.op == "grad":
+            gp.gp_mll_grad_pathwise(p.kind, p.theta, X, V, prec=prec)
+        elif args.op == "rff":
+            gp.gp_rff_prior_sample(p.kind, p.theta, X, om, c2, Wp, prec=prec)
+        else:
+            gp.gp_solve_cg(p.kind, p.theta, X, V, max_iters=10, tol=0.0, prec=prec)
+
+    call()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.repeat):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"op": args.op, "n": args.n, "repeat": args.repeat,
+                      "ms_per_call": e0.elapsed_time(e1) / args.repeat}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["tc16", "fp32"], default=None)
+    ap.add_argument("--prec", choices=["tc16", "fp32"], default="tc16")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--max-iters", type=int, default=1000)
-    ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--sub-cpu-seconds", type=float, default=3.0)
+    ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--no-subrecords", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--kernel-reps", type=int, default=10)
     ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation", "diagnostics"],
                     default="pathwise")
+    ap.add_argument("--op", choices=["mvm", "grad", "rff", "cg", "unit-rates"], default=None)
+    ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--abl-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-gps", type=int, default=256)
     args = ap.parse_args()
+    if args.op is not None:
+        if args.op != "unit-rates" and args.n == 32768 and "--n" not in sys.argv:
+            args.n = 16384
+        run_op(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
@@ -937,22 +1227,7 @@ def main():
     if args.workload == "diagnostics":
         run_diagnostics(args)
         return
-    if args.prec is None:
-        args.prec = "tc16" if _tc_ok() else "fp32"
     run_ours(args)
-
-
-def _tc_ok():
-    import torch
-
-    import paper_2405_18457_gb300 as gp
-
-    try:
-        X = torch.zeros((1, 1), device="cuda")
-        gp.gp_kernel_mvm(0, [1.0, 1.0, 1.0], X, torch.zeros((1, 1), device="cuda"), prec=gp.GP_PREC_TC16)
-        return True
-    except gp.GPError:
-        return False
 
 
 if __name__ == "__main__":

@@ -119,6 +119,17 @@ int gp_diag_product_time(double *total_ms, long long *count);
 int gp_device_check(cudaStream_t stream);
 int gp_diag_timeout_probe(long long wait_cycles, cudaStream_t stream);
 
+/* Unit-rate probe (no counterpart in the paper; it gives the roofline of the kernel-matrix
+ * kernels, which are bound by the special-function unit).  Measures, on the current device,
+ * the throughput of ex2.approx, rsqrt.approx, sin.approx, cos.approx (MUFU), FP32 FMA and
+ * FP64 FMA as thread-instructions per SM per SM clock (median over the SMs; one 1024-thread
+ * CTA per SM with eight independent chains per thread, timed by clock64 between CTA
+ * barriers, so the rates do not depend on the clock).  rates: HOST array of 6 doubles in that
+ * order.  iters: rounds per thread (about 4096 gives a stable figure in well under a second).
+ * ws: DEVICE scratch of gp_diag_unit_rates_workspace() bytes.  Synchronises `stream`. */
+size_t gp_diag_unit_rates_workspace(void);
+int gp_diag_unit_rates(int iters, double *rates, void *ws, size_t ws_bytes, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Kernel matrix-vector products (Sec. 2 H_theta; Eq. standard_system,        */
 /* Eq. pathwise_system; every solver's "linear operator H(.)", Alg. 1-3)     */
@@ -173,9 +184,16 @@ size_t gp_kernel_mvm_f64_workspace(int64_t n1, int64_t n2, int d, int nrhs);
  *              system b / (||b|| + 1e-12) and rescaled on exit (App. B).
  *   max_iters: iteration budget T (one CG iteration = one epoch).
  *   tol      : relative residual tolerance tau; stop_rule a gp_stop_t.
- * A column whose gamma = r^T r falls to <= 1e-30 is frozen.  Returns GP_OK with
- * info filled (synchronises stream), GP_ERR_BREAKDOWN if a residual becomes
- * non-finite. */
+ * A column whose gamma = r^T r falls to <= 1e-30 is frozen.  The iterations carry
+ * Alg. 1's recursive residual; when the loop stops on it, the true residual
+ * b~ - H v is recomputed once (one product, FP64 differences and norms) and the
+ * tolerance is judged on it: a solve whose true residual misses tau restarts from
+ * it (d = r) within its budget, and info's res_y / res_z are always true-residual
+ * norms.  The product is the form's own operator for GP_PREC_TC16 and the FP64
+ * form, and the FP64 product of the FP32 inputs for GP_PREC_FP32.  The tensor-core
+ * operator is within about 1e-3 of ||H v|| of the exact one, so that form certifies
+ * max(tau - 1e-3, tau / 2) on it.  Returns GP_OK with info filled (synchronises
+ * stream), GP_ERR_BREAKDOWN if a residual becomes non-finite. */
 int gp_solve_cg(int kind, const double *theta, int d, const float *X, int64_t n,
                 const float *B, int nrhs, float *V_inout, int64_t max_iters, double tol,
                 int stop_rule, int prec, gp_solve_info_t *info,
@@ -213,7 +231,10 @@ size_t gp_solve_pcg_f64_workspace(int64_t n, int d, int nrhs, int rank);
  * H[i,i]^-1 r[i] to v[i] and subtracts H[:, i] H[i,i]^-1 r[i] from r.  The
  * inverse of every diagonal block is computed once per call from its Cholesky
  * factor (cached for the whole solve).  max_iters counts block iterations
- * (epochs x n / block_size).  1 <= block_size <= 1024. */
+ * (epochs x n / block_size).  1 <= block_size <= 1024.  When the loop stops on the
+ * residual the panels maintain, the true residual is recomputed (one full product;
+ * not counted in max_iters) and judged as in gp_solve_cg, including the
+ * tensor-core form's certified tolerance max(tau - 1e-3, tau / 2). */
 int gp_solve_ap(int kind, const double *theta, int d, const float *X, int64_t n,
                 const float *B, int nrhs, float *V_inout, int64_t block_size, int64_t max_iters,
                 double tol, int stop_rule, int prec, gp_solve_info_t *info,
@@ -360,8 +381,10 @@ size_t gp_bilinear_grad_f64_workspace(int64_t n, int d, int R);
  * gp_mll_grad_workspace(n, d, s, prec) is the amount a call needs.  Requests
  * that need more return GP_ERR_INVALID_ARG with the
  * required size in gp_last_error().  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress), so make that first call before
- * any stream capture.  All calls on a device share the array: calls whose work
+ * array's device address (cudaGetSymbolAddress) and also does the library's other
+ * one-time set-up for that device (the shared-memory limits of the kernels it
+ * launches, the address of the device status word), so make that first call
+ * before any stream capture.  All calls on a device share the array: calls whose work
  * overlaps on the GPU (unordered streams) race and must not be issued.  Results
  * equal gp_mll_grad_pathwise's for the same arguments. */
 #define GP_NOALLOC_SCRATCH_BYTES (8u << 20)
@@ -479,8 +502,13 @@ int gp_batch_mvm(gp_batch_t *b, const float *V, float *Y, int add_noise, cudaStr
 /* Alg. 1 on every member (normalised systems, split norms, loop condition
  * GP_STOP_BOTH or GP_STOP_EITHER as gp_solve_cg), V_inout the warm start and
  * the solution.  Exactly `iters` iterations are enqueued; a member whose loop
- * condition fails is skipped from then on.  info: DEVICE array of G reports
- * (or NULL), written at the end. */
+ * condition fails is skipped from then on.  Every 10 iterations and after the
+ * last one, the true residual of each member that stopped on its recursive
+ * residual is recomputed (one grouped product over those members); a member whose
+ * true residual misses the tolerance restarts from it.  The tolerance is certified
+ * on the tensor-core operator at max(tau - 1e-3, tau / 2), and the reported norms
+ * are true-residual norms.  info: DEVICE array of G reports (or NULL), written at
+ * the end. */
 int gp_batch_solve_cg(gp_batch_t *b, const float *B, float *V_inout, int64_t iters, double tol,
                       int stop_rule, gp_solve_info_t *info, cudaStream_t stream);
 /* Eq. mll_grad per member into grad (DEVICE, packed like theta): standard

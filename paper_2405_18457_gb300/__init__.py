@@ -37,6 +37,7 @@ from ._binding import (  # noqa: F401
     gp_predict,
     gp_device_check,
     gp_diag_timeout_probe,
+    gp_diag_unit_rates,
     gp_rkhs_sqdist,
     gp_rff_prior_sample,
     gp_solve_ap,

@@ -115,6 +115,8 @@ _SIGS = {
     "gp_rff_prior_sample_f64": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _vp]),
     "gp_device_check": (_i, [_vp]),
     "gp_diag_timeout_probe": (_i, [ctypes.c_longlong, _vp]),
+    "gp_diag_unit_rates_workspace": (_sz, []),
+    "gp_diag_unit_rates": (_i, [_i, _pd, _vp, _sz, _vp]),
     "gp_rff_prior_sample_ws": (_i, [_i, _pd, _i, _vp, _i64, _i, _vp, _vp, _vp, _i, _vp, _i64, _i, _vp, _sz, _vp]),
     "gp_rff_prior_sample_workspace": (_sz, [_i, _i, _i, _i]),
     "gp_pathwise_rhs": (_i, [_pd, _i, _vp, _vp, _vp, _i64, _i, _vp, _vp]),
@@ -155,6 +157,20 @@ def gp_diag_launches() -> int:
 def gp_device_check():
     """Raise GPError(GP_ERR_TIMEOUT) if a bounded device wait gave up since the last check."""
     _check(library().gp_device_check(_stream()))
+
+
+UNIT_RATE_NAMES = ("ex2", "rsqrt", "sin", "cos", "ffma", "dfma")
+
+
+def gp_diag_unit_rates(iters=4096, device=None):
+    """Measured thread-instructions per SM per clock of ex2, rsqrt, sin, cos (MUFU), FP32 FMA and
+    FP64 FMA on the current device (gp_diag_unit_rates), as a dict."""
+    lib = library()
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    ws, wsb = _ws(lib.gp_diag_unit_rates_workspace(), dev)
+    out = (ctypes.c_double * 6)()
+    _check(lib.gp_diag_unit_rates(int(iters), out, _ptr(ws), wsb, _stream()))
+    return {k: float(v) for k, v in zip(UNIT_RATE_NAMES, out)}
 
 
 def gp_diag_timeout_probe(wait_cycles):

@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <map>
 #include <mutex>
+#include <set>
 #include <utility>
 #include <vector>
 
@@ -83,6 +85,40 @@ void prof_end(cudaStream_t st) {
     cudaEventRecord(e, st);
     p.spans.push_back(Span{p.open, e, p.open_tag});
     p.open = nullptr;
+}
+
+namespace {
+std::mutex g_dev_mu;                                   // guards the two per-device caches below
+std::set<std::pair<int, const void *>> g_smem_raised;  // (device, kernel) pairs already set up
+std::map<int, int> g_sm_count;                          // device -> SM count
+}  // namespace
+
+int ensure_max_dyn_smem(const void *kernel) {
+    int dev = 0;
+    GP_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    if (g_smem_raised.count({dev, kernel})) return GP_OK;
+    GP_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    g_smem_raised.insert({dev, kernel});
+    return GP_OK;
+}
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    auto it = g_sm_count.find(dev);
+    if (it != g_sm_count.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    g_sm_count[dev] = sms;
+    return sms;
 }
 
 int check_ws(void *ws, size_t ws_bytes, size_t need) {

@@ -315,6 +315,7 @@ __global__ void ap_norm_kernel(int R, int P, const double *part, SolverState *st
         st->status = GP_OK;
     }
     finish_norms(st, sq, R, first ? 0 : st->iter + 1, max_iters, tol, stop_rule);
+    if (first) st->certified = 1;  // the initial residual b~ - H v0 is a true residual
 }
 
 }  // namespace
@@ -348,6 +349,7 @@ size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec) {
     c.take<int>(1);
     c.take<SolverState>(1);
     c.take<char>(std::max(ap_panel_ws<T>(n, bs, d, R, prec), mvm_workspace<T>(n, n, d, R, prec)));
+    if (std::is_same<T, float>::value && prec == GP_PREC_FP32) c.take<char>(f64_residual_workspace(n, d, R));
     return c.bytes();
 }
 
@@ -377,10 +379,17 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     SolverState *sd = c.take<SolverState>(1);
     size_t mwb = std::max(ap_panel_ws<T>(n, bs, kp.d, R, prec), mvm_workspace<T>(n, n, kp.d, R, prec));
     void *mw = c.take<char>(mwb);
+    const bool check64 = std::is_same<T, float>::value && prec == GP_PREC_FP32;
+    const size_t c64b = check64 ? f64_residual_workspace(n, kp.d, R) : 0;
+    void *c64w = check64 ? c.take<char>(c64b) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
     const dim3 gp_((unsigned)P, (unsigned)R);
+    // the tolerance the true residual is certified to on this form's operator (tensor-core
+    // panels are within about kTcOperatorErr of the exact product)
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16 && tol > 0.0)
+        tol = std::max(tol - kTcOperatorErr, 0.5 * tol);
     // ---- block inverses H[i,i]^-1 (cached for the whole solve)
     GP_TRY_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
     ap_build_blocks_kernel<T><<<dim3(bsp / 16, bsp / 16, nb), dim3(16, 16), 0, st>>>(kp, X, n, bs, bsp, Hb);
@@ -459,13 +468,13 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // read on the device.
     bool tc_panel = false;
     TcMvmArgs ta{};
-    void *tw = nullptr;
+    void *tw = nullptr, *pbuf = nullptr;
     size_t twb = 0;
     if constexpr (std::is_same<T, float>::value) {
         if (prec == GP_PREC_TC16) {
             tc_panel = true;
             Carver pc(mw);
-            void *pbuf = pc.take<char>(tc_points_bytes(n, kp.d));
+            pbuf = pc.take<char>(tc_points_bytes(n, kp.d));
             twb = tc_mvm_workspace(n, bs, R);
             tw = pc.take<char>(twb);
             TcPoints pts;
@@ -492,7 +501,14 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         }
     }
     const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16));
+    // The residual of Alg. 2 is updated by the panel products (recursive); when the loop stops
+    // on it, the true residual b~ - H v is recomputed (FP64 differences and norms) and replaces
+    // it; the tolerance is judged on it, and a solve whose true residual misses the tolerance is
+    // resumed within its budget, so the reported norms are true-residual norms.
     int64_t t = 0, chunk = 8;
+    int checks = 0;
+    double prev_y = 0.0, prev_z = 0.0;
+    for (;;) {
     while (!hs.done && t < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - t);
         for (int64_t it = 0; it < k; ++it, ++t) {
@@ -516,6 +532,35 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         }
         chunk = std::min<int64_t>(chunk * 2, 64);
         GP_TRY(poll_state(sd, &hs, st));
+    }
+    if (hs.status != GP_OK || hs.certified) break;
+    // (the full product uses the scratch that holds the panel's prepared points; the FP32 form
+    // takes the FP64 product, as gp_solve_cg does)
+    if (check64) {
+        if constexpr (std::is_same<T, float>::value)
+            GP_TRY(f64_residual(kp, X, n, B, V, R, scale, r, part, P, c64w, c64b, st));
+    } else {
+        GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
+        true_residual_kernel<T, T><<<gp_, 256, 0, st>>>(B, HV, r, n, P, scale, part, nullptr);
+    }
+    true_state_kernel<<<1, 256, 0, st>>>(R, P, nullptr, part, nullptr, sd, (long long)max_iters, tol, stop_rule, 1);
+    GP_TRY(check_launch("ap true residual", 2));
+    GP_TRY(poll_state(sd, &hs, st));
+    t = hs.iter;
+    if (hs.done) break;
+    // a resumed solve whose true residual did not fall by 10% since the previous check has
+    // reached the accuracy its arithmetic attains: stop there, not converged
+    if (checks > 0 && std::max(hs.res_y / prev_y, hs.res_z / prev_z) > 0.9) break;
+    prev_y = hs.res_y;
+    prev_z = hs.res_z;
+    ++checks;
+    if constexpr (std::is_same<T, float>::value) {
+        if (tc_panel) {
+            TcPoints pts;
+            GP_TRY(tc_prepare_points(kp, X, n, pbuf, &pts, st));
+        }
+    }
+    chunk = 4;
     }
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
     GP_TRY(check_launch("ap rescale"));

@@ -23,16 +23,7 @@ namespace {
 constexpr int XB = 64;   // tile edge (rows and columns)
 constexpr int XT = 256;  // threads per block
 
-int sm_count() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    return sms;
-}
+int sm_count() { return device_sm_count(); }
 
 struct DxPlan {
     int row_tiles, jsplit;
@@ -184,12 +175,7 @@ __global__ void bilinear_value_kernel(const KP<T> kp, const double *g, double *v
 
 template <typename T, int KPT>
 int launch_dx(const GradArgs<T> &a, int sym, const DxPlan &pl, double *partial, T *dX, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(dx_simt_kernel<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxDynSmem));
-        attr_set = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)dx_simt_kernel<T, KPT>));
     dim3 grid((unsigned)pl.row_tiles, (unsigned)pl.jsplit);
     dx_simt_kernel<T, KPT><<<grid, XT, dx_smem<T>(a.kp.d, a.R, sym), st>>>(a, sym, pl.jsplit, partial);
     GP_TRY(check_launch("dx_simt_kernel"));

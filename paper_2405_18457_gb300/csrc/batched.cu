@@ -61,6 +61,8 @@ struct gp_batch {
         double *part, *scale, *gamma, *alpha, *beta;
         SolverState *state;
         int *done;
+        int *cdone;  // member done with a state from a true residual (skipped by its recomputation)
+        int *cskip;  // members a true-residual check leaves alone: certified, or still iterating
         double *gpart, *spart;
         int *err;
         void *tcg;         // workspace of the tensor-core gradient, reused member by member
@@ -94,6 +96,8 @@ struct gp_batch {
         o->beta = c.take<double>((size_t)G * R);
         o->state = c.take<SolverState>(G);
         o->done = c.take<int>(G);
+        o->cdone = c.take<int>(G);
+        o->cskip = c.take<int>(G);
         o->gpart = c.take<double>((size_t)gp::bt::GSTRIDE * std::max<size_t>(gitems.size(), 1));
         o->spart = c.take<double>(std::max<size_t>(nch, 1));
         o->err = c.take<int>(1);
@@ -113,16 +117,7 @@ struct gp_batch {
 namespace gp {
 namespace bt {
 
-int nsms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    return sms;
-}
+int nsms() { return device_sm_count(); }
 
 // ---------------------------------------------------------------- parameters
 // Member parameters from the packed device theta [l_1..l_d, s_f, sigma] per member.
@@ -240,7 +235,8 @@ __global__ void bt_init_residual_kernel(const BMember *mem, const BChunk *chunks
 // ---------------------------------------------------------------- CG (Alg. 1) per member
 // one block per member: warps over the columns, lanes over the member's chunks
 __global__ void bt_cg_start_kernel(const BMember *mem, int G, int R, int nch, const double *part, double *gamma,
-                                   SolverState *state, int *done, long long max_iters, double tol, int stop_rule) {
+                                   SolverState *state, int *done, int *cdone, long long max_iters, double tol,
+                                   int stop_rule) {
     const int g = blockIdx.x;
     if (g >= G) return;
     __shared__ double sq[kMaxBatchR];
@@ -259,7 +255,9 @@ __global__ void bt_cg_start_kernel(const BMember *mem, int G, int R, int nch, co
         st->status = GP_OK;
         st->res0 = 0.0;
         finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
+        st->certified = 1;  // the initial residual b~ - H v0 is a true residual
         done[g] = st->done;
+        cdone[g] = st->done;
     }
 }
 
@@ -327,6 +325,70 @@ __global__ void bt_cg_beta_kernel(const BMember *mem, int G, int R, int nch, con
         SolverState *st = state + g;
         finish_norms(st, sq, R, st->iter + 1, max_iters, tol, stop_rule);
         done[g] = st->done;
+    }
+}
+
+// Members a true-residual check covers: done on their recursive residual (or by the budget)
+// and not yet certified.
+__global__ void bt_check_flags_kernel(int G, const int *done, const int *cdone, int *cskip) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G) cskip[g] = (cdone[g] || !done[g]) ? 1 : 0;
+}
+
+// True residual r = b~ - H v of each member not flagged in skip (App. B "Linear System Solver"),
+// FP64 differences stored in FP32 and also as the restart direction d (used only if the member
+// misses the tolerance and resumes), partial sums of ||r||^2 (from the FP64 differences).
+__global__ void bt_true_residual_kernel(const BMember *mem, const BChunk *chunks, int nch, const float *B,
+                                        const float *HV, float *r, float *d, int R, const double *scale,
+                                        double *part, const int *skip) {
+    __shared__ double red[32];
+    const int c = blockIdx.y;
+    for (int q = blockIdx.x; q < nch; q += gridDim.x) {
+        const BChunk k = chunks[q];
+        if (skip[k.member]) continue;
+        const BMember &m = mem[k.member];
+        const double f = 1.0 / scale[(int64_t)k.member * R + c];
+        const int64_t base = m.vo + (int64_t)c * m.n;
+        double s = 0.0;
+        for (int rr = threadIdx.x; rr < kBatchChunk; rr += blockDim.x) {
+            const int64_t i = (int64_t)k.start + rr;
+            if (i >= m.n) break;
+            const double v = (double)B[base + i] * f - (double)HV[base + i];
+            r[base + i] = (float)v;
+            d[base + i] = (float)v;
+            s += v * v;
+        }
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) part[(int64_t)c * nch + q] = s;
+    }
+}
+
+// Per member not flagged in skip (one block each), after its true residual: gamma <- ||r||^2,
+// the split norms and the loop condition at the current iteration count from the true norms
+// (a member stopped by its recursive residual restarts from the true one when it misses the
+// tolerance), marked certified; cdone set when the member is done.
+__global__ void bt_true_state_kernel(const BMember *mem, int G, int R, int nch, const double *part, double *gamma,
+                                     SolverState *state, int *done, int *cdone, const int *skip, long long max_iters,
+                                     double tol, int stop_rule) {
+    const int g = blockIdx.x;
+    if (g >= G || skip[g]) return;
+    __shared__ double sq[kMaxBatchR];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = w; c < R; c += nw) {
+        const double v = member_sum_warp(part, nch, c, mem[g]);
+        if ((threadIdx.x & 31) == 0) {
+            sq[c] = v;
+            gamma[(int64_t)g * R + c] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SolverState *st = state + g;
+        if (st->status == GP_OK) st->done = 0;
+        finish_norms(st, sq, R, st->iter, max_iters, tol, stop_rule);
+        st->certified = 1;
+        done[g] = st->done;
+        cdone[g] = st->done;
     }
 }
 
@@ -665,9 +727,13 @@ int batch_prepare(gp_batch *b, const double *theta, const float *X, cudaStream_t
     return tc_group_prepare(b->kind, p.mem, b->G, p.chunks, (int)b->chunks.size(), X, p.PA, p.PB, b->KD, st);
 }
 
+constexpr int64_t kCheckEvery = 10;  // iterations between the batched solver's true-residual checks
+
 int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, int stop_rule,
              gp_solve_info_t *info, cudaStream_t st) {
     auto &p = b->p;
+    // the tolerance the true residual is certified to on the tensor-core operator
+    if (tol > 0.0) tol = std::max(tol - kTcOperatorErr, 0.5 * tol);
     const int G = b->G, R = b->R, nch = (int)b->chunks.size();
     const dim3 gc = chunk_grid(b, R);
     const unsigned gmr = (unsigned)cdiv((int64_t)G * R, 128), gmw = (unsigned)cdiv((int64_t)G * R * 32, 256);
@@ -680,9 +746,23 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     GP_TRY(batch_apply(b, V, p.Hd, 1.0f, nullptr, st));
     bt_init_residual_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, p.Hd, p.r, p.dd, R, p.scale);
     bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.r, p.r, p.part, nullptr);
-    bt_cg_start_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, (long long)iters,
-                                          tol, stop_rule);
+    bt_cg_start_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, p.cdone,
+                                                    (long long)iters, tol, stop_rule);
     GP_TRY(check_launch("batched cg start", 3));
+    // True residual b~ - H v of the members that stopped on their recursive residual and are
+    // not yet certified: every kCheckEvery iterations (a member whose true residual misses the
+    // tolerance restarts from it) and after the last iteration (the reported norms and flags).
+    // Members still iterating keep their recursive residual: replacing it mid-solve with a
+    // product of the whole iterate injects that product's rounding into the recurrence.
+    auto true_residuals = [&]() -> int {
+        bt_check_flags_kernel<<<(unsigned)cdiv(G, 128), 128, 0, st>>>(G, p.done, p.cdone, p.cskip);
+        GP_TRY(batch_apply(b, V, p.Hd, 1.0f, p.cskip, st));
+        bt_true_residual_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, p.Hd, p.r, p.dd, R, p.scale, p.part,
+                                                    p.cskip);
+        bt_true_state_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, p.cdone,
+                                                          p.cskip, (long long)iters, tol, stop_rule);
+        return check_launch("batched cg true residual", 3);
+    };
     for (int64_t it = 0; it < iters; ++it) {
         GP_TRY(batch_apply(b, p.dd, p.Hd, 1.0f, p.done, st));
         bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.dd, p.Hd, p.part, p.done);
@@ -693,7 +773,9 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
                                              (long long)iters, tol, stop_rule);
         bt_cg_dir_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.dd, p.r, R, p.beta, p.done);
         GP_TRY(check_launch("batched cg iteration", 5));
+        if ((it + 1) % kCheckEvery == 0 && it + 1 < iters) GP_TRY(true_residuals());
     }
+    GP_TRY(true_residuals());
     bt_scale_cols_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, V, R, p.scale, 0);
     GP_TRY(check_launch("batched cg rescale"));
     if (info) {
@@ -889,7 +971,7 @@ int gp_batch_bind(gp_batch_t *b, void *ws, size_t ws_bytes, cudaStream_t stream)
     const size_t need = b->carve(ws, &p);
     GP_TRY(check_ws(ws, ws_bytes, need));
     GP_TRY(tc_group_setup());
-    GP_TRY_CUDA(cudaFuncSetAttribute(bt_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    GP_TRY(ensure_max_dyn_smem((const void *)bt_grad_kernel));
     if (grad_smem(b->R) > (size_t)kMaxDynSmem) {
         set_error("too many right-hand sides for the batched gradient tile");
         return GP_ERR_UNSUPPORTED;

@@ -49,6 +49,13 @@ void prof_end(cudaStream_t st);
 // minus headroom for the kernels' small static arrays).
 constexpr int kMaxDynSmem = 220 * 1024;
 
+// Per-device one-time set-up, safe to call from several host threads.  A kernel attribute
+// applies to the device that is current when it is set, so the first launch of `kernel` on
+// each device raises its dynamic shared-memory limit to kMaxDynSmem there.
+int ensure_max_dyn_smem(const void *kernel);
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sm_count();
+
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t rup(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 

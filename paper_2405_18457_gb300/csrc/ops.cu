@@ -239,11 +239,7 @@ int launch_rff(const KP<T> &kp, const T *X, int64_t n, int m, const T *omega_hat
         set_error("rff: d=%d too large", d);
         return GP_ERR_UNSUPPORTED;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(rff_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr_set = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)rff_kernel<T>));
     dim3 grid((unsigned)cdiv(n, RP), (unsigned)cdiv(s, RS));
     rff_kernel<T><<<grid, 256, smem, st>>>(kp, X, n, m, omega_hat, chi2, W, s, F, ldf);
     return check_launch("rff_kernel");

@@ -281,11 +281,7 @@ int precond_build(const KP<T> &kp, const T *X, int64_t n, int R, int k, void *ws
     P.w = c.take<double>((size_t)k * R);
     P.inv_sigma2 = 1.0 / ((double)kp.sigma * (double)kp.sigma);
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
-    static bool attr = false;
-    if (!attr) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(pc_lr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)pc_lr_kernel<T>));
     const unsigned nb = (unsigned)std::min<int64_t>(cdiv(n, 256), 2048);
     pc_init_kernel<T><<<nb, 256, 0, st>>>(dg, n, kp.sf2, flags);
     GP_TRY_CUDA(cudaMemsetAsync(flags + 1, 0, sizeof(int), st));

@@ -277,11 +277,7 @@ int rf_dq(int d) { return d <= 4 ? 1 : d <= 8 ? 2 : d <= 16 ? 4 : 8; }
 
 template <int DQ>
 int launch_rff_kernel(const CUtensorMap &mW, const RfParams &p, size_t smem, int64_t grid, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(tc_rff_kernel<DQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_rff_kernel<DQ>));
     tc_rff_kernel<DQ><<<(unsigned)grid, RF_THREADS, smem, st>>>(mW, p);
     return GP_OK;
 }

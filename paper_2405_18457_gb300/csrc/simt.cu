@@ -16,16 +16,7 @@ constexpr int BM = 64;   // rows of a tile
 constexpr int BN = 64;   // columns of a tile
 constexpr int NT = 256;  // threads per block (16 x 16)
 
-int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    return sms;
-}
+int num_sms() { return device_sm_count(); }
 
 template <typename T>
 struct SplitPlan {
@@ -186,12 +177,7 @@ __global__ void mvm_reduce_kernel(const MvmArgs<T> a, int nsplit, const T *parti
 template <typename T, int CPT>
 int launch_mvm(const MvmArgs<T> &a, const SplitPlan<T> &pl, T *partial, cudaStream_t st) {
     size_t smem = mvm_smem<T>(a.kp.d, CPT);
-    static bool attr_set = false;
-    if (!attr_set) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(mvm_simt_kernel<T, CPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr_set = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)mvm_simt_kernel<T, CPT>));
     dim3 grid((unsigned)cdiv(a.n1, BM), (unsigned)pl.nsplit, (unsigned)pl.zchunks);
     prof_begin(st);
     mvm_simt_kernel<T, CPT><<<grid, NT, smem, st>>>(a, pl.nsplit, partial);
@@ -462,12 +448,7 @@ constexpr int DIAG_BLOCKS = 256;
 template <typename T, int DMAX>
 int launch_grad(const GradArgs<T> &a, const GradPlan<T> &pl, double *partial, double *dpart,
                 cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(grad_simt_kernel<T, DMAX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr_set = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)grad_simt_kernel<T, DMAX>));
     size_t smem = grad_smem<T>(a.kp.d, a.R);
     dim3 grid((unsigned)pl.row_tiles, (unsigned)pl.jsplit);
     grad_simt_kernel<T, DMAX><<<grid, NT, smem, st>>>(a, pl.jsplit, partial);

@@ -12,6 +12,16 @@ namespace {
 
 constexpr double kNormEps = 1e-12;   // eps of the normalisation b / (||b|| + eps)
 constexpr double kFreeze = 1e-30;    // CG column frozen once gamma <= this
+// The tensor-core operator (fp16 kernel values and operands, FP32 accumulation) is within about
+// 1e-3 of ||H v|| of the exact product, the bound its parity tests hold it to; a residual
+// certified on it at tol - kTcOperatorErr is then at most about tol for the exact operator.
+constexpr double kTcOperatorErr = 1e-3;
+
+// x (float) -> y (double), count elements
+__global__ void widen_kernel(const float *x, double *y, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
 
 // Row partitions of the per-column partial sums: enough blocks (partitions x columns)
 // to fill the GPU for the vector updates, at most 64 partials per column.  A partition
@@ -112,6 +122,7 @@ __device__ void finish_state(SolverState *st, const double *rt, int R, long long
     st->res_y = ry;
     st->res_z = rz;
     st->iter = t;
+    st->certified = 0;
     bool finite = isfinite(ry) && isfinite(rz);
     bool conv = (stop_rule == GP_STOP_EITHER) ? (ry <= tol || rz <= tol) : (ry <= tol && rz <= tol);
     st->converged = conv ? 1 : 0;
@@ -138,6 +149,56 @@ __device__ void finish_norms_block(SolverState *st, double *sq, int R, long long
     for (int c = threadIdx.x; c < R; c += blockDim.x) sq[c] = sqrt(sq[c]);
     __syncthreads();
     if (threadIdx.x == 0) finish_state(st, sq, R, t, max_iters, tol, stop_rule);
+}
+
+// True residual (App. B "Linear System Solver": r = b - H u, here of the normalised system):
+// r = b~ - H v with b~ = b / scale, both terms taken in FP64 and the difference stored in T;
+// the partial sums of ||r||^2 come from the FP64 differences.  Skipped while *skip != 0 (a
+// periodic recomputation enqueued after the solve has stopped).  grid P x R
+template <typename T, typename TH>
+__global__ void true_residual_kernel(const T *B, const TH *Hv, T *r, int64_t n, int P, const double *scale,
+                                     double *partN, const int *skip) {
+    if (skip && *skip) return;
+    const int p = blockIdx.x, c = blockIdx.y;
+    const int64_t per = part_len(n, P);
+    const int64_t i0 = min(n, (int64_t)p * per), i1 = min(n, i0 + per);
+    const double f = 1.0 / scale[c];
+    const int64_t off = (int64_t)c * n;
+    double sum = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double v = (double)B[off + i] * f - (double)Hv[off + i];
+        r[off + i] = (T)v;
+        sum += v * v;
+    }
+    __shared__ double red[32];
+    sum = warp_sum(sum);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        partN[(int64_t)c * P + p] = t;
+    }
+}
+
+// State after a true-residual recomputation: (CG) gamma <- r^T P^-1 r (partG; = ||r||^2 without
+// a preconditioner) for the next iteration, when gamma is given; the split norms from partN and the loop condition at
+// the current iteration count, marked certified.  reopen = 0: a periodic recomputation during
+// the solve (skipped once done is latched).  reopen = 1: the check after the loop stopped; done
+// is re-evaluated from the true norms, so a solve whose recursive residual met the tolerance
+// while its true residual does not is resumed.  One block, R <= 512.
+__global__ void true_state_kernel(int R, int P, const double *partG, const double *partN, double *gamma,
+                                     SolverState *st, long long max_iters, double tol, int stop_rule, int reopen) {
+    if (!reopen && st->done) return;
+    __shared__ double sq[512];
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        sq[c] = sum_parts(partN, c, P);
+        if (gamma) gamma[c] = sum_parts(partG, c, P);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && reopen && st->status == GP_OK) st->done = 0;
+    finish_norms_block(st, sq, R, st->iter, max_iters, tol, stop_rule);
+    if (threadIdx.x == 0) st->certified = 1;
 }
 
 }  // namespace

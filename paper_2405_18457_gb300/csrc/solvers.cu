@@ -33,6 +33,7 @@ __global__ void cg_start_kernel(int R, int P, const double *partG, const double 
     }
     __syncthreads();
     finish_norms_block(st, sq, R, 0, max_iters, tol, stop_rule);
+    if (threadIdx.x == 0) st->certified = 1;  // r = b~ - H v0 is a true residual
 }
 
 // alpha = gamma / d^T H d, frozen columns get 0.
@@ -341,6 +342,66 @@ struct HOp {
 };
 
 // ===========================================================================
+// True residual with the FP64 product (FP32 form's check)
+// ===========================================================================
+size_t f64_residual_workspace(int64_t n, int d, int R) {
+    Carver c(nullptr);
+    c.take<double>((size_t)n * d);
+    c.take<double>((size_t)R * n);
+    c.take<double>((size_t)R * n);
+    c.take<char>(mvm_simt_workspace<double>(n, n, R));
+    return c.bytes();
+}
+
+int f64_residual(const KP<float> &kp, const float *X, int64_t n, const float *B, const float *V, int R,
+                 const double *scale, float *r, double *partN, int P, void *ws, size_t ws_bytes, cudaStream_t st) {
+    Carver c(ws);
+    double *X64 = c.take<double>((size_t)n * kp.d);
+    double *V64 = c.take<double>((size_t)R * n);
+    double *HV64 = c.take<double>((size_t)R * n);
+    const size_t mb = mvm_simt_workspace<double>(n, n, R);
+    void *mw = c.take<char>(mb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    KP<double> k64;
+    k64.kind = kp.kind;
+    k64.d = kp.d;
+    for (int k = 0; k < kp.d; ++k) {
+        k64.ell[k] = (double)kp.ell[k];
+        k64.inv_ell[k] = 1.0 / (double)kp.ell[k];
+    }
+    k64.sf = (double)kp.sf;
+    k64.sf2 = k64.sf * k64.sf;
+    k64.sigma = (double)kp.sigma;
+    k64.sigma2 = k64.sigma * k64.sigma;
+    const unsigned nb = (unsigned)std::min<int64_t>(cdiv((int64_t)R * n, 256), 4096);
+    widen_kernel<<<nb, 256, 0, st>>>(X, X64, n * kp.d);
+    widen_kernel<<<nb, 256, 0, st>>>(V, V64, (int64_t)R * n);
+    GP_TRY(check_launch("widen_kernel", 2));
+    MvmArgs<double> a{};
+    a.kp = k64;
+    a.X1 = X64;
+    a.n1 = n;
+    a.X2 = X64;
+    a.n2 = n;
+    a.n2_total = n;
+    a.V = V64;
+    a.ldv = n;
+    a.R = R;
+    a.Y = HV64;
+    a.ldy = n;
+    a.alpha = 1.0;
+    a.beta = 0.0;
+    a.diag_coef = k64.sigma2;
+    a.Vd = V64;
+    a.ldvd = n;
+    a.ndiag = n;
+    GP_TRY(mvm_simt<double>(a, mw, mb, st));
+    true_residual_kernel<float, double><<<dim3((unsigned)P, (unsigned)R), 256, 0, st>>>(B, HV64, r, n, P, scale,
+                                                                                         partN, nullptr);
+    return check_launch("true_residual_kernel");
+}
+
+// ===========================================================================
 // Conjugate gradients, Alg. 1 (P = identity)
 // ===========================================================================
 template <typename T>
@@ -354,6 +415,7 @@ size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank) {
     c.take<int>(1);                                         // block counter of the direction kernel
     c.take<SolverState>(1);
     c.take<char>(HOp<T>::workspace(n, d, R, prec));
+    if (std::is_same<T, float>::value && prec == GP_PREC_FP32) c.take<char>(f64_residual_workspace(n, d, R));
     if (pc_rank > 0) {
         c.take<T>((size_t)R * n);                           // p = P^-1 r
         c.take<double>((size_t)R * P);                      // r^T p partial sums
@@ -387,6 +449,9 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     SolverState *sd = c.take<SolverState>(1);
     size_t opb = HOp<T>::workspace(n, kp.d, R, prec);
     void *opw = c.take<char>(opb);
+    const bool check64 = std::is_same<T, float>::value && prec == GP_PREC_FP32;
+    const size_t c64b = check64 ? f64_residual_workspace(n, kp.d, R) : 0;
+    void *c64w = check64 ? c.take<char>(c64b) : nullptr;
     T *pz = pc ? c.take<T>((size_t)R * n) : nullptr;
     double *partG = pc ? c.take<double>((size_t)R * P) : part;
     const size_t pcb = pc ? precond_workspace<T>(n, R, pc_rank) : 0;
@@ -395,6 +460,8 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
 
     HOp<T> op;
     GP_TRY(op.init(kp, X, n, R, prec, opw, opb, st));
+    // the tolerance the true residual is certified to on this form's operator
+    if (op.tc && tol > 0.0) tol = std::max(tol - kTcOperatorErr, 0.5 * tol);
     Precond<T> pcd{};
     if (pc) GP_TRY(precond_build<T>(kp, X, n, R, pc_rank, pcw, pcb, &pcd, st));
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
@@ -427,46 +494,96 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // of a chunk return immediately, so a chunk overshoot costs only empty launches.
     // Chunks of 8, 4, 4, 4, 8, 16, 32, 32, ... iterations between polls: a warm-started solve
     // typically needs about ten, so few empty iterations are enqueued past convergence.
+    //
+    // The iterations carry Alg. 1's recursive residual, which drifts from b~ - H v under the
+    // products' rounding.  When the loop stops on it (unless the state already comes from a
+    // true residual), the true residual is recomputed once (FP64 differences and norms) and
+    // the tolerance is judged on it; if it misses, CG restarts from it (d = r, or P^-1 r)
+    // within the budget.  The FP32 form recomputes it with the FP64 product: a product of H
+    // with the whole iterate carries an error of about u ||H|| ||v||, which in FP32 on an
+    // ill-conditioned system lies far above the residuals CG reaches (measured: replacing the
+    // recursive residual by an FP32 true residual every 10 iterations made CG diverge on the
+    // small workload).  The reported norms are therefore always true-residual norms.
     SolverState hs{};
     // The first chunk follows the previous solve on this thread (warm-started solves of one
     // optimisation take similar counts), so that most solves poll once.
     static thread_local int64_t last_iters = 0;
-    int64_t launched = 0, chunk = last_iters > 0 ? std::min<int64_t>(std::max<int64_t>(last_iters + 1, 4), 64) : 8;
+    int64_t chunk = last_iters > 0 ? std::min<int64_t>(std::max<int64_t>(last_iters + 1, 4), 64) : 8;
+    int64_t ti = 0;  // host index of the next enqueued iteration (selects gamma's parity array)
     int polls = 0, timed_out = 0;
-    while (launched < max_iters) {
-        int64_t k = std::min<int64_t>(chunk, max_iters - launched);
-        for (int64_t it = 0; it < k; ++it) {
-            GP_TRY(op.apply(dd, Hd, done, st));
-            coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
-            if (!pc) {
-                const int64_t ti = launched + it;
-                const double *gcur = gamma + (ti & 1) * R;
-                double *gnext = gamma + ((ti + 1) & 1) * R;
-                cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, part, gcur, alpha, partN, sd);
-                cg_dir_fused_kernel<T><<<gd, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
-                                                           (long long)max_iters, tol, stop_rule, R, sqn, dcount);
-                GP_TRY(check_launch("cg iteration", 3));
-                continue;
+    // gamma array the iteration with host index i reads as its current gamma
+    auto gamma_at = [&](int64_t i) { return pc ? gamma : gamma + (i & 1) * R; };
+    auto poll = [&]() -> int { return op.tc ? poll_state_tc(sd, &hs, &timed_out, st) : poll_state(sd, &hs, st); };
+    int64_t dev_iters = 0;  // iterations the device has performed, as of the last poll
+    int checks = 0;         // failed true-residual checks so far (restarts)
+    double prev_y = 0.0, prev_z = 0.0;
+    for (;;) {
+        const int64_t left = max_iters - dev_iters;
+        int64_t phase = 0;
+        while (phase < left) {
+            const int64_t k = std::min<int64_t>(chunk, left - phase);
+            for (int64_t it = 0; it < k; ++it, ++ti) {
+                GP_TRY(op.apply(dd, Hd, done, st));
+                coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
+                if (!pc) {
+                    const double *gcur = gamma_at(ti);
+                    double *gnext = gamma_at(ti + 1);
+                    cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, part, gcur, alpha, partN, sd);
+                    cg_dir_fused_kernel<T><<<gd, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
+                                                               (long long)max_iters, tol, stop_rule, R, sqn, dcount);
+                    GP_TRY(check_launch("cg iteration", 3));
+                } else {
+                    cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
+                    cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
+                    GP_TRY(precond_apply<T>(pcd, r, pz, done, st));
+                    coldot_kernel<T><<<gp_, 256, 0, st>>>(r, pz, n, P, partG, done);
+                    cg_beta_kernel<<<1, 256, 0, st>>>(R, P, partG, part, gamma, alpha, beta, sd, (long long)max_iters,
+                                                      tol, stop_rule);
+                    cg_dir_kernel<T><<<gv, 256, 0, st>>>(dd, pz, n, beta, sd);
+                    GP_TRY(check_launch("cg iteration", 6));
+                }
             }
-            cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
-            cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
-            if (pc) {
-                GP_TRY(precond_apply<T>(pcd, r, pz, done, st));
-                coldot_kernel<T><<<gp_, 256, 0, st>>>(r, pz, n, P, partG, done);
-            }
-            cg_beta_kernel<<<1, 256, 0, st>>>(R, P, partG, part, gamma, alpha, beta, sd, (long long)max_iters, tol,
-                                              stop_rule);
-            cg_dir_kernel<T><<<gv, 256, 0, st>>>(dd, pc ? pz : r, n, beta, sd);
-            GP_TRY(check_launch("cg iteration", pc ? 6 : 5));
+            phase += k;
+            ++polls;
+            chunk = polls < 4 ? 4 : std::min<int64_t>(polls == 4 ? 8 : chunk * 2, 32);
+            GP_TRY(poll());
+            if (hs.done) break;
         }
-        launched += k;
-        ++polls;
-        chunk = polls < 4 ? 4 : std::min<int64_t>(polls == 4 ? 8 : chunk * 2, 32);
-        GP_TRY(op.tc ? poll_state_tc(sd, &hs, &timed_out, st) : poll_state(sd, &hs, st));
-        if (hs.done) break;
+        if (phase == 0) GP_TRY(poll());
+        dev_iters = hs.iter;
+        if (timed_out || hs.status != GP_OK || hs.certified) break;
+        // the loop stopped on the recursive residual: recompute the true one and judge it
+        if (check64) {
+            if constexpr (std::is_same<T, float>::value)
+                GP_TRY(f64_residual(kp, X, n, B, V, R, scale, r, partN, P, c64w, c64b, st));
+        } else {
+            GP_TRY(op.apply(V, Hd, nullptr, st));
+            true_residual_kernel<T, T><<<gp_, 256, 0, st>>>(B, Hd, r, n, P, scale, partN, nullptr);
+            GP_TRY(check_launch("cg true residual"));
+        }
+        // restart direction (used only if the check fails): d = r, or P^-1 r with gamma = r^T P^-1 r
+        if (pc) {
+            GP_TRY(precond_apply<T>(pcd, r, pz, nullptr, st));
+            coldot_kernel<T><<<gp_, 256, 0, st>>>(r, pz, n, P, partG, nullptr);
+            GP_TRY(check_launch("cg restart (preconditioned)"));
+        }
+        GP_TRY_CUDA(cudaMemcpyAsync(dd, pc ? pz : r, sizeof(T) * (size_t)R * n, cudaMemcpyDeviceToDevice, st));
+        true_state_kernel<<<1, 256, 0, st>>>(R, P, pc ? partG : partN, partN, gamma_at(ti), sd, (long long)max_iters,
+                                             tol, stop_rule, 1);
+        GP_TRY(check_launch("cg true-residual state"));
+        GP_TRY(poll());
+        dev_iters = hs.iter;
+        if (timed_out || hs.done) break;
+        // A restart that did not lower the true residual (by 10%) since the previous check means
+        // the form's arithmetic has reached the accuracy it can attain on this system: stop
+        // there, not converged, rather than spend the budget on further restarts.
+        if (checks > 0 && std::max(hs.res_y / prev_y, hs.res_z / prev_z) > 0.9) break;
+        prev_y = hs.res_y;
+        prev_z = hs.res_z;
+        ++checks;
+        chunk = 4;  // restarted from a residual close to the tolerance
     }
     // the loop ends on a poll (the state no longer changes), so the rescale is not waited for
-    if (launched == 0) GP_TRY(poll_state(sd, &hs, st));
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 0);
     GP_TRY(check_launch("cg rescale"));
     fill_info(hs, info);

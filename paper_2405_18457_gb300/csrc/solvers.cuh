@@ -74,6 +74,12 @@ int precond_build(const KP<T> &kp, const T *X, int64_t n, int R, int k, void *ws
 template <typename T>
 int precond_apply(const Precond<T> &P, const T *r, T *p, const int *done, cudaStream_t st);
 
+// The true residual r = b~ - H v of a normalised iterate with the FP64 product of FP32 inputs
+// (the check of the FP32 form's solvers), partial sums of ||r||^2 into partN (P x R).
+size_t f64_residual_workspace(int64_t n, int d, int R);
+int f64_residual(const KP<float> &kp, const float *X, int64_t n, const float *B, const float *V, int R,
+                 const double *scale, float *r, double *partN, int P, void *ws, size_t ws_bytes, cudaStream_t st);
+
 // Solvers (App. B, Alg. 1-3).
 template <typename T>
 size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank = 0);
@@ -101,7 +107,7 @@ struct SolverState {
     int done;
     int status;
     int converged;
-    int pad;
+    int certified;  // CG: res_y / res_z (and converged) come from a recomputed true residual
     long long iter;
     double res_y;
     double res_z;

@@ -1130,16 +1130,7 @@ int make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, u
 int kd_for(int d) { return (int)rup(3 * d + 4, 64); }
 int rpad_for(int R) { return (int)rup(R, 16); }
 
-int num_sms_tc() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    return sms;
-}
+int num_sms_tc() { return device_sm_count(); }
 
 // The persistent schedule (split code kPersist): one CTA per SM over equal runs of
 // (row tile, column tile) pairs; nseg = the most row segments one CTA can meet.
@@ -1239,12 +1230,7 @@ size_t smem_for(int KD, int R_pad, int npb, int nv) {
 template <int KIND, int KAT, bool PERSIST>
 int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mV,
                       const KParams &kp, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<KIND, KAT, PERSIST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-        attr = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<KIND, KAT, PERSIST>));
     tc_mvm_kernel<KIND, KAT, PERSIST><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
     return GP_OK;
 }
@@ -1263,17 +1249,26 @@ int tc_make_map16(CUtensorMap *m, const void *base, uint64_t inner, uint64_t out
     return make_map(m, base, inner, outer, box_inner, box_outer);
 }
 
+// The status word's device address, looked up once per device (a symbol's address differs
+// between devices) under a lock.
 int *tc_timeout_word() {
-    static int *w = nullptr;
-    if (!w) {
-        void *a = nullptr;
-        if (cudaGetSymbolAddress(&a, g_tc_timeout) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        w = static_cast<int *>(a);
+    static std::mutex mu;
+    static std::map<int, int *> words;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return w;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = words.find(dev);
+    if (it != words.end()) return it->second;
+    void *a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_tc_timeout) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    words[dev] = static_cast<int *>(a);
+    return static_cast<int *>(a);
 }
 
 int tc_timeout_status(cudaStream_t st) {
@@ -1314,18 +1309,24 @@ int tc_timeout_probe(long long limit, cudaStream_t st) {
 }
 
 bool tc_available() {
-    static int ok = -1;
-    if (ok < 0) {
-        int dev = 0, major = 0, minor = 0;
-        ok = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
-            ok = (major == 10 && minor == 3) && encode_fn() != nullptr;
-        else
-            cudaGetLastError();
+    static std::mutex mu;
+    static std::map<int, bool> ok;
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
-    return ok == 1;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = ok.find(dev);
+    if (it != ok.end()) return it->second;
+    bool v = false;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+        v = (major == 10 && minor == 3) && encode_fn() != nullptr;
+    else
+        cudaGetLastError();
+    ok[dev] = v;
+    return v;
 }
 
 // Buffer of a prepared pair: PA (n1_pad x KD), PB (n2_pad x KD), bound, dscale.
@@ -1655,18 +1656,12 @@ void tc_autotune_reset() {
 // member against a run of its own column tiles), items ordered longest first so the
 // block scheduler fills the SMs like a longest-processing-time list schedule.
 int tc_group_setup() {
-    static bool done = false;
-    if (done) return GP_OK;
-    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_RBF, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kMaxDynSmem));
-    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kMaxDynSmem));
-    GP_TRY_CUDA(cudaFuncSetAttribute(tc_mvm_kernel<GP_MATERN32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kMaxDynSmem));
-    done = true;
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 1>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 2>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 3>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 1>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 2>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 3>));
     return GP_OK;
 }
 
@@ -1776,6 +1771,11 @@ struct GParams {
     int km_steps;  // K = 16 steps of GEMM-M that touch real right-hand sides (ceil(R / 16))
     int64_t n, col_tiles;
     int nsplit;
+    // Symmetric sweep (sym_h > 0; U and W the same block, so M and the summand are symmetric
+    // in i and j): only the column tiles from the row tile's diagonal block on, off-diagonal
+    // tiles counted twice.  Row tile I's range [2I, 2 RT) is cut into ceil((RT - I) / sym_h)
+    // near-equal items; CTA e takes item e (row tiles in order, so longer items come first).
+    int64_t row_tiles, sym_h;
     const float *dscale;
     const float *guw;  // 1 / (G_u G_w)
     const float *X;
@@ -1787,6 +1787,29 @@ struct GParams {
     double *partial;
     int *err;
 };
+
+// F(M) = sum_{m=1..M} ceil(m / h): items of the row tiles with m = 1..M tiles pairs left.
+__host__ __device__ __forceinline__ int64_t sym_items_upto(int64_t M, int64_t h) {
+    const int64_t q = M / h, r = M - q * h;
+    return h * q * (q + 1) / 2 + r * (q + 1);
+}
+
+// Item e of the symmetric sweep: row tile I (the largest with prefix(I) <= e, where
+// prefix(I) = F(RT) - F(RT - I) items precede row tile I) and its column-tile range.
+__device__ __forceinline__ void sym_item(int64_t e, int64_t RT, int64_t h, int64_t *I, int64_t *c0, int64_t *c1) {
+    const int64_t FT = sym_items_upto(RT, h);
+    int64_t lo = 0, hi = RT - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (FT - sym_items_upto(RT - mid, h) <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t m = RT - lo, k = (m + h - 1) / h, part = e - (FT - sym_items_upto(m, h));
+    const int64_t len = 2 * m;  // column tiles from 2 I to the end (64-column tiles, 128-row tiles)
+    *I = lo;
+    *c0 = 2 * lo + part * len / k;
+    *c1 = 2 * lo + (part + 1) * len / k;
+}
 
 template <int KIND, int KAT>  // KAT: 64-wide atoms of the distance contraction (KD / 64)
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -1826,11 +1849,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     double *xch = reinterpret_cast<double *>(bars + 64);   // 256 doubles: per-row sums of warpgroup 1
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TM;
-    const int64_t per = cdiv(p.col_tiles, p.nsplit);
-    const int64_t t0 = (int64_t)blockIdx.y * per;
-    const int64_t t1 = min(p.col_tiles, t0 + per);
+    int64_t row_tile, t0, t1;
+    if (p.sym_h > 0) {
+        sym_item(blockIdx.x, p.row_tiles, p.sym_h, &row_tile, &t0, &t1);
+    } else {
+        const int64_t per = cdiv(p.col_tiles, p.nsplit);
+        row_tile = blockIdx.x;
+        t0 = (int64_t)blockIdx.y * per;
+        t1 = min(p.col_tiles, t0 + per);
+    }
+    const int64_t row0 = row_tile * TM;
     const int ntiles = (int)max((int64_t)0, t1 - t0);
+    // symmetric sweep: column tiles past the diagonal block count twice (log2 weight 1)
+    const int64_t twice_from = p.sym_h > 0 ? 2 * row_tile + 2 : INT64_MAX;
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
@@ -1986,6 +2017,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
             const uint32_t taS = tS + b * 128 + lane_off, taM = taS + 64;
             const uint32_t taP = taS;
+            const float cw = (t0 + it >= twice_from) ? 1.0f : 0.0f;  // log2 of the tile's weight
             float rs = 0.0f, sk = 0.0f;
 #pragma unroll 1
             for (int ch = 0; ch < GTN / 32; ++ch) {
@@ -2003,12 +2035,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const float M = __uint_as_float(rM[2 * e + h]);
                         float kp_, phi_;
                         if (KIND == GP_RBF) {
-                            kp_ = ex2_approx(fminf(S * dsc, 0.0f));
+                            kp_ = ex2_approx(fminf(fmaf(S, dsc, cw), cw));
                             phi_ = kp_;
                         } else {
                             float u = fmaxf(S * dsc, 1e-30f);
                             float q = u * rsqrt_approx(u);
-                            phi_ = ex2_approx(-q);
+                            phi_ = ex2_approx(cw - q);
                             kp_ = fmaf(q, kLn2, 1.0f) * phi_;
                         }
                         w[h] = phi_ * M;
@@ -2184,18 +2216,14 @@ __global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int6
 struct GradPlanTc {
     int KD, KM, N3p, ns, nb3, nsplit;
     int64_t n_pad, row_tiles, col_tiles;
+    int64_t sym_h, sym_items;  // symmetric sweep: tiles pairs per item (x 2 column tiles), items
     size_t smem;
 };
 
 template <int KIND, int KAT>
 int launch_grad_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mU,
                        const CUtensorMap &mW, const CUtensorMap &mB3, const GParams &p, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        GP_TRY_CUDA(cudaFuncSetAttribute(tc_grad_kernel<KIND, KAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxDynSmem));
-        attr = true;
-    }
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_grad_kernel<KIND, KAT>));
     tc_grad_kernel<KIND, KAT><<<grid, NTHREADS, smem, st>>>(mA, mB, mU, mW, mB3, p);
     return GP_OK;
 }
@@ -2209,6 +2237,11 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
     g.row_tiles = g.n_pad / TM;
     g.col_tiles = g.n_pad / GTN;
     g.nsplit = pick_uniform_split(g.row_tiles, g.col_tiles, nullptr);
+    // symmetric sweep: about six waves of items over the SMs, at least 8 tile pairs per item
+    // (a CTA's fixed start-up and epilogue cost about four tiles)
+    const int64_t waves = 6 * (int64_t)num_sms_tc();
+    g.sym_h = std::max<int64_t>(8, cdiv(g.row_tiles * g.row_tiles, 2 * waves));
+    g.sym_items = sym_items_upto(g.row_tiles, g.sym_h);
     const size_t a = (size_t)TM * g.KD * 2 + (size_t)TM * g.KM * 2;
     const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2;
     const size_t b3 = (size_t)g.N3p * 128;
@@ -2241,7 +2274,7 @@ size_t tc_grad_workspace(int64_t n, int d, int R) {
     c.take<unsigned int>(2);
     c.take<float>(1);
     c.take<int>(1);
-    c.take<double>((size_t)g.row_tiles * g.nsplit * (d + 1));
+    c.take<double>((size_t)std::max<int64_t>(g.row_tiles * g.nsplit, g.sym_items) * (d + 1));
     c.take<double>(256);
     return c.bytes();
 }
@@ -2263,8 +2296,11 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     float *guw = c.take<float>(1);
     c.take<int>(1);  // (kept for the workspace layout)
     int *err = tc_timeout_word();
-    const int nblocks = (int)(g.row_tiles * g.nsplit);
-    double *partial = c.take<double>((size_t)nblocks * (d + 1));
+    // U and W the same block with one lambda per column (the pathwise estimator): M and the
+    // summand are symmetric in i and j, so the upper triangle of tiles suffices
+    const bool sym = a.U0 == a.W0 && a.U == a.W && (a.R == 1 || a.ldu == a.ldw);
+    const int nblocks = (int)(sym ? g.sym_items : g.row_tiles * g.nsplit);
+    double *partial = c.take<double>((size_t)std::max<int64_t>(g.row_tiles * g.nsplit, g.sym_items) * (d + 1));
     double *dpart = c.take<double>(256);
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
@@ -2305,7 +2341,9 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     p.sf2 = a.kp.sf2;
     p.partial = partial;
     p.err = err;
-    dim3 grid((unsigned)g.row_tiles, (unsigned)g.nsplit);
+    p.row_tiles = g.row_tiles;
+    p.sym_h = sym ? g.sym_h : 0;
+    dim3 grid = sym ? dim3((unsigned)g.sym_items, 1) : dim3((unsigned)g.row_tiles, (unsigned)g.nsplit);
     const int kat = g.KD / 64;  // <= 2 since d <= 32
     prof_begin(st, 1);
     if (a.kp.kind == GP_RBF) {

@@ -16,7 +16,7 @@ from paper_2405_18457_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-gp = pytest.importorskip("paper_2405_18457_gb300")
+import paper_2405_18457_gb300 as gp  # noqa: E402  (a missing package fails the run)
 
 SHAPES = [(1, 3), (100, 4), (300, 8), (700, 16), (257, 32)]
 
@@ -117,7 +117,9 @@ def test_batch_cg_reaches_tolerance_with_true_residual(dev):
         Br = Bg.astype(np.float64)
         r = Br - oracle.kernel_mvm(0, thg, Xr, Xr, Vg.double().cpu().numpy(), add_noise=True)
         rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
-        assert rn[0] <= 1.5e-2 and rn[1:].mean() <= 1.5e-2, (g, rn)
+        assert rn[0] <= 1e-2 and rn[1:].mean() <= 1e-2, (g, rn)
+        # reported norms: the member's true residual on the tensor-core operator
+        assert abs(info[g]["res_y"] - rn[0]) <= 3e-3 and abs(info[g]["res_z"] - rn[1:].mean()) <= 3e-3, (g, info[g])
 
 
 def test_batch_cg_members_stop_independently(dev):

@@ -8,7 +8,8 @@ by one (sampled rows of the product), in the tensor-core launch configurations t
   batched   256 RBF members, n ~ LogUniform[512, 65536], d in {4, 8, 16, 32}, 17 vectors each:
             the grouped product of gp_batch_mvm
 
-Tolerance: 1e-3 relative (Frobenius over the sampled rows), the bound for the 16-bit form.
+Tolerance: 1e-3 relative (Frobenius over the sampled rows), the bound for the 16-bit form, and
+4e-3 for each sampled row on its own (parity_util.close).
 """
 import numpy as np
 import pytest
@@ -19,7 +20,7 @@ from paper_2405_18457_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-gp = pytest.importorskip("paper_2405_18457_gb300")
+import paper_2405_18457_gb300 as gp  # noqa: E402  (a missing package fails the run)
 
 
 @pytest.fixture(scope="module")
@@ -29,10 +30,7 @@ def dev():
     return torch.device("cuda:0")
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+from parity_util import close  # noqa: E402
 
 
 def test_ap_workload_full_size_product_and_panel_sampled_rows(dev):
@@ -46,14 +44,14 @@ def test_ap_workload_full_size_product_and_panel_sampled_rows(dev):
                          prec=gp.GP_PREC_TC16).cpu().numpy()
     rows = np.random.default_rng(22).choice(n, size=24, replace=False)
     ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float64), add_noise=True, rows=rows)
-    assert rel(Y[:, rows], ref) < 1e-3
+    assert close(Y[:, rows], ref, 1e-3)
     # panel shape of Alg. 2: every row against one block of b = 1024 columns
     blk = slice(5 * 1024, 6 * 1024)
     Vb = V[:, blk].copy()
     Yp = gp.gp_kernel_mvm(p.kind, p.theta, Xt, torch.tensor(Vb, device=dev), X2=Xt[blk].contiguous(),
                           prec=gp.GP_PREC_TC16).cpu().numpy()
     refp = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr[blk], Vb.astype(np.float64), rows=rows)
-    assert rel(Yp[:, rows], refp) < 1e-3
+    assert close(Yp[:, rows], refp, 1e-3)
 
 
 def test_sgd_workload_full_size_row_panel_sampled_rows(dev):
@@ -69,7 +67,7 @@ def test_sgd_workload_full_size_row_panel_sampled_rows(dev):
     pick = np.random.default_rng(25).choice(512, size=12, replace=False)
     Xr = X32.astype(np.float64)
     ref = oracle.kernel_mvm(p.kind, p.theta, Xr[batch], Xr, V.astype(np.float64), rows=pick)
-    assert rel(G[:, pick], ref) < 1e-3
+    assert close(G[:, pick], ref, 1e-3)
 
 
 def test_batched_workload_full_size_sampled_rows(dev):
@@ -93,4 +91,4 @@ def test_batched_workload_full_size_sampled_rows(dev):
         Xr = m.X.astype(np.float32).astype(np.float64)
         rows = np.random.default_rng(27 + g).choice(m.n, size=min(16, m.n), replace=False)
         ref = oracle.kernel_mvm(m.kind, m.theta, Xr, Xr, Vs[g].astype(np.float64), add_noise=True, rows=rows)
-        assert rel(Ys[g].cpu().numpy()[:, rows], ref) < 1e-3, g
+        assert close(Ys[g].cpu().numpy()[:, rows], ref, 1e-3), g

@@ -16,7 +16,7 @@ from paper_2405_18457_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-gp = pytest.importorskip("paper_2405_18457_gb300")
+import paper_2405_18457_gb300 as gp  # noqa: E402  (a missing package fails the run)
 
 
 @pytest.fixture(scope="module")
@@ -30,29 +30,13 @@ def t(a, dev, dtype=torch.float32):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
-def tc_built():
-    try:
-        X = torch.zeros((1, 1), device="cuda")
-        gp.gp_kernel_mvm(0, [1.0, 1.0, 1.0], X, torch.zeros((1, 1), device="cuda"), prec=gp.GP_PREC_TC16)
-        return True
-    except gp.GPError as e:
-        if e.status == -6:
-            return False
-        raise
+from parity_util import close, rel  # noqa: E402
 
 
 PRECS = [("f64", None, 1e-10), ("f32", gp.GP_PREC_FP32, 1e-5), ("tc16", gp.GP_PREC_TC16, 1e-3)]
 
 
 def run_mvm(prec_name, prec, kind, th, X1, X2, V, add_noise, dev):
-    if prec_name == "tc16" and not tc_built():
-        pytest.skip("tensor-core path not built")
     dt = torch.float64 if prec_name == "f64" else torch.float32
     X1t = t(X1, dev, dt)
     X2t = X1t if X2 is None else t(X2, dev, dt)
@@ -74,7 +58,7 @@ def test_hv_matches_oracle(dev, prec_name, prec, tol, kind, n, d, R):
     V = rng.standard_normal((R, n))
     Y = run_mvm(prec_name, prec, kind, th, X, None, V, True, dev)
     ref = oracle.kernel_mvm(kind, th, X, X, V, add_noise=True)
-    assert rel(Y, ref) < tol
+    assert close(Y, ref, tol)
 
 
 @pytest.mark.parametrize("prec_name,prec,tol", PRECS)
@@ -85,7 +69,7 @@ def test_cross_kernel_product_matches_oracle(dev, prec_name, prec, tol):
     th = np.concatenate([rng.uniform(0.8, 2.0, size=7), [0.9, 0.2]])
     V = rng.standard_normal((12, 517))
     Y = run_mvm(prec_name, prec, oracle.MATERN32, th, X1, X2, V, False, dev)
-    assert rel(Y, oracle.kernel_mvm(oracle.MATERN32, th, X1, X2, V)) < tol
+    assert close(Y, oracle.kernel_mvm(oracle.MATERN32, th, X1, X2, V), tol)
 
 
 @pytest.mark.parametrize("prec_name,prec,tol", PRECS)
@@ -94,7 +78,7 @@ def test_small_problem_workload_matches_oracle(dev, prec_name, prec, tol):
     p = workloads.small()
     B = np.vstack([p.y, p.Z])
     Y = run_mvm(prec_name, prec, p.kind, p.theta, p.X, None, B, True, dev)
-    assert rel(Y, oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, B, add_noise=True)) < tol
+    assert close(Y, oracle.kernel_mvm(p.kind, p.theta, p.X, p.X, B, add_noise=True), tol)
 
 
 @pytest.mark.parametrize("prec_name,prec,tol", PRECS[1:])
@@ -108,7 +92,7 @@ def test_full_size_pathwise_workload_sampled_rows(dev, prec_name, prec, tol):
     Xr = p.X.astype(np.float32).astype(np.float64)
     ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float32).astype(np.float64), add_noise=True,
                             rows=rows)
-    assert rel(Y[:, rows], ref) < tol
+    assert close(Y[:, rows], ref, tol)
 
 
 def test_empty_column_set_gives_zeros(dev):
@@ -125,8 +109,6 @@ def test_empty_column_set_gives_zeros(dev):
 @pytest.mark.parametrize("kind", [oracle.RBF, oracle.MATERN32])
 @pytest.mark.parametrize("estimator", ["standard", "pathwise"])
 def test_gradient_estimators_match_oracle(dev, prec_name, prec, tol, kind, estimator):
-    if prec_name == "tc16" and not tc_built():
-        pytest.skip("tensor-core path not built")
     rng = np.random.default_rng(5)
     n, d, s = 203, 6, 8
     X = rng.uniform(-1, 1, size=(n, d))
@@ -138,14 +120,91 @@ def test_gradient_estimators_match_oracle(dev, prec_name, prec, tol, kind, estim
     Vr = Vsol.astype(np.float32).astype(np.float64) if dt == torch.float32 else Vsol
     Zr = Z.astype(np.float32).astype(np.float64) if dt == torch.float32 else Z
     pr = prec if prec is not None else gp.GP_PREC_FP32
+    lam = np.concatenate([[0.5], np.full(s, -0.5 / s)])
     if estimator == "standard":
         g = gp.gp_mll_grad_standard(kind, th, t(X, dev, dt), t(Vsol, dev, dt), t(Z, dev, dt), prec=pr)
         ref = oracle.grad_standard(kind, th, Xr, Vr, Zr)
+        W = np.vstack([Vr[:1], Zr])
     else:
         g = gp.gp_mll_grad_pathwise(kind, th, t(X, dev, dt), t(Vsol, dev, dt), prec=pr)
         ref = oracle.grad_pathwise(kind, th, Xr, Vr)
-    g = g.cpu().numpy()
-    assert np.abs(g - ref).max() <= tol * np.abs(ref).max()
+        W = Vr
+    scale = oracle.grad_bilinear(kind, th, Xr, np.abs(Vr), np.abs(W), np.abs(lam))
+    _per_component_ok(g.cpu().numpy(), ref, scale, tol)
+
+
+def _grad_case(kind, n, d, s, seed, full_pathwise=False):
+    """Inputs of a gradient check in FP32 (as the GPU sees them) and the estimator's terms."""
+    if full_pathwise:
+        p = workloads.pathwise()
+        X = p.X.astype(np.float32)
+        th = p.theta
+    else:
+        rng = np.random.default_rng([seed, n, d, s])
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        th = np.concatenate([rng.uniform(0.7, 1.6, size=d) * np.sqrt(d / 8.0), [1.1, 0.3]])
+    Vsol = (workloads.vectors(s + 1, X.shape[0], seed=seed) * 0.8).astype(np.float32)
+    Z = workloads.vectors(s, X.shape[0], seed=seed + 1).astype(np.float32)
+    return X, th, Vsol, Z
+
+
+def _per_component_ok(g, ref, scale, rtol):
+    """|g_k - ref_k| <= rtol |ref_k| + rtol S_k, with S_k = sum_c |lambda_c| |u_c|^T |dH/dtheta_k| |w_c|
+    (the estimator evaluated on absolute values: every dH/dtheta_k is elementwise non-negative),
+    so each length-scale component is checked against its own size, not the largest one."""
+    err = np.abs(g - ref)
+    bound = rtol * np.abs(ref) + rtol * scale
+    assert np.all(err <= bound), (err / np.maximum(bound, 1e-300)).tolist()
+
+
+@pytest.mark.parametrize("estimator", ["pathwise", "standard"])
+@pytest.mark.parametrize("kind,n,d,s", [
+    (oracle.MATERN32, 4099, 16, 63),    # R = 64: one 64-wide U/W atom, four GEMM-M steps
+    (oracle.MATERN32, 4099, 16, 64),    # R = 65: the benched shape; second atom, five steps
+    (oracle.MATERN32, 4099, 16, 79),    # R = 80
+    (oracle.RBF, 4099, 16, 127),        # R = 128: two full atoms
+    (oracle.RBF, 2500, 26, 64),         # d = 26: two 64-wide atoms of the distance contraction
+    (oracle.MATERN32, 2049, 32, 64),    # d = 32: the widest tensor-core gradient
+])
+def test_tc16_gradient_matches_oracle_per_component(dev, estimator, kind, n, d, s):
+    """The tensor-core gradient kernel at the right-hand-side counts and dimensions the solvers
+    and the benchmark use (Eq. mll_grad with Eq. trace / Eq. pathwise_estimator), against the
+    oracle, component by component (ragged n: the last 128-row and 64-column tiles are partial)."""
+    X, th, Vsol, Z = _grad_case(kind, n, d, s, seed=40 + s)
+    Xr, Vr, Zr = (a.astype(np.float64) for a in (X, Vsol, Z))
+    lam = np.concatenate([[0.5], np.full(s, -0.5 / s)])
+    if estimator == "pathwise":
+        g = gp.gp_mll_grad_pathwise(kind, th, t(X, dev), t(Vsol, dev), prec=gp.GP_PREC_TC16).cpu().numpy()
+        ref = oracle.grad_pathwise(kind, th, Xr, Vr)
+        W = Vr
+    else:
+        g = gp.gp_mll_grad_standard(kind, th, t(X, dev), t(Vsol, dev), t(Z, dev),
+                                    prec=gp.GP_PREC_TC16).cpu().numpy()
+        ref = oracle.grad_standard(kind, th, Xr, Vr, Zr)
+        W = np.vstack([Vr[:1], Zr])
+    scale = oracle.grad_bilinear(kind, th, Xr, np.abs(Vr), np.abs(W), np.abs(lam))
+    _per_component_ok(g, ref, scale, 1e-3)
+
+
+@pytest.mark.parametrize("estimator", ["pathwise", "standard"])
+def test_tc16_gradient_full_pathwise_workload_per_component(dev, estimator):
+    """The benchmark's gradient call at full size: n = 32768, d = 16, Matern-3/2, s = 64 (R = 65),
+    against the FP64 oracle over all n^2 pairs, component by component."""
+    X, th, Vsol, Z = _grad_case(oracle.MATERN32, 0, 16, 64, seed=77, full_pathwise=True)
+    Xr, Vr, Zr = (a.astype(np.float64) for a in (X, Vsol, Z))
+    s = 64
+    lam = np.concatenate([[0.5], np.full(s, -0.5 / s)])
+    if estimator == "pathwise":
+        g = gp.gp_mll_grad_pathwise(oracle.MATERN32, th, t(X, dev), t(Vsol, dev), prec=gp.GP_PREC_TC16)
+        ref = oracle.grad_pathwise(oracle.MATERN32, th, Xr, Vr)
+        W = Vr
+    else:
+        g = gp.gp_mll_grad_standard(oracle.MATERN32, th, t(X, dev), t(Vsol, dev), t(Z, dev),
+                                    prec=gp.GP_PREC_TC16)
+        ref = oracle.grad_standard(oracle.MATERN32, th, Xr, Vr, Zr)
+        W = np.vstack([Vr[:1], Zr])
+    scale = oracle.grad_bilinear(oracle.MATERN32, th, Xr, np.abs(Vr), np.abs(W), np.abs(lam))
+    _per_component_ok(g.cpu().numpy(), ref, scale, 1e-3)
 
 
 # --------------------------------------------------------------------------- solvers
@@ -155,8 +214,6 @@ def test_cg_iterates_match_oracle(dev, prec_name, prec, tol, iters):
     """Fixed iterations from a warm start: iterate-by-iterate parity with Alg. 1.
     CG amplifies product rounding from one iteration to the next, so the fp16
     tensor-core form is compared after 2 iterations."""
-    if prec_name == "tc16" and not tc_built():
-        pytest.skip("tensor-core path not built")
     rng = np.random.default_rng(7)
     n, d, R = 300, 4, 5
     X = rng.standard_normal((n, d))
@@ -189,11 +246,14 @@ def test_cg_reaches_tolerance_with_true_residual(dev, prec_name, prec, stop_rule
     Br = B if dt == torch.float64 else B.astype(np.float32).astype(np.float64)
     r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, Vh, add_noise=True)
     rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
-    slack = 1.5 if prec_name != "tc16" else 5.0
     if stop_rule == 0:
-        assert rn[0] <= slack * tol and rn[1:].mean() <= slack * tol
+        assert rn[0] <= tol and rn[1:].mean() <= tol
     else:
-        assert min(rn[0], rn[1:].mean()) <= slack * tol
+        assert min(rn[0], rn[1:].mean()) <= tol
+    # the reported norms are those of the recomputed true residual
+    slack = (1e-2 if prec_name == "f32" else 1e-6) * tol  # FP32-rounded hyperparameters in the check
+    assert info.res_y == pytest.approx(rn[0], rel=1e-3, abs=slack)
+    assert info.res_z == pytest.approx(rn[1:].mean(), rel=1e-3, abs=slack)
 
 
 @pytest.mark.parametrize("warm", [False, True])
@@ -201,8 +261,6 @@ def test_tc16_cg_at_the_paper_tolerance_true_residual(dev, warm):
     """fp16 tensor-core products at tau = 0.01 on the pathwise workload's shape (Matern-3/2,
     X ~ N(0, I), sigma = 0.3): the true FP64 residual of the returned solution meets tau, and a
     warm start from the previous solution after a small theta change needs fewer iterations."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     p = workloads.pathwise(n=3000, d=8, s=16, m=256, seed=3)
     X32 = p.X.astype(np.float32)
     Xr = X32.astype(np.float64)
@@ -221,7 +279,10 @@ def test_tc16_cg_at_the_paper_tolerance_true_residual(dev, warm):
         V, th = V2, th2
     r = Br - oracle.kernel_mvm(p.kind, th, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
     rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
-    assert rn[0] <= 1.5e-2 and rn[1:].mean() <= 1.5e-2
+    assert rn[0] <= 1e-2 and rn[1:].mean() <= 1e-2
+    # reported norms: the true residual on the tensor-core operator, whose residuals differ from
+    # the exact ones by its rounding (measured up to about 1.3e-3 of ||b|| on this shape)
+    assert abs(info.res_y - rn[0]) <= 3e-3 and abs(info.res_z - rn[1:].mean()) <= 3e-3
 
 
 @pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-9), ("f32", gp.GP_PREC_FP32, 1e-4)])
@@ -239,7 +300,13 @@ def test_ap_iterates_match_oracle(dev, prec_name, prec, tol, n, bs):
     Vr, ir = oracle.solve_ap(oracle.RBF, th, X, B, block_size=bs, max_iters=iters, tol=0.0)
     assert info.iters == ir["iters"]
     assert rel(V.double().cpu().numpy(), Vr) < tol
-    assert info.res_z == pytest.approx(ir["res_z"], rel=1e3 * tol)
+    # the reported norms are the returned iterate's true residual (recomputed when the loop stops)
+    Xr = X if dt == torch.float64 else X.astype(np.float32).astype(np.float64)
+    Br = B if dt == torch.float64 else B.astype(np.float32).astype(np.float64)
+    res = Br - oracle.kernel_mvm(oracle.RBF, th, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
+    rn = np.linalg.norm(res, axis=1) / np.linalg.norm(Br, axis=1)
+    # (the FP32 form's check runs in FP64 on the FP32-rounded hyperparameters)
+    assert info.res_z == pytest.approx(rn[1:].mean(), rel=1e-3, abs=(1e-2 if prec_name == "f32" else 1e-3) * tol)
 
 
 def test_ap_converges_to_dense_solution(dev):
@@ -259,8 +326,6 @@ def test_ap_converges_to_dense_solution(dev):
 def test_tc16_ap_iterates_match_oracle(dev, n, bs):
     """Tensor-core column panel (device-resident block offset): a few iterations of Alg. 2
     against the oracle; the fp16 panel error is below 1e-3 per iteration."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     rng = np.random.default_rng(n + 1)
     d, R = 5, 4
     X = rng.standard_normal((n, d))
@@ -279,8 +344,6 @@ def test_tc16_ap_iterates_match_oracle(dev, n, bs):
 def test_tc16_ap_reaches_tolerance_true_residual(dev):
     """Alg. 2 with the tensor-core panel to tau = 0.01 on the pathwise workload's shape; the true
     FP64 residual of the returned solution meets tau."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     p = workloads.pathwise(n=2000, d=8, s=8, m=256, seed=5)
     X32 = p.X.astype(np.float32)
     B = np.vstack([p.y_noise, p.Z]).astype(np.float32)
@@ -290,14 +353,13 @@ def test_tc16_ap_reaches_tolerance_true_residual(dev):
     Xr, Br = X32.astype(np.float64), B.astype(np.float64)
     r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
     rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
-    assert rn[0] <= 1.5e-2 and rn[1:].mean() <= 1.5e-2
+    assert rn[0] <= 1e-2 and rn[1:].mean() <= 1e-2
+    assert abs(info.res_y - rn[0]) <= 3e-3 and abs(info.res_z - rn[1:].mean()) <= 3e-3
 
 
 def test_tc16_sgd_iterates_match_oracle(dev):
     """Tensor-core row panel (batch rows against all points, many column splits): a few
     iterations of Alg. 3 against the oracle."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     rng = np.random.default_rng(19)
     n, d, R, batch, iters = 3000, 4, 4, 64, 4
     X = rng.standard_normal((n, d)).astype(np.float32)
@@ -356,7 +418,7 @@ def test_rff_prior_sample_matches_oracle(dev, dtype, prec, tol, kind):
                                t(p.chi2, dev, dtype), t(p.W_probe, dev, dtype), prec=prec)
     cast = (lambda a: a) if dtype == torch.float64 else (lambda a: a.astype(np.float32).astype(np.float64))
     ref = oracle.rff_prior(kind, p.theta, cast(p.X), cast(p.omega_hat), cast(p.chi2), cast(p.W_probe))
-    assert rel(F.double().cpu().numpy(), ref) < tol
+    assert close(F.double().cpu().numpy(), ref, tol)
 
 
 @pytest.mark.parametrize("n,d,s,m", [(300, 32, 128, 64), (260, 4, 129, 96), (128, 1, 1, 2)])
@@ -368,7 +430,7 @@ def test_rff_tensor_core_limits(dev, n, d, s, m):
                                t(p.W_probe, dev), prec=gp.GP_PREC_TC16)
     f = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
     ref = oracle.rff_prior(p.kind, p.theta, f(p.X), f(p.omega_hat), f(p.chi2), f(p.W_probe))
-    assert rel(F.double().cpu().numpy(), ref) < 2e-5
+    assert close(F.double().cpu().numpy(), ref, 2e-5)
 
 
 def test_rff_full_size_sampled_points(dev):
@@ -381,7 +443,7 @@ def test_rff_full_size_sampled_points(dev):
     for prec in (gp.GP_PREC_TC16, gp.GP_PREC_FP32):
         F = gp.gp_rff_prior_sample(p.kind, p.theta, t(p.X, dev), t(p.omega_hat, dev), t(p.chi2, dev),
                                    t(p.W_probe, dev), prec=prec)
-        assert rel(F.double().cpu().numpy()[:, rows], ref) < 2e-5
+        assert close(F.double().cpu().numpy()[:, rows], ref, 2e-5)
 
 
 def test_pathwise_rhs_and_posterior_samples_match_oracle(dev):
@@ -399,14 +461,12 @@ def test_pathwise_rhs_and_posterior_samples_match_oracle(dev):
     out = gp.gp_posterior_samples(p.kind, p.theta, t(Xs, dev), t(p.X, dev), t(Vsol, dev), t(Fs, dev),
                                   prec=gp.GP_PREC_FP32)
     ref = oracle.posterior_samples(p.kind, p.theta, f(Xs), f(p.X), f(Vsol), f(Fs))
-    assert rel(out.double().cpu().numpy(), ref) < 1e-5
+    assert close(out.double().cpu().numpy(), ref, 1e-5)
 
 
 def test_autotuned_split_is_used_and_keeps_parity(dev):
     """The autotuner times candidate column splits for one shape and records the fastest;
     products of that shape (standalone and inside CG) still match the oracle."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     p = workloads.pathwise(n=2500, d=6, s=8, m=64, seed=7)
     X32 = p.X.astype(np.float32)
     V = workloads.vectors(9, 2500, seed=3).astype(np.float32)
@@ -416,7 +476,7 @@ def test_autotuned_split_is_used_and_keeps_parity(dev):
         Y = gp.gp_kernel_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), add_noise=True, prec=gp.GP_PREC_TC16)
         Xr = X32.astype(np.float64)
         ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float64), add_noise=True)
-        assert rel(Y.cpu().numpy(), ref) < 1e-3
+        assert close(Y.cpu().numpy(), ref, 1e-3)
         B = np.vstack([p.y_noise, p.Z]).astype(np.float32)
         Vs, info = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), max_iters=300, tol=1e-2,
                                   prec=gp.GP_PREC_TC16)
@@ -430,8 +490,6 @@ def test_persistent_schedule_rows_straddling_ctas(dev, n, R):
     """At these sizes the product runs one CTA per SM over equal runs of tile pairs, so most
     128-row tiles are shared by two or more CTAs and summed by the reduction; rows of shared
     and unshared tiles (first, last, ragged) match the oracle, and so does CG with it."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     p = workloads.pathwise(n=n, d=8, s=R - 1, m=64, seed=17)
     X32 = p.X.astype(np.float32)
     V = workloads.vectors(R, n, seed=18).astype(np.float32)
@@ -443,7 +501,7 @@ def test_persistent_schedule_rows_straddling_ctas(dev, n, R):
                            np.random.default_rng(19).choice(n, size=48, replace=False)])
     Xr = X32.astype(np.float64)
     ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float64), add_noise=True, rows=rows)
-    assert rel(Y[:, rows], ref) < 1e-3
+    assert close(Y[:, rows], ref, 1e-3)
     # deterministic: the same call twice gives the same bits
     Y2 = gp.gp_kernel_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), add_noise=True,
                           prec=gp.GP_PREC_TC16).cpu().numpy()
@@ -453,8 +511,6 @@ def test_persistent_schedule_rows_straddling_ctas(dev, n, R):
 @pytest.mark.parametrize("prec_name,prec,tol", [("f32", gp.GP_PREC_FP32, 1e-5), ("tc16", gp.GP_PREC_TC16, 2e-3)])
 def test_predictions_match_oracle(dev, prec_name, prec, tol):
     """Predictive mean/variance and test RMSE/log-likelihood from the pathwise solutions."""
-    if prec_name == "tc16" and not tc_built():
-        pytest.skip("tensor-core path not built")
     p = workloads.pathwise(n=1500, d=6, s=12, m=256, seed=9)
     rng = np.random.default_rng(10)
     Xs = rng.standard_normal((700, 6)).astype(np.float32)
@@ -466,8 +522,8 @@ def test_predictions_match_oracle(dev, prec_name, prec, tol):
                                    prec=prec)
     m_ref, v_ref, (rmse, llh) = oracle.predict(p.kind, p.theta, Xs.astype(np.float64), X32.astype(np.float64),
                                                Vsol.astype(np.float64), Fs.astype(np.float64), ys.astype(np.float64))
-    assert rel(mean.cpu().numpy(), m_ref) < tol
-    assert rel(var.cpu().numpy(), v_ref) < tol
+    assert close(mean.cpu().numpy(), m_ref, tol)
+    assert close(var.cpu().numpy(), v_ref, tol)
     met = met.cpu().numpy()
     assert abs(met[0] - rmse) <= tol * rmse and abs(met[1] - llh) <= 10 * tol * abs(llh)
 
@@ -515,7 +571,7 @@ def test_pcg_reaches_tolerance_in_fewer_iterations_fp32(dev):
     Xr, Br = X32.astype(np.float64), B.astype(np.float64)
     r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
     rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
-    assert rn[0] <= 1.5 * tol and rn[1:].mean() <= 1.5 * tol
+    assert rn[0] <= tol and rn[1:].mean() <= tol
 
 
 def test_tc16_pcg_at_the_paper_tolerance_true_residual(dev):
@@ -524,8 +580,6 @@ def test_tc16_pcg_at_the_paper_tolerance_true_residual(dev):
     workload, see the plain-CG tests): converged and the true FP64 residual meets tau.  In this
     high-dimensional shape the kernel spectrum is flat, so a rank-100 factor barely changes the
     iteration count (the FP32 test above shows the reduction on the small workload)."""
-    if not tc_built():
-        pytest.skip("tensor-core path not built")
     p = workloads.pathwise(n=3000, d=8, s=16, m=256, seed=3)
     X32 = p.X.astype(np.float32)
     B = np.vstack([p.y_noise, p.Z]).astype(np.float32)
@@ -535,4 +589,4 @@ def test_tc16_pcg_at_the_paper_tolerance_true_residual(dev):
     Xr, Br = X32.astype(np.float64), B.astype(np.float64)
     r = Br - oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.double().cpu().numpy(), add_noise=True)
     rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
-    assert rn[0] <= 1.5e-2 and rn[1:].mean() <= 1.5e-2
+    assert rn[0] <= 1e-2 and rn[1:].mean() <= 1e-2
