@@ -312,7 +312,8 @@ def run_ours(args):
         # schedule of the product chosen by timing (column splits), before any timed work
         Vt = torch.randn((prob.s + 1, n), dtype=torch.float32, device=dev)
         best, best_ms = gp.gp_autotune_mvm(prob.kind, prob.theta, rep.X, Vt, reps=3)
-        tuned = {"column_splits": best, "ms": best_ms}
+        gbest, gbest_ms = gp.gp_autotune_grad(prob.kind, prob.theta, rep.X, Vt, None, reps=3)
+        tuned = {"column_splits": best, "ms": best_ms, "gradient_tile_pairs_per_item": gbest, "gradient_ms": gbest_ms}
 
     def barrier():
         if dist is not None:
@@ -1151,7 +1152,7 @@ def run_op(args):
                           "ffma_tflops": sms * rates["ffma"] * 2 * clk * 1e6 / 1e12,
                           "dfma_tflops": sms * rates["dfma"] * 2 * clk * 1e6 / 1e12}))
         return
-    prec = gp.GP_PREC_TC16 if args.prec == "tc16" else gp.GP_PREC_FP32
+    prec = {"tc16": gp.GP_PREC_TC16, "fp32": gp.GP_PREC_FP32, "tc16x3": gp.GP_PREC_TC16X3}[args.prec]
     p = workloads.pathwise(n=args.n, d=16, s=64, m=2048, seed=0)
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
     X = t(p.X)
@@ -1187,7 +1188,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["tc16", "fp32"], default="tc16")
+    ap.add_argument("--prec", choices=["tc16", "fp32", "tc16x3"], default="tc16",
+                    help="tc16x3 (the split tensor-core product) for --op mvm only")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -1215,6 +1217,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.prec == "tc16x3":
+        raise SystemExit("--prec tc16x3 applies to --op mvm only")
     if args.workload == "batched":
         run_batched(args)
         return

@@ -70,7 +70,13 @@ typedef enum {
 } gp_status_t;
 
 typedef enum { GP_RBF = 0, GP_MATERN32 = 1 } gp_kernel_t;
-typedef enum { GP_PREC_FP32 = 1, GP_PREC_TC16 = 2 } gp_prec_t;
+/* Precision forms.  GP_PREC_FP32: CUDA-core FP32 tiles.  GP_PREC_TC16: tcgen05 fp16 operands
+ * (kernel values, vectors and a hi/lo-split distance) with FP32 accumulation.
+ * GP_PREC_TC16X3 (gp_kernel_mvm only; the solvers use it for their true residuals): the same
+ * with the kernel values and the vectors split into fp16 high + low parts and
+ * Y = P_hi V_hi + P_hi V_lo + P_lo V_hi, FP32-class products (relative error about 1e-6
+ * instead of 1e-3) at a tensor-core rate. */
+typedef enum { GP_PREC_FP32 = 1, GP_PREC_TC16 = 2, GP_PREC_TC16X3 = 3 } gp_prec_t;
 
 /* Loop condition of Alg. 1-3.  GP_STOP_BOTH (default): iterate while
  * t < budget and (||r_y|| > tol or ||r_z|| > tol), i.e. stop once BOTH split
@@ -140,6 +146,7 @@ int gp_diag_unit_rates(int iters, double *rates, void *ws, size_t ws_bytes, cuda
  *   V  : nrhs vectors of length n2 (stride ldv >= n2), Y : nrhs x n1 (ldy >= n1).
  *   add_noise = 1 requires X1 == X2 and n1 == n2 and gives H V.
  *   n1 = 0 or n2 = 0 or nrhs = 0 is a valid no-op (Y is zeroed when n2 = 0).
+ * prec: GP_PREC_FP32, GP_PREC_TC16 or GP_PREC_TC16X3 (gp_prec_t).
  * Y must not overlap V or X.  Error: GP_ERR_INVALID_ARG on bad sizes/pointers. */
 int gp_kernel_mvm(int kind, const double *theta, int d,
                   const float *X1, int64_t n1, const float *X2, int64_t n2,
@@ -166,6 +173,32 @@ int gp_autotune_mvm(int kind, const double *theta, int d, const float *X, int64_
 size_t gp_autotune_mvm_workspace(int64_t n, int d, int nrhs);
 void gp_autotune_reset(void);
 
+/* Autotuner of the tensor-core gradient's work split (the paper has no counterpart).  Times
+ * the fused estimator of gp_mll_grad_pathwise (Z = NULL: U = W = Vsol, the symmetric sweep
+ * over the upper triangle of tiles, candidates = tile pairs per CTA item) or of
+ * gp_mll_grad_standard (Z = the s probes: the full sweep, candidates = column splits per
+ * 128-row tile), `reps` timed runs each after a warm-up, and records the fastest for the
+ * shape (distance and vector contraction widths, row tiles, symmetric or not); later
+ * gradients of that shape use it.  best_param, best_ms: HOST outputs.  Vsol: (s+1) x n, Z:
+ * s x n, device.  ws: gp_autotune_grad_workspace(n, d, s) bytes.  Synchronises `stream`;
+ * not for use inside a stream capture.  GP_ERR_UNSUPPORTED when the tensor-core gradient
+ * does not cover (d, s) (d > 32 or s + 1 > 256). */
+int gp_autotune_grad(int kind, const double *theta, int d, const float *X, int64_t n,
+                     const float *Vsol, int s, const float *Z, int reps, int64_t *best_param,
+                     double *best_ms, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t gp_autotune_grad_workspace(int64_t n, int d, int s);
+
+/* The autotuner's table on disk.  gp_autotune_save writes every recorded choice (products and
+ * gradients) to a text file tagged with the current device's name, compute capability and SM
+ * count; gp_autotune_load adds a file's entries to the table, refusing a file written on
+ * another kind of device (GP_ERR_INVALID_ARG, message in gp_last_error()).  When the
+ * environment variable GP_AUTOTUNE_CACHE names a file, the library reads it at its first
+ * tuned lookup and writes the table back to it after every tuning call.  gp_autotune_count()
+ * is the number of recorded choices. */
+int gp_autotune_save(const char *path);
+int gp_autotune_load(const char *path);
+int64_t gp_autotune_count(void);
+
 /* FP64 form of gp_kernel_mvm (plain CUDA-core FP64 tiles). */
 int gp_kernel_mvm_f64(int kind, const double *theta, int d,
                       const double *X1, int64_t n1, const double *X2, int64_t n2,
@@ -189,10 +222,12 @@ size_t gp_kernel_mvm_f64_workspace(int64_t n1, int64_t n2, int d, int nrhs);
  * b~ - H v is recomputed once (one product, FP64 differences and norms) and the
  * tolerance is judged on it: a solve whose true residual misses tau restarts from
  * it (d = r) within its budget, and info's res_y / res_z are always true-residual
- * norms.  The product is the form's own operator for GP_PREC_TC16 and the FP64
- * form, and the FP64 product of the FP32 inputs for GP_PREC_FP32.  The tensor-core
- * operator is within about 1e-3 of ||H v|| of the exact one, so that form certifies
- * max(tau - 1e-3, tau / 2) on it.  Returns GP_OK with info filled (synchronises
+ * norms.  The true residual (like the initial one of a warm start) is taken with
+ * an FP32-class product: the split tensor-core product (GP_PREC_TC16X3) for
+ * GP_PREC_TC16, the FP64 product of the FP32 inputs for GP_PREC_FP32, the FP64
+ * product for the FP64 form.  A restart that does not lower the true residual by
+ * 10% ends the solve (not converged): the form's arithmetic has reached what it
+ * can attain on the system.  Returns GP_OK with info filled (synchronises
  * stream), GP_ERR_BREAKDOWN if a residual becomes non-finite. */
 int gp_solve_cg(int kind, const double *theta, int d, const float *X, int64_t n,
                 const float *B, int nrhs, float *V_inout, int64_t max_iters, double tol,
@@ -232,9 +267,9 @@ size_t gp_solve_pcg_f64_workspace(int64_t n, int d, int nrhs, int rank);
  * inverse of every diagonal block is computed once per call from its Cholesky
  * factor (cached for the whole solve).  max_iters counts block iterations
  * (epochs x n / block_size).  1 <= block_size <= 1024.  When the loop stops on the
- * residual the panels maintain, the true residual is recomputed (one full product;
- * not counted in max_iters) and judged as in gp_solve_cg, including the
- * tensor-core form's certified tolerance max(tau - 1e-3, tau / 2). */
+ * residual the panels maintain, the true residual is recomputed (one full product
+ * of the FP32 class, as in gp_solve_cg; not counted in max_iters) and judged as in
+ * gp_solve_cg; so is the initial residual of a warm start. */
 int gp_solve_ap(int kind, const double *theta, int d, const float *X, int64_t n,
                 const float *B, int nrhs, float *V_inout, int64_t block_size, int64_t max_iters,
                 double tol, int stop_rule, int prec, gp_solve_info_t *info,
@@ -505,10 +540,10 @@ int gp_batch_mvm(gp_batch_t *b, const float *V, float *Y, int add_noise, cudaStr
  * condition fails is skipped from then on.  Every 10 iterations and after the
  * last one, the true residual of each member that stopped on its recursive
  * residual is recomputed (one grouped product over those members); a member whose
- * true residual misses the tolerance restarts from it.  The tolerance is certified
- * on the tensor-core operator at max(tau - 1e-3, tau / 2), and the reported norms
- * are true-residual norms.  info: DEVICE array of G reports (or NULL), written at
- * the end. */
+ * true residual misses the tolerance restarts from it.  True residuals (and the
+ * initial residual) use the split tensor-core product when s + 1 <= 80 (the plain
+ * one above), and the reported norms are true-residual norms.  info: DEVICE array of G reports (or
+ * NULL), written at the end. */
 int gp_batch_solve_cg(gp_batch_t *b, const float *B, float *V_inout, int64_t iters, double tol,
                       int stop_rule, gp_solve_info_t *info, cudaStream_t stream);
 /* Eq. mll_grad per member into grad (DEVICE, packed like theta): standard

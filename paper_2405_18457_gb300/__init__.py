@@ -16,14 +16,19 @@ from ._binding import (  # noqa: F401
     GP_MATERN32,
     GP_PREC_FP32,
     GP_PREC_TC16,
+    GP_PREC_TC16X3,
     GP_RBF,
     GP_STOP_BOTH,
     GP_STOP_EITHER,
     GPError,
     SolveInfo,
     gp_adam_softplus_step,
+    gp_autotune_count,
+    gp_autotune_grad,
+    gp_autotune_load,
     gp_autotune_mvm,
     gp_autotune_reset,
+    gp_autotune_save,
     gp_bilinear_grad,
     gp_diag_kernel_time,
     gp_diag_launches,

@@ -13,6 +13,7 @@ GP_RBF = 0
 GP_MATERN32 = 1
 GP_PREC_FP32 = 1
 GP_PREC_TC16 = 2
+GP_PREC_TC16X3 = 3
 GP_STOP_BOTH = 0
 GP_STOP_EITHER = 1
 
@@ -105,6 +106,11 @@ _SIGS = {
     "gp_autotune_mvm": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i, ctypes.POINTER(_i), _pd, _vp, _sz, _vp]),
     "gp_autotune_mvm_workspace": (_sz, [_i64, _i, _i]),
     "gp_autotune_reset": (None, []),
+    "gp_autotune_grad": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i, _vp, _i, ctypes.POINTER(_i64), _pd, _vp, _sz, _vp]),
+    "gp_autotune_grad_workspace": (_sz, [_i64, _i, _i]),
+    "gp_autotune_save": (_i, [ctypes.c_char_p]),
+    "gp_autotune_load": (_i, [ctypes.c_char_p]),
+    "gp_autotune_count": (_i64, []),
     "gp_predict": (_i, [_i, _pd, _i, _vp, _i64, _vp, _i64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp]),
     "gp_predict_workspace": (_sz, [_i64, _i64, _i, _i, _i]),
     "gp_rkhs_sqdist": (_i, [_i, _pd, _i, _vp, _i64, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp]),
@@ -298,6 +304,40 @@ def gp_autotune_mvm(kind, theta, X, V, reps=3):
 
 def gp_autotune_reset():
     library().gp_autotune_reset()
+
+
+def gp_autotune_grad(kind, theta, X, Vsol, Z=None, reps=3):
+    """Times the tensor-core gradient's work splits for this shape (pathwise estimator when Z is
+    None, else the standard estimator with probes Z) and records the fastest; returns
+    (best work-split parameter, its time in ms)."""
+    lib = library()
+    _dev(X, torch.float32, "X", 2)
+    n, d = X.shape
+    _dev(Vsol, torch.float32, "Vsol", 2)
+    s = Vsol.shape[0] - 1
+    if Z is not None:
+        _dev(Z, torch.float32, "Z", 2)
+    th, thp = _theta(theta, d)
+    ws, wsb = _ws(lib.gp_autotune_grad_workspace(n, d, s), X.device)
+    best = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib.gp_autotune_grad(kind, thp, d, _ptr(X), n, _ptr(Vsol), s, _ptr(Z), int(reps), ctypes.byref(best),
+                                ctypes.byref(ms), _ptr(ws), wsb, _stream()))
+    return int(best.value), float(ms.value)
+
+
+def gp_autotune_save(path):
+    """Writes the autotuner's recorded choices to `path` (tagged with this device)."""
+    _check(library().gp_autotune_save(str(path).encode()))
+
+
+def gp_autotune_load(path):
+    """Adds the choices recorded in `path` (written on this kind of device) to the table."""
+    _check(library().gp_autotune_load(str(path).encode()))
+
+
+def gp_autotune_count():
+    return int(library().gp_autotune_count())
 
 
 def _info(inf: _Info) -> SolveInfo:

@@ -214,6 +214,12 @@ int check_prec(int prec) {
     return GP_OK;
 }
 
+// The products also take the split tensor-core form.
+int check_prec_mvm(int prec) {
+    if (prec == GP_PREC_TC16X3) return check_prec(GP_PREC_TC16);
+    return check_prec(prec);
+}
+
 template <typename T>
 int mvm_common(int kind, const double *theta, int d, const T *X1, int64_t n1, const T *X2, int64_t n2,
                const T *V, int64_t ldv, int nrhs, T *Y, int64_t ldy, int add_noise, int prec, void *ws,
@@ -227,7 +233,7 @@ int mvm_common(int kind, const double *theta, int d, const T *X1, int64_t n1, co
         REQ(ldv >= n2, "ldv (%lld) must be >= n2 (%lld)", (long long)ldv, (long long)n2);
     }
     REQ(add_noise == 0 || (X1 == X2 && n1 == n2), "add_noise requires X1 == X2 and n1 == n2");
-    if (sizeof(T) == sizeof(float)) GP_TRY(check_prec(prec));
+    if (sizeof(T) == sizeof(float)) GP_TRY(check_prec_mvm(prec));
     KP<T> kp;
     GP_TRY(make_kp<T>(kind, theta, d, &kp));
     if (n2 == 0) {
@@ -703,6 +709,62 @@ int gp_autotune_mvm(int kind, const double *theta, int d, const float *X, int64_
 }
 
 void gp_autotune_reset(void) { tc_autotune_reset(); }
+
+size_t gp_autotune_grad_workspace(int64_t n, int d, int s) {
+    Carver c(nullptr);
+    c.take<double>((size_t)d + 2);
+    c.take<char>(grad_workspace<float>(n, d, s + 1, GP_PREC_TC16));
+    return c.bytes();
+}
+
+int gp_autotune_grad(int kind, const double *theta, int d, const float *X, int64_t n, const float *Vsol, int s,
+                     const float *Z, int reps, int64_t *best_param, double *best_ms, void *ws, size_t ws_bytes,
+                     cudaStream_t stream) {
+    GP_API_BEGIN
+    KP<float> kp;
+    GP_TRY(make_kp<float>(kind, theta, d, &kp));
+    REQ(n >= 1 && s >= 1, "need n >= 1 and s >= 1");
+    REQ(X && Vsol && best_param && best_ms, "null pointer argument");
+    REQ(reps >= 1 && reps <= 100, "reps must be in [1, 100]");
+    GP_TRY(check_prec(GP_PREC_TC16));
+    Carver c(ws);
+    double *g = c.take<double>((size_t)d + 2);
+    const size_t gwb = grad_workspace<float>(n, d, s + 1, GP_PREC_TC16);
+    void *gw = c.take<char>(gwb);
+    GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    GradArgs<float> a;
+    a.kp = kp;
+    a.X = X;
+    a.n = n;
+    a.U0 = Vsol;
+    a.U = Vsol + n;
+    a.ldu = n;
+    a.W0 = Vsol;
+    a.W = Z ? Z : Vsol + n;  // standard estimator: (v_j, z_j); pathwise: (zhat_j, zhat_j)
+    a.ldw = n;
+    a.R = s + 1;
+    a.lam0 = 0.5;
+    a.lam_rest = -0.5 / (double)s;
+    a.grad = g;
+    return tc_autotune_grad(a, reps, gw, gwb, stream, best_param, best_ms);
+    GP_API_END
+}
+
+int gp_autotune_save(const char *path) {
+    GP_API_BEGIN
+    REQ(path != nullptr && *path, "path must be a non-empty string");
+    return tc_autotune_save(path);
+    GP_API_END
+}
+
+int gp_autotune_load(const char *path) {
+    GP_API_BEGIN
+    REQ(path != nullptr && *path, "path must be a non-empty string");
+    return tc_autotune_load(path);
+    GP_API_END
+}
+
+int64_t gp_autotune_count(void) { return tc_autotune_count(); }
 
 // ------------------------------------------------------------------ bilinear-form derivatives
 }  // extern "C"

@@ -386,10 +386,8 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
 
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
     const dim3 gp_((unsigned)P, (unsigned)R);
-    // the tolerance the true residual is certified to on this form's operator (tensor-core
-    // panels are within about kTcOperatorErr of the exact product)
-    if (std::is_same<T, float>::value && prec == GP_PREC_TC16 && tol > 0.0)
-        tol = std::max(tol - kTcOperatorErr, 0.5 * tol);
+    // true residuals (initial and final) of the tensor-core form use its split products
+    const int prec_true = prec == GP_PREC_TC16 ? GP_PREC_TC16X3 : prec;
     // ---- block inverses H[i,i]^-1 (cached for the whole solve)
     GP_TRY_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
     ap_build_blocks_kernel<T><<<dim3(bsp / 16, bsp / 16, nb), dim3(16, 16), 0, st>>>(kp, X, n, bs, bsp, Hb);
@@ -426,7 +424,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
     GP_TRY(check_launch("ap setup", 3));
-    GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
+    GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec_true, mw, mwb, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
     ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 1);
@@ -540,7 +538,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         if constexpr (std::is_same<T, float>::value)
             GP_TRY(f64_residual(kp, X, n, B, V, R, scale, r, part, P, c64w, c64b, st));
     } else {
-        GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
+        GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec_true, mw, mwb, st));
         true_residual_kernel<T, T><<<gp_, 256, 0, st>>>(B, HV, r, n, P, scale, part, nullptr);
     }
     true_state_kernel<<<1, 256, 0, st>>>(R, P, nullptr, part, nullptr, sd, (long long)max_iters, tol, stop_rule, 1);

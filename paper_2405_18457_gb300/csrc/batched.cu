@@ -83,7 +83,8 @@ struct gp_batch {
             o->PA[k] = c.take<uint16_t>((size_t)std::max<int64_t>(class_rows[k], 1) * KD[k]);
             o->PB[k] = c.take<uint16_t>((size_t)std::max<int64_t>(class_rows[k], 1) * KD[k]);
         }
-        o->V16 = c.take<uint16_t>((size_t)R_pad * (size_t)std::max<int64_t>(v_cols, 1));
+        // high parts, then the split form's low parts
+        o->V16 = c.take<uint16_t>((size_t)2 * R_pad * (size_t)std::max<int64_t>(v_cols, 1));
         o->vinv = c.take<float>((size_t)G * R_pad);
         o->colmax = c.take<unsigned>((size_t)G * R_pad);
         o->r = c.take<float>((size_t)R * N);
@@ -688,12 +689,17 @@ dim3 chunk_grid(const gp_batch *b, int cols) {
 
 size_t grad_smem(int R) { return sizeof(float) * (size_t)(2 * GT * kBatchMaxD + 2 * GT * R); }
 
-// Y = H V (diag = 1) or K V (diag = 0) for every member not flagged in mdone.
-int batch_apply(gp_batch *b, const float *V, float *Y, float diag, const int *mdone, cudaStream_t st) {
+// Y = H V (diag = 1) or K V (diag = 0) for every member not flagged in mdone; split: the split
+// tensor-core products (FP32-class, for true residuals).
+int batch_apply(gp_batch *b, const float *V, float *Y, float diag, const int *mdone, cudaStream_t st,
+                bool split = false) {
     auto &p = b->p;
     const int nch = (int)b->chunks.size();
+    // batches of more than 80 right-hand sides per member take the plain form for true
+    // residuals too (the split form's accumulators hold 80 columns)
+    split = split && tc_split_fits_rpad(b->R_pad);
     GP_TRY(tc_group_convert(p.mem, b->G, p.chunks, nch, V, b->R, b->R_pad, p.colmax, p.V16, b->v_cols, p.vinv,
-                            mdone, st));
+                            mdone, st, split));
     for (int k = 0; k < 3; ++k) {
         if (b->items[k].empty()) continue;
         TcGroupArgs a{};
@@ -715,6 +721,7 @@ int batch_apply(gp_batch *b, const float *V, float *Y, float diag, const int *md
         a.Vd = V;
         a.diag = diag;
         a.err = p.err;
+        a.split = split ? 1 : 0;
         GP_TRY(tc_group_mvm(a, st));
     }
     return GP_OK;
@@ -732,8 +739,6 @@ constexpr int64_t kCheckEvery = 10;  // iterations between the batched solver's 
 int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, int stop_rule,
              gp_solve_info_t *info, cudaStream_t st) {
     auto &p = b->p;
-    // the tolerance the true residual is certified to on the tensor-core operator
-    if (tol > 0.0) tol = std::max(tol - kTcOperatorErr, 0.5 * tol);
     const int G = b->G, R = b->R, nch = (int)b->chunks.size();
     const dim3 gc = chunk_grid(b, R);
     const unsigned gmr = (unsigned)cdiv((int64_t)G * R, 128), gmw = (unsigned)cdiv((int64_t)G * R * 32, 256);
@@ -742,8 +747,8 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     bt_norm_scale_kernel<<<gmr, 128, 0, st>>>(p.mem, G, R, nch, p.part, p.scale);
     bt_scale_cols_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, V, R, p.scale, 1);
     GP_TRY(check_launch("batched cg setup", 3));
-    // r = b~ - H v ; d = r ; gamma = r^T r
-    GP_TRY(batch_apply(b, V, p.Hd, 1.0f, nullptr, st));
+    // r = b~ - H v ; d = r ; gamma = r^T r  (a true residual: split products)
+    GP_TRY(batch_apply(b, V, p.Hd, 1.0f, nullptr, st, true));
     bt_init_residual_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, p.Hd, p.r, p.dd, R, p.scale);
     bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.r, p.r, p.part, nullptr);
     bt_cg_start_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, p.cdone,
@@ -756,7 +761,7 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     // product of the whole iterate injects that product's rounding into the recurrence.
     auto true_residuals = [&]() -> int {
         bt_check_flags_kernel<<<(unsigned)cdiv(G, 128), 128, 0, st>>>(G, p.done, p.cdone, p.cskip);
-        GP_TRY(batch_apply(b, V, p.Hd, 1.0f, p.cskip, st));
+        GP_TRY(batch_apply(b, V, p.Hd, 1.0f, p.cskip, st, true));
         bt_true_residual_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, p.Hd, p.r, p.dd, R, p.scale, p.part,
                                                     p.cskip);
         bt_true_state_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, p.cdone,

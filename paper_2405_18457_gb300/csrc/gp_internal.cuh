@@ -257,6 +257,9 @@ struct TcMvmArgs {
     int64_t ncols;
     const int64_t *col0_dev;
     int diag_from_col0;
+    // Split form: kernel values and V as fp16 high + low parts, Y += P_hi V_hi + P_hi V_lo +
+    // P_lo V_hi (about 2^-22 relative per term instead of 2^-11; three GEMM2 passes per tile).
+    int split;
 };
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R);
 // Row operand for points X1 that are a subset of an already prepared set `like` (same
@@ -287,6 +290,11 @@ size_t tc_autotune_workspace(int64_t n, int R);
 int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStream_t st, int *best_split,
                 double *best_ms);
 void tc_autotune_reset();
+int tc_autotune_grad(const GradArgs<float> &a, int reps, void *ws, size_t ws_bytes, cudaStream_t st, int64_t *best_v,
+                     double *best_ms);
+int tc_autotune_save(const char *path);
+int tc_autotune_load(const char *path);
+int64_t tc_autotune_count();
 
 // ---------------------------------------------------------------------------
 // Batches of independent GPs (batched.cu): device tables shared with tc.cu
@@ -351,16 +359,20 @@ struct TcGroupArgs {
     const float *Vd;
     float diag;          // 1: add sigma_g^2 Vd (H V), 0: K V
     int *err;
+    int split;           // split form (V16 holds R_pad high rows, then R_pad low rows)
 };
 int tc_group_mvm(const TcGroupArgs &a, cudaStream_t st);
+// Whether the split form of the grouped product takes R_pad right-hand sides in one pass.
+bool tc_split_fits_rpad(int R_pad);
 // Operands of every member from its device-side parameters (BMember inv_ell, bound):
 // PA/PB rows of class c at PA[c], PB[c] (KD[c] halves per row).
 int tc_group_prepare(int kind, BMember *members, int G, const BChunk *chunks, int nchunks, const float *X,
                      void *const *PA, void *const *PB, const int *KD, cudaStream_t st);
-// fp16 right-hand sides: V16[c][cb_g + i] = V_g[c][i] * 2^-e_gc, vinv[g][c] = 2^e_gc.
+// fp16 right-hand sides: V16[c][cb_g + i] = V_g[c][i] * 2^-e_gc, vinv[g][c] = 2^e_gc; with
+// split also the low parts at rows R_pad + c.
 int tc_group_convert(const BMember *members, int G, const BChunk *chunks, int nchunks, const float *V, int R,
                      int R_pad, unsigned *colmax, void *V16, int64_t v_cols, float *vinv, const int *mdone,
-                     cudaStream_t st);
+                     cudaStream_t st, bool split = false);
 int tc_group_setup();  // one-time kernel attributes (call before any stream capture)
 
 // ---------------------------------------------------------------------------

@@ -12,7 +12,7 @@ namespace gp {
 // ===========================================================================
 template <typename T>
 size_t mvm_workspace(int64_t n1, int64_t n2, int d, int R, int prec) {
-    if (std::is_same<T, float>::value && prec == GP_PREC_TC16) {
+    if (std::is_same<T, float>::value && (prec == GP_PREC_TC16 || prec == GP_PREC_TC16X3)) {
         Carver c(nullptr);
         c.take<char>(tc_points_bytes(n1, d));
         c.take<char>(tc_points_bytes(n2, d));
@@ -26,7 +26,7 @@ template <typename T>
 int apply_mvm(const KP<T> &kp, const T *X1, int64_t n1, const T *X2, int64_t n2, const T *V, int64_t ldv,
               int R, T *Y, int64_t ldy, int add_noise, int prec, void *ws, size_t ws_bytes, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) {
-        if (prec == GP_PREC_TC16) {
+        if (prec == GP_PREC_TC16 || prec == GP_PREC_TC16X3) {
             Carver c(ws);
             void *pa = c.take<char>(tc_points_bytes(n1, kp.d));
             void *pb = c.take<char>(tc_points_bytes(n2, kp.d));
@@ -55,6 +55,7 @@ int apply_mvm(const KP<T> &kp, const T *X1, int64_t n1, const T *X2, int64_t n2,
             a.drow0 = 0;
             a.ndiag = add_noise ? n1 : 0;
             a.done = nullptr;
+            a.split = prec == GP_PREC_TC16X3 ? 1 : 0;
             return tc_mvm(a, tw, tcw, st);
         }
     }

@@ -12,11 +12,6 @@ namespace {
 
 constexpr double kNormEps = 1e-12;   // eps of the normalisation b / (||b|| + eps)
 constexpr double kFreeze = 1e-30;    // CG column frozen once gamma <= this
-// The tensor-core operator (fp16 kernel values and operands, FP32 accumulation) is within about
-// 1e-3 of ||H v|| of the exact product, the bound its parity tests hold it to; a residual
-// certified on it at tol - kTcOperatorErr is then at most about tol for the exact operator.
-constexpr double kTcOperatorErr = 1e-3;
-
 // x (float) -> y (double), count elements
 __global__ void widen_kernel(const float *x, double *y, int64_t count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)

@@ -293,8 +293,9 @@ struct HOp {
         wsb = wb;
         return GP_OK;
     }
-    // Y = alpha * K V + beta * Y + diag (sigma^2 V unless overridden)
-    int apply(const T *V, T *Y, const int *done, cudaStream_t st) {
+    // Y = alpha * K V + beta * Y + diag (sigma^2 V unless overridden); split: the tensor-core
+    // form's split products (FP32-class), for true residuals
+    int apply(const T *V, T *Y, const int *done, cudaStream_t st, bool split = false) {
         if constexpr (std::is_same<T, float>::value) {
             if (tc) {
                 TcMvmArgs a{};
@@ -315,6 +316,7 @@ struct HOp {
                 a.drow0 = 0;
                 a.ndiag = n;
                 a.done = done;
+                a.split = split ? 1 : 0;
                 return tc_mvm(a, ws, wsb, st);
             }
         }
@@ -460,8 +462,6 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
 
     HOp<T> op;
     GP_TRY(op.init(kp, X, n, R, prec, opw, opb, st));
-    // the tolerance the true residual is certified to on this form's operator
-    if (op.tc && tol > 0.0) tol = std::max(tol - kTcOperatorErr, 0.5 * tol);
     Precond<T> pcd{};
     if (pc) GP_TRY(precond_build<T>(kp, X, n, R, pc_rank, pcw, pcb, &pcd, st));
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
@@ -476,8 +476,8 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
     GP_TRY(check_launch("cg setup", 3));
-    // r = b~ - H v ; p = P^-1 r ; d = p ; gamma = r^T p
-    GP_TRY(op.apply(V, Hd, nullptr, st));
+    // r = b~ - H v ; p = P^-1 r ; d = p ; gamma = r^T p  (a true residual: split products)
+    GP_TRY(op.apply(V, Hd, nullptr, st, true));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, Hd, r, dd, n, scale);
     GP_TRY(check_launch("cg residual"));
     if (pc) {
@@ -503,7 +503,9 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // with the whole iterate carries an error of about u ||H|| ||v||, which in FP32 on an
     // ill-conditioned system lies far above the residuals CG reaches (measured: replacing the
     // recursive residual by an FP32 true residual every 10 iterations made CG diverge on the
-    // small workload).  The reported norms are therefore always true-residual norms.
+    // small workload); the tensor-core form uses its split products (FP32-class), since its
+    // plain fp16 product is off by about 2^-11 ||H|| ||v||.  The initial residual is computed the
+    // same way.  The reported norms are therefore always true-residual norms.
     SolverState hs{};
     // The first chunk follows the previous solve on this thread (warm-started solves of one
     // optimisation take similar counts), so that most solves poll once.
@@ -557,7 +559,7 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             if constexpr (std::is_same<T, float>::value)
                 GP_TRY(f64_residual(kp, X, n, B, V, R, scale, r, partN, P, c64w, c64b, st));
         } else {
-            GP_TRY(op.apply(V, Hd, nullptr, st));
+            GP_TRY(op.apply(V, Hd, nullptr, st, true));
             true_residual_kernel<T, T><<<gp_, 256, 0, st>>>(B, Hd, r, n, P, scale, partN, nullptr);
             GP_TRY(check_launch("cg true residual"));
         }

@@ -33,10 +33,16 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <cmath>
+#include <string>
 #include <tuple>
+#include <vector>
 
 namespace gp {
 
@@ -51,6 +57,8 @@ constexpr int NTHREADS = 416;     // gradient kernel: producer, 3 MMA issuers, 2
 constexpr int kPersist = -1;       // split code of the persistent product schedule
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
+constexpr int kSplitGroup = 8;       // split form: tiles per tensor-memory accumulation group
+constexpr int kSplitMaxRpad = 80;    // split form: padded right-hand sides per pass (256 + 3 R_pad <= 512)
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -105,6 +113,83 @@ __device__ __forceinline__ void eval_chunk64(const uint32_t (&r)[64], uint32_t (
                            kernel_of<KIND, SCALED>(__uint_as_float(r[2 * e + 1]), dscale));
 }
 
+// 32 tile values of one row -> k / s_f^2 as 16 packed fp16 pairs of its high part h(k) and 16 of
+// its low part h(k - h(k)) (the split form of the product: k = high + low to about 2^-22).
+template <int KIND, bool SCALED>
+__device__ __forceinline__ void eval_chunk_split(const uint32_t (&r)[32], uint32_t (&ph)[16], uint32_t (&pl)[16],
+                                                 float dscale) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const float k0 = kernel_of<KIND, SCALED>(__uint_as_float(r[2 * e]), dscale);
+        const float k1 = kernel_of<KIND, SCALED>(__uint_as_float(r[2 * e + 1]), dscale);
+        const __half2 h = __floats2half2_rn(k0, k1);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(k0 - hf.x, k1 - hf.y);
+        ph[e] = *reinterpret_cast<const uint32_t *>(&h);
+        pl[e] = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// Kernel values of one 128-column tile of this thread's row, written over the S columns at taS
+// once read.  Plain form: two halves of 64 columns, each to 32 packed columns at taS + 32 half
+// (one 64-column load and one 32-column store per half, fewer tensor-memory instructions
+// competing with the MMA issue).  Split form: four quarters of 32 columns, quarter q to
+// high parts at taS + 32 q and low parts at taS + 32 q + 16.
+template <int KIND, bool SPLIT>
+__device__ __forceinline__ void eval_tile(uint32_t taS, bool unit, float dsc) {
+    if constexpr (!SPLIT) {
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            uint32_t r[64];
+            tmem_ld64(taS + half * 64, r);
+            tmem_ld_wait();
+            uint32_t pk[32];
+            if (unit)
+                eval_chunk64<KIND, false>(r, pk, dsc);
+            else
+                eval_chunk64<KIND, true>(r, pk, dsc);
+            tmem_st32(taS + half * 32, pk);
+        }
+    } else {
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            uint32_t r[32];
+            tmem_ld32(taS + q * 32, r);
+            tmem_ld_wait();
+            uint32_t ph[16], pl[16];
+            if (unit)
+                eval_chunk_split<KIND, false>(r, ph, pl, dsc);
+            else
+                eval_chunk_split<KIND, true>(r, ph, pl, dsc);
+            tmem_st16(taS + q * 32, ph);
+            tmem_st16(taS + q * 32 + 16, pl);
+        }
+    }
+}
+
+// GEMM2 of one tile: Y += P V over the tile's 128 columns in K = 16 steps (A = kernel values
+// in tensor memory at aP, B = the V tile's 64-column atoms in shared memory at dv).  Split form:
+// Y += P_hi V_hi + P_hi V_lo + P_lo V_hi (the low x low term, about 2^-22 relative, dropped),
+// V_lo in atoms 2 and 3 of the slot.  acc0: accumulate into Y from the first step on.
+template <bool SPLIT>
+__device__ __forceinline__ void gemm2_tile(uint32_t tY, uint32_t aP, uint64_t dv, uint32_t va_units, uint32_t id2,
+                                           bool acc0) {
+#pragma unroll
+    for (int k = 0; k < TN / 16; ++k) {
+        const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
+        const uint32_t acc = (acc0 || k > 0) ? 1u : 0u;
+        if constexpr (!SPLIT) {
+            mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, acc);
+        } else {
+            const uint32_t aH = aP + (uint32_t)(k >> 1) * 32 + (uint32_t)(k & 1) * 8, aL = aH + 16;
+            const uint64_t bH = dv + kv * va_units + ko, bL = dv + (2 + kv) * va_units + ko;
+            mma_ts(tY, aH, bH, id2, acc);
+            mma_ts(tY, aH, bL, id2, 1u);
+            mma_ts(tY, aL, bH, id2, 1u);
+        }
+    }
+}
+
 struct KParams {
     int R, R_pad, KD;
     int npb, nv;         // depths of the PB-tile and V-tile shared-memory rings
@@ -141,7 +226,7 @@ struct KParams {
 
 // KAT: 64-wide atoms of the distance contraction (KD / 64); PERSIST: the persistent schedule
 // (single problem; a separate instantiation so that the other schedules keep their code).
-template <int KIND, int KAT, bool PERSIST = false>
+template <int KIND, int KAT, bool PERSIST = false, bool SPLIT = false>
 __global__ void __launch_bounds__(MVM_THREADS, 1)
     tc_mvm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const __grid_constant__ CUtensorMap mapV, const KParams p) {
@@ -154,7 +239,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     const uint32_t a_bytes = (uint32_t)TM * p.KD * 2;
     const uint32_t b_bytes = (uint32_t)TN * p.KD * 2;
     const uint32_t v_atom = (uint32_t)R_pad * 128;
-    const uint32_t v_bytes = 2 * v_atom;
+    const uint32_t v_bytes = (SPLIT ? 4 : 2) * v_atom;  // split form: high then low atoms
     // Two independent rings: PB tiles are needed by GEMM1 about two tiles before the
     // V tiles are needed by GEMM2, and each ring slot is released as soon as its own
     // GEMM has read it, so the loads run several tiles ahead of the tensor cores.
@@ -175,7 +260,12 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     uint64_t *y_full = t_free + 3;
     uint64_t *y_empty = y_full + 1;  // persistent: the evaluation threads have read Y
     uint64_t *a_empty = y_empty + 1; // persistent: GEMM1 is done with the row operand
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_empty + 1);
+    // split form: GEMM2 accumulates groups of kSplitGroup tiles into two alternating buffers,
+    // which the evaluation warps add into a running FP32 sum (yg_full: a group's GEMM2 done;
+    // yg_empty: its buffer read out)
+    uint64_t *yg_full = a_empty + 1;
+    uint64_t *yg_empty = yg_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(yg_empty + 2);
     volatile int *s_err = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -255,6 +345,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         mbar_init(y_full, 1);
         mbar_init(y_empty, 256);
         mbar_init(a_empty, 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&yg_full[k], 1);
+            mbar_init(&yg_empty[k], 256);
+        }
         *s_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -271,6 +365,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     // its first 64 columns), the Y accumulator at 384 (R_pad <= 128 columns).
     const uint32_t tmem = *tmem_slot;
     const uint32_t tS0 = tmem, tY = tmem + 384;
+    // Split form (single segment): two tile buffers at columns 0 / 128, the two group
+    // accumulators at 256 and 256 + R_pad, the running sum at 256 + 2 R_pad (R_pad <= 80).
+    constexpr int NB = SPLIT ? 2 : 3;  // tile buffers
+    const uint32_t tDg = tmem + 256, tYs = tmem + 256 + 2 * (uint32_t)R_pad;
     if constexpr (!PERSIST) {
         if (warp == 0 && ntiles > 0) {
             // ------------------------------------------------ TMA producer: row operand + PB ring
@@ -302,6 +400,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                     mbar_expect_tx(&v_full[s], v_bytes);
                     tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
                     tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
+                    if constexpr (SPLIT) {
+                        tma_load_2d(sV + 2 * v_atom, &mapV, &v_full[s], j0, R_pad);
+                        tma_load_2d(sV + 3 * v_atom, &mapV, &v_full[s], j0 + 64, R_pad);
+                    }
                 }
             }
         } else if (warp == 1 && ntiles > 0) {
@@ -317,11 +419,11 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             const uint64_t dA = sdesc(sA), dPB = sdesc(sPB);
             const uint32_t b_units = b_bytes >> 4;
             bool ok = mbar_wait_warp(a_full, 0, s_err);
-            // GEMM1 of tile it into buffer it % 3, once GEMM2 of tile it - 3 has consumed it.
+            // GEMM1 of tile it into buffer it % NB, once GEMM2 of tile it - NB has consumed it.
             for (int it = 0; ok && it < ntiles; ++it) {
-                const int s = it % NPB, b = it % 3;
+                const int s = it % NPB, b = it % NB;
                 if (!mbar_wait_warp(&pb_full[s], (it / NPB) & 1, s_err)) break;
-                if (it >= 3 && !mbar_wait_warp(&t_free[b], ((it / 3) - 1) & 1, s_err)) break;
+                if (it >= NB && !mbar_wait_warp(&t_free[b], ((it / NB) - 1) & 1, s_err)) break;
                 tc_fence_after();
                 const uint64_t db = dPB + (uint64_t)s * b_units;
                 const uint32_t dS = tS0 + b * 128;
@@ -344,20 +446,27 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             const uint64_t dV = sdesc(sVr);
             const uint32_t v_units = v_bytes >> 4, va_units = v_atom >> 4;
             for (int it = 0; it < ntiles; ++it) {
-                const int s = it % NV, b = it % 3;
+                const int s = it % NV, b = it % NB;
+                // split form: group gi of kSplitGroup tiles into accumulator gi % 2, restarted once
+                // the evaluation warps have read out group gi - 2
+                const int gi = it / kSplitGroup;
+                const bool gfirst = (it % kSplitGroup) == 0;
+                const bool glast = (it % kSplitGroup) == kSplitGroup - 1 || it == ntiles - 1;
+                if (SPLIT && gfirst && gi >= 2 && !mbar_wait_warp(&yg_empty[gi & 1], ((gi >> 1) - 1) & 1, s_err))
+                    break;
                 if (!mbar_wait_warp(&v_full[s], (it / NV) & 1, s_err)) break;
-                if (!mbar_wait_warp(&t_kval[b], (it / 3) & 1, s_err)) break;
+                if (!mbar_wait_warp(&t_kval[b], (it / NB) & 1, s_err)) break;
                 tc_fence_after();
                 const uint64_t dv = dV + (uint64_t)s * v_units;
                 const uint32_t aP = tS0 + b * 128;
                 if (leader) {
-#pragma unroll
-                    for (int k = 0; k < TN / 16; ++k) {
-                        const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                        mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (it > 0 || k > 0) ? 1u : 0u);
-                    }
+                    if constexpr (SPLIT)
+                        gemm2_tile<SPLIT>(tDg + (uint32_t)(gi & 1) * R_pad, aP, dv, va_units, id2, !gfirst);
+                    else
+                        gemm2_tile<SPLIT>(tY, aP, dv, va_units, id2, it > 0);
                     mma_commit(&v_empty[s]);
                     mma_commit(&t_free[b]);
+                    if (SPLIT && glast) mma_commit(&yg_full[gi & 1]);
                 }
                 __syncwarp();
             }
@@ -374,43 +483,62 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
             const bool unit = (dsc == 1.0f);
             bool ok = true;
+            // split form: read-out of group g's accumulator into the running sum (FP32, rounded
+            // to nearest), this warpgroup's alternate 16-column chunks, then release the buffer
+            const int ngroups = SPLIT ? (int)cdiv(ntiles, kSplitGroup) : 0;
+            int rg = 0;  // next group to read out
+            auto readout = [&](int g) {
+                if (!ok) return;
+                ok = mbar_wait(&yg_full[g & 1], (g >> 1) & 1, s_err);
+                if (!ok) return;
+                tc_fence_after();
+                const uint32_t tD = tDg + (uint32_t)(g & 1) * R_pad + lane_off;
+                for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
+                    uint32_t r[16], q[16];
+                    tmem_ld16(tD + c0, r);
+                    if (g > 0) tmem_ld16(tYs + lane_off + c0, q);
+                    tmem_ld_wait();
+                    if (g > 0) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(q[e]));
+                    }
+                    tmem_st16(tYs + lane_off + c0, r);
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(&yg_empty[g & 1]);
+            };
             for (int it = wg; it < ntiles; it += 2) {
-                const int b = it % 3;
-                if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
+                const int b = it % NB;
+                if (!mbar_wait(&t_full[b], (it / NB) & 1, s_err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taS = tS0 + b * 128 + lane_off;
-                const uint32_t taP = taS;
-#pragma unroll 1
-                for (int half = 0; half < 2; ++half) {
-                    // one 64-column load and one 32-column store per half: fewer tensor-memory
-                    // instructions competing with the MMA issue for the same queue
-                    uint32_t r[64];
-                    tmem_ld64(taS + half * 64, r);
-                    tmem_ld_wait();
-                    uint32_t pk[32];
-                    if (unit)
-                        eval_chunk64<KIND, false>(r, pk, dsc);
-                    else
-                        eval_chunk64<KIND, true>(r, pk, dsc);
-                    tmem_st32(taP + half * 32, pk);
-                }
+                eval_tile<KIND, SPLIT>(tS0 + b * 128 + lane_off, unit, dsc);
                 if (!ok) break;
                 tmem_st_wait();
                 tc_fence_before();
                 mbar_arrive(&t_kval[b]);
+                if constexpr (SPLIT) {
+                    // groups in which this warpgroup has no tile left
+                    while (rg < ngroups && it + 2 >= min(ntiles, (rg + 1) * kSplitGroup)) readout(rg++);
+                }
+            }
+            if constexpr (SPLIT) {
+                while (ok && rg < ngroups) readout(rg++);
             }
             // epilogue: Y rows from TMEM lanes, one row per thread; the two warpgroups
-            // take alternate 16-column chunks of the right-hand sides
-            if (ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
+            // take alternate 16-column chunks of the right-hand sides (the split form's running
+            // sum holds this warpgroup's own chunks)
+            if (!SPLIT && ok && ntiles > 0) ok = mbar_wait(y_full, 0, s_err);
             if (ok && ntiles > 0) {
                 tc_fence_after();
                 const int64_t i = ioff + wq * 32 + lane;
                 for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
                     uint32_t r[16];
-                    tmem_ld16(tY + lane_off + c0, r);
+                    tmem_ld16((SPLIT ? tYs : tY) + lane_off + c0, r);
                     tmem_ld_wait();
                     if (i < n1) {
 #pragma unroll
@@ -492,6 +620,10 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                     mbar_expect_tx(&v_full[s], v_bytes);
                     tma_load_2d(sV, &mapV, &v_full[s], j0, 0);
                     tma_load_2d(sV + v_atom, &mapV, &v_full[s], j0 + 64, 0);
+                    if constexpr (SPLIT) {
+                        tma_load_2d(sV + 2 * v_atom, &mapV, &v_full[s], j0, R_pad);
+                        tma_load_2d(sV + 3 * v_atom, &mapV, &v_full[s], j0 + 64, R_pad);
+                    }
                 }
             }
         } else if (warp == 1 && ntiles > 0) {
@@ -549,11 +681,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                 const uint64_t dv = dV + (uint64_t)s * v_units;
                 const uint32_t aP = tS0 + b * 128;
                 if (leader) {
-#pragma unroll
-                    for (int k = 0; k < TN / 16; ++k) {
-                        const uint32_t kv = (uint32_t)(k >> 2), ko = (uint32_t)(k & 3) * 2;
-                        mma_ts(tY, aP + k * 8, dv + kv * va_units + ko, id2, (!first || k > 0) ? 1u : 0u);
-                    }
+                    gemm2_tile<SPLIT>(tY, aP, dv, va_units, id2, !first);
                     mma_commit(&v_empty[s]);
                     mma_commit(&t_free[b]);
                     if (last) mma_commit(y_full);
@@ -629,22 +757,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t taS = tS0 + b * 128 + lane_off;
-                    const uint32_t taP = taS;
-#pragma unroll 1
-                    for (int half = 0; half < 2; ++half) {
-                        // one 64-column load and one 32-column store per half: fewer tensor-memory
-                        // instructions competing with the MMA issue for the same queue
-                        uint32_t r[64];
-                        tmem_ld64(taS + half * 64, r);
-                        tmem_ld_wait();
-                        uint32_t pk[32];
-                        if (unit)
-                            eval_chunk64<KIND, false>(r, pk, dsc);
-                        else
-                            eval_chunk64<KIND, true>(r, pk, dsc);
-                        tmem_st32(taP + half * 32, pk);
-                    }
+                    eval_tile<KIND, SPLIT>(tS0 + b * 128 + lane_off, unit, dsc);
                     if (!ok) break;
                     tmem_st_wait();
                     tc_fence_before();
@@ -992,7 +1105,7 @@ __global__ void tc_group_colmax_kernel(const BMember *mem, const BChunk *chunks,
 // the 128-padded size and for c >= R); vinv = 2^(e-1).
 __global__ void tc_group_convert_kernel(const BMember *mem, const BChunk *chunks, int nchunks, const float *V, int R,
                                         int R_pad, const unsigned *colmax, __half *V16, int64_t v_cols, float *vinv,
-                                        const int *mdone) {
+                                        const int *mdone, int split) {
     const int c = blockIdx.y;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const BChunk k = chunks[ch];
@@ -1014,10 +1127,14 @@ __global__ void tc_group_convert_kernel(const BMember *mem, const BChunk *chunks
         const int64_t n_pad = rup(m.n, TM);
         const float *v = V + m.vo + (int64_t)c * m.n;
         __half *out = V16 + (int64_t)c * v_cols + m.cb;
+        __half *lo = split ? out + (int64_t)R_pad * v_cols : nullptr;  // low parts (split form)
         for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
             const int64_t i = (int64_t)k.start + r;
             if (i >= n_pad) break;
-            out[i] = __float2half_rn((c < R && i < m.n) ? v[i] * scale : 0.0f);
+            const float x = (c < R && i < m.n) ? v[i] * scale : 0.0f;
+            const __half h = __float2half_rn(x);
+            out[i] = h;
+            if (lo) lo[i] = __float2half_rn(x - __half2float(h));
         }
     }
 }
@@ -1040,9 +1157,10 @@ __global__ void tc_colmax_kernel(const float *V, int64_t ldv, int64_t n, int P, 
     }
 }
 
-// V16[c][j] = fp16(V[c][j] * 2^-e_c) for j < n, 0 up to n_pad and for c >= R.
+// V16[c][j] = fp16(V[c][j] * 2^-e_c) for j < n, 0 up to n_pad and for c >= R; with V16lo also
+// the low part fp16(V[c][j] * 2^-e_c - V16[c][j]) (the split form).
 __global__ void tc_convert_kernel(const float *V, int64_t ldv, int64_t n, int64_t n_pad, int R, int P,
-                                  const float *part, __half *V16, float *vinv, const int *done) {
+                                  const float *part, __half *V16, __half *V16lo, float *vinv, const int *done) {
     if (done && *done) return;
     const int c = blockIdx.y;
     float scale = 0.0f, inv = 1.0f;
@@ -1073,17 +1191,27 @@ __global__ void tc_convert_kernel(const float *V, int64_t ldv, int64_t n, int64_
              q += (int64_t)gridDim.x * blockDim.x) {
             float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (c < R && 4 * q < n) v = reinterpret_cast<const float4 *>(vc)[q];
-            __half2 lo = __floats2half2_rn(v.x * scale, v.y * scale), hi = __floats2half2_rn(v.z * scale, v.w * scale);
+            const float4 w = make_float4(v.x * scale, v.y * scale, v.z * scale, v.w * scale);
+            __half2 lo = __floats2half2_rn(w.x, w.y), hi = __floats2half2_rn(w.z, w.w);
             uint2 u;
             u.x = *reinterpret_cast<uint32_t *>(&lo);
             u.y = *reinterpret_cast<uint32_t *>(&hi);
             reinterpret_cast<uint2 *>(V16 + (int64_t)c * n_pad)[q] = u;
+            if (V16lo) {
+                const float2 fl = __half22float2(lo), fh = __half22float2(hi);
+                __half2 rl = __floats2half2_rn(w.x - fl.x, w.y - fl.y), rh = __floats2half2_rn(w.z - fh.x, w.w - fh.y);
+                u.x = *reinterpret_cast<uint32_t *>(&rl);
+                u.y = *reinterpret_cast<uint32_t *>(&rh);
+                reinterpret_cast<uint2 *>(V16lo + (int64_t)c * n_pad)[q] = u;
+            }
         }
         return;
     }
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += (int64_t)gridDim.x * blockDim.x) {
         float v = (c < R && j < n) ? vc[j] * scale : 0.0f;
-        V16[(int64_t)c * n_pad + j] = __float2half_rn(v);
+        const __half h = __float2half_rn(v);
+        V16[(int64_t)c * n_pad + j] = h;
+        if (V16lo) V16lo[(int64_t)c * n_pad + j] = __float2half_rn(v - __half2float(h));
     }
 }
 
@@ -1185,23 +1313,126 @@ size_t partial_floats(int split, int64_t n1, int R, int64_t row_tiles, int64_t c
     return split > 1 ? (size_t)split * R * n1 : 0;
 }
 
-// Split counts chosen by timing (gp_autotune_mvm), keyed by the product's shape in tiles;
-// they replace the model's choice wherever the caller's workspace holds their partial sums.
+// Choices of the autotuner (gp_autotune_mvm, gp_autotune_grad), keyed by kernel and shape:
+//   product  : (0, R_pad, row tiles, column tiles) -> split code (kPersist or column splits)
+//   gradient : (1, KD, KM, row tiles, symmetric)   -> tile pairs per item (symmetric sweep) or
+//                                                     column splits per row tile
+// They replace the built-in rules wherever the caller's workspace holds what they need.  The
+// table can be written to and read from a text file (gp_autotune_save / gp_autotune_load), and
+// is read at first use from the file named by GP_AUTOTUNE_CACHE (and written back to it after
+// every tuning call) when that variable is set.
+using TuneKey = std::array<int64_t, 5>;
 struct TuneTable {
     std::mutex mu;
-    std::map<std::tuple<int, int64_t, int64_t>, int> best;  // (R_pad, row tiles, col tiles) -> splits
+    std::map<TuneKey, int64_t> best;
+    bool env_loaded = false;
 };
 TuneTable &tune_table() {
     static TuneTable t;
     return t;
 }
-thread_local int g_force_split = 0;  // set by the autotuner while it times one candidate
+thread_local int g_force_split = 0;      // set by the autotuner while it times one candidate
+thread_local int64_t g_force_grad = 0;   // likewise for the gradient kernel's work split
 
-int tuned_split(int R_pad, int64_t row_tiles, int64_t col_tiles) {
+// Device identity written into (and checked against) a cache file.
+std::string tune_device_id() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return std::string("unknown");
+    }
+    std::string name(prop.name);
+    for (char &ch : name)
+        if (ch == ' ') ch = '_';
+    return name + "_sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_x" +
+           std::to_string(prop.multiProcessorCount);
+}
+
+// Reads a cache file into t (lock held).  Returns GP_OK, or GP_ERR_INVALID_ARG for a missing
+// or unreadable file, another device's file or a malformed line (the table is then unchanged).
+int tune_read_locked(TuneTable &t, const char *path) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) {
+        set_error("autotune cache %s cannot be opened", path);
+        return GP_ERR_INVALID_ARG;
+    }
+    char head[64] = {0}, dev[256] = {0};
+    int ver = 0;
+    if (std::fscanf(f, "%63s %d %255s", head, &ver, dev) != 3 || std::string(head) != "gp_gb300_autotune" ||
+        ver != 1) {
+        std::fclose(f);
+        set_error("autotune cache %s: not a version-1 cache file", path);
+        return GP_ERR_INVALID_ARG;
+    }
+    if (tune_device_id() != dev) {
+        std::fclose(f);
+        set_error("autotune cache %s was written on another device (%s)", path, dev);
+        return GP_ERR_INVALID_ARG;
+    }
+    std::map<TuneKey, int64_t> rd;
+    long long k0, k1, k2, k3, k4, v;
+    int got;
+    while ((got = std::fscanf(f, "%lld %lld %lld %lld %lld %lld", &k0, &k1, &k2, &k3, &k4, &v)) == 6)
+        rd[TuneKey{k0, k1, k2, k3, k4}] = v;
+    std::fclose(f);
+    if (got != EOF) {
+        set_error("autotune cache %s: malformed entry", path);
+        return GP_ERR_INVALID_ARG;
+    }
+    for (const auto &e : rd) t.best[e.first] = e.second;
+    return GP_OK;
+}
+
+int tune_write_locked(const TuneTable &t, const char *path) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) {
+        set_error("autotune cache %s cannot be written", path);
+        return GP_ERR_INVALID_ARG;
+    }
+    std::fprintf(f, "gp_gb300_autotune 1 %s\n", tune_device_id().c_str());
+    for (const auto &e : t.best)
+        std::fprintf(f, "%lld %lld %lld %lld %lld %lld\n", (long long)e.first[0], (long long)e.first[1],
+                     (long long)e.first[2], (long long)e.first[3], (long long)e.first[4], (long long)e.second);
+    const bool ok = std::fclose(f) == 0 && std::rename(tmp.c_str(), path) == 0;
+    if (!ok) {
+        set_error("autotune cache %s cannot be written", path);
+        return GP_ERR_INVALID_ARG;
+    }
+    return GP_OK;
+}
+
+// Reads GP_AUTOTUNE_CACHE once per process (lock held); a missing or unusable file leaves the
+// built-in rules in place.
+void tune_env_load_locked(TuneTable &t) {
+    if (t.env_loaded) return;
+    t.env_loaded = true;
+    const char *path = std::getenv("GP_AUTOTUNE_CACHE");
+    if (path && *path && tune_read_locked(t, path) != GP_OK) clear_error();
+}
+
+// The entry for key, or 0.
+int64_t tune_get(const TuneKey &key) {
     TuneTable &t = tune_table();
     std::lock_guard<std::mutex> g(t.mu);
-    auto it = t.best.find(std::make_tuple(R_pad, row_tiles, col_tiles));
+    tune_env_load_locked(t);
+    auto it = t.best.find(key);
     return it == t.best.end() ? 0 : it->second;
+}
+
+int tune_put(const TuneKey &key, int64_t v) {
+    tune_get(key);  // the environment's cache first, so that writing it back keeps its entries
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    t.best[key] = v;
+    const char *path = std::getenv("GP_AUTOTUNE_CACHE");
+    if (path && *path) return tune_write_locked(t, path);
+    return GP_OK;
+}
+
+int tuned_split(int R_pad, int64_t row_tiles, int64_t col_tiles) {
+    return (int)tune_get(TuneKey{0, R_pad, row_tiles, col_tiles, 0});
 }
 
 // The split a product of this shape uses: forced (autotuner), tuned, or the cost model.
@@ -1212,9 +1443,10 @@ int split_for(int R_pad, int64_t row_tiles, int64_t col_tiles) {
 }
 
 // Ring depths of the product kernel: up to 4 V slots (GEMM2 runs about two tiles behind
-// GEMM1), the rest of shared memory for PB slots (at most MAX_RING).
-void rings_for(int KD, int R_pad, int *npb, int *nv) {
-    const size_t a = (size_t)TM * KD * 2, b = (size_t)TN * KD * 2, v = 2 * (size_t)R_pad * 128;
+// GEMM1), the rest of shared memory for PB slots (at most MAX_RING).  The split form's V slot
+// holds the high and the low parts (twice the bytes).
+void rings_for(int KD, int R_pad, int *npb, int *nv, bool split = false) {
+    const size_t a = (size_t)TM * KD * 2, b = (size_t)TN * KD * 2, v = (split ? 4 : 2) * (size_t)R_pad * 128;
     const size_t budget = kMaxDynSmem - 4096 - a;
     int nvv = 4;
     while (nvv > 2 && nvv * v + 3 * b > budget) --nvv;
@@ -1223,23 +1455,41 @@ void rings_for(int KD, int R_pad, int *npb, int *nv) {
     *npb = (int)std::min<size_t>(MAX_RING, left / b);
 }
 
-size_t smem_for(int KD, int R_pad, int npb, int nv) {
-    return 1024 + (size_t)TM * KD * 2 + (size_t)npb * TN * KD * 2 + (size_t)nv * 2 * R_pad * 128 + 512;
+size_t smem_for(int KD, int R_pad, int npb, int nv, bool split = false) {
+    return 1024 + (size_t)TM * KD * 2 + (size_t)npb * TN * KD * 2 + (size_t)nv * (split ? 4 : 2) * R_pad * 128 + 512;
 }
 
-template <int KIND, int KAT, bool PERSIST>
+// Right-hand sides per pass of the split form for a contraction width KD: the largest multiple
+// of 16 (at most kMaxRhsPerPass) whose rings fit shared memory.
+int split_rhs_per_pass(int KD) {
+    for (int r = kSplitMaxRpad; r >= 16; r -= 16) {
+        int npb = 0, nv = 0;
+        rings_for(KD, r, &npb, &nv, true);
+        if (npb >= 2 && nv >= 2) return r;
+    }
+    return 0;
+}
+
+template <int KIND, int KAT, bool PERSIST, bool SPLIT>
 int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mV,
                       const KParams &kp, cudaStream_t st) {
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<KIND, KAT, PERSIST>));
-    tc_mvm_kernel<KIND, KAT, PERSIST><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<KIND, KAT, PERSIST, SPLIT>));
+    tc_mvm_kernel<KIND, KAT, PERSIST, SPLIT><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
     return GP_OK;
 }
 
 template <int KIND, int KAT>
 int launch_mvm_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mV,
-                      const KParams &kp, cudaStream_t st) {
-    return kp.persist ? launch_mvm_kernel<KIND, KAT, true>(grid, smem, mA, mB, mV, kp, st)
-                      : launch_mvm_kernel<KIND, KAT, false>(grid, smem, mA, mB, mV, kp, st);
+                      const KParams &kp, bool split, cudaStream_t st) {
+    if (split) {  // the split form runs a single segment per CTA (no persistent schedule)
+        if (kp.persist) {
+            set_error("internal: the split product has no persistent schedule");
+            return GP_ERR_UNSUPPORTED;
+        }
+        return launch_mvm_kernel<KIND, KAT, false, true>(grid, smem, mA, mB, mV, kp, st);
+    }
+    return kp.persist ? launch_mvm_kernel<KIND, KAT, true, false>(grid, smem, mA, mB, mV, kp, st)
+                      : launch_mvm_kernel<KIND, KAT, false, false>(grid, smem, mA, mB, mV, kp, st);
 }
 
 }  // namespace
@@ -1415,7 +1665,7 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
 size_t tc_mvm_workspace_for(int64_t n1, int64_t p2, int R, int nsplit) {
     const int R_pad = rpad_for(std::min(R, kMaxRhsPerPass));
     Carver c(nullptr);
-    c.take<__half>((size_t)R_pad * p2);
+    c.take<__half>((size_t)2 * R_pad * p2);  // V16: high parts, then the split form's low parts
     c.take<float>(256);
     c.take<float>((size_t)std::min(R, kMaxRhsPerPass) * 64);
     c.take<int>(1);
@@ -1431,10 +1681,12 @@ size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
     const int64_t row_tiles = cdiv(std::max<int64_t>(n1, 1), TM), col_tiles = cdiv(p2, TN);
     // room for the partial sums of both the tuned and the model's choice
     const int s1 = split_for(R_pad, row_tiles, col_tiles), s2 = pick_split(row_tiles, col_tiles);
-    const size_t pf = std::max(partial_floats(s1, n1, R, row_tiles, col_tiles),
-                               partial_floats(s2, n1, R, row_tiles, col_tiles));
+    const int s3 = pick_uniform_split(row_tiles, col_tiles, nullptr);  // the split form's schedule
+    const size_t pf = std::max(std::max(partial_floats(s1, n1, R, row_tiles, col_tiles),
+                                        partial_floats(s2, n1, R, row_tiles, col_tiles)),
+                               partial_floats(s3, n1, std::min(R, kSplitMaxRpad), row_tiles, col_tiles));
     Carver c(nullptr);
-    c.take<__half>((size_t)R_pad * p2);            // V16
+    c.take<__half>((size_t)2 * R_pad * p2);        // V16 (high parts; low parts of the split form)
     c.take<float>(256);                            // vinv
     c.take<float>((size_t)R * 64);                 // column max partials
     c.take<int>(1);                                // error flag
@@ -1443,12 +1695,18 @@ size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
 }
 
 int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
-    if (a.R > kMaxRhsPerPass) {
-        // wide blocks of right-hand sides: kMaxRhsPerPass at a time (the Y accumulator's
-        // share of tensor memory)
-        for (int c0 = 0; c0 < a.R; c0 += kMaxRhsPerPass) {
+    // right-hand sides per pass: the Y accumulator's share of tensor memory; for the split form
+    // also what its doubled V slots leave of shared memory
+    const int per_pass = a.split ? std::min(kMaxRhsPerPass, split_rhs_per_pass(a.rows.KD)) : kMaxRhsPerPass;
+    if (per_pass < 1) {
+        set_error("split tensor-core product: tile does not fit shared memory (KD=%d)", a.rows.KD);
+        return GP_ERR_UNSUPPORTED;
+    }
+    if (a.R > per_pass) {
+        // wide blocks of right-hand sides: per_pass at a time
+        for (int c0 = 0; c0 < a.R; c0 += per_pass) {
             TcMvmArgs b = a;
-            b.R = std::min(kMaxRhsPerPass, a.R - c0);
+            b.R = std::min(per_pass, a.R - c0);
             b.V = a.V + (int64_t)c0 * a.ldv;
             b.Y = a.Y + (int64_t)c0 * a.ldy;
             b.Vd = a.Vd ? a.Vd + (int64_t)c0 * a.ldvd : nullptr;
@@ -1462,25 +1720,26 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int R_pad = rpad_for(a.R);
     const int64_t p2 = rup(std::max<int64_t>(n2, 1), TN);
     const int64_t row_tiles = cdiv(n1, TM), col_tiles = cdiv(p2, TN);
-    int nsplit = split_for(R_pad, row_tiles, col_tiles);
+    // the split form takes column splits only (its group read-out has one segment per CTA)
+    int nsplit = a.split ? pick_uniform_split(row_tiles, col_tiles, nullptr) : split_for(R_pad, row_tiles, col_tiles);
     {
         // a tuned split whose partial sums do not fit the caller's workspace falls back to
         // the model's choice
         Carver probe(nullptr);
-        probe.take<__half>((size_t)R_pad * p2);
+        probe.take<__half>((size_t)2 * R_pad * p2);
         probe.take<float>(256);
         probe.take<float>((size_t)a.R * 64);
         probe.take<int>(1);
         const size_t pf = partial_floats(nsplit, n1, a.R, row_tiles, col_tiles);
         if (pf > 0) probe.take<float>(pf);
-        if (probe.bytes() > ws_bytes && g_force_split == 0) nsplit = pick_split(row_tiles, col_tiles);
+        if (probe.bytes() > ws_bytes && g_force_split == 0) nsplit = a.split ? 1 : pick_split(row_tiles, col_tiles);
     }
     const bool persist = (nsplit == kPersist);
     int pgrid = 0, pseg = 0;
     if (persist) persist_geom(row_tiles, col_tiles, &pgrid, &pseg);
     const size_t pfl = partial_floats(nsplit, n1, a.R, row_tiles, col_tiles);
     Carver c(ws);
-    __half *V16 = c.take<__half>((size_t)R_pad * p2);
+    __half *V16 = c.take<__half>((size_t)2 * R_pad * p2);  // rows [0, R_pad): high; [R_pad, 2 R_pad): low
     float *vinv = c.take<float>(256);
     float *cm = c.take<float>((size_t)a.R * 64);
     c.take<int>(1);  // (kept for the workspace layout)
@@ -1490,15 +1749,15 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
     tc_colmax_kernel<<<dim3(P, a.R), 256, 0, st>>>(a.V, a.ldv, n2, P, cm, a.done);
     tc_convert_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(p2, 1024), 256), R_pad), 256, 0, st>>>(
-        a.V, a.ldv, n2, p2, a.R, P, cm, V16, vinv, a.done);
+        a.V, a.ldv, n2, p2, a.R, P, cm, V16, a.split ? V16 + (size_t)R_pad * p2 : nullptr, vinv, a.done);
     GP_TRY(check_launch("tc rhs conversion", 2));
 
     CUtensorMap mA, mB, mV;
     GP_TRY(make_map(&mA, a.rows.PA, KD, a.rows.n_pad, 64, TM));
     GP_TRY(make_map(&mB, a.cols.PB, KD, a.cols.n_pad, 64, TN));
-    GP_TRY(make_map(&mV, V16, p2, R_pad, 64, R_pad));
+    GP_TRY(make_map(&mV, V16, p2, a.split ? 2 * R_pad : R_pad, 64, R_pad));
     int npb = 0, nv = 0;
-    rings_for(KD, R_pad, &npb, &nv);
+    rings_for(KD, R_pad, &npb, &nv, a.split);
     if (npb < 2 || nv < 2) {
         set_error("tensor-core tile does not fit shared memory (d=%d, R=%d)", (KD - 4) / 3, a.R);
         return GP_ERR_UNSUPPORTED;
@@ -1533,7 +1792,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.col0_dev = a.col0_dev;
     kp.diag_from_col0 = a.diag_from_col0;
     kp.ncols_total = a.cols.n;
-    const size_t smem = smem_for(KD, R_pad, npb, nv);
+    const size_t smem = smem_for(KD, R_pad, npb, nv, a.split);
     dim3 grid = persist ? dim3((unsigned)pgrid, 1) : dim3((unsigned)row_tiles, (unsigned)nsplit);
     const int kat = KD / 64;
     if (kat > 3) {
@@ -1542,13 +1801,13 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     }
     prof_begin(st);
     if (a.kind == GP_RBF) {
-        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_RBF, 1>(grid, smem, mA, mB, mV, kp, st));
-        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_RBF, 2>(grid, smem, mA, mB, mV, kp, st));
-        else GP_TRY(launch_mvm_kernel<GP_RBF, 3>(grid, smem, mA, mB, mV, kp, st));
+        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_RBF, 1>(grid, smem, mA, mB, mV, kp, a.split != 0, st));
+        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_RBF, 2>(grid, smem, mA, mB, mV, kp, a.split != 0, st));
+        else GP_TRY(launch_mvm_kernel<GP_RBF, 3>(grid, smem, mA, mB, mV, kp, a.split != 0, st));
     } else {
-        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_MATERN32, 1>(grid, smem, mA, mB, mV, kp, st));
-        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_MATERN32, 2>(grid, smem, mA, mB, mV, kp, st));
-        else GP_TRY(launch_mvm_kernel<GP_MATERN32, 3>(grid, smem, mA, mB, mV, kp, st));
+        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_MATERN32, 1>(grid, smem, mA, mB, mV, kp, a.split != 0, st));
+        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_MATERN32, 2>(grid, smem, mA, mB, mV, kp, a.split != 0, st));
+        else GP_TRY(launch_mvm_kernel<GP_MATERN32, 3>(grid, smem, mA, mB, mV, kp, a.split != 0, st));
     }
     prof_end(st);
     GP_TRY(check_launch("tc_mvm_kernel"));
@@ -1629,11 +1888,7 @@ int tc_autotune(const TcMvmArgs &a, int reps, void *ws, size_t ws_bytes, cudaStr
         set_error("autotune: the workspace holds no candidate");
         return GP_ERR_WORKSPACE;
     }
-    {
-        TuneTable &t = tune_table();
-        std::lock_guard<std::mutex> g(t.mu);
-        t.best[std::make_tuple(R_pad, row_tiles, col_tiles)] = best;
-    }
+    GP_TRY(tune_put(TuneKey{0, R_pad, row_tiles, col_tiles, 0}, best));
     *best_split = best;
     *best_ms = best_t;
     return GP_OK;
@@ -1650,23 +1905,56 @@ void tc_autotune_reset() {
     TuneTable &t = tune_table();
     std::lock_guard<std::mutex> g(t.mu);
     t.best.clear();
+    t.env_loaded = true;  // a reset table stays empty (the environment's cache is not re-read)
+}
+
+int tc_autotune_save(const char *path) {
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    return tune_write_locked(t, path);
+}
+
+int tc_autotune_load(const char *path) {
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    t.env_loaded = true;
+    return tune_read_locked(t, path);
+}
+
+int64_t tc_autotune_count() {
+    TuneTable &t = tune_table();
+    std::lock_guard<std::mutex> g(t.mu);
+    tune_env_load_locked(t);
+    return (int64_t)t.best.size();
 }
 
 // Grouped product over a batch of independent GPs: one CTA per work item (128 rows of a
 // member against a run of its own column tiles), items ordered longest first so the
 // block scheduler fills the SMs like a longest-processing-time list schedule.
 int tc_group_setup() {
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 1>));
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 2>));
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 3>));
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 1>));
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 2>));
-    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 3>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 1, false, false>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 2, false, false>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 3, false, false>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 1, false, false>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 2, false, false>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 3, false, false>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 1, false, true>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 2, false, true>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_RBF, 3, false, true>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 1, false, true>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 2, false, true>));
+    GP_TRY(ensure_max_dyn_smem((const void *)tc_mvm_kernel<GP_MATERN32, 3, false, true>));
     return GP_OK;
 }
 
+bool tc_split_fits_rpad(int R_pad) { return R_pad <= kSplitMaxRpad; }
+
 int tc_group_mvm(const TcGroupArgs &a, cudaStream_t st) {
     if (a.nitems == 0) return GP_OK;
+    if (a.split && a.R_pad > kSplitMaxRpad) {
+        set_error("split batched product supports at most %d right-hand sides", kSplitMaxRpad);
+        return GP_ERR_UNSUPPORTED;
+    }
     if (a.R > kMaxRhsPerPass) {
         set_error("batched product supports at most %d right-hand sides", kMaxRhsPerPass);
         return GP_ERR_UNSUPPORTED;
@@ -1680,9 +1968,9 @@ int tc_group_mvm(const TcGroupArgs &a, cudaStream_t st) {
     CUtensorMap mA, mB, mV;
     GP_TRY(make_map(&mA, a.PA, a.KD, a.class_rows, 64, TM));
     GP_TRY(make_map(&mB, a.PB, a.KD, a.class_rows, 64, TN));
-    GP_TRY(make_map(&mV, a.V16, a.v_cols, a.R_pad, 64, a.R_pad));
+    GP_TRY(make_map(&mV, a.V16, a.v_cols, a.split ? 2 * a.R_pad : a.R_pad, 64, a.R_pad));
     int npb = 0, nv = 0;
-    rings_for(a.KD, a.R_pad, &npb, &nv);
+    rings_for(a.KD, a.R_pad, &npb, &nv, a.split != 0);
     if (npb < 2 || nv < 2) {
         set_error("tensor-core tile does not fit shared memory (KD=%d, R=%d)", a.KD, a.R);
         return GP_ERR_UNSUPPORTED;
@@ -1704,17 +1992,18 @@ int tc_group_mvm(const TcGroupArgs &a, cudaStream_t st) {
     kp.items = a.items;
     kp.members = a.members;
     kp.mdone = a.mdone;
-    const size_t smem = smem_for(a.KD, a.R_pad, npb, nv);
+    const size_t smem = smem_for(a.KD, a.R_pad, npb, nv, a.split != 0);
     dim3 grid((unsigned)a.nitems, 1);
+    const bool sp = a.split != 0;
     prof_begin(st);
     if (a.kind == GP_RBF) {
-        if (kat == 1) tc_mvm_kernel<GP_RBF, 1><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
-        else if (kat == 2) tc_mvm_kernel<GP_RBF, 2><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
-        else tc_mvm_kernel<GP_RBF, 3><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_RBF, 1>(grid, smem, mA, mB, mV, kp, sp, st));
+        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_RBF, 2>(grid, smem, mA, mB, mV, kp, sp, st));
+        else GP_TRY(launch_mvm_kernel<GP_RBF, 3>(grid, smem, mA, mB, mV, kp, sp, st));
     } else {
-        if (kat == 1) tc_mvm_kernel<GP_MATERN32, 1><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
-        else if (kat == 2) tc_mvm_kernel<GP_MATERN32, 2><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
-        else tc_mvm_kernel<GP_MATERN32, 3><<<grid, MVM_THREADS, smem, st>>>(mA, mB, mV, kp);
+        if (kat == 1) GP_TRY(launch_mvm_kernel<GP_MATERN32, 1>(grid, smem, mA, mB, mV, kp, sp, st));
+        else if (kat == 2) GP_TRY(launch_mvm_kernel<GP_MATERN32, 2>(grid, smem, mA, mB, mV, kp, sp, st));
+        else GP_TRY(launch_mvm_kernel<GP_MATERN32, 3>(grid, smem, mA, mB, mV, kp, sp, st));
     }
     prof_end(st);
     return check_launch("tc_mvm_kernel (batched)");
@@ -1739,13 +2028,14 @@ int tc_group_prepare(int kind, BMember *members, int G, const BChunk *chunks, in
 
 int tc_group_convert(const BMember *members, int G, const BChunk *chunks, int nchunks, const float *V, int R,
                      int R_pad, unsigned *colmax, void *V16, int64_t v_cols, float *vinv, const int *mdone,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool split) {
     if (nchunks == 0) return GP_OK;
     GP_TRY_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned) * (size_t)G * R_pad, st));
     const unsigned nb = (unsigned)std::min(nchunks, 4 * num_sms_tc());
     tc_group_colmax_kernel<<<dim3(nb, R), 256, 0, st>>>(members, chunks, nchunks, V, R, R_pad, colmax, mdone);
     tc_group_convert_kernel<<<dim3(nb, R_pad), 256, 0, st>>>(members, chunks, nchunks, V, R, R_pad, colmax,
-                                                            static_cast<__half *>(V16), v_cols, vinv, mdone);
+                                                            static_cast<__half *>(V16), v_cols, vinv, mdone,
+                                                            split ? 1 : 0);
     return check_launch("batched rhs conversion", 2);
 }
 
@@ -2216,9 +2506,11 @@ __global__ void tc_b3_kernel(const KP<float> kp, const float *X, int64_t n, int6
 struct GradPlanTc {
     int KD, KM, N3p, ns, nb3, nsplit;
     int64_t n_pad, row_tiles, col_tiles;
-    int64_t sym_h, sym_items;  // symmetric sweep: tiles pairs per item (x 2 column tiles), items
+    int64_t sym_h, sym_items;  // symmetric sweep: tile pairs per item (x 2 column tiles), items
+    int64_t max_blocks;        // CTAs (partial sums) the workspace provides for
     size_t smem;
 };
+constexpr int kGradMaxSplit = 8;  // column splits per row tile the gradient's workspace covers
 
 template <int KIND, int KAT>
 int launch_grad_kernel(dim3 grid, size_t smem, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mU,
@@ -2242,6 +2534,9 @@ GradPlanTc plan_tc_grad(int64_t n, int d, int R) {
     const int64_t waves = 6 * (int64_t)num_sms_tc();
     g.sym_h = std::max<int64_t>(8, cdiv(g.row_tiles * g.row_tiles, 2 * waves));
     g.sym_items = sym_items_upto(g.row_tiles, g.sym_h);
+    // room for the autotuner's candidates: up to kGradMaxSplit splits, up to 32 waves of items
+    g.max_blocks = std::max<int64_t>(g.row_tiles * std::max(g.nsplit, kGradMaxSplit),
+                                     std::max<int64_t>(g.sym_items, 32 * (int64_t)num_sms_tc()));
     const size_t a = (size_t)TM * g.KD * 2 + (size_t)TM * g.KM * 2;
     const size_t st = (size_t)GTN * g.KD * 2 + (size_t)GTN * g.KM * 2;
     const size_t b3 = (size_t)g.N3p * 128;
@@ -2274,7 +2569,7 @@ size_t tc_grad_workspace(int64_t n, int d, int R) {
     c.take<unsigned int>(2);
     c.take<float>(1);
     c.take<int>(1);
-    c.take<double>((size_t)std::max<int64_t>(g.row_tiles * g.nsplit, g.sym_items) * (d + 1));
+    c.take<double>((size_t)g.max_blocks * (d + 1));
     c.take<double>(256);
     return c.bytes();
 }
@@ -2299,8 +2594,18 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     // U and W the same block with one lambda per column (the pathwise estimator): M and the
     // summand are symmetric in i and j, so the upper triangle of tiles suffices
     const bool sym = a.U0 == a.W0 && a.U == a.W && (a.R == 1 || a.ldu == a.ldw);
+    // work split: forced (autotuner), tuned, or the built-in rule -- within the workspace
+    {
+        int64_t v = g_force_grad != 0 ? g_force_grad : tune_get(TuneKey{1, g.KD, g.KM, g.row_tiles, sym ? 1 : 0});
+        if (sym && v >= 1 && sym_items_upto(g.row_tiles, v) <= g.max_blocks) {
+            g.sym_h = v;
+            g.sym_items = sym_items_upto(g.row_tiles, v);
+        } else if (!sym && v >= 1 && v <= g.col_tiles && g.row_tiles * v <= g.max_blocks) {
+            g.nsplit = (int)v;
+        }
+    }
     const int nblocks = (int)(sym ? g.sym_items : g.row_tiles * g.nsplit);
-    double *partial = c.take<double>((size_t)std::max<int64_t>(g.row_tiles * g.nsplit, g.sym_items) * (d + 1));
+    double *partial = c.take<double>((size_t)g.max_blocks * (d + 1));
     double *dpart = c.take<double>(256);
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
@@ -2358,6 +2663,72 @@ int tc_grad(const GradArgs<float> &a, void *ws, size_t ws_bytes, cudaStream_t st
     prof_end(st);
     GP_TRY(check_launch("tc_grad_kernel"));
     return grad_tail<float>(a, nblocks, partial, dpart, st);
+}
+
+// Times the tensor-core gradient for a ladder of work splits (tile pairs per item of the
+// symmetric sweep, or column splits per row tile) and records the fastest for the shape.
+// Synchronises `st`; not for use inside a stream capture.
+int tc_autotune_grad(const GradArgs<float> &a, int reps, void *ws, size_t ws_bytes, cudaStream_t st, int64_t *best_v,
+                     double *best_ms) {
+    const int d = a.kp.d;
+    if (!tc_grad_fits(a.n, d, a.R)) {
+        set_error("autotune: the tensor-core gradient does not cover d=%d, R=%d", d, a.R);
+        return GP_ERR_UNSUPPORTED;
+    }
+    const GradPlanTc g = plan_tc_grad(a.n, d, a.R);
+    const bool sym = a.U0 == a.W0 && a.U == a.W && (a.R == 1 || a.ldu == a.ldw);
+    std::vector<int64_t> cand;
+    if (sym) {
+        const int64_t RT = g.row_tiles, sms = num_sms_tc();
+        for (double w : {1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0, 16.0, 24.0, 32.0}) {
+            const int64_t h = std::max<int64_t>(2, (int64_t)std::ceil((double)RT * RT / (2.0 * w * sms)));
+            if (sym_items_upto(RT, h) <= g.max_blocks) cand.push_back(h);
+        }
+    } else {
+        for (int k = 1; k <= kGradMaxSplit; ++k)
+            if (k <= g.col_tiles && g.row_tiles * k <= g.max_blocks) cand.push_back(k);
+    }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GP_TRY_CUDA(cudaEventCreate(&e0));
+    GP_TRY_CUDA(cudaEventCreate(&e1));
+    int64_t best = 0;
+    double best_t = 1e300;
+    int rc = GP_OK;
+    for (int64_t v : cand) {
+        g_force_grad = v;
+        double t_min = 1e300;
+        for (int r = 0; r <= reps && rc == GP_OK; ++r) {  // the first run is a warm-up
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = GP_ERR_CUDA;
+            if (rc == GP_OK) rc = tc_grad(a, ws, ws_bytes, st);
+            if (rc == GP_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = GP_ERR_CUDA;
+            if (rc == GP_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = GP_ERR_CUDA;
+            float ms = 0.0f;
+            if (rc == GP_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = GP_ERR_CUDA;
+            if (rc == GP_OK && r > 0) t_min = std::min(t_min, (double)ms);
+        }
+        g_force_grad = 0;
+        if (rc != GP_OK) break;
+        if (t_min < best_t) {
+            best_t = t_min;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GP_OK) {
+        set_error("autotune: a timed gradient failed");
+        return rc;
+    }
+    if (best == 0) {
+        set_error("autotune: no candidate work split");
+        return GP_ERR_UNSUPPORTED;
+    }
+    GP_TRY(tune_put(TuneKey{1, g.KD, g.KM, g.row_tiles, sym ? 1 : 0}, best));
+    *best_v = best;
+    *best_ms = best_t;
+    return GP_OK;
 }
 
 }  // namespace gp

@@ -118,8 +118,8 @@ def test_batch_cg_reaches_tolerance_with_true_residual(dev):
         r = Br - oracle.kernel_mvm(0, thg, Xr, Xr, Vg.double().cpu().numpy(), add_noise=True)
         rn = np.linalg.norm(r, axis=1) / np.linalg.norm(Br, axis=1)
         assert rn[0] <= 1e-2 and rn[1:].mean() <= 1e-2, (g, rn)
-        # reported norms: the member's true residual on the tensor-core operator
-        assert abs(info[g]["res_y"] - rn[0]) <= 3e-3 and abs(info[g]["res_z"] - rn[1:].mean()) <= 3e-3, (g, info[g])
+        # reported norms: the member's true residual, taken with the split tensor-core product
+        assert abs(info[g]["res_y"] - rn[0]) <= 1e-4 and abs(info[g]["res_z"] - rn[1:].mean()) <= 1e-4, (g, info[g])
 
 
 def test_batch_cg_members_stop_independently(dev):
