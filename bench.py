@@ -506,7 +506,22 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms, clk_mhz, cpu_seconds):
+def run_solver_workload(args):
+    """The alternating-projection or SGD workload on its own (python bench.py --workload ap|sgd):
+    solver_record's line.  --solver-iters overrides the iteration budget (for profiling)."""
+    torch, gp, workloads, dev = _gpu_setup()
+    rates = gp.gp_diag_unit_rates(4096)
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = solver_record(torch, gp, workloads, dev, args.workload, rates, peaks, peak_src, sms,
+                        peaks.get("sm_max_mhz", 2070.0), args.cpu_seconds, iters_override=args.solver_iters)
+    out.update({"n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f16-tensor/f32/f64", "data": "synthetic (seeded)"})
+    print(json.dumps(out))
+
+
+def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms, clk_mhz, cpu_seconds,
+                  iters_override=0):
     """One warm-started pathwise marginal-likelihood step of the alternating-projection workload
     (which = "ap": n = 262144, d = 26, RBF, AP with 1024-row blocks, a budget of 10 epochs = 2560
     block iterations; Alg. 2, Sec. 5 "The Effects of Early Stopping") or the SGD workload
@@ -518,6 +533,8 @@ def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms,
     n, d, R = p.n, p.d, p.s + 1
     bs = 1024 if which == "ap" else 512
     iters = 10 * n // bs if which == "ap" else 1000
+    if iters_override:
+        iters = iters_override
     tf = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
     X = tf(p.X)
     om, c2, Wp, w = tf(p.omega_hat), tf(p.chi2), tf(p.W_probe), tf(p.Z)
@@ -541,8 +558,9 @@ def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms,
                                   prec=gp.GP_PREC_TC16)
         return gp.gp_solve_sgd(p.kind, th, X, B, idx, lr=lr, momentum=0.9, V0=V, tol=0.01, prec=gp.GP_PREC_TC16)
 
-    # untimed first solve (the warm start), and the SGD step size: the largest of the grid that does
-    # not diverge on it (App. B "Stochastic Gradient Descent"; the reading of the paper's rule)
+    # untimed first step (cold solve, gradient, Adam), which gives the timed step its warm start
+    # at new hyperparameters; the SGD step size is the largest of the grid that does not diverge
+    # on the first solve (App. B "Stochastic Gradient Descent"; the reading of the paper's rule)
     B = rhs(theta)
     if which == "sgd":
         for lr in (50.0, 20.0, 10.0, 5.0, 2.0, 1.0, 0.5):
@@ -555,6 +573,9 @@ def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms,
                 continue
     else:
         solve(theta, B)
+    g = gp.gp_mll_grad_pathwise(p.kind, theta, X, V, prec=gp.GP_PREC_TC16)
+    lr_adam = 0.1 if n < 50000 else 0.03  # App. B "Iterative Optimiser": 0.03 above 50k points
+    theta = gp.gp_adam_softplus_step(nu, m_, v_, 1, g.cpu().numpy(), lr=lr_adam)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
@@ -565,7 +586,7 @@ def solver_record(torch, gp, workloads, dev, which, rates, peaks, peak_src, sms,
     g = gp.gp_mll_grad_pathwise(p.kind, theta, X, V, prec=gp.GP_PREC_TC16)
     gh = g.cpu().numpy()
     ev[3].record()
-    theta = gp.gp_adam_softplus_step(nu, m_, v_, 1, gh, lr=0.1)
+    theta = gp.gp_adam_softplus_step(nu, m_, v_, 2, gh, lr=lr_adam)
     torch.cuda.synchronize()
     step_s = ev[0].elapsed_time(ev[3]) / 1e3
     solve_s = ev[1].elapsed_time(ev[2]) / 1e3
@@ -1130,7 +1151,8 @@ def run_op(args):
     right-hand sides, seeded synthetic inputs), `repeat` calls, for profilers (a capture of one
     kernel on a case that ends in seconds): mvm (gp_kernel_mvm, H V), grad (gp_mll_grad_pathwise),
     rff (gp_rff_prior_sample), cg (gp_solve_cg, 10 iterations), unit-rates (gp_diag_unit_rates).
-    --time prints the mean time per call (CUDA events)."""
+    Prints the mean time per call (CUDA events).  --autotune tunes the shape first; with
+    GP_AUTOTUNE_CACHE set the choice is saved, and a later run (under a profiler) reads it."""
     import torch
 
     import paper_2405_18457_gb300 as gp
@@ -1169,6 +1191,13 @@ def run_op(args):
         else:
             gp.gp_solve_cg(p.kind, p.theta, X, V, max_iters=10, tol=0.0, prec=prec)
 
+    if args.autotune:
+        # record this shape's tuned choices (written to GP_AUTOTUNE_CACHE when set, so that a later
+        # process -- a profiler run -- uses them without tuning)
+        if args.op in ("mvm", "cg"):
+            gp.gp_autotune_mvm(p.kind, p.theta, X, V, reps=3)
+        if args.op == "grad":
+            gp.gp_autotune_grad(p.kind, p.theta, X, V, None, reps=3)
     call()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -1199,10 +1228,12 @@ def main():
     ap.add_argument("--no-subrecords", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--kernel-reps", type=int, default=10)
-    ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation", "diagnostics"],
+    ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation", "diagnostics", "ap", "sgd"],
                     default="pathwise")
+    ap.add_argument("--solver-iters", type=int, default=0, help="--workload ap|sgd: iteration budget override")
     ap.add_argument("--op", choices=["mvm", "grad", "rff", "cg", "unit-rates"], default=None)
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--autotune", action="store_true", help="--op: tune the operation's shape first")
     ap.add_argument("--abl-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-gps", type=int, default=256)
@@ -1230,6 +1261,9 @@ def main():
         return
     if args.workload == "diagnostics":
         run_diagnostics(args)
+        return
+    if args.workload in ("ap", "sgd"):
+        run_solver_workload(args)
         return
     run_ours(args)
 

@@ -222,10 +222,10 @@ size_t gp_kernel_mvm_f64_workspace(int64_t n1, int64_t n2, int d, int nrhs);
  * b~ - H v is recomputed once (one product, FP64 differences and norms) and the
  * tolerance is judged on it: a solve whose true residual misses tau restarts from
  * it (d = r) within its budget, and info's res_y / res_z are always true-residual
- * norms.  The true residual (like the initial one of a warm start) is taken with
- * an FP32-class product: the split tensor-core product (GP_PREC_TC16X3) for
- * GP_PREC_TC16, the FP64 product of the FP32 inputs for GP_PREC_FP32, the FP64
- * product for the FP64 form.  A restart that does not lower the true residual by
+ * norms.  That true residual is taken with an FP32-class product: the split
+ * tensor-core product (GP_PREC_TC16X3) for GP_PREC_TC16, the FP64 product of the
+ * FP32 inputs for GP_PREC_FP32, the FP64 product for the FP64 form (the initial
+ * residual of a warm start uses the form's own product).  A restart that does not lower the true residual by
  * 10% ends the solve (not converged): the form's arithmetic has reached what it
  * can attain on the system.  Returns GP_OK with info filled (synchronises
  * stream), GP_ERR_BREAKDOWN if a residual becomes non-finite. */
@@ -269,7 +269,7 @@ size_t gp_solve_pcg_f64_workspace(int64_t n, int d, int nrhs, int rank);
  * (epochs x n / block_size).  1 <= block_size <= 1024.  When the loop stops on the
  * residual the panels maintain, the true residual is recomputed (one full product
  * of the FP32 class, as in gp_solve_cg; not counted in max_iters) and judged as in
- * gp_solve_cg; so is the initial residual of a warm start. */
+ * gp_solve_cg. */
 int gp_solve_ap(int kind, const double *theta, int d, const float *X, int64_t n,
                 const float *B, int nrhs, float *V_inout, int64_t block_size, int64_t max_iters,
                 double tol, int stop_rule, int prec, gp_solve_info_t *info,
@@ -412,7 +412,8 @@ size_t gp_bilinear_grad_f64_workspace(int64_t n, int d, int R);
  * process exit).  With prec = GP_PREC_FP32 the scratch holds only block partial
  * sums, enough for n up to about 3.9 million points at d = 16 (2 million at
  * d = 32); with GP_PREC_TC16 it also holds the fp16 tensor-core operands (about
- * 0.9 KB per point at d = 16, s = 64), enough for n up to about 9000 points.
+ * 0.9 KB per point at d = 16, s = 64) and the work-split partials, enough for n
+ * up to about 8500 points.
  * gp_mll_grad_workspace(n, d, s, prec) is the amount a call needs.  Requests
  * that need more return GP_ERR_INVALID_ARG with the
  * required size in gp_last_error().  The first call on each device looks up the
@@ -540,9 +541,9 @@ int gp_batch_mvm(gp_batch_t *b, const float *V, float *Y, int add_noise, cudaStr
  * condition fails is skipped from then on.  Every 10 iterations and after the
  * last one, the true residual of each member that stopped on its recursive
  * residual is recomputed (one grouped product over those members); a member whose
- * true residual misses the tolerance restarts from it.  True residuals (and the
- * initial residual) use the split tensor-core product when s + 1 <= 80 (the plain
- * one above), and the reported norms are true-residual norms.  info: DEVICE array of G reports (or
+ * true residual misses the tolerance restarts from it.  These checks use the split
+ * tensor-core product when s + 1 <= 80 (the plain one above; the initial residual
+ * always the plain one), and the reported norms are true-residual norms.  info: DEVICE array of G reports (or
  * NULL), written at the end. */
 int gp_batch_solve_cg(gp_batch_t *b, const float *B, float *V_inout, int64_t iters, double tol,
                       int stop_rule, gp_solve_info_t *info, cudaStream_t stream);

@@ -315,7 +315,7 @@ __global__ void ap_norm_kernel(int R, int P, const double *part, SolverState *st
         st->status = GP_OK;
     }
     finish_norms(st, sq, R, first ? 0 : st->iter + 1, max_iters, tol, stop_rule);
-    if (first) st->certified = 1;  // the initial residual b~ - H v0 is a true residual
+    if (first == 2) st->certified = 1;  // the initial residual came from an exact-class product
 }
 
 }  // namespace
@@ -386,8 +386,10 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
 
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
     const dim3 gp_((unsigned)P, (unsigned)R);
-    // true residuals (initial and final) of the tensor-core form use its split products
+    // the true residual the tolerance is judged on: the tensor-core form's split product (the
+    // initial residual uses the form's own product; the final check catches its error)
     const int prec_true = prec == GP_PREC_TC16 ? GP_PREC_TC16X3 : prec;
+    const bool exact_start = !(std::is_same<T, float>::value && (prec == GP_PREC_TC16 || prec == GP_PREC_FP32));
     // ---- block inverses H[i,i]^-1 (cached for the whole solve)
     GP_TRY_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
     ap_build_blocks_kernel<T><<<dim3(bsp / 16, bsp / 16, nb), dim3(16, 16), 0, st>>>(kp, X, n, bs, bsp, Hb);
@@ -424,10 +426,10 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
     GP_TRY(check_launch("ap setup", 3));
-    GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec_true, mw, mwb, st));
+    GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
-    ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 1);
+    ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, exact_start ? 2 : 1);
     GP_TRY(check_launch("ap start", 3));
 
     int hfail = 0;

@@ -256,9 +256,9 @@ __global__ void bt_cg_start_kernel(const BMember *mem, int G, int R, int nch, co
         st->status = GP_OK;
         st->res0 = 0.0;
         finish_norms(st, sq, R, 0, max_iters, tol, stop_rule);
-        st->certified = 1;  // the initial residual b~ - H v0 is a true residual
+        st->certified = 0;  // the initial residual came from the plain product
         done[g] = st->done;
-        cdone[g] = st->done;
+        cdone[g] = 0;
     }
 }
 
@@ -747,8 +747,8 @@ int batch_cg(gp_batch *b, const float *B, float *V, int64_t iters, double tol, i
     bt_norm_scale_kernel<<<gmr, 128, 0, st>>>(p.mem, G, R, nch, p.part, p.scale);
     bt_scale_cols_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, V, R, p.scale, 1);
     GP_TRY(check_launch("batched cg setup", 3));
-    // r = b~ - H v ; d = r ; gamma = r^T r  (a true residual: split products)
-    GP_TRY(batch_apply(b, V, p.Hd, 1.0f, nullptr, st, true));
+    // r = b~ - H v ; d = r ; gamma = r^T r  (the plain product; the checks catch its error)
+    GP_TRY(batch_apply(b, V, p.Hd, 1.0f, nullptr, st));
     bt_init_residual_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, B, p.Hd, p.r, p.dd, R, p.scale);
     bt_dot_kernel<<<gc, 256, 0, st>>>(p.mem, p.chunks, nch, p.r, p.r, p.part, nullptr);
     bt_cg_start_kernel<<<(unsigned)G, 256, 0, st>>>(p.mem, G, R, nch, p.part, p.gamma, p.state, p.done, p.cdone,

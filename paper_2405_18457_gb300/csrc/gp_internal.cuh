@@ -260,7 +260,14 @@ struct TcMvmArgs {
     // Split form: kernel values and V as fp16 high + low parts, Y += P_hi V_hi + P_hi V_lo +
     // P_lo V_hi (about 2^-22 relative per term instead of 2^-11; three GEMM2 passes per tile).
     int split;
+    // V already converted by the caller (plain form, R <= 128): tc_rhs_pad(R) rows of
+    // tc_cols_pad(n2) fp16 values (zero beyond n2 and R), V scaled per column by 1 / vinv_pre[c]
+    // (a power of two); V is then only read for the diagonal term.
+    const void *V16pre;
+    const float *vinv_pre;
 };
+int tc_rhs_pad(int R);            // right-hand sides padded for the tensor-core product
+int64_t tc_cols_pad(int64_t n);   // columns padded to whole tiles
 size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R);
 // Row operand for points X1 that are a subset of an already prepared set `like` (same
 // scale): the batch rows of the stochastic-gradient panel.

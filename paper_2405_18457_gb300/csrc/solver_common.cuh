@@ -3,6 +3,8 @@
 
 #include "solvers.cuh"
 
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -177,18 +179,21 @@ __global__ void true_residual_kernel(const T *B, const TH *Hv, T *r, int64_t n, 
 }
 
 // State after a true-residual recomputation: (CG) gamma <- r^T P^-1 r (partG; = ||r||^2 without
-// a preconditioner) for the next iteration, when gamma is given; the split norms from partN and the loop condition at
-// the current iteration count, marked certified.  reopen = 0: a periodic recomputation during
-// the solve (skipped once done is latched).  reopen = 1: the check after the loop stopped; done
-// is re-evaluated from the true norms, so a solve whose recursive residual met the tolerance
+// a preconditioner) for the next iteration, when gamma is given, and the restart direction's
+// bound ||r|| when dbound is given; the split norms from partN and the loop condition at the
+// current iteration count, marked certified.  reopen = 0: a recomputation during the solve
+// (skipped once done is latched).  reopen = 1: the check after the loop stopped; done is
+// re-evaluated from the true norms, so a solve whose recursive residual met the tolerance
 // while its true residual does not is resumed.  One block, R <= 512.
 __global__ void true_state_kernel(int R, int P, const double *partG, const double *partN, double *gamma,
-                                     SolverState *st, long long max_iters, double tol, int stop_rule, int reopen) {
+                                  SolverState *st, long long max_iters, double tol, int stop_rule, int reopen,
+                                  double *dbound = nullptr) {
     if (!reopen && st->done) return;
     __shared__ double sq[512];
     for (int c = threadIdx.x; c < R; c += blockDim.x) {
         sq[c] = sum_parts(partN, c, P);
         if (gamma) gamma[c] = sum_parts(partG, c, P);
+        if (dbound) dbound[c] = sqrt(sq[c]) * (1.0 + 1e-6);
     }
     __syncthreads();
     if (threadIdx.x == 0 && reopen && st->status == GP_OK) st->done = 0;

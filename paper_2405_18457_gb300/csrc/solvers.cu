@@ -21,11 +21,13 @@ namespace {
 // split norms from ||r||^2 (partN); sets done if already converged.
 // One block, one thread per column (R <= 512).
 __global__ void cg_start_kernel(int R, int P, const double *partG, const double *partN, double *gamma,
-                                SolverState *st, long long max_iters, double tol, int stop_rule) {
+                                SolverState *st, long long max_iters, double tol, int stop_rule, int certified,
+                                double *dbound) {
     __shared__ double sq[512];
     for (int c = threadIdx.x; c < R; c += blockDim.x) {
         sq[c] = sum_parts(partN, c, P);
         gamma[c] = sum_parts(partG, c, P);
+        if (dbound) dbound[c] = sqrt(sq[c]) * (1.0 + 1e-6);  // the first direction is r: bound ||r||
     }
     if (threadIdx.x == 0) {
         st->done = 0;
@@ -33,7 +35,7 @@ __global__ void cg_start_kernel(int R, int P, const double *partG, const double 
     }
     __syncthreads();
     finish_norms_block(st, sq, R, 0, max_iters, tol, stop_rule);
-    if (threadIdx.x == 0) st->certified = 1;  // r = b~ - H v0 is a true residual
+    if (threadIdx.x == 0) st->certified = certified;  // r = b~ - H v0 from an exact-class product
 }
 
 // alpha = gamma / d^T H d, frozen columns get 0.
@@ -181,13 +183,28 @@ __global__ void cg_update_fused_kernel(T *v, T *r, const T *d, const T *Hd, int6
 // the R blocks (0, .) to do so (a counter, reset by that block) takes the split norms, the
 // iteration count and the loop condition.  A block that starts after `done` is latched skips
 // its part of d, which the finished solve no longer needs.  grid G x R
+// The tensor-core operand of the next product, written by the direction kernel (tensor-core
+// form): D16[c][i] = fp16(d_c[i] * 2^(1-e_c)) with a power-of-two scale from a bound on
+// max_i |d_c[i]| known before d is formed, |r_i| + |beta| |d_old,i| <= ||r|| + |beta| B_old (B
+// the previous direction's bound; the first direction is r, B = ||r||), so no column-max pass
+// is needed; vinv[c] = 2^(e_c - 1) undoes the scale.  Rows are p2 halves (columns padded with
+// zeros, zeroed once per solve).
+struct DirOperand {
+    __half *D16;
+    int64_t p2;
+    float *vinv;
+    const double *bcur;
+    double *bnext;
+};
+
 template <typename T>
 __global__ void cg_dir_fused_kernel(T *d, const T *r, int64_t n, int P, const double *partN, const double *gcur,
                                     double *gnext, const double *alpha, SolverState *st, long long max_iters,
-                                    double tol, int stop_rule, int R, double *sq, int *counter) {
+                                    double tol, int stop_rule, int R, double *sq, int *counter, DirOperand op16) {
     if (st->done) return;
     const int c = blockIdx.y;
     __shared__ double s_b;
+    __shared__ float s_scale;
     __shared__ int s_last;
     if (threadIdx.x < 32) {
         const double gn = sum_parts_warp(partN, c, P);
@@ -195,6 +212,21 @@ __global__ void cg_dir_fused_kernel(T *d, const T *r, int64_t n, int P, const do
             const bool active = alpha[c] != 0.0;
             s_b = active ? gn / gcur[c] : 0.0;
             s_last = 0;
+            if (op16.D16) {
+                const double bnew = sqrt(gn) * (1.0 + 1e-6) + fabs(s_b) * op16.bcur[c];
+                int e = 0;
+                float scale = 1.0f, inv = 1.0f;
+                if (bnew > 0.0 && isfinite(bnew)) {
+                    frexp(bnew, &e);  // bnew = f 2^e, f in [0.5, 1): |d| * 2^(1-e) < 2
+                    scale = ldexpf(1.0f, 1 - e);
+                    inv = ldexpf(1.0f, e - 1);
+                }
+                s_scale = scale;
+                if (blockIdx.x == 0) {
+                    op16.bnext[c] = bnew;
+                    op16.vinv[c] = inv;
+                }
+            }
             if (blockIdx.x == 0) {
                 gnext[c] = active ? gn : gcur[c];
                 sq[c] = gn;
@@ -220,6 +252,8 @@ __global__ void cg_dir_fused_kernel(T *d, const T *r, int64_t n, int P, const do
     const T b = (T)s_b;
     bool done4 = false;
     if constexpr (std::is_same<T, float>::value) {
+        const float sc = op16.D16 ? s_scale : 0.0f;
+        __half *h16 = op16.D16 ? op16.D16 + (int64_t)c * op16.p2 : nullptr;
         if ((n & 3) == 0) {
             float4 *d4 = reinterpret_cast<float4 *>(d + (int64_t)c * n);
             const float4 *r4 = reinterpret_cast<const float4 *>(r + (int64_t)c * n);
@@ -232,6 +266,23 @@ __global__ void cg_dir_fused_kernel(T *d, const T *r, int64_t n, int P, const do
                 dv.z = rv.z + b * dv.z;
                 dv.w = rv.w + b * dv.w;
                 d4[q] = dv;
+                if (h16) {
+                    __half2 lo = __floats2half2_rn(dv.x * sc, dv.y * sc), hi = __floats2half2_rn(dv.z * sc, dv.w * sc);
+                    uint2 u;
+                    u.x = *reinterpret_cast<uint32_t *>(&lo);
+                    u.y = *reinterpret_cast<uint32_t *>(&hi);
+                    reinterpret_cast<uint2 *>(h16)[q] = u;
+                }
+            }
+            done4 = true;
+        }
+        if (!done4) {
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+                 i += (int64_t)gridDim.x * blockDim.x) {
+                const int64_t e = (int64_t)c * n + i;
+                const float v = r[e] + b * d[e];
+                d[e] = v;
+                if (h16) h16[i] = __float2half_rn(v * sc);
             }
             done4 = true;
         }
@@ -295,7 +346,8 @@ struct HOp {
     }
     // Y = alpha * K V + beta * Y + diag (sigma^2 V unless overridden); split: the tensor-core
     // form's split products (FP32-class), for true residuals
-    int apply(const T *V, T *Y, const int *done, cudaStream_t st, bool split = false) {
+    int apply(const T *V, T *Y, const int *done, cudaStream_t st, bool split = false, const void *V16pre = nullptr,
+              const float *vinv_pre = nullptr) {
         if constexpr (std::is_same<T, float>::value) {
             if (tc) {
                 TcMvmArgs a{};
@@ -317,6 +369,8 @@ struct HOp {
                 a.ndiag = n;
                 a.done = done;
                 a.split = split ? 1 : 0;
+                a.V16pre = V16pre;
+                a.vinv_pre = vinv_pre;
                 return tc_mvm(a, ws, wsb, st);
             }
         }
@@ -418,6 +472,11 @@ size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank) {
     c.take<SolverState>(1);
     c.take<char>(HOp<T>::workspace(n, d, R, prec));
     if (std::is_same<T, float>::value && prec == GP_PREC_FP32) c.take<char>(f64_residual_workspace(n, d, R));
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16 && pc_rank == 0 && R <= 128) {
+        c.take<__half>((size_t)tc_rhs_pad(R) * tc_cols_pad(n));  // the directions' fp16 operand
+        c.take<float>(256);
+        c.take<double>(2 * (size_t)R);
+    }
     if (pc_rank > 0) {
         c.take<T>((size_t)R * n);                           // p = P^-1 r
         c.take<double>((size_t)R * P);                      // r^T p partial sums
@@ -454,6 +513,13 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     const bool check64 = std::is_same<T, float>::value && prec == GP_PREC_FP32;
     const size_t c64b = check64 ? f64_residual_workspace(n, kp.d, R) : 0;
     void *c64w = check64 ? c.take<char>(c64b) : nullptr;
+    // tensor-core form without a preconditioner: the direction kernel writes the next product's
+    // fp16 operand itself (no column-max and conversion launches per iteration)
+    const bool d16 = std::is_same<T, float>::value && prec == GP_PREC_TC16 && !pc && R <= 128;
+    const int64_t p2 = tc_cols_pad(n);
+    __half *D16 = d16 ? c.take<__half>((size_t)tc_rhs_pad(R) * p2) : nullptr;
+    float *vinv16 = d16 ? c.take<float>(256) : nullptr;
+    double *dbnd = d16 ? c.take<double>(2 * (size_t)R) : nullptr;
     T *pz = pc ? c.take<T>((size_t)R * n) : nullptr;
     double *partG = pc ? c.take<double>((size_t)R * P) : part;
     const size_t pcb = pc ? precond_workspace<T>(n, R, pc_rank) : 0;
@@ -471,13 +537,15 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     const int *done = &sd->done;
 
     GP_TRY_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int), st));
+    if (d16) GP_TRY_CUDA(cudaMemsetAsync(D16, 0, sizeof(__half) * (size_t)tc_rhs_pad(R) * p2, st));
     // normalisation (App. B): scale_c = ||b_c|| + eps, v <- v / scale
     coldot_kernel<T><<<gp_, 256, 0, st>>>(B, B, n, P, part, nullptr);
     norm_scale_kernel<<<1, 256, 0, st>>>(R, P, part, scale);
     scale_cols_kernel<T><<<gv, 256, 0, st>>>(V, n, scale, 1);
     GP_TRY(check_launch("cg setup", 3));
-    // r = b~ - H v ; p = P^-1 r ; d = p ; gamma = r^T p  (a true residual: split products)
-    GP_TRY(op.apply(V, Hd, nullptr, st, true));
+    // r = b~ - H v ; p = P^-1 r ; d = p ; gamma = r^T p  (with the form's own product: its error
+    // is caught by the check when the loop stops)
+    GP_TRY(op.apply(V, Hd, nullptr, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, Hd, r, dd, n, scale);
     GP_TRY(check_launch("cg residual"));
     if (pc) {
@@ -486,7 +554,9 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         coldot_kernel<T><<<gp_, 256, 0, st>>>(r, pz, n, P, partG, nullptr);
     }
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
-    cg_start_kernel<<<1, 256, 0, st>>>(R, P, partG, part, gamma, sd, (long long)max_iters, tol, stop_rule);
+    // the FP32 form's initial residual is not of the check's (FP64) class either
+    cg_start_kernel<<<1, 256, 0, st>>>(R, P, partG, part, gamma, sd, (long long)max_iters, tol, stop_rule,
+                                       (op.tc || check64) ? 0 : 1, dbnd);
     GP_TRY(check_launch("cg start", pc ? 3 : 2));
 
     // Iterations are enqueued speculatively in chunks without waiting for the start-up
@@ -504,8 +574,8 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // ill-conditioned system lies far above the residuals CG reaches (measured: replacing the
     // recursive residual by an FP32 true residual every 10 iterations made CG diverge on the
     // small workload); the tensor-core form uses its split products (FP32-class), since its
-    // plain fp16 product is off by about 2^-11 ||H|| ||v||.  The initial residual is computed the
-    // same way.  The reported norms are therefore always true-residual norms.
+    // plain fp16 product is off by about 2^-11 ||H|| ||v||.  The reported norms are therefore
+    // always true-residual norms.
     SolverState hs{};
     // The first chunk follows the previous solve on this thread (warm-started solves of one
     // optimisation take similar counts), so that most solves poll once.
@@ -516,6 +586,7 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // gamma array the iteration with host index i reads as its current gamma
     auto gamma_at = [&](int64_t i) { return pc ? gamma : gamma + (i & 1) * R; };
     auto poll = [&]() -> int { return op.tc ? poll_state_tc(sd, &hs, &timed_out, st) : poll_state(sd, &hs, st); };
+    bool d16_valid = false;  // D16 holds the current direction (written by the last direction kernel)
     int64_t dev_iters = 0;  // iterations the device has performed, as of the last poll
     int checks = 0;         // failed true-residual checks so far (restarts)
     double prev_y = 0.0, prev_z = 0.0;
@@ -525,15 +596,22 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         while (phase < left) {
             const int64_t k = std::min<int64_t>(chunk, left - phase);
             for (int64_t it = 0; it < k; ++it, ++ti) {
-                GP_TRY(op.apply(dd, Hd, done, st));
+                if (d16_valid)
+                    GP_TRY(op.apply(dd, Hd, done, st, false, D16, vinv16));
+                else
+                    GP_TRY(op.apply(dd, Hd, done, st));
                 coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
                 if (!pc) {
                     const double *gcur = gamma_at(ti);
                     double *gnext = gamma_at(ti + 1);
+                    const DirOperand o16{D16, p2, vinv16, d16 ? dbnd + (ti & 1) * R : nullptr,
+                                         d16 ? dbnd + ((ti + 1) & 1) * R : nullptr};
                     cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, part, gcur, alpha, partN, sd);
                     cg_dir_fused_kernel<T><<<gd, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
-                                                               (long long)max_iters, tol, stop_rule, R, sqn, dcount);
+                                                               (long long)max_iters, tol, stop_rule, R, sqn, dcount,
+                                                               o16);
                     GP_TRY(check_launch("cg iteration", 3));
+                    d16_valid = d16;
                 } else {
                     cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
                     cg_update_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, alpha, part, sd);
@@ -571,7 +649,8 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         }
         GP_TRY_CUDA(cudaMemcpyAsync(dd, pc ? pz : r, sizeof(T) * (size_t)R * n, cudaMemcpyDeviceToDevice, st));
         true_state_kernel<<<1, 256, 0, st>>>(R, P, pc ? partG : partN, partN, gamma_at(ti), sd, (long long)max_iters,
-                                             tol, stop_rule, 1);
+                                             tol, stop_rule, 1, d16 ? dbnd + (ti & 1) * R : nullptr);
+        d16_valid = false;  // the restart direction is converted by the product itself
         GP_TRY(check_launch("cg true-residual state"));
         GP_TRY(poll());
         dev_iters = hs.iter;

@@ -1257,6 +1257,10 @@ int make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, u
 
 int kd_for(int d) { return (int)rup(3 * d + 4, 64); }
 int rpad_for(int R) { return (int)rup(R, 16); }
+}  // namespace
+int tc_rhs_pad(int R) { return rpad_for(R); }
+int64_t tc_cols_pad(int64_t n) { return rup(std::max<int64_t>(n, 1), TN); }
+namespace {
 
 int num_sms_tc() { return device_sm_count(); }
 
@@ -1707,6 +1711,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         for (int c0 = 0; c0 < a.R; c0 += per_pass) {
             TcMvmArgs b = a;
             b.R = std::min(per_pass, a.R - c0);
+            b.V16pre = nullptr;  // a caller's converted operand covers all columns at once
             b.V = a.V + (int64_t)c0 * a.ldv;
             b.Y = a.Y + (int64_t)c0 * a.ldy;
             b.Vd = a.Vd ? a.Vd + (int64_t)c0 * a.ldvd : nullptr;
@@ -1746,11 +1751,17 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     int *err = tc_timeout_word();
     float *partial = pfl > 0 ? c.take<float>(pfl) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
-    const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
-    tc_colmax_kernel<<<dim3(P, a.R), 256, 0, st>>>(a.V, a.ldv, n2, P, cm, a.done);
-    tc_convert_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(p2, 1024), 256), R_pad), 256, 0, st>>>(
-        a.V, a.ldv, n2, p2, a.R, P, cm, V16, a.split ? V16 + (size_t)R_pad * p2 : nullptr, vinv, a.done);
-    GP_TRY(check_launch("tc rhs conversion", 2));
+    const bool pre = a.V16pre != nullptr && !a.split;  // operand converted by the caller
+    if (pre) {
+        V16 = static_cast<__half *>(const_cast<void *>(a.V16pre));
+        vinv = const_cast<float *>(a.vinv_pre);
+    } else {
+        const int P = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(n2, 4096)));
+        tc_colmax_kernel<<<dim3(P, a.R), 256, 0, st>>>(a.V, a.ldv, n2, P, cm, a.done);
+        tc_convert_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(p2, 1024), 256), R_pad), 256, 0, st>>>(
+            a.V, a.ldv, n2, p2, a.R, P, cm, V16, a.split ? V16 + (size_t)R_pad * p2 : nullptr, vinv, a.done);
+        GP_TRY(check_launch("tc rhs conversion", 2));
+    }
 
     CUtensorMap mA, mB, mV;
     GP_TRY(make_map(&mA, a.rows.PA, KD, a.rows.n_pad, 64, TM));
