@@ -197,7 +197,9 @@ __global__ void identity_kernel(T *Zb, int bsp, int nb) {
     }
 }
 
-// score[b] = sum_{rows of block b} (sum_c r_c[row])^2
+// score[b] = sum_{rows of block b} (sum_c r_c[row])^2.  The row's sum over the right-hand sides
+// is taken in the vectors' own precision (FP64 runs at 1/74 of the FP32 rate on this GPU; an
+// FP32 sum of R FP32 values is within R u of the exact one), the block's sum of squares in FP64.
 template <typename T>
 __global__ void ap_score_kernel(const T *r, int64_t n, int R, int bs, double *score, const SolverState *st) {
     if (st->done) return;
@@ -205,9 +207,9 @@ __global__ void ap_score_kernel(const T *r, int64_t n, int R, int bs, double *sc
     const int64_t lo = (int64_t)b * bs, hi = min(n, lo + bs);
     double s = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        double t = 0.0;
-        for (int c = 0; c < R; ++c) t += (double)r[(int64_t)c * n + i];
-        s += t * t;
+        T t = T(0);
+        for (int c = 0; c < R; ++c) t += r[(int64_t)c * n + i];
+        s += (double)(t * t);
     }
     __shared__ double red[32];
     s = warp_sum(s);
@@ -251,10 +253,13 @@ __global__ void ap_select_kernel(const double *score, int nb, int bs, int64_t *c
     if (threadIdx.x == 0) *col0 = (int64_t)bi[0] * bs;
 }
 
-// delta[c][a] = sum_a' Hinv[blk][a][a'] r[c][lo + a'],  a < bs (rows beyond n -> 0)
+// Partial block solves: dpart[ks][c][a] = sum over the ks-th K range of Hinv[blk][a][a'] r[c][lo + a'],
+// a < bs (rows beyond n -> 0).  grid (bs/64, R/16, kSplitK): the K ranges split the work over
+// enough CTAs to fill the GPU (one 1024 x 1024 block against 65 vectors is 68M FMA).
+constexpr int kSplitK = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, int bs, const T *r, int64_t n, int R,
-                                                       const int64_t *col0, T *delta, const SolverState *st) {
+                                                       const int64_t *col0, T *dpart, const SolverState *st) {
     if (st->done) return;
     __shared__ T Hs[64][33];
     __shared__ T Rs[32][17];
@@ -262,17 +267,20 @@ __global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, i
     const int blk = (int)(lo / bs);
     const int m = (int)min((int64_t)bs, n - lo);
     const T *Hm = Hinv + (int64_t)blk * bsp * bsp;
-    const int a0 = blockIdx.x * 64, c0 = blockIdx.y * 16;
+    const int a0 = blockIdx.x * 64, c0 = blockIdx.y * 16, ks = blockIdx.z;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int kper = (int)rup(cdiv(m, kSplitK), 32);
+    const int kb = ks * kper, ke = min(m, kb + kper);
+    T *delta = dpart + (int64_t)ks * R * bs;
     T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int k0 = 0; k0 < m; k0 += 32) {
+    for (int k0 = kb; k0 < ke; k0 += 32) {
         for (int e = tid; e < 64 * 32; e += 256) {
             int aa = e / 32, kk = e % 32;
-            Hs[aa][kk] = (a0 + aa < m && k0 + kk < m) ? Hm[(int64_t)(a0 + aa) * bsp + k0 + kk] : T(0);
+            Hs[aa][kk] = (a0 + aa < m && k0 + kk < ke) ? Hm[(int64_t)(a0 + aa) * bsp + k0 + kk] : T(0);
         }
         for (int e = tid; e < 32 * 16; e += 256) {
             int cc = e / 32, kk = e % 32;
-            Rs[kk][cc] = (k0 + kk < m && c0 + cc < R) ? r[(int64_t)(c0 + cc) * n + lo + k0 + kk] : T(0);
+            Rs[kk][cc] = (k0 + kk < ke && c0 + cc < R) ? r[(int64_t)(c0 + cc) * n + lo + k0 + kk] : T(0);
         }
         __syncthreads();
 #pragma unroll 8
@@ -292,30 +300,36 @@ __global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, i
     }
 }
 
-// v[c][lo + a] += delta[c][a]
+// delta[c][a] = sum_ks dpart[ks][c][a] (K ranges in a fixed order); v[c][lo + a] += delta[c][a]
 template <typename T>
-__global__ void ap_vupdate_kernel(T *V, int64_t n, int bs, const int64_t *col0, const T *delta,
+__global__ void ap_vupdate_kernel(T *V, int64_t n, int bs, int R, const int64_t *col0, const T *dpart, T *delta,
                                   const SolverState *st) {
     if (st->done) return;
     const int c = blockIdx.y;
     const int64_t lo = *col0;
     const int m = (int)min((int64_t)bs, n - lo);
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x)
-        V[(int64_t)c * n + lo + a] += delta[(int64_t)c * bs + a];
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < bs; a += gridDim.x * blockDim.x) {
+        T dl = T(0);
+        for (int ks = 0; ks < kSplitK; ++ks) dl += dpart[((int64_t)ks * R + c) * bs + a];
+        delta[(int64_t)c * bs + a] = dl;
+        if (a < m) V[(int64_t)c * n + lo + a] += dl;
+    }
 }
 
+// Split norms and the loop condition from the ||r||^2 partials; the columns' sums in parallel (one
+// thread per column; a single thread summing R x P partials in FP64 took ~0.3 ms).  One block.
 __global__ void ap_norm_kernel(int R, int P, const double *part, SolverState *st, long long max_iters, double tol,
                                int stop_rule, int first) {
-    if (threadIdx.x != 0) return;
     if (!first && st->done) return;
-    double sq[512];
-    for (int c = 0; c < R; ++c) sq[c] = sum_parts(part, c, P);
-    if (first) {
+    __shared__ double sq[512];
+    for (int c = threadIdx.x; c < R; c += blockDim.x) sq[c] = sum_parts(part, c, P);
+    if (threadIdx.x == 0 && first) {
         st->done = 0;
         st->status = GP_OK;
     }
-    finish_norms(st, sq, R, first ? 0 : st->iter + 1, max_iters, tol, stop_rule);
-    if (first == 2) st->certified = 1;  // the initial residual came from an exact-class product
+    __syncthreads();
+    finish_norms_block(st, sq, R, first ? 0 : st->iter + 1, max_iters, tol, stop_rule);
+    if (threadIdx.x == 0 && first == 2) st->certified = 1;  // the initial residual came from an exact-class product
 }
 
 }  // namespace
@@ -340,6 +354,7 @@ size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec) {
     c.take<T>((size_t)R * n);               // residual
     c.take<T>((size_t)R * n);               // H v (set-up)
     c.take<T>((size_t)R * bs);              // delta
+    c.take<T>((size_t)kSplitK * R * bs);    // partial block solves
     c.take<T>((size_t)nb * bsp * bsp);      // factor / inverse
     c.take<T>((size_t)nb * bsp * bsp);      // L^-1
     c.take<double>((size_t)R * P);
@@ -369,6 +384,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     T *r = c.take<T>((size_t)R * n);
     T *HV = c.take<T>((size_t)R * n);
     T *delta = c.take<T>((size_t)R * bs);
+    T *dpart = c.take<T>((size_t)kSplitK * R * bs);
     T *Hb = c.take<T>((size_t)nb * bsp * bsp);
     T *Zb = c.take<T>((size_t)nb * bsp * bsp);
     double *part = c.take<double>((size_t)R * P);
@@ -429,7 +445,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
-    ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, exact_start ? 2 : 1);
+    ap_norm_kernel<<<1, 256, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, exact_start ? 2 : 1);
     GP_TRY(check_launch("ap start", 3));
 
     int hfail = 0;
@@ -500,7 +516,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             ta.done = &sd->done;
         }
     }
-    const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16));
+    const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16), (unsigned)kSplitK);
     // The residual of Alg. 2 is updated by the panel products (recursive); when the loop stops
     // on it, the true residual b~ - H v is recomputed (FP64 differences and norms) and replaces
     // it; the tolerance is judged on it, and a solve whose true residual misses the tolerance is
@@ -514,8 +530,8 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         for (int64_t it = 0; it < k; ++it, ++t) {
             ap_score_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, sd);
             ap_select_kernel<<<1, 1024, 0, st>>>(score, nb, bs, col0, sd);
-            ap_delta_kernel<T><<<gdel, 256, 0, st>>>(Hb, bsp, bs, r, n, R, col0, delta, sd);
-            ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, col0, delta, sd);
+            ap_delta_kernel<T><<<gdel, 256, 0, st>>>(Hb, bsp, bs, r, n, R, col0, dpart, sd);
+            ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, R, col0, dpart, delta, sd);
             GP_TRY(check_launch("ap iteration", 4));
             if constexpr (std::is_same<T, float>::value) {
                 if (tc_panel) {
@@ -527,7 +543,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
                 GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
             }
             coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, &sd->done);
-            ap_norm_kernel<<<1, 32, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 0);
+            ap_norm_kernel<<<1, 256, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 0);
             GP_TRY(check_launch("ap norms", 2));
         }
         chunk = std::min<int64_t>(chunk * 2, 64);

@@ -708,21 +708,33 @@ __global__ void sgd_gather_kernel(const T *X, int d, const int32_t *idx, int64_t
 // g[c][q] = (K V)[c][q] + sigma^2 v[c][idx q] - b~[c][idx q]  (in place in G)
 // and the residual estimate update r[c][idx q] <- g, maintaining sum r^2 per
 // column incrementally in FP64: rsq[c] += g^2 - r_old^2.
+// With gmax (tensor-core form): also the batch gradient's column maxima (atomicMax on float bits)
+// for the step's operand bound, and the next step's maxima buffers zeroed.
 template <typename T>
 __global__ void sgd_grad_kernel(T *G, const T *V, const T *Bn, T *r, int64_t n, const int32_t *idx,
                                 int64_t batch, T sigma2, const int *slot, double *rsq_delta_part,
-                                const SolverState *st) {
+                                const SolverState *st, unsigned *gmax, unsigned *vmax_zero, unsigned *mmax_zero) {
     if (st->done) return;
     const int c = blockIdx.y;
     double s = 0.0;
+    float gm = 0.0f;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < batch; q += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = idx[q];
         int64_t e = (int64_t)c * n + i;
         T g = G[(int64_t)c * batch + q] + sigma2 * V[e] - Bn[e];
         G[(int64_t)c * batch + q] = g;
+        gm = fmaxf(gm, fabsf((float)g));
         if (slot[i] == (int)q) {  // one writer per row even if an index repeats
             T old = r[e];
             s += (double)g * (double)g - (double)old * (double)old;
+        }
+    }
+    if (gmax) {
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&gmax[c], __float_as_uint(gm));
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            vmax_zero[c] = 0u;
+            mmax_zero[c] = 0u;
         }
     }
     __shared__ double red[32];
@@ -736,20 +748,109 @@ __global__ void sgd_grad_kernel(T *G, const T *V, const T *Bn, T *r, int64_t n, 
     }
 }
 
-// Dense step over all rows: m = rho m - (lr/b) g ; v += m ; r[i] = g on batch rows.
+// The next row panel's fp16 operand, written by the step kernel (tensor-core form): V16[c][i] =
+// fp16(v_c[i] 2^(1-e_c)) with a power-of-two scale from a bound on max_i |v_c[i]| known before
+// the step, B = max|v_old| + rho max|m_old| + (lr/b) max|g| >= max|v_old + m_new| (the maxima
+// exact: the previous step's, taken with atomicMax on float bits, and the batch gradient's);
+// vinv[c] = 2^(e_c - 1).  The maxima are double-buffered by iteration parity.
+struct SgdOperand {
+    __half *V16;
+    int64_t p2;
+    float *vinv;
+    const unsigned *vmax_cur, *mmax_cur;  // this step's inputs' maxima
+    unsigned *vmax_next, *mmax_next;      // this step's outputs' maxima (zeroed before the step)
+    const unsigned *gmax;                 // the batch gradient's maxima (this iteration)
+    unsigned *gmax_next;                  // zeroed here for the next iteration's gradient
+};
+
+// Dense step over all rows: m = rho m - (lr/b) g ; v += m ; r[i] = g on batch rows.  One thread
+// per row over all right-hand sides (the row's batch slot read once); warps walk the rows in
+// warp-aligned strides so that the maxima's shuffles always see full warps.  256 threads.
+constexpr int kSgdMaxR = 512;
 template <typename T>
-__global__ void sgd_step_kernel(T *Vv, T *M, T *r, const T *G, int64_t n, int64_t batch, const int *slot,
-                                T rho, T lrb, const SolverState *st) {
+__global__ void __launch_bounds__(256) sgd_step_kernel(T *Vv, T *M, T *r, const T *G, int64_t n, int64_t batch, int R,
+                                                       const int *slot, T rho, T lrb, const SolverState *st,
+                                                       SgdOperand op16) {
     if (st->done) return;
-    const int c = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t e = (int64_t)c * n + i;
-        int q = slot[i];
-        T g = (q >= 0) ? G[(int64_t)c * batch + q] : T(0);
-        T m = rho * M[e] - lrb * g;
-        M[e] = m;
-        Vv[e] += m;
-        if (q >= 0) r[e] = g;
+    __shared__ float s_scale[kSgdMaxR];
+    __shared__ unsigned s_vmax[8][64];  // per warp, the current chunk of 64 columns
+    __shared__ unsigned s_mmax[8][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool f16 = op16.V16 != nullptr;
+    if (f16) {
+        for (int c = threadIdx.x; c < R; c += blockDim.x) {
+            const double bnd = (double)__uint_as_float(op16.vmax_cur[c]) + (double)rho * __uint_as_float(op16.mmax_cur[c]) +
+                               (double)lrb * __uint_as_float(op16.gmax[c]);
+            float scale = 1.0f;
+            int e = 0;
+            if (bnd > 0.0 && isfinite(bnd)) {
+                frexp(bnd * (1.0 + 1e-6), &e);  // |v| 2^(1-e) < 2
+                scale = ldexpf(1.0f, 1 - e);
+            }
+            s_scale[c] = scale;
+            if (blockIdx.x == 0) {
+                op16.vinv[c] = 1.0f / scale;
+                op16.gmax_next[c] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+    // columns in chunks of 64 so that the per-warp maxima fit shared memory
+    for (int cb = 0; cb < R; cb += 64) {
+        const int ce = min(R, cb + 64);
+        if (f16) {
+            for (int e = threadIdx.x; e < 8 * 64; e += blockDim.x) {
+                s_vmax[e >> 6][e & 63] = 0u;
+                s_mmax[e >> 6][e & 63] = 0u;
+            }
+            __syncthreads();
+        }
+        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n;
+             i0 += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t i = i0 + lane;
+            const bool act = i < n;
+            const int q = act ? slot[i] : -1;
+            for (int c = cb; c < ce; ++c) {
+                const int64_t e = (int64_t)c * n + i;
+                T v = T(0), m = T(0);
+                if (act) {
+                    const T g = (q >= 0) ? G[(int64_t)c * batch + q] : T(0);
+                    m = rho * M[e] - lrb * g;
+                    M[e] = m;
+                    v = Vv[e] + m;
+                    Vv[e] = v;
+                    if (q >= 0) r[e] = g;
+                }
+                if constexpr (std::is_same<T, float>::value) {
+                    if (f16) {
+                        if (act) op16.V16[(int64_t)c * op16.p2 + i] = __float2half_rn(v * s_scale[c]);
+                        // exact maxima for the next step's bound (non-negative floats order as their bits)
+                        unsigned vb = __float_as_uint(fabsf(v)), mb = __float_as_uint(fabsf(m));
+                        for (int o = 16; o > 0; o >>= 1) {
+                            vb = max(vb, __shfl_xor_sync(0xffffffffu, vb, o));
+                            mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+                        }
+                        if (lane == 0) {
+                            s_vmax[warp][c - cb] = max(s_vmax[warp][c - cb], vb);
+                            s_mmax[warp][c - cb] = max(s_mmax[warp][c - cb], mb);
+                        }
+                    }
+                }
+            }
+        }
+        if (f16) {
+            __syncthreads();
+            for (int c = cb + threadIdx.x; c < ce; c += blockDim.x) {
+                unsigned vb = 0u, mb = 0u;
+                for (int w = 0; w < 8; ++w) {
+                    vb = max(vb, s_vmax[w][c - cb]);
+                    mb = max(mb, s_mmax[w][c - cb]);
+                }
+                atomicMax(&op16.vmax_next[c], vb);
+                atomicMax(&op16.mmax_next[c], mb);
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -757,6 +858,16 @@ __global__ void sgd_clear_slots_kernel(const int32_t *idx, int64_t batch, int *s
     if (st->done) return;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < batch; q += (int64_t)gridDim.x * blockDim.x)
         slot[idx[q]] = -1;
+}
+
+// out[c] = max_i |V[c][i]| as float bits (atomicMax; out zeroed by the caller).  grid (blocks, R)
+__global__ void absmax_cols_kernel(const float *V, int64_t n, unsigned *out) {
+    const int c = blockIdx.y;
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(V[(int64_t)c * n + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&out[c], __float_as_uint(m));
 }
 
 __global__ void fill_int_kernel(int *p, int64_t cnt, int v) {
@@ -831,6 +942,11 @@ size_t sgd_workspace(int64_t n, int d, int R, int64_t batch, int prec) {
     for (int k = 0; k < 2; ++k) c.take<double>(R);
     c.take<SolverState>(1);
     c.take<char>(sgd_panel_ws<T>(batch, n, d, R, prec));
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16 && R <= 128) {
+        c.take<__half>((size_t)tc_rhs_pad(R) * tc_cols_pad(n));  // the step's fp16 operand of v
+        c.take<float>(256);
+        c.take<unsigned>(6 * (size_t)R);                         // maxima of v, m, g (x 2)
+    }
     return c.bytes();
 }
 
@@ -858,6 +974,12 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     SolverState *sd = c.take<SolverState>(1);
     size_t pwb = sgd_panel_ws<T>(batch, n, d, R, prec);
     void *pw = c.take<char>(pwb);
+    // tensor-core form: the step writes the next panel's fp16 operand of v itself
+    const bool v16 = std::is_same<T, float>::value && prec == GP_PREC_TC16 && R <= 128;
+    const int64_t p2 = tc_cols_pad(n);
+    __half *V16 = v16 ? c.take<__half>((size_t)tc_rhs_pad(R) * p2) : nullptr;
+    float *vinv16 = v16 ? c.take<float>(256) : nullptr;
+    unsigned *mx = v16 ? c.take<unsigned>(6 * (size_t)R) : nullptr;  // vmax[2], mmax[2], gmax[2]
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 2048), (unsigned)R);
@@ -872,6 +994,13 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     GP_TRY_CUDA(cudaMemsetAsync(M, 0, sizeof(T) * R * n, st));
     GP_TRY_CUDA(cudaMemcpyAsync(r, Bn, sizeof(T) * R * n, cudaMemcpyDeviceToDevice, st));
     fill_int_kernel<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 4096), 256, 0, st>>>(slot, n, -1);
+    if (v16) {
+        GP_TRY_CUDA(cudaMemsetAsync(V16, 0, sizeof(__half) * (size_t)tc_rhs_pad(R) * p2, st));
+        GP_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned) * 6 * (size_t)R, st));
+        if constexpr (std::is_same<T, float>::value)
+            absmax_cols_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(n, 256), 256), (unsigned)R), 256, 0, st>>>(
+                V, n, mx);  // vmax[0] = max |v0| (the normalised warm start)
+    }
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
     sgd_start_kernel<<<1, 32, 0, st>>>(R, P, part, rsq, sd, (long long)max_iters, tol, stop_rule);
     GP_TRY(check_launch("sgd setup", 7));
@@ -905,6 +1034,8 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     }
     int64_t t = 0, chunk = 8;
     const T lrb = (T)(lr / (double)batch);
+    const unsigned gsz = (unsigned)std::min<int64_t>(cdiv(n, 256), 2048);
+    unsigned *vmax = mx, *mmax = mx ? mx + 2 * R : nullptr, *gmx = mx ? mx + 4 * R : nullptr;
     while (!hs.done && t < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - t);
         for (int64_t it = 0; it < k; ++it, ++t) {
@@ -915,6 +1046,8 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
             if constexpr (std::is_same<T, float>::value) {
                 if (prec == GP_PREC_TC16) {
                     GP_TRY(tc_prepare_rows(kp, Xb, batch, ta.cols, rbuf, &ta.rows, st));
+                    ta.V16pre = (v16 && t > 0) ? V16 : nullptr;  // written by the previous step
+                    ta.vinv_pre = vinv16;
                     GP_TRY(tc_mvm(ta, tw, twb, st));
                 } else {
                     MvmArgs<T> a{};
@@ -930,8 +1063,15 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
                 a.alpha = T(1); a.beta = T(0); a.diag_coef = T(0); a.done = &sd->done;
                 GP_TRY(mvm_simt<T>(a, pw, pwb, st));
             }
-            sgd_grad_kernel<T><<<dim3(nbg, R), 256, 0, st>>>(G, V, Bn, r, n, bi, batch, kp.sigma2, slot, dpart, sd);
-            sgd_step_kernel<T><<<gv, 256, 0, st>>>(V, M, r, G, n, batch, slot, (T)rho, lrb, sd);
+            const int pc = (int)(t & 1), pn = (int)((t + 1) & 1);
+            sgd_grad_kernel<T><<<dim3(nbg, R), 256, 0, st>>>(G, V, Bn, r, n, bi, batch, kp.sigma2, slot, dpart, sd,
+                                                            v16 ? gmx + pc * R : nullptr,
+                                                            v16 ? vmax + pn * R : nullptr,
+                                                            v16 ? mmax + pn * R : nullptr);
+            const SgdOperand o16{V16, p2, vinv16, v16 ? vmax + pc * R : nullptr, v16 ? mmax + pc * R : nullptr,
+                                 v16 ? vmax + pn * R : nullptr, v16 ? mmax + pn * R : nullptr,
+                                 v16 ? gmx + pc * R : nullptr, v16 ? gmx + pn * R : nullptr};
+            sgd_step_kernel<T><<<gsz, 256, 0, st>>>(V, M, r, G, n, batch, R, slot, (T)rho, lrb, sd, o16);
             sgd_clear_slots_kernel<<<(unsigned)cdiv(batch, 256), 256, 0, st>>>(bi, batch, slot, sd);
             sgd_norm_kernel<<<1, 32, 0, st>>>(R, nbg, dpart, rsq, sd, (long long)max_iters, tol, stop_rule);
             GP_TRY(check_launch("sgd iteration", 4));
