@@ -197,28 +197,56 @@ __global__ void identity_kernel(T *Zb, int bsp, int nb) {
     }
 }
 
-// score[b] = sum_{rows of block b} (sum_c r_c[row])^2.  The row's sum over the right-hand sides
-// is taken in the vectors' own precision (FP64 runs at 1/74 of the FP32 rate on this GPU; an
-// FP32 sum of R FP32 values is within R u of the exact one), the block's sum of squares in FP64.
+// One pass over r per iteration for both of the solver's reductions: score[b] = sum over the rows
+// of block b of (sum_c r_c[row])^2 (the row sums in the vectors' precision) and bpart[c][b] =
+// sum over the rows of block b of r_c[row]^2 (the split norms' partials).  One CTA of 256
+// threads per block of at most 1024 rows; each warp sums its rows' squares per column by
+// shuffles into its own shared-memory slot (no block barrier inside the column loop), the
+// warps' slots are added in a fixed order at the end (FP64).  R <= 512.
 template <typename T>
-__global__ void ap_score_kernel(const T *r, int64_t n, int R, int bs, double *score, const SolverState *st) {
-    if (st->done) return;
-    const int b = blockIdx.x;
+__global__ void __launch_bounds__(256) ap_score_norm_kernel(const T *r, int64_t n, int R, int bs, double *score,
+                                                            double *bpart, const SolverState *st, int skip_done) {
+    if (skip_done && st->done) return;
+    const int b = blockIdx.x, nb = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t lo = (int64_t)b * bs, hi = min(n, lo + bs);
-    double s = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        T t = T(0);
-        for (int c = 0; c < R; ++c) t += r[(int64_t)c * n + i];
-        s += (double)(t * t);
+    constexpr int kRows = 4;  // rows per thread (bs <= 1024)
+    __shared__ T wsq[8][512];  // in the vectors' precision (FP32 squares of an FP64 residual underflow)
+    __shared__ double red[8];
+    T t[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) t[k] = T(0);
+    for (int c = 0; c < R; ++c) {
+        const T *rc = r + (int64_t)c * n;
+        T sq = T(0);
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
+            const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
+            if (i < hi) {
+                const T x = rc[i];
+                t[k] += x;
+                sq += x * x;
+            }
+        }
+        T v = sq;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) wsq[warp][c] = v;
     }
-    __shared__ double red[32];
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) s += (double)(t[k] * t[k]);
     s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    if (lane == 0) red[warp] = s;
     __syncthreads();
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double a = 0.0;
+        for (int w = 0; w < 8; ++w) a += (double)wsq[w][c];
+        bpart[(int64_t)c * nb + b] = a;
+    }
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        score[b] = t;
+        double a = 0.0;
+        for (int w = 0; w < 8; ++w) a += red[w];
+        score[b] = a;
     }
 }
 
@@ -360,6 +388,7 @@ size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec) {
     c.take<double>((size_t)R * P);
     c.take<double>((size_t)R);
     c.take<double>((size_t)nb);
+    c.take<double>((size_t)R * nb);        // per-block partials of ||r_c||^2
     c.take<int64_t>(1);
     c.take<int>(1);
     c.take<SolverState>(1);
@@ -390,6 +419,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     double *part = c.take<double>((size_t)R * P);
     double *scale = c.take<double>(R);
     double *score = c.take<double>(nb);
+    double *bpart = c.take<double>((size_t)R * nb);
     int64_t *col0 = c.take<int64_t>(1);
     int *fail = c.take<int>(1);
     SolverState *sd = c.take<SolverState>(1);
@@ -444,8 +474,8 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(check_launch("ap setup", 3));
     GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
-    coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
-    ap_norm_kernel<<<1, 256, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, exact_start ? 2 : 1);
+    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0);
+    ap_norm_kernel<<<1, 256, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule, exact_start ? 2 : 1);
     GP_TRY(check_launch("ap start", 3));
 
     int hfail = 0;
@@ -528,11 +558,11 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     while (!hs.done && t < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - t);
         for (int64_t it = 0; it < k; ++it, ++t) {
-            ap_score_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, sd);
+            // the scores of the current residual come from the previous pass over r
             ap_select_kernel<<<1, 1024, 0, st>>>(score, nb, bs, col0, sd);
             ap_delta_kernel<T><<<gdel, 256, 0, st>>>(Hb, bsp, bs, r, n, R, col0, dpart, sd);
             ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, R, col0, dpart, delta, sd);
-            GP_TRY(check_launch("ap iteration", 4));
+            GP_TRY(check_launch("ap iteration", 3));
             if constexpr (std::is_same<T, float>::value) {
                 if (tc_panel) {
                     GP_TRY(tc_mvm(ta, tw, twb, st));
@@ -542,8 +572,8 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             } else {
                 GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
             }
-            coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, &sd->done);
-            ap_norm_kernel<<<1, 256, 0, st>>>(R, P, part, sd, (long long)max_iters, tol, stop_rule, 0);
+            ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 1);
+            ap_norm_kernel<<<1, 256, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule, 0);
             GP_TRY(check_launch("ap norms", 2));
         }
         chunk = std::min<int64_t>(chunk * 2, 64);
@@ -560,7 +590,9 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         true_residual_kernel<T, T><<<gp_, 256, 0, st>>>(B, HV, r, n, P, scale, part, nullptr);
     }
     true_state_kernel<<<1, 256, 0, st>>>(R, P, nullptr, part, nullptr, sd, (long long)max_iters, tol, stop_rule, 1);
-    GP_TRY(check_launch("ap true residual", 2));
+    // the block scores of the replaced residual (for the next selection; its norms are set)
+    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0);
+    GP_TRY(check_launch("ap true residual", 3));
     GP_TRY(poll_state(sd, &hs, st));
     t = hs.iter;
     if (hs.done) break;

@@ -713,7 +713,8 @@ __global__ void sgd_gather_kernel(const T *X, int d, const int32_t *idx, int64_t
 template <typename T>
 __global__ void sgd_grad_kernel(T *G, const T *V, const T *Bn, T *r, int64_t n, const int32_t *idx,
                                 int64_t batch, T sigma2, const int *slot, double *rsq_delta_part,
-                                const SolverState *st, unsigned *gmax, unsigned *vmax_zero, unsigned *mmax_zero) {
+                                const SolverState *st, unsigned *gmax, const float *pv, const float *pm, int nblk,
+                                float *vmax, float *mmax) {
     if (st->done) return;
     const int c = blockIdx.y;
     double s = 0.0;
@@ -732,9 +733,31 @@ __global__ void sgd_grad_kernel(T *G, const T *V, const T *Bn, T *r, int64_t n, 
     if (gmax) {
         for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
         if ((threadIdx.x & 31) == 0) atomicMax(&gmax[c], __float_as_uint(gm));
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            vmax_zero[c] = 0u;
-            mmax_zero[c] = 0u;
+        if (pv && blockIdx.x == 0) {
+            // the previous step's maxima of v and m from its blocks' partial maxima
+            float a = 0.0f, b = 0.0f;
+            for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+                a = fmaxf(a, pv[(int64_t)c * nblk + k]);
+                b = fmaxf(b, pm[(int64_t)c * nblk + k]);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+                b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+            }
+            __shared__ float s_a[32], s_b[32];
+            if ((threadIdx.x & 31) == 0) {
+                s_a[threadIdx.x >> 5] = a;
+                s_b[threadIdx.x >> 5] = b;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                    a = fmaxf(a, s_a[w]);
+                    b = fmaxf(b, s_b[w]);
+                }
+                vmax[c] = a;
+                mmax[c] = b;
+            }
         }
     }
     __shared__ double red[32];
@@ -751,105 +774,133 @@ __global__ void sgd_grad_kernel(T *G, const T *V, const T *Bn, T *r, int64_t n, 
 // The next row panel's fp16 operand, written by the step kernel (tensor-core form): V16[c][i] =
 // fp16(v_c[i] 2^(1-e_c)) with a power-of-two scale from a bound on max_i |v_c[i]| known before
 // the step, B = max|v_old| + rho max|m_old| + (lr/b) max|g| >= max|v_old + m_new| (the maxima
-// exact: the previous step's, taken with atomicMax on float bits, and the batch gradient's);
-// vinv[c] = 2^(e_c - 1).  The maxima are double-buffered by iteration parity.
+// exact: the previous step's, from its per-block partial maxima reduced by the next gradient
+// kernel, and the batch gradient's); vinv[c] = 2^(e_c - 1).
 struct SgdOperand {
     __half *V16;
     int64_t p2;
     float *vinv;
-    const unsigned *vmax_cur, *mmax_cur;  // this step's inputs' maxima
-    unsigned *vmax_next, *mmax_next;      // this step's outputs' maxima (zeroed before the step)
-    const unsigned *gmax;                 // the batch gradient's maxima (this iteration)
-    unsigned *gmax_next;                  // zeroed here for the next iteration's gradient
+    const float *vmax, *mmax;  // maxima of this step's inputs v, m (per column)
+    float *pv, *pm;            // this step's per-block maxima of its outputs (R x nblk)
+    int nblk;
+    const unsigned *gmax;      // the batch gradient's maxima (this iteration, float bits)
+    unsigned *gmax_next;       // zeroed here for the next iteration's gradient
 };
 
-// Dense step over all rows: m = rho m - (lr/b) g ; v += m ; r[i] = g on batch rows.  One thread
-// per row over all right-hand sides (the row's batch slot read once); warps walk the rows in
-// warp-aligned strides so that the maxima's shuffles always see full warps.  256 threads.
-constexpr int kSgdMaxR = 512;
-template <typename T>
-__global__ void __launch_bounds__(256) sgd_step_kernel(T *Vv, T *M, T *r, const T *G, int64_t n, int64_t batch, int R,
-                                                       const int *slot, T rho, T lrb, const SolverState *st,
-                                                       SgdOperand op16) {
+// W consecutive elements as one 16-byte access (W = 1: scalar).
+template <typename T, int W>
+struct SgdVec {
+    using type = T;
+};
+template <>
+struct SgdVec<float, 4> {
+    using type = float4;
+};
+template <>
+struct SgdVec<double, 2> {
+    using type = double2;
+};
+constexpr int kSgdUnroll = 2;  // row groups per thread with their loads in flight together
+
+// Dense step over all rows: m = rho m - (lr/b) g ; v += m ; r[i] = g on batch rows.  grid
+// (blocks, R): one column per blockIdx.y; each thread takes W consecutive rows (one 16-byte load
+// of m and of v) in kSgdUnroll grid-strided groups whose loads are issued before any arithmetic,
+// so that enough bytes are in flight for HBM.  Requires n % W == 0 and 16-byte aligned columns
+// for W > 1.  With the fp16 operand each thread keeps running maxima of |v| and |m|, and each
+// block writes its maxima (no atomics).
+template <typename T, int W>
+__global__ void __launch_bounds__(256) sgd_step_kernel(T *__restrict__ Vv, T *__restrict__ M, T *__restrict__ r,
+                                                       const T *__restrict__ G, int64_t n, int64_t batch,
+                                                       const int *__restrict__ slot, T rho, T lrb,
+                                                       const SolverState *st, SgdOperand op16) {
+    using VT = typename SgdVec<T, W>::type;
     if (st->done) return;
-    __shared__ float s_scale[kSgdMaxR];
-    __shared__ unsigned s_vmax[8][64];  // per warp, the current chunk of 64 columns
-    __shared__ unsigned s_mmax[8][64];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.y;
     const bool f16 = op16.V16 != nullptr;
+    float scale = 1.0f;
     if (f16) {
-        for (int c = threadIdx.x; c < R; c += blockDim.x) {
-            const double bnd = (double)__uint_as_float(op16.vmax_cur[c]) + (double)rho * __uint_as_float(op16.mmax_cur[c]) +
-                               (double)lrb * __uint_as_float(op16.gmax[c]);
-            float scale = 1.0f;
-            int e = 0;
-            if (bnd > 0.0 && isfinite(bnd)) {
-                frexp(bnd * (1.0 + 1e-6), &e);  // |v| 2^(1-e) < 2
-                scale = ldexpf(1.0f, 1 - e);
-            }
-            s_scale[c] = scale;
-            if (blockIdx.x == 0) {
-                op16.vinv[c] = 1.0f / scale;
-                op16.gmax_next[c] = 0u;
-            }
+        const double bnd = (double)op16.vmax[c] + (double)rho * op16.mmax[c] + (double)lrb * __uint_as_float(op16.gmax[c]);
+        int e = 0;
+        if (bnd > 0.0 && isfinite(bnd)) {
+            frexp(bnd * (1.0 + 1e-6), &e);  // |v| 2^(1-e) < 2
+            scale = ldexpf(1.0f, 1 - e);
         }
-        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            op16.vinv[c] = 1.0f / scale;
+            op16.gmax_next[c] = 0u;
+        }
     }
-    // columns in chunks of 64 so that the per-warp maxima fit shared memory
-    for (int cb = 0; cb < R; cb += 64) {
-        const int ce = min(R, cb + 64);
-        if (f16) {
-            for (int e = threadIdx.x; e < 8 * 64; e += blockDim.x) {
-                s_vmax[e >> 6][e & 63] = 0u;
-                s_mmax[e >> 6][e & 63] = 0u;
+    VT *Vc = reinterpret_cast<VT *>(Vv + (int64_t)c * n);
+    VT *Mc = reinterpret_cast<VT *>(M + (int64_t)c * n);
+    T *rc = r + (int64_t)c * n;
+    const T *Gc = G + (int64_t)c * batch;
+    const int64_t nv = n / W, stride = (int64_t)gridDim.x * blockDim.x;
+    float vm = 0.0f, mm = 0.0f;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < nv; j0 += kSgdUnroll * stride) {
+        VT mv[kSgdUnroll], vv[kSgdUnroll];
+#pragma unroll
+        for (int u = 0; u < kSgdUnroll; ++u) {
+            const int64_t j = j0 + u * stride;
+            if (j < nv) {
+                mv[u] = Mc[j];
+                vv[u] = Vc[j];
             }
-            __syncthreads();
         }
-        for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n;
-             i0 += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t i = i0 + lane;
-            const bool act = i < n;
-            const int q = act ? slot[i] : -1;
-            for (int c = cb; c < ce; ++c) {
-                const int64_t e = (int64_t)c * n + i;
-                T v = T(0), m = T(0);
-                if (act) {
-                    const T g = (q >= 0) ? G[(int64_t)c * batch + q] : T(0);
-                    m = rho * M[e] - lrb * g;
-                    M[e] = m;
-                    v = Vv[e] + m;
-                    Vv[e] = v;
-                    if (q >= 0) r[e] = g;
-                }
-                if constexpr (std::is_same<T, float>::value) {
-                    if (f16) {
-                        if (act) op16.V16[(int64_t)c * op16.p2 + i] = __float2half_rn(v * s_scale[c]);
-                        // exact maxima for the next step's bound (non-negative floats order as their bits)
-                        unsigned vb = __float_as_uint(fabsf(v)), mb = __float_as_uint(fabsf(m));
-                        for (int o = 16; o > 0; o >>= 1) {
-                            vb = max(vb, __shfl_xor_sync(0xffffffffu, vb, o));
-                            mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-                        }
-                        if (lane == 0) {
-                            s_vmax[warp][c - cb] = max(s_vmax[warp][c - cb], vb);
-                            s_mmax[warp][c - cb] = max(s_mmax[warp][c - cb], mb);
-                        }
+#pragma unroll
+        for (int u = 0; u < kSgdUnroll; ++u) {
+            const int64_t j = j0 + u * stride;
+            if (j >= nv) break;
+            T *m = reinterpret_cast<T *>(&mv[u]);
+            T *v = reinterpret_cast<T *>(&vv[u]);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const int64_t i = j * W + k;
+                const int q = slot[i];
+                const T g = (q >= 0) ? Gc[q] : T(0);
+                m[k] = rho * m[k] - lrb * g;
+                v[k] += m[k];
+                if (q >= 0) rc[i] = g;
+            }
+            Mc[j] = mv[u];
+            Vc[j] = vv[u];
+            if constexpr (std::is_same<T, float>::value) {
+                if (f16) {
+                    alignas(8) __half h[W];
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        h[k] = __float2half_rn(v[k] * scale);
+                        vm = fmaxf(vm, fabsf(v[k]));
+                        mm = fmaxf(mm, fabsf(m[k]));
+                    }
+                    __half *dst = op16.V16 + (int64_t)c * op16.p2 + j * W;
+                    if constexpr (W == 4) {
+                        *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(h);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < W; ++k) dst[k] = h[k];
                     }
                 }
             }
         }
-        if (f16) {
-            __syncthreads();
-            for (int c = cb + threadIdx.x; c < ce; c += blockDim.x) {
-                unsigned vb = 0u, mb = 0u;
-                for (int w = 0; w < 8; ++w) {
-                    vb = max(vb, s_vmax[w][c - cb]);
-                    mb = max(mb, s_mmax[w][c - cb]);
-                }
-                atomicMax(&op16.vmax_next[c], vb);
-                atomicMax(&op16.mmax_next[c], mb);
+    }
+    if (f16) {
+        __shared__ float s_v[8], s_m[8];
+        for (int o = 16; o > 0; o >>= 1) {
+            vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+            mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_v[threadIdx.x >> 5] = vm;
+            s_m[threadIdx.x >> 5] = mm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                vm = fmaxf(vm, s_v[w]);
+                mm = fmaxf(mm, s_m[w]);
             }
-            __syncthreads();
+            op16.pv[(int64_t)c * op16.nblk + blockIdx.x] = vm;
+            op16.pm[(int64_t)c * op16.nblk + blockIdx.x] = mm;
         }
     }
 }
@@ -945,7 +996,9 @@ size_t sgd_workspace(int64_t n, int d, int R, int64_t batch, int prec) {
     if (std::is_same<T, float>::value && prec == GP_PREC_TC16 && R <= 128) {
         c.take<__half>((size_t)tc_rhs_pad(R) * tc_cols_pad(n));  // the step's fp16 operand of v
         c.take<float>(256);
-        c.take<unsigned>(6 * (size_t)R);                         // maxima of v, m, g (x 2)
+        c.take<float>(2 * (size_t)R);                            // maxima of v, m
+        c.take<unsigned>(2 * (size_t)R);                         // maxima of g (x 2)
+        c.take<float>(2 * (size_t)R * 2048);                     // the step's per-block maxima
     }
     return c.bytes();
 }
@@ -979,7 +1032,9 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     const int64_t p2 = tc_cols_pad(n);
     __half *V16 = v16 ? c.take<__half>((size_t)tc_rhs_pad(R) * p2) : nullptr;
     float *vinv16 = v16 ? c.take<float>(256) : nullptr;
-    unsigned *mx = v16 ? c.take<unsigned>(6 * (size_t)R) : nullptr;  // vmax[2], mmax[2], gmax[2]
+    float *vmm = v16 ? c.take<float>(2 * (size_t)R) : nullptr;          // vmax, mmax
+    unsigned *gmx = v16 ? c.take<unsigned>(2 * (size_t)R) : nullptr;    // gmax[2]
+    float *pvm = v16 ? c.take<float>(2 * (size_t)R * 2048) : nullptr;   // per-block maxima of v, m
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 2048), (unsigned)R);
@@ -996,10 +1051,11 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     fill_int_kernel<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 4096), 256, 0, st>>>(slot, n, -1);
     if (v16) {
         GP_TRY_CUDA(cudaMemsetAsync(V16, 0, sizeof(__half) * (size_t)tc_rhs_pad(R) * p2, st));
-        GP_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned) * 6 * (size_t)R, st));
+        GP_TRY_CUDA(cudaMemsetAsync(vmm, 0, sizeof(float) * 2 * (size_t)R, st));
+        GP_TRY_CUDA(cudaMemsetAsync(gmx, 0, sizeof(unsigned) * 2 * (size_t)R, st));
         if constexpr (std::is_same<T, float>::value)
             absmax_cols_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(n, 256), 256), (unsigned)R), 256, 0, st>>>(
-                V, n, mx);  // vmax[0] = max |v0| (the normalised warm start)
+                V, n, reinterpret_cast<unsigned *>(vmm));  // max |v0| (non-negative float bits = the float)
     }
     coldot_kernel<T><<<gp_, 256, 0, st>>>(r, r, n, P, part, nullptr);
     sgd_start_kernel<<<1, 32, 0, st>>>(R, P, part, rsq, sd, (long long)max_iters, tol, stop_rule);
@@ -1034,8 +1090,14 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     }
     int64_t t = 0, chunk = 8;
     const T lrb = (T)(lr / (double)batch);
-    const unsigned gsz = (unsigned)std::min<int64_t>(cdiv(n, 256), 2048);
-    unsigned *vmax = mx, *mmax = mx ? mx + 2 * R : nullptr, *gmx = mx ? mx + 4 * R : nullptr;
+    float *vmax = vmm, *mmax = vmm ? vmm + R : nullptr;
+    float *pv = pvm, *pm = pvm ? pvm + (size_t)R * 2048 : nullptr;
+    // the step kernel's launch: 16-byte accesses where every column starts 16-byte aligned
+    constexpr int kW = 16 / sizeof(T);
+    const bool vec = (n % kW == 0) && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(M) |
+                                        reinterpret_cast<uintptr_t>(r)) % 16 == 0);
+    const dim3 gs((unsigned)std::min<int64_t>(cdiv(vec ? n / kW : n, 256 * kSgdUnroll), 2048), (unsigned)R);
+    const int nblk = (int)gs.x;  // <= 2048, the per-block maxima's row length
     while (!hs.done && t < max_iters) {
         int64_t k = std::min<int64_t>(chunk, max_iters - t);
         for (int64_t it = 0; it < k; ++it, ++t) {
@@ -1065,13 +1127,14 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
             }
             const int pc = (int)(t & 1), pn = (int)((t + 1) & 1);
             sgd_grad_kernel<T><<<dim3(nbg, R), 256, 0, st>>>(G, V, Bn, r, n, bi, batch, kp.sigma2, slot, dpart, sd,
-                                                            v16 ? gmx + pc * R : nullptr,
-                                                            v16 ? vmax + pn * R : nullptr,
-                                                            v16 ? mmax + pn * R : nullptr);
-            const SgdOperand o16{V16, p2, vinv16, v16 ? vmax + pc * R : nullptr, v16 ? mmax + pc * R : nullptr,
-                                 v16 ? vmax + pn * R : nullptr, v16 ? mmax + pn * R : nullptr,
-                                 v16 ? gmx + pc * R : nullptr, v16 ? gmx + pn * R : nullptr};
-            sgd_step_kernel<T><<<gsz, 256, 0, st>>>(V, M, r, G, n, batch, R, slot, (T)rho, lrb, sd, o16);
+                                                            v16 ? gmx + pc * R : nullptr, (v16 && t > 0) ? pv : nullptr,
+                                                            pm, nblk, vmax, mmax);
+            const SgdOperand o16{V16, p2, vinv16, vmax, mmax, pv, pm, nblk, v16 ? gmx + pc * R : nullptr,
+                                 v16 ? gmx + pn * R : nullptr};
+            if (vec)
+                sgd_step_kernel<T, kW><<<gs, 256, 0, st>>>(V, M, r, G, n, batch, slot, (T)rho, lrb, sd, o16);
+            else
+                sgd_step_kernel<T, 1><<<gs, 256, 0, st>>>(V, M, r, G, n, batch, slot, (T)rho, lrb, sd, o16);
             sgd_clear_slots_kernel<<<(unsigned)cdiv(batch, 256), 256, 0, st>>>(bi, batch, slot, sd);
             sgd_norm_kernel<<<1, 32, 0, st>>>(R, nbg, dpart, rsq, sd, (long long)max_iters, tol, stop_rule);
             GP_TRY(check_launch("sgd iteration", 4));

@@ -357,11 +357,13 @@ def test_tc16_ap_reaches_tolerance_true_residual(dev):
     assert abs(info.res_y - rn[0]) <= 1e-4 and abs(info.res_z - rn[1:].mean()) <= 1e-4
 
 
-def test_tc16_sgd_iterates_match_oracle(dev):
+@pytest.mark.parametrize("n", [3000, 3001])
+def test_tc16_sgd_iterates_match_oracle(dev, n):
     """Tensor-core row panel (batch rows against all points, many column splits): a few
-    iterations of Alg. 3 against the oracle."""
+    iterations of Alg. 3 against the oracle (n = 3001: the step's scalar path, rows not a
+    multiple of the 16-byte vector)."""
     rng = np.random.default_rng(19)
-    n, d, R, batch, iters = 3000, 4, 4, 64, 4
+    d, R, batch, iters = 4, 4, 64, 4
     X = rng.standard_normal((n, d)).astype(np.float32)
     th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.6]])
     B = rng.standard_normal((R, n)).astype(np.float32)
@@ -374,10 +376,11 @@ def test_tc16_sgd_iterates_match_oracle(dev):
     assert rel(V.double().cpu().numpy(), Vr) < 5e-3
 
 
+@pytest.mark.parametrize("n", [180, 181])
 @pytest.mark.parametrize("prec_name,prec,tol", [("f64", None, 1e-9), ("f32", gp.GP_PREC_FP32, 1e-4)])
-def test_sgd_iterates_match_oracle(dev, prec_name, prec, tol):
+def test_sgd_iterates_match_oracle(dev, prec_name, prec, tol, n):
     rng = np.random.default_rng(9)
-    n, d, R, batch, iters = 180, 3, 4, 16, 25
+    d, R, batch, iters = 3, 4, 16, 25
     X = rng.standard_normal((n, d))
     th = np.concatenate([rng.uniform(0.7, 1.3, size=d), [1.0, 0.6]])
     B = rng.standard_normal((R, n))
