@@ -219,7 +219,8 @@ size_t gp_kernel_mvm_f64_workspace(int64_t n1, int64_t n2, int d, int nrhs);
  *   tol      : relative residual tolerance tau; stop_rule a gp_stop_t.
  * A column whose gamma = r^T r falls to <= 1e-30 is frozen.  The iterations carry
  * Alg. 1's recursive residual; when the loop stops on it, the true residual
- * b~ - H v is recomputed once (one product, FP64 differences and norms) and the
+ * b~ - H v is recomputed once (one product; each difference rounded about once, the
+ * norms accumulated in FP64) and the
  * tolerance is judged on it: a solve whose true residual misses tau restarts from
  * it (d = r) within its budget, and info's res_y / res_z are always true-residual
  * norms.  That true residual is taken with an FP32-class product: the split

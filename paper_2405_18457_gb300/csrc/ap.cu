@@ -548,7 +548,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     }
     const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16), (unsigned)kSplitK);
     // The residual of Alg. 2 is updated by the panel products (recursive); when the loop stops
-    // on it, the true residual b~ - H v is recomputed (FP64 differences and norms) and replaces
+    // on it, the true residual b~ - H v is recomputed (differences rounded once, FP64 norms) and replaces
     // it; the tolerance is judged on it, and a solve whose true residual misses the tolerance is
     // resumed within its budget, so the reported norms are true-residual norms.
     int64_t t = 0, chunk = 8;

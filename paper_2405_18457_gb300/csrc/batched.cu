@@ -203,13 +203,12 @@ __global__ void bt_scale_cols_kernel(const BMember *mem, const BChunk *chunks, i
     for (int q = blockIdx.x; q < nch; q += gridDim.x) {
         const BChunk k = chunks[q];
         const BMember &m = mem[k.member];
-        const double sc = scale[(int64_t)k.member * R + c];
-        const double f = inv ? 1.0 / sc : sc;
+        const ColFactor f = block_factor(scale + (int64_t)k.member * R, c, inv);
         float *v = V + m.vo + (int64_t)c * m.n;
         for (int r = threadIdx.x; r < kBatchChunk; r += blockDim.x) {
             const int64_t i = (int64_t)k.start + r;
             if (i >= m.n) break;
-            v[i] = (float)((double)v[i] * f);
+            v[i] = fmaf(v[i], f.h, v[i] * f.l);
         }
     }
 }
@@ -221,12 +220,12 @@ __global__ void bt_init_residual_kernel(const BMember *mem, const BChunk *chunks
     for (int q = blockIdx.x; q < nch; q += gridDim.x) {
         const BChunk k = chunks[q];
         const BMember &m = mem[k.member];
-        const double f = 1.0 / scale[(int64_t)k.member * R + c];
+        const ColFactor f = block_factor(scale + (int64_t)k.member * R, c, 1);
         const int64_t base = m.vo + (int64_t)c * m.n;
         for (int rr = threadIdx.x; rr < kBatchChunk; rr += blockDim.x) {
             const int64_t i = (int64_t)k.start + rr;
             if (i >= m.n) break;
-            const float v = (float)((double)B[base + i] * f) - HV[base + i];
+            const float v = fmaf(B[base + i], f.h, fmaf(B[base + i], f.l, -HV[base + i]));
             r[base + i] = v;
             d[base + i] = v;
         }
@@ -337,8 +336,9 @@ __global__ void bt_check_flags_kernel(int G, const int *done, const int *cdone, 
 }
 
 // True residual r = b~ - H v of each member not flagged in skip (App. B "Linear System Solver"),
-// FP64 differences stored in FP32 and also as the restart direction d (used only if the member
-// misses the tolerance and resumes), partial sums of ||r||^2 (from the FP64 differences).
+// each difference two FP32 fused multiply-adds (1 / scale as a sum of two floats), stored as r
+// and as the restart direction d (used only if the member misses the tolerance and resumes);
+// partial sums of ||r||^2 with four FP32 squares per FP64 addition.
 __global__ void bt_true_residual_kernel(const BMember *mem, const BChunk *chunks, int nch, const float *B,
                                         const float *HV, float *r, float *d, int R, const double *scale,
                                         double *part, const int *skip) {
@@ -348,17 +348,25 @@ __global__ void bt_true_residual_kernel(const BMember *mem, const BChunk *chunks
         const BChunk k = chunks[q];
         if (skip[k.member]) continue;
         const BMember &m = mem[k.member];
-        const double f = 1.0 / scale[(int64_t)k.member * R + c];
+        const ColFactor f = block_factor(scale + (int64_t)k.member * R, c, 1);
         const int64_t base = m.vo + (int64_t)c * m.n;
         double s = 0.0;
+        float acc = 0.0f;
+        int nacc = 0;
         for (int rr = threadIdx.x; rr < kBatchChunk; rr += blockDim.x) {
             const int64_t i = (int64_t)k.start + rr;
             if (i >= m.n) break;
-            const double v = (double)B[base + i] * f - (double)HV[base + i];
-            r[base + i] = (float)v;
-            d[base + i] = (float)v;
-            s += v * v;
+            const float v = fmaf(B[base + i], f.h, fmaf(B[base + i], f.l, -HV[base + i]));
+            r[base + i] = v;
+            d[base + i] = v;
+            acc = fmaf(v, v, acc);
+            if (++nacc == 4) {
+                s += (double)acc;
+                acc = 0.0f;
+                nacc = 0;
+            }
         }
+        s += (double)acc;
         s = block_sum(s, red);
         if (threadIdx.x == 0) part[(int64_t)c * nch + q] = s;
     }

@@ -265,6 +265,13 @@ struct TcMvmArgs {
     // (a power of two); V is then only read for the diagonal term.
     const void *V16pre;
     const float *vinv_pre;
+    // Optional (persistent schedule, one pass): per column c and CTA b, dotpart[c * G + b] =
+    // the CTA's share of dotv_c^T y_c (dotv with stride lddv); dotpart holds R x 256 doubles.
+    // *dot_parts (when set) receives G, or 0 when the product did not take the sums.
+    const float *dotv;
+    int64_t lddv;
+    double *dotpart;
+    int *dot_parts;
 };
 int tc_rhs_pad(int R);            // right-hand sides padded for the tensor-core product
 int64_t tc_cols_pad(int64_t n);   // columns padded to whole tiles

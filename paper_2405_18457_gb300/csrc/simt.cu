@@ -391,25 +391,34 @@ __global__ void __launch_bounds__(NT) grad_simt_kernel(const GradArgs<T> a, int 
     }
 }
 
-// sum_c lam_c U_c . W_c, per-block partials (the sigma term: dH/dsigma = 2 sigma I).
+// sum_c lam_c U_c . W_c, per-block partials (the sigma term: dH/dsigma = 2 sigma I).  Blocks
+// walk groups of 32 rows (lane = row, so every column read is coalesced); warp w of a block
+// takes the columns c = w, w + 8, ...  The products of a row group and their sum over the
+// warp's columns are taken in T, with one FP64 addition per group (FP64 arithmetic and
+// conversions run at a small fraction of the FP32 rate on this GPU).
 template <typename T>
 __global__ void diag_dot_kernel(const GradArgs<T> a, double *partial) {
     const int64_t n = a.n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double t = a.lam0 * (double)a.U0[i] * (double)a.W0[i];
-        double r = 0.0;
-        for (int c = 1; c < a.R; ++c)
-            r += (double)a.U[(int64_t)(c - 1) * a.ldu + i] * (double)a.W[(int64_t)(c - 1) * a.ldw + i];
-        s += t + a.lam_rest * r;
+    for (int64_t i = (int64_t)blockIdx.x * 32 + lane; i - lane < n; i += (int64_t)gridDim.x * 32) {
+        if (i >= n) continue;
+        T g0 = T(0), gr = T(0);
+        for (int c = warp; c < a.R; c += nw) {
+            if (c == 0)
+                g0 = a.U0[i] * a.W0[i];
+            else
+                gr = fma(a.U[(int64_t)(c - 1) * a.ldu + i], a.W[(int64_t)(c - 1) * a.ldw + i], gr);
+        }
+        s += a.lam0 * (double)g0 + a.lam_rest * (double)gr;
     }
     __shared__ double red[32];
     s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        for (int w = 0; w < nw; ++w) t += red[w];
         partial[blockIdx.x] = t;
     }
 }

@@ -81,28 +81,68 @@ __device__ __forceinline__ double sum_parts(const double *part, int c, int P) {
     return s;
 }
 
+// A block's column factor f = (inv ? 1 / scale[c] : scale[c]) in FP64 and as a sum of two floats
+// fh + fl (f to about 2^-48), computed once by thread 0: FP64 division and float <-> double
+// conversions run at a small fraction of the FP32 rate on this GPU, so taking them in every
+// thread would dominate these memory-bound kernels.  Called by every thread of the block (it
+// synchronises); repeated calls in one kernel are safe.
+struct ColFactor {
+    double d;
+    float h, l;
+};
+__device__ __forceinline__ ColFactor block_factor(const double *scale, int c, int inv) {
+    __shared__ double s_d;
+    __shared__ float s_h, s_l;
+    __syncthreads();  // a previous call's values are no longer read
+    if (threadIdx.x == 0) {
+        const double f = inv ? 1.0 / scale[c] : scale[c];
+        s_d = f;
+        s_h = (float)f;
+        s_l = (float)(f - (double)s_h);
+    }
+    __syncthreads();
+    return ColFactor{s_d, s_h, s_l};
+}
+
 // scale[c] = sqrt(sum parts) + eps
 __global__ void norm_scale_kernel(int R, int P, const double *part, double *scale) {
     for (int c = threadIdx.x; c < R; c += blockDim.x) scale[c] = sqrt(sum_parts(part, c, P)) + kNormEps;
 }
 
-// V[c] *= (inv ? 1/scale[c] : scale[c])
+// V[c] *= (inv ? 1/scale[c] : scale[c]).  For float the FP64 factor is carried as fh + fl, and
+// v f = fma(v, fh, v fl) is the FP64 product rounded about once, in FP32 arithmetic only.
 template <typename T>
 __global__ void scale_cols_kernel(T *V, int64_t n, const double *scale, int inv) {
     const int c = blockIdx.y;
-    const double f = inv ? 1.0 / scale[c] : scale[c];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        V[(int64_t)c * n + i] = (T)((double)V[(int64_t)c * n + i] * f);
+    const ColFactor cf = block_factor(scale, c, inv);
+    if constexpr (std::is_same<T, float>::value) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const float v = V[(int64_t)c * n + i];
+            V[(int64_t)c * n + i] = fmaf(v, cf.h, v * cf.l);
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            V[(int64_t)c * n + i] *= cf.d;
+    }
 }
 
-// r = B / scale - HV ; d = r
+// r = B / scale - HV ; d = r.  For float, b / scale is B fh + B fl (the FP64 factor as a sum of
+// two floats), so the difference sees b / scale to about 2^-48.
 template <typename T>
 __global__ void init_residual_kernel(const T *B, const T *HV, T *r, T *d, int64_t n, const double *scale) {
     const int c = blockIdx.y;
-    const double f = 1.0 / scale[c];
+    const ColFactor cf = block_factor(scale, c, 1);
+    T fh, fl;
+    if constexpr (std::is_same<T, float>::value) {
+        fh = cf.h;
+        fl = cf.l;
+    } else {
+        fh = cf.d;
+        fl = 0.0;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t e = (int64_t)c * n + i;
-        T v = (T)((double)B[e] * f) - HV[e];
+        T v = fma(B[e], fh, fma(B[e], fl, -HV[e]));
         r[e] = v;
         if (d) d[e] = v;
     }
@@ -149,9 +189,11 @@ __device__ void finish_norms_block(SolverState *st, double *sq, int R, long long
 }
 
 // True residual (App. B "Linear System Solver": r = b - H u, here of the normalised system):
-// r = b~ - H v with b~ = b / scale, both terms taken in FP64 and the difference stored in T;
-// the partial sums of ||r||^2 come from the FP64 differences.  Skipped while *skip != 0 (a
-// periodic recomputation enqueued after the solve has stopped).  grid P x R
+// r = b~ - H v with b~ = b / scale.  With an FP64 product (TH = double) the difference is taken
+// in FP64 and stored in T.  With an FP32 product it is two FP32 fused multiply-adds with the FP64
+// factor 1 / scale carried as a sum of two floats (b~ to about 2^-48, the difference rounded
+// about once), and four squares are summed in FP32 per FP64 addition.  The partial sums of
+// ||r||^2 go to partN.  Skipped while *skip != 0.  grid P x R
 template <typename T, typename TH>
 __global__ void true_residual_kernel(const T *B, const TH *Hv, T *r, int64_t n, int P, const double *scale,
                                      double *partN, const int *skip) {
@@ -159,13 +201,30 @@ __global__ void true_residual_kernel(const T *B, const TH *Hv, T *r, int64_t n, 
     const int p = blockIdx.x, c = blockIdx.y;
     const int64_t per = part_len(n, P);
     const int64_t i0 = min(n, (int64_t)p * per), i1 = min(n, i0 + per);
-    const double f = 1.0 / scale[c];
+    const ColFactor cf = block_factor(scale, c, 1);
     const int64_t off = (int64_t)c * n;
     double sum = 0.0;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const double v = (double)B[off + i] * f - (double)Hv[off + i];
-        r[off + i] = (T)v;
-        sum += v * v;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TH, float>::value) {
+        float acc = 0.0f;
+        int k = 0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const float v = fmaf(B[off + i], cf.h, fmaf(B[off + i], cf.l, -Hv[off + i]));
+            r[off + i] = v;
+            acc = fmaf(v, v, acc);
+            if (++k == 4) {
+                sum += (double)acc;
+                acc = 0.0f;
+                k = 0;
+            }
+        }
+        sum += (double)acc;
+    } else {
+        const double f = cf.d;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const double v = (double)B[off + i] * f - (double)Hv[off + i];
+            r[off + i] = (T)v;
+            sum += v * v;
+        }
     }
     __shared__ double red[32];
     sum = warp_sum(sum);

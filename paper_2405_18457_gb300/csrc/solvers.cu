@@ -110,17 +110,18 @@ __global__ void cg_dir_kernel(T *d, const T *r, int64_t n, const double *beta, c
 }
 
 // Fused forms of one iteration without a preconditioner (two launches instead of four).
-// alpha_c = gamma_c / d_c^T H d_c from the d^T H d partials (summed in a fixed order by every
-// block; block 0 of column c records alpha_c), then v += alpha d, r -= alpha Hd and the
-// partial sums of ||r||^2 into partN.  grid P x R
+// alpha_c = gamma_c / d_c^T H d_c from the PD partials of d^T H d per column (summed in a fixed
+// order by every block; block 0 of column c records alpha_c), then v += alpha d, r -= alpha Hd
+// and the partial sums of ||r||^2 into partN.  grid P x R
 template <typename T>
 __global__ void cg_update_fused_kernel(T *v, T *r, const T *d, const T *Hd, int64_t n, int P, const double *partD,
-                                       const double *gcur, double *alpha, double *partN, const SolverState *st) {
+                                       int PD, const double *gcur, double *alpha, double *partN,
+                                       const SolverState *st) {
     if (st->done) return;
     const int p = blockIdx.x, c = blockIdx.y;
     __shared__ double s_al;
     if (threadIdx.x < 32) {
-        const double dHd = sum_parts_warp(partD, c, P);
+        const double dHd = sum_parts_warp(partD, c, PD);
         if (threadIdx.x == 0) {
             const double g = gcur[c];
             const double al = (g > kFreeze && dHd > 0.0 && isfinite(dHd)) ? g / dHd : 0.0;
@@ -346,8 +347,11 @@ struct HOp {
     }
     // Y = alpha * K V + beta * Y + diag (sigma^2 V unless overridden); split: the tensor-core
     // form's split products (FP32-class), for true residuals
+    // dotpart / nparts (tensor-core form): the product also takes the per-CTA partial sums of
+    // V^T Y per column when its schedule allows (*nparts = their count per column, else 0).
     int apply(const T *V, T *Y, const int *done, cudaStream_t st, bool split = false, const void *V16pre = nullptr,
-              const float *vinv_pre = nullptr) {
+              const float *vinv_pre = nullptr, double *dotpart = nullptr, int *nparts = nullptr) {
+        if (nparts) *nparts = 0;
         if constexpr (std::is_same<T, float>::value) {
             if (tc) {
                 TcMvmArgs a{};
@@ -371,6 +375,10 @@ struct HOp {
                 a.split = split ? 1 : 0;
                 a.V16pre = V16pre;
                 a.vinv_pre = vinv_pre;
+                a.dotv = V;
+                a.lddv = n;
+                a.dotpart = dotpart;
+                a.dot_parts = nparts;
                 return tc_mvm(a, ws, wsb, st);
             }
         }
@@ -476,6 +484,7 @@ size_t cg_workspace(int64_t n, int d, int R, int prec, int pc_rank) {
         c.take<__half>((size_t)tc_rhs_pad(R) * tc_cols_pad(n));  // the directions' fp16 operand
         c.take<float>(256);
         c.take<double>(2 * (size_t)R);
+        c.take<double>((size_t)R * 256);                   // d^T H d partials of the product's CTAs
     }
     if (pc_rank > 0) {
         c.take<T>((size_t)R * n);                           // p = P^-1 r
@@ -520,6 +529,7 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     __half *D16 = d16 ? c.take<__half>((size_t)tc_rhs_pad(R) * p2) : nullptr;
     float *vinv16 = d16 ? c.take<float>(256) : nullptr;
     double *dbnd = d16 ? c.take<double>(2 * (size_t)R) : nullptr;
+    double *dotp = d16 ? c.take<double>((size_t)R * 256) : nullptr;
     T *pz = pc ? c.take<T>((size_t)R * n) : nullptr;
     double *partG = pc ? c.take<double>((size_t)R * P) : part;
     const size_t pcb = pc ? precond_workspace<T>(n, R, pc_rank) : 0;
@@ -567,7 +577,7 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     //
     // The iterations carry Alg. 1's recursive residual, which drifts from b~ - H v under the
     // products' rounding.  When the loop stops on it (unless the state already comes from a
-    // true residual), the true residual is recomputed once (FP64 differences and norms) and
+    // true residual), the true residual is recomputed once (differences rounded once, FP64 norms) and
     // the tolerance is judged on it; if it misses, CG restarts from it (d = r, or P^-1 r)
     // within the budget.  The FP32 form recomputes it with the FP64 product: a product of H
     // with the whole iterate carries an error of about u ||H|| ||v||, which in FP32 on an
@@ -596,21 +606,24 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         while (phase < left) {
             const int64_t k = std::min<int64_t>(chunk, left - phase);
             for (int64_t it = 0; it < k; ++it, ++ti) {
-                if (d16_valid)
-                    GP_TRY(op.apply(dd, Hd, done, st, false, D16, vinv16));
-                else
-                    GP_TRY(op.apply(dd, Hd, done, st));
-                coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
+                // d^T H d: partial sums from the product itself where it takes them
+                int nd = 0;
+                GP_TRY(op.apply(dd, Hd, done, st, false, d16_valid ? D16 : nullptr, d16_valid ? vinv16 : nullptr,
+                                pc ? nullptr : dotp, &nd));
+                if (nd == 0) coldot_kernel<T><<<gp_, 256, 0, st>>>(dd, Hd, n, P, part, done);
+                const double *pdot = nd > 0 ? dotp : part;
+                const int ndot = nd > 0 ? nd : P;
                 if (!pc) {
                     const double *gcur = gamma_at(ti);
                     double *gnext = gamma_at(ti + 1);
                     const DirOperand o16{D16, p2, vinv16, d16 ? dbnd + (ti & 1) * R : nullptr,
                                          d16 ? dbnd + ((ti + 1) & 1) * R : nullptr};
-                    cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, part, gcur, alpha, partN, sd);
+                    cg_update_fused_kernel<T><<<gp_, 256, 0, st>>>(V, r, dd, Hd, n, P, pdot, ndot, gcur, alpha, partN,
+                                                                    sd);
                     cg_dir_fused_kernel<T><<<gd, 256, 0, st>>>(dd, r, n, P, partN, gcur, gnext, alpha, sd,
                                                                (long long)max_iters, tol, stop_rule, R, sqn, dcount,
                                                                o16);
-                    GP_TRY(check_launch("cg iteration", 3));
+                    GP_TRY(check_launch("cg iteration", nd > 0 ? 2 : 3));
                     d16_valid = d16;
                 } else {
                     cg_alpha_kernel<<<1, 256, 0, st>>>(R, P, part, gamma, alpha, sd);
@@ -819,16 +832,25 @@ __global__ void __launch_bounds__(256) sgd_step_kernel(T *__restrict__ Vv, T *__
     const bool f16 = op16.V16 != nullptr;
     float scale = 1.0f;
     if (f16) {
-        const double bnd = (double)op16.vmax[c] + (double)rho * op16.mmax[c] + (double)lrb * __uint_as_float(op16.gmax[c]);
-        int e = 0;
-        if (bnd > 0.0 && isfinite(bnd)) {
-            frexp(bnd * (1.0 + 1e-6), &e);  // |v| 2^(1-e) < 2
-            scale = ldexpf(1.0f, 1 - e);
+        // the column's scale, once per block (FP64 arithmetic is slow on this GPU)
+        __shared__ float s_scale;
+        if (threadIdx.x == 0) {
+            const double bnd =
+                (double)op16.vmax[c] + (double)rho * op16.mmax[c] + (double)lrb * __uint_as_float(op16.gmax[c]);
+            int e = 0;
+            float sc = 1.0f;
+            if (bnd > 0.0 && isfinite(bnd)) {
+                frexp(bnd * (1.0 + 1e-6), &e);  // |v| 2^(1-e) < 2
+                sc = ldexpf(1.0f, 1 - e);
+            }
+            s_scale = sc;
+            if (blockIdx.x == 0) {
+                op16.vinv[c] = 1.0f / sc;
+                op16.gmax_next[c] = 0u;
+            }
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            op16.vinv[c] = 1.0f / scale;
-            op16.gmax_next[c] = 0u;
-        }
+        __syncthreads();
+        scale = s_scale;
     }
     VT *Vc = reinterpret_cast<VT *>(Vv + (int64_t)c * n);
     VT *Mc = reinterpret_cast<VT *>(M + (int64_t)c * n);

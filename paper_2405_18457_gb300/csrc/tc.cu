@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cstdio>
 #include <cstdlib>
@@ -57,6 +58,7 @@ constexpr int NTHREADS = 416;     // gradient kernel: producer, 3 MMA issuers, 2
 constexpr int kPersist = -1;       // split code of the persistent product schedule
 constexpr int MVM_THREADS = 384;  // product kernel: producer, MMA, 2 idle, 2 x 4 evaluation warps
 constexpr int kMaxRhsPerPass = 128;  // right-hand sides per product pass (TMEM columns 384..511)
+constexpr int kPersistMaxGrid = 256;  // persistent schedule: at most this many CTAs (d^T y partials per column)
 constexpr int kSplitGroup = 8;       // split form: tiles per tensor-memory accumulation group
 constexpr int kSplitMaxRpad = 80;    // split form: padded right-hand sides per pass (256 + 3 R_pad <= 512)
 constexpr float kLog2e = 1.4426950408889634f;
@@ -209,8 +211,8 @@ struct KParams {
     // persistent schedule (single problem): CTA b takes the (row tile, column tile) pairs
     // [T b / G, T (b+1) / G) in row-major order, T = ptotal, G = pgrid = gridDim.x; a run of
     // pairs in one row tile is a segment.  Only a CTA's first and last segments can miss part
-    // of their row tile; such a segment writes its sums to slot 2 b (first) or 2 b + 1 (last)
-    // and tc_reduce_persist_kernel combines the slots of each row tile.
+    // of their row tile; such a segment writes its sums to slot 2 b (first) or 2 b + 1 (last),
+    // and the last CTA to finish a piece of the row tile combines the slots (see pcnt).
     int persist;
     int64_t ptotal;
     int pgrid;
@@ -222,7 +224,34 @@ struct KParams {
     const int64_t *col0_dev;
     int diag_from_col0;     // diagonal rows start at *col0_dev, clipped to ncols_total
     int64_t ncols_total;
+    // persistent schedule: arrival counters of the shared row tiles' pieces (8 per row tile;
+    // high word the launch's generation pgen, low word the arrivals), and optionally the
+    // partial sums d^T y per column and CTA (dotpart[c * G + b], d = dotv with stride lddv)
+    unsigned long long *pcnt;
+    unsigned pgen;
+    const float *dotv;
+    int64_t lddv;
+    double *dotpart;
 };
+
+// CTA of the persistent schedule that takes pair g (CTA b takes [T b / G, T (b + 1) / G)).
+__device__ __forceinline__ int64_t cta_of_pair(int64_t g, int64_t T, int G) { return ((g + 1) * G + T - 1) / T - 1; }
+
+// Arrival on a shared row tile's piece counter; 1 for the arrival that completes `need` in this
+// launch's generation.  Each retry means another CTA's arrival landed first (a CTA arrives once
+// per piece and launch), so the loop is short; it is bounded all the same.
+__device__ __forceinline__ int arrive_last(unsigned long long *cnt, unsigned gen, unsigned need, volatile int *err) {
+    unsigned long long old = atomicAdd(cnt, 0ull);
+    for (int tries = 0; tries < 4096; ++tries) {
+        const unsigned now = ((unsigned)(old >> 32) == gen) ? (unsigned)old : 0u;
+        const unsigned long long nw = ((unsigned long long)gen << 32) | (unsigned long long)(now + 1);
+        const unsigned long long seen = atomicCAS(cnt, old, nw);
+        if (seen == old) return (now + 1 == need) ? 1 : 0;
+        old = seen;
+    }
+    *err = 1;
+    return 0;
+}
 
 // KAT: 64-wide atoms of the distance contraction (KD / 64); PERSIST: the persistent schedule
 // (single problem; a separate instantiation so that the other schedules keep their code).
@@ -233,6 +262,8 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
     if (p.done && *p.done) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // persistent schedule: d^T y sums per evaluation warp and owned column (4 KB)
+    __shared__ double s_dot[PERSIST ? 8 : 1][PERSIST ? 64 : 1];
     const int katoms = p.KD / 64;
     const int R_pad = p.R_pad;
     const int NPB = p.npb, NV = p.nv;
@@ -536,23 +567,33 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             if (ok && ntiles > 0) {
                 tc_fence_after();
                 const int64_t i = ioff + wq * 32 + lane;
+                const bool diag = diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag;
                 for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
                     uint32_t r[16];
                     tmem_ld16((SPLIT ? tYs : tY) + lane_off + c0, r);
                     tmem_ld_wait();
                     if (i < n1) {
+                        // the loads of the chunk (scales, diagonal vector) before the first store,
+                        // so that they are in flight together (a previous Y, beta != 0, is read
+                        // with the store)
+                        float v[16], vd[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int c = c0 + e;
+                            const bool okc = c < p.R;
+                            v[e] = okc ? sf2 * vinv[c] * __uint_as_float(r[e]) : 0.0f;
+                            vd[e] = (okc && p.nsplit <= 1 && diag) ? Vd[(int64_t)c * ldvd + (i - drow0)] : 0.0f;
+                        }
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             const int c = c0 + e;
                             if (c >= p.R) break;
-                            float v = sf2 * vinv[c] * __uint_as_float(r[e]);
                             if (p.nsplit > 1) {
-                                p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v;
+                                p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v[e];
                             } else {
-                                float y = p.alpha * v;
+                                float y = p.alpha * v[e];
                                 if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
-                                if (diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
-                                    y += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
+                                if (diag) y += diag_coef * vd[e];
                                 Yp[(int64_t)c * ldy + i] = y;
                             }
                         }
@@ -697,62 +738,136 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             // buffer of its own and the warpgroup never waits for GEMM2.
             const int wg = (warp - 4) >> 2;
             const int wq = warp & 3;  // TMEM lane quarter this warp may access
+            const int piece = warp - 4;  // this warp's rows x columns piece of a row tile (of 8)
             const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
             const bool unit = (dsc == 1.0f);
+            const bool dot = p.dotpart != nullptr;
             bool ok = true;
+            s_dot[piece][lane] = 0.0;
+            s_dot[piece][lane + 32] = 0.0;
+            __syncwarp();
+            // d^T y of the rows this CTA finalises: products of one 16-column chunk, summed over
+            // the warp's 32 rows in FP32 and added in FP64 to the warp's slots (chunk k of the
+            // warpgroup's columns c0 = 16 wg + 32 k at 16 k)
+            auto dot_add = [&](const float (&pr)[16], int k) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float v = pr[e];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) s_dot[piece][16 * k + e] += (double)v;
+                }
+            };
+            // Final row i of Y for the 16 columns c0 .. c0 + 15 from their product sums v (alpha,
+            // beta and diagonal terms), and the products dotv y into pr.  The loads of the chunk
+            // are issued before the first store, so that they are in flight together (a previous
+            // Y, beta != 0, is read with the store).
+            auto finish16 = [&](int64_t i, int c0, const float (&v)[16], float (&pr)[16]) {
+                const bool diag = diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag;
+                float vd[16], dv[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int c = c0 + e;
+                    const bool okc = i < n1 && c < p.R;
+                    vd[e] = (okc && diag) ? Vd[(int64_t)c * ldvd + (i - drow0)] : 0.0f;
+                    dv[e] = (okc && dot) ? __ldg(&p.dotv[(int64_t)c * p.lddv + i]) : 0.0f;
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int c = c0 + e;
+                    pr[e] = 0.0f;
+                    if (i < n1 && c < p.R) {
+                        float y = p.alpha * v[e];
+                        if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
+                        if (diag) y += diag_coef * vd[e];
+                        Yp[(int64_t)c * ldy + i] = y;
+                        pr[e] = dv[e] * y;
+                    }
+                }
+            };
+            // A row tile that several CTAs share: each CTA's warp `piece` has written its rows x
+            // columns of the tile's partial sums to its slot; the warp that arrives last on the
+            // piece's counter (of any of those CTAs) sums the slots in CTA order and finishes
+            // the piece's rows.  The counters carry the launch's generation in their high word,
+            // so a count left by an earlier (aborted) launch restarts at zero.
+            auto shared_tile = [&](int64_t r) {
+                const int64_t T = p.ptotal;
+                const int G = (int)gridDim.x;
+                const int64_t bf = cta_of_pair(r * ctiles, T, G), bl = cta_of_pair((r + 1) * ctiles - 1, T, G);
+                __threadfence();  // this lane's slot writes, visible before the arrival
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) last = arrive_last(&p.pcnt[r * 8 + piece], p.pgen, (unsigned)(bl - bf + 1), s_err);
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (!last) return;
+                __syncwarp();  // lane 0's arrival, then every lane's acquire fence and reads
+                __threadfence();
+                const int s0 = (T * bf / G < r * ctiles) ? 1 : 0;  // the first CTA's slot (its last segment)
+                const int row = wq * 32 + lane;
+                const int64_t i = r * TM + row;
+                for (int c0 = 16 * wg, k = 0; c0 < R_pad; c0 += 32, ++k) {
+                    // the slots in CTA order, 16 independent loads per slot
+                    float v[16], pr[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = 0.0f;
+                    for (int64_t q = bf; q <= bl; ++q) {
+                        const float *src = p.partial + ((q * 2 + (q == bf ? s0 : 0)) * p.R) * TM + row;
+                        float t[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            t[e] = (i < n1 && c0 + e < p.R) ? __ldcg(src + (int64_t)(c0 + e) * TM) : 0.0f;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] += t[e];
+                    }
+                    finish16(i, c0, v, pr);
+                    if (dot) dot_add(pr, k);
+                }
+            };
             // Read-out of segment sg's accumulator: final rows when the segment is a whole row
-            // tile of an unsplit product, else partial sums (split slice or persistent slot).
-            // Both warpgroups take alternate 16-column chunks, then release Y to GEMM2.
+            // tile, else this CTA's slot of a shared row tile (slot 2 b for its first segment,
+            // 2 b + 1 for its last).  Both warpgroups take alternate 16-column chunks, release
+            // Y to GEMM2, then (shared tile) arrive on the piece's counter.
             auto epilogue = [&](int sg) {
                 if (!ok) return;
-                ok = mbar_wait(y_full, sg & 1, s_err);
+                ok = mbar_wait_warp(y_full, sg & 1, s_err);
                 if (!ok) return;
                 tc_fence_after();
-                bool whole = p.nsplit <= 1;
-                int64_t io = ioff;
-                if (PERSIST) {
-                    const int64_t r = r_first + sg;
-                    const int64_t s0 = max(tb0, r * ctiles), s1 = min(tb0 + ntiles, (r + 1) * ctiles);
-                    whole = (s0 == r * ctiles) && (s1 == (r + 1) * ctiles);
-                    io = r * TM;
-                }
-                const int64_t i = io + wq * 32 + lane;
-                for (int c0 = 16 * wg; c0 < R_pad; c0 += 32) {
-                    uint32_t r[16];
-                    tmem_ld16(tY + lane_off + c0, r);
+                const int64_t r = r_first + sg;
+                const int64_t s0 = max(tb0, r * ctiles), s1 = min(tb0 + ntiles, (r + 1) * ctiles);
+                const bool whole = (s0 == r * ctiles) && (s1 == (r + 1) * ctiles);
+                const int64_t i = r * TM + wq * 32 + lane;
+                for (int c0 = 16 * wg, k = 0; c0 < R_pad; c0 += 32, ++k) {
+                    uint32_t rr[16];
+                    tmem_ld16(tY + lane_off + c0, rr);
                     tmem_ld_wait();
-                    if (i < n1) {
+                    float v[16];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int c = c0 + e;
-                            if (c >= p.R) break;
-                            float v = sf2 * vinv[c] * __uint_as_float(r[e]);
-                            if (PERSIST && !whole) {
-                                p.partial[(((int64_t)blockIdx.x * 2 + (sg > 0)) * p.R + c) * TM + (wq * 32 + lane)] = v;
-                            } else if (!whole) {
-                                p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v;
-                            } else {
-                                float y = p.alpha * v;
-                                if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
-                                if (diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
-                                    y += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
-                                Yp[(int64_t)c * ldy + i] = y;
-                            }
+                    for (int e = 0; e < 16; ++e) v[e] = (c0 + e < p.R) ? sf2 * vinv[c0 + e] * __uint_as_float(rr[e]) : 0.0f;
+                    if (!whole) {
+                        if (i < n1) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e)
+                                if (c0 + e < p.R)
+                                    p.partial[(((int64_t)blockIdx.x * 2 + (sg > 0)) * p.R + c0 + e) * TM + (wq * 32 + lane)] =
+                                        v[e];
                         }
+                    } else {
+                        float pr[16];
+                        finish16(i, c0, v, pr);
+                        if (dot) dot_add(pr, k);
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(y_empty);
+                if (!whole) shared_tile(r);
             };
-            const int nseg = ntiles <= 0 ? 0 : (PERSIST ? (int)((tb0 + ntiles - 1) / ctiles - r_first) + 1 : 1);
+            const int nseg = ntiles <= 0 ? 0 : (int)((tb0 + ntiles - 1) / ctiles - r_first) + 1;
             int it = wg;
             for (int sg = 0; sg < nseg; ++sg) {
                 // this warpgroup's tiles of segment sg, then the segment's read-out
-                const int seg_end =
-                    PERSIST ? (int)min((int64_t)ntiles, (r_first + sg + 1) * ctiles - tb0) : ntiles;
+                const int seg_end = (int)min((int64_t)ntiles, (r_first + sg + 1) * ctiles - tb0);
                 for (; ok && it < seg_end; it += 2) {
                     const int b = it % 3;
-                    if (!mbar_wait(&t_full[b], (it / 3) & 1, s_err)) {
+                    if (!mbar_wait_warp(&t_full[b], (it / 3) & 1, s_err)) {
                         ok = false;
                         break;
                     }
@@ -773,6 +888,15 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
+    if constexpr (PERSIST) {
+        // this CTA's d^T y partial per column: the four warps of the column's warpgroup, in order
+        if (p.dotpart && threadIdx.x < p.R) {
+            const int c = threadIdx.x, wgc = (c >> 4) & 1, slot = (c >> 5) * 16 + (c & 15);
+            double t = 0.0;
+            for (int q = 0; q < 4; ++q) t += s_dot[wgc * 4 + q][slot];
+            p.dotpart[(int64_t)c * gridDim.x + blockIdx.x] = t;
+        }
+    }
     if (threadIdx.x == 0 && *s_err && p.err) atomicExch(p.err, 1);
 }
 
@@ -790,40 +914,6 @@ __global__ void tc_reduce_kernel(KParams p) {
     float s = 0.0f;
     for (int sp = 0; sp < p.nsplit; ++sp) s += p.partial[((int64_t)sp * p.R + c) * p.n1 + i];
     float y = p.alpha * s;
-    if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
-    if (p.diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
-        y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - drow0)];
-    p.Y[(int64_t)c * p.ldy + i] = y;
-}
-
-// Row tiles of a persistent product that several CTAs share, listed by the host: entry e is
-// row tile r[e], computed by the CTAs bf[e] .. bf[e] + nb[e] - 1; the first of them holds it
-// in slot s0[e] (its last segment), the others in slot 0 (their first segment).
-constexpr int kPTabMax = 256;  // >= the persistent grid (one CTA per SM)
-struct PTable {
-    int n;
-    int r[kPTabMax];
-    short bf[kPTabMax];
-    unsigned short nb[kPTabMax];
-    unsigned char s0[kPTabMax];
-};
-
-// Sums the slots of each shared row tile in CTA order (deterministic), then the epilogue;
-// grid (table entries, right-hand sides), one thread per row.
-__global__ void tc_reduce_persist_kernel(KParams p, const PTable tab) {
-    if (p.done && *p.done) return;
-    const int e = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
-    const int64_t i = (int64_t)tab.r[e] * TM + t;
-    if (i >= p.n1) return;
-    int64_t drow0 = p.drow0, ndiag = p.ndiag;
-    if (p.col0_dev && p.diag_from_col0) {
-        drow0 = *p.col0_dev;
-        ndiag = min(ndiag, p.ncols_total - drow0);
-    }
-    const int64_t b0 = tab.bf[e];
-    float sum = p.partial[((b0 * 2 + tab.s0[e]) * p.R + c) * TM + t];
-    for (int k = 1; k < tab.nb[e]; ++k) sum += p.partial[(((b0 + k) * 2) * p.R + c) * TM + t];
-    float y = p.alpha * sum;
     if (p.beta != 0.0f) y += p.beta * p.Y[(int64_t)c * p.ldy + i];
     if (p.diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag)
         y += p.diag_coef * p.Vd[(int64_t)c * p.ldvd + (i - drow0)];
@@ -923,6 +1013,10 @@ __device__ __forceinline__ uint32_t pack2(__half a, __half b) {
 }
 __device__ __forceinline__ __half lo_half(uint32_t u) { return __ushort_as_half((unsigned short)(u & 0xFFFFu)); }
 __device__ __forceinline__ __half hi_half(uint32_t u) { return __ushort_as_half((unsigned short)(u >> 16)); }
+
+// tc_operands_kernel takes one warp per point: 8 points per 256-thread block, at most 32 blocks
+// per SM (a grid-strided walk beyond that).
+inline unsigned operand_blocks(int64_t n_pad) { return (unsigned)std::min<int64_t>(cdiv(n_pad, 8), 152 * 32); }
 
 __global__ void tc_operands_kernel(const KP<float> kp, float c, const float *X, int64_t n, int64_t n_pad, int KD,
                                    const unsigned int *bound, __half *PA, __half *PB, float *dscale_out,
@@ -1268,7 +1362,7 @@ int num_sms_tc() { return device_sm_count(); }
 // (row tile, column tile) pairs; nseg = the most row segments one CTA can meet.
 void persist_geom(int64_t row_tiles, int64_t col_tiles, int *G, int *nseg) {
     const int64_t T = row_tiles * col_tiles;
-    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(std::min(num_sms_tc(), kPTabMax), T));
+    const int64_t g = std::max<int64_t>(1, std::min<int64_t>(std::min(num_sms_tc(), kPersistMaxGrid), T));
     *G = (int)g;
     *nseg = (int)(cdiv(cdiv(T, g), col_tiles) + 1);
 }
@@ -1611,7 +1705,7 @@ int tc_prepare_points_dev(const KP<float> &kp, const float *X, int64_t n, void *
     GP_TRY_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned int), st));
     const unsigned nb = (unsigned)std::min<int64_t>(cdiv(n_pad, 256), 1024);
     tc_bound_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, bound, inv_dev);
-    tc_operands_kernel<<<nb, 256, 0, st>>>(kp, cf, X, n, n_pad, KD, bound, PA, PB, dscale, inv_dev);
+    tc_operands_kernel<<<operand_blocks(n_pad), 256, 0, st>>>(kp, cf, X, n, n_pad, KD, bound, PA, PB, dscale, inv_dev);
     GP_TRY(check_launch("tc operand preparation", 2));
     out->PA = PA;
     out->PB = PB;
@@ -1641,9 +1735,9 @@ int tc_prepare_pair(const KP<float> &kp, const float *X1, int64_t n1, const floa
                                                                                        nullptr);
     tc_bound_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(kp, cf, X2, n2, bound,
                                                                                        nullptr);
-    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(
+    tc_operands_kernel<<<operand_blocks(p1), 256, 0, st>>>(
         kp, cf, X1, n1, p1, KD, bound, PA, nullptr, dscale, nullptr);
-    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p2, 256), 1024), 256, 0, st>>>(
+    tc_operands_kernel<<<operand_blocks(p2), 256, 0, st>>>(
         kp, cf, X2, n2, p2, KD, bound, nullptr, PB, nullptr, nullptr);
     GP_TRY(check_launch("tc pair preparation", 4));
     *rows = TcPoints{PA, nullptr, n1, p1, KD, dscale, bound};
@@ -1659,11 +1753,20 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
     __half *PA = c.take<__half>((size_t)p1 * KD);
     const float cf = (kp.kind == GP_RBF) ? -0.5f * kLog2e : 3.0f * kLog2e * kLog2e;
     // the bound of the prepared superset fixes the same power-of-two scale
-    tc_operands_kernel<<<(unsigned)std::min<int64_t>(cdiv(p1, 256), 1024), 256, 0, st>>>(
+    tc_operands_kernel<<<operand_blocks(p1), 256, 0, st>>>(
         kp, cf, X1, n1, p1, KD, like.bound, PA, nullptr, nullptr, nullptr);
     GP_TRY(check_launch("tc row preparation"));
     *out = TcPoints{PA, nullptr, n1, p1, KD, like.dscale, like.bound};
     return GP_OK;
+}
+
+// Generation of a persistent launch: distinct for every launch of the process (an odd multiple
+// mod 2^32 of a running count is a bijection), never 0.
+unsigned next_generation() {
+    static std::atomic<unsigned> count{0};
+    unsigned g = 0;
+    while (g == 0) g = (count.fetch_add(1, std::memory_order_relaxed) + 1u) * 0x9E3779B1u;
+    return g;
 }
 
 size_t tc_mvm_workspace_for(int64_t n1, int64_t p2, int R, int nsplit) {
@@ -1673,6 +1776,7 @@ size_t tc_mvm_workspace_for(int64_t n1, int64_t p2, int R, int nsplit) {
     c.take<float>(256);
     c.take<float>((size_t)std::min(R, kMaxRhsPerPass) * 64);
     c.take<int>(1);
+    c.take<unsigned long long>((size_t)cdiv(std::max<int64_t>(n1, 1), TM) * 8);
     const size_t pf = partial_floats(nsplit, n1, std::min(R, kMaxRhsPerPass), cdiv(std::max<int64_t>(n1, 1), TM),
                                      cdiv(p2, TN));
     if (pf > 0) c.take<float>(pf);
@@ -1694,6 +1798,7 @@ size_t tc_mvm_workspace(int64_t n1, int64_t n2, int R) {
     c.take<float>(256);                            // vinv
     c.take<float>((size_t)R * 64);                 // column max partials
     c.take<int>(1);                                // error flag
+    c.take<unsigned long long>((size_t)row_tiles * 8);  // shared row tiles' arrival counters
     if (pf > 0) c.take<float>(pf);                 // partial sums
     return c.bytes();
 }
@@ -1706,12 +1811,15 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         set_error("split tensor-core product: tile does not fit shared memory (KD=%d)", a.rows.KD);
         return GP_ERR_UNSUPPORTED;
     }
+    if (a.dot_parts) *a.dot_parts = 0;
     if (a.R > per_pass) {
         // wide blocks of right-hand sides: per_pass at a time
         for (int c0 = 0; c0 < a.R; c0 += per_pass) {
             TcMvmArgs b = a;
             b.R = std::min(per_pass, a.R - c0);
             b.V16pre = nullptr;  // a caller's converted operand covers all columns at once
+            b.dotpart = nullptr;  // d^T y partials only for a single pass
+            b.dot_parts = nullptr;
             b.V = a.V + (int64_t)c0 * a.ldv;
             b.Y = a.Y + (int64_t)c0 * a.ldy;
             b.Vd = a.Vd ? a.Vd + (int64_t)c0 * a.ldvd : nullptr;
@@ -1735,6 +1843,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
         probe.take<float>(256);
         probe.take<float>((size_t)a.R * 64);
         probe.take<int>(1);
+        probe.take<unsigned long long>((size_t)row_tiles * 8);
         const size_t pf = partial_floats(nsplit, n1, a.R, row_tiles, col_tiles);
         if (pf > 0) probe.take<float>(pf);
         if (probe.bytes() > ws_bytes && g_force_split == 0) nsplit = a.split ? 1 : pick_split(row_tiles, col_tiles);
@@ -1748,6 +1857,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     float *vinv = c.take<float>(256);
     float *cm = c.take<float>((size_t)a.R * 64);
     c.take<int>(1);  // (kept for the workspace layout)
+    unsigned long long *pcnt = c.take<unsigned long long>((size_t)row_tiles * 8);
     int *err = tc_timeout_word();
     float *partial = pfl > 0 ? c.take<float>(pfl) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
@@ -1803,6 +1913,16 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     kp.col0_dev = a.col0_dev;
     kp.diag_from_col0 = a.diag_from_col0;
     kp.ncols_total = a.cols.n;
+    if (persist) {
+        kp.pcnt = pcnt;
+        kp.pgen = next_generation();
+        if (a.dotpart) {
+            kp.dotv = a.dotv;
+            kp.lddv = a.lddv;
+            kp.dotpart = a.dotpart;
+        }
+    }
+    if (a.dot_parts) *a.dot_parts = (persist && a.dotpart) ? pgrid : 0;
     const size_t smem = smem_for(KD, R_pad, npb, nv, a.split);
     dim3 grid = persist ? dim3((unsigned)pgrid, 1) : dim3((unsigned)row_tiles, (unsigned)nsplit);
     const int kat = KD / 64;
@@ -1823,29 +1943,7 @@ int tc_mvm(const TcMvmArgs &a, void *ws, size_t ws_bytes, cudaStream_t st) {
     prof_end(st);
     GP_TRY(check_launch("tc_mvm_kernel"));
     if (persist) {
-        // row tiles that straddle a CTA boundary (a boundary inside a row tile)
-        PTable tab;
-        tab.n = 0;
-        const int64_t T = kp.ptotal, C = col_tiles;
-        for (int64_t bb = 1; bb < pgrid; ++bb) {
-            const int64_t gb = T * bb / pgrid;
-            if (gb % C == 0) continue;
-            const int r = (int)(gb / C);
-            if (tab.n > 0 && tab.r[tab.n - 1] == r) {
-                ++tab.nb[tab.n - 1];
-                continue;
-            }
-            const int e = tab.n++;
-            const int64_t gprev = T * (bb - 1) / pgrid;
-            tab.r[e] = r;
-            tab.bf[e] = (short)(bb - 1);
-            tab.nb[e] = 2;
-            tab.s0[e] = (unsigned char)(r > gprev / C ? 1 : 0);
-        }
-        if (tab.n > 0) {
-            tc_reduce_persist_kernel<<<dim3((unsigned)tab.n, (unsigned)a.R), TM, 0, st>>>(kp, tab);
-            GP_TRY(check_launch("tc_reduce_persist_kernel"));
-        }
+        // the shared row tiles are finished inside the kernel
     } else if (nsplit > 1) {
         tc_reduce_kernel<<<dim3((unsigned)cdiv(n1, 256), a.R), 256, 0, st>>>(kp);
         GP_TRY(check_launch("tc_reduce_kernel"));
@@ -2448,7 +2546,18 @@ __global__ void tc_uw_bound_kernel(GradArgs<float> a, unsigned int *bnd) {
         mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
         mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
     }
+    // one atomic per block and bound (same-address atomics serialise)
+    __shared__ float s_u[32], s_w[32];
     if ((threadIdx.x & 31) == 0) {
+        s_u[threadIdx.x >> 5] = mu;
+        s_w[threadIdx.x >> 5] = mw;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mu = fmaxf(mu, s_u[w]);
+            mw = fmaxf(mw, s_w[w]);
+        }
         atomicMax(&bnd[0], __float_as_uint(mu));
         atomicMax(&bnd[1], __float_as_uint(mw));
     }

@@ -509,6 +509,16 @@ def test_persistent_schedule_rows_straddling_ctas(dev, n, R):
     Y2 = gp.gp_kernel_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), add_noise=True,
                           prec=gp.GP_PREC_TC16).cpu().numpy()
     assert np.array_equal(Y, Y2)
+    if n == 20000:
+        # CG on the same schedule: its products also return d^T H d per CTA for the step size
+        B = workloads.vectors(R, n, seed=20).astype(np.float32)
+        V0 = (0.1 * workloads.vectors(R, n, seed=21)).astype(np.float32)
+        Vg, info = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), V0=t(V0, dev), max_iters=2, tol=0.0,
+                                  prec=gp.GP_PREC_TC16)
+        Vr, ir = oracle.solve_cg(p.kind, p.theta, Xr, B.astype(np.float64), V0=V0.astype(np.float64), max_iters=2,
+                                 tol=0.0)
+        assert info.iters == ir["iters"] == 2
+        assert close(Vg.double().cpu().numpy(), Vr, 3e-3)
 
 
 @pytest.mark.parametrize("prec_name,prec,tol", [("f32", gp.GP_PREC_FP32, 1e-5), ("tc16", gp.GP_PREC_TC16, 2e-3)])
