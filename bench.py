@@ -1150,7 +1150,9 @@ def run_op(args):
     """Single hot-path operations on the pathwise workload's shape (d = 16, Matern-3/2, 65
     right-hand sides, seeded synthetic inputs), `repeat` calls, for profilers (a capture of one
     kernel on a case that ends in seconds): mvm (gp_kernel_mvm, H V), grad (gp_mll_grad_pathwise),
-    rff (gp_rff_prior_sample), cg (gp_solve_cg, 10 iterations), unit-rates (gp_diag_unit_rates).
+    rff (gp_rff_prior_sample), cg (gp_solve_cg, 10 iterations), unit-rates (gp_diag_unit_rates);
+    panel: the alternating-projections column panel's shape (K(X, X_block) V, n = 262144, d = 26,
+    RBF, a block of 1024 points, 65 vectors).
     Prints the mean time per call (CUDA events).  --autotune tunes the shape first; with
     GP_AUTOTUNE_CACHE set the choice is saved, and a later run (under a profiler) reads it."""
     import torch
@@ -1175,14 +1177,24 @@ def run_op(args):
                           "dfma_tflops": sms * rates["dfma"] * 2 * clk * 1e6 / 1e12}))
         return
     prec = {"tc16": gp.GP_PREC_TC16, "fp32": gp.GP_PREC_FP32, "tc16x3": gp.GP_PREC_TC16X3}[args.prec]
-    p = workloads.pathwise(n=args.n, d=16, s=64, m=2048, seed=0)
     t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
-    X = t(p.X)
-    V = t(workloads.vectors(p.s + 1, p.n, seed=1))
-    om, c2, Wp = t(p.omega_hat), t(p.chi2), t(p.W_probe)
+    if args.op == "panel":
+        # the alternating-projections column panel's shape: all n = 262144 points (d = 26, RBF)
+        # against one block of 1024 points, 65 vectors
+        p = workloads.ap()
+        X = t(p.X)
+        Xb = X[:1024].contiguous()
+        V = t(workloads.vectors(p.s + 1, 1024, seed=1))
+    else:
+        p = workloads.pathwise(n=args.n, d=16, s=64, m=2048, seed=0)
+        X = t(p.X)
+        V = t(workloads.vectors(p.s + 1, p.n, seed=1))
+        om, c2, Wp = t(p.omega_hat), t(p.chi2), t(p.W_probe)
 
     def call():
-        if args.op == "mvm":
+        if args.op == "panel":
+            gp.gp_kernel_mvm(p.kind, p.theta, X, V, X2=Xb, prec=prec)
+        elif args.op == "mvm":
             gp.gp_kernel_mvm(p.kind, p.theta, X, V, add_noise=True, prec=prec)
         elif args.op == "grad":
             gp.gp_mll_grad_pathwise(p.kind, p.theta, X, V, prec=prec)
@@ -1207,7 +1219,7 @@ def run_op(args):
         call()
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"op": args.op, "n": args.n, "repeat": args.repeat,
+    print(json.dumps({"op": args.op, "n": p.n, "repeat": args.repeat,
                       "ms_per_call": e0.elapsed_time(e1) / args.repeat}))
 
 
@@ -1231,7 +1243,7 @@ def main():
     ap.add_argument("--workload", choices=["pathwise", "batched", "small", "ablation", "diagnostics", "ap", "sgd"],
                     default="pathwise")
     ap.add_argument("--solver-iters", type=int, default=0, help="--workload ap|sgd: iteration budget override")
-    ap.add_argument("--op", choices=["mvm", "grad", "rff", "cg", "unit-rates"], default=None)
+    ap.add_argument("--op", choices=["mvm", "panel", "grad", "rff", "cg", "unit-rates"], default=None)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--autotune", action="store_true", help="--op: tune the operation's shape first")
     ap.add_argument("--abl-steps", type=int, default=10)

@@ -204,33 +204,57 @@ __global__ void identity_kernel(T *Zb, int bsp, int nb) {
 // shuffles into its own shared-memory slot (no block barrier inside the column loop), the
 // warps' slots are added in a fixed order at the end (FP64).  R <= 512.
 template <typename T>
-__global__ void __launch_bounds__(256) ap_score_norm_kernel(const T *r, int64_t n, int R, int bs, double *score,
-                                                            double *bpart, const SolverState *st, int skip_done) {
+__global__ void __launch_bounds__(256) ap_score_norm_kernel(T *r, int64_t n, int R, int bs, double *score,
+                                                            double *bpart, const SolverState *st, int skip_done,
+                                                            const T *Kd, const T *delta, const int64_t *col0,
+                                                            T sigma2) {
     if (skip_done && st->done) return;
     const int b = blockIdx.x, nb = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t lo = (int64_t)b * bs, hi = min(n, lo + bs);
+    // with Kd: first the residual update of the block iteration, r -= K(X, X_blk) delta + sigma^2
+    // delta on the selected block's rows (Kd = K(X, X_blk) delta from the panel product)
+    const int64_t c0 = Kd ? *col0 : -1;
     constexpr int kRows = 4;  // rows per thread (bs <= 1024)
+    constexpr int kCols = 4;  // columns whose loads are issued together (before any store)
     __shared__ T wsq[8][512];  // in the vectors' precision (FP32 squares of an FP64 residual underflow)
     __shared__ double red[8];
     T t[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) t[k] = T(0);
-    for (int c = 0; c < R; ++c) {
-        const T *rc = r + (int64_t)c * n;
-        T sq = T(0);
+    for (int cb = 0; cb < R; cb += kCols) {
+        T x[kCols][kRows];
 #pragma unroll
-        for (int k = 0; k < kRows; ++k) {
-            const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
-            if (i < hi) {
-                const T x = rc[i];
-                t[k] += x;
-                sq += x * x;
+        for (int j = 0; j < kCols; ++j) {
+#pragma unroll
+            for (int k = 0; k < kRows; ++k) {
+                const int c = cb + j;
+                const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
+                T v = T(0);
+                if (c < R && i < hi) {
+                    v = r[(int64_t)c * n + i];
+                    if (Kd) {
+                        v -= Kd[(int64_t)c * n + i];
+                        if (i >= c0 && i < c0 + bs) v -= sigma2 * delta[(int64_t)c * bs + (i - c0)];
+                    }
+                }
+                x[j][k] = v;
             }
         }
-        T v = sq;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) wsq[warp][c] = v;
+#pragma unroll
+        for (int j = 0; j < kCols; ++j) {
+            const int c = cb + j;
+            T sq = T(0);
+#pragma unroll
+            for (int k = 0; k < kRows; ++k) {
+                const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
+                if (Kd && c < R && i < hi) r[(int64_t)c * n + i] = x[j][k];
+                t[k] += x[j][k];
+                sq += x[j][k] * x[j][k];
+            }
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0 && c < R) wsq[warp][c] = sq;
+        }
     }
     double s = 0.0;
 #pragma unroll
@@ -285,6 +309,7 @@ __global__ void ap_select_kernel(const double *score, int nb, int bs, int64_t *c
 // a < bs (rows beyond n -> 0).  grid (bs/64, R/16, kSplitK): the K ranges split the work over
 // enough CTAs to fill the GPU (one 1024 x 1024 block against 65 vectors is 68M FMA).
 constexpr int kSplitK = 8;
+constexpr int kNormThreads = 1024;  // ap_norm_kernel's block
 template <typename T>
 __global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, int bs, const T *r, int64_t n, int R,
                                                        const int64_t *col0, T *dpart, const SolverState *st) {
@@ -328,29 +353,66 @@ __global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, i
     }
 }
 
-// delta[c][a] = sum_ks dpart[ks][c][a] (K ranges in a fixed order); v[c][lo + a] += delta[c][a]
+// delta[c][a] = sum_ks dpart[ks][c][a] (K ranges in a fixed order); v[c][lo + a] += delta[c][a].
+// With D16 (tensor-core panel, one block per column) also the panel product's fp16 operand:
+// V16[c][a] = fp16(delta * 2^(1-e)) with max_a |delta[c][a]| = f 2^e, f in [0.5, 1), and
+// vinv[c] = 2^(e-1) -- the product's own conversion rule, without its two launches.
 template <typename T>
 __global__ void ap_vupdate_kernel(T *V, int64_t n, int bs, int R, const int64_t *col0, const T *dpart, T *delta,
-                                  const SolverState *st) {
+                                  const SolverState *st, __half *D16, int64_t p2, float *vinv) {
     if (st->done) return;
     const int c = blockIdx.y;
     const int64_t lo = *col0;
     const int m = (int)min((int64_t)bs, n - lo);
+    float mx = 0.0f;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < bs; a += gridDim.x * blockDim.x) {
         T dl = T(0);
         for (int ks = 0; ks < kSplitK; ++ks) dl += dpart[((int64_t)ks * R + c) * bs + a];
         delta[(int64_t)c * bs + a] = dl;
         if (a < m) V[(int64_t)c * n + lo + a] += dl;
+        mx = fmaxf(mx, fabsf((float)dl));
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (D16) {
+            __shared__ float red[32];
+            __shared__ float s_scale;
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float t = 0.0f;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+                int e = 0;
+                float scale = 1.0f, inv = 1.0f;
+                if (t > 0.0f && isfinite(t)) {
+                    frexpf(t, &e);
+                    scale = ldexpf(1.0f, 1 - e);
+                    inv = ldexpf(1.0f, e - 1);
+                }
+                s_scale = scale;
+                vinv[c] = inv;
+            }
+            __syncthreads();
+            const float sc = s_scale;
+            // each thread converts the entries it has just written
+            for (int a = threadIdx.x; a < bs; a += blockDim.x)
+                D16[(int64_t)c * p2 + a] = __float2half_rn(delta[(int64_t)c * bs + a] * sc);
+        }
     }
 }
 
 // Split norms and the loop condition from the ||r||^2 partials; the columns' sums in parallel (one
-// thread per column; a single thread summing R x P partials in FP64 took ~0.3 ms).  One block.
+// warp per column; one thread per column summing its P partials in a dependent chain took
+// ~27 us, a single thread for all R x P ~0.3 ms).  One block of kNormThreads.
 __global__ void ap_norm_kernel(int R, int P, const double *part, SolverState *st, long long max_iters, double tol,
                                int stop_rule, int first) {
     if (!first && st->done) return;
     __shared__ double sq[512];
-    for (int c = threadIdx.x; c < R; c += blockDim.x) sq[c] = sum_parts(part, c, P);
+    // a warp per column: its P partials in one round of loads, then a fixed butterfly
+    for (int c = (int)(threadIdx.x >> 5); c < R; c += (int)(blockDim.x >> 5)) {
+        const double v = sum_parts_warp(part, c, P);
+        if ((threadIdx.x & 31) == 0) sq[c] = v;
+    }
     if (threadIdx.x == 0 && first) {
         st->done = 0;
         st->status = GP_OK;
@@ -394,6 +456,10 @@ size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec) {
     c.take<SolverState>(1);
     c.take<char>(std::max(ap_panel_ws<T>(n, bs, d, R, prec), mvm_workspace<T>(n, n, d, R, prec)));
     if (std::is_same<T, float>::value && prec == GP_PREC_FP32) c.take<char>(f64_residual_workspace(n, d, R));
+    if (std::is_same<T, float>::value && prec == GP_PREC_TC16 && R <= 128) {
+        c.take<__half>((size_t)tc_rhs_pad(R) * tc_cols_pad(std::min<int64_t>(bs, n)));  // the update's fp16 operand
+        c.take<float>(256);
+    }
     return c.bytes();
 }
 
@@ -428,7 +494,13 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     const bool check64 = std::is_same<T, float>::value && prec == GP_PREC_FP32;
     const size_t c64b = check64 ? f64_residual_workspace(n, kp.d, R) : 0;
     void *c64w = check64 ? c.take<char>(c64b) : nullptr;
+    // tensor-core panel: the block update kernel writes the product's fp16 operand itself
+    const bool d16 = std::is_same<T, float>::value && prec == GP_PREC_TC16 && R <= 128;
+    const int64_t p2b = tc_cols_pad(bs);
+    __half *D16 = d16 ? c.take<__half>((size_t)tc_rhs_pad(R) * p2b) : nullptr;
+    float *vinv16 = d16 ? c.take<float>(256) : nullptr;
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
+    if (d16) GP_TRY_CUDA(cudaMemsetAsync(D16, 0, sizeof(__half) * (size_t)tc_rhs_pad(R) * p2b, st));
 
     const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
     const dim3 gp_((unsigned)P, (unsigned)R);
@@ -474,8 +546,9 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(check_launch("ap setup", 3));
     GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
-    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0);
-    ap_norm_kernel<<<1, 256, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule, exact_start ? 2 : 1);
+    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0, nullptr, nullptr, nullptr, T(0));
+    ap_norm_kernel<<<1, kNormThreads, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule,
+                                              exact_start ? 2 : 1);
     GP_TRY(check_launch("ap start", 3));
 
     int hfail = 0;
@@ -531,19 +604,20 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             ta.ncols = bs;
             ta.col0_dev = col0;
             ta.diag_from_col0 = 1;
+            // Kd = K(X, X_blk) delta into HV; the score kernel applies r -= Kd + sigma^2 delta (reading
+            // the residual once there rather than in every row segment of the product's epilogue)
             ta.V = delta;
             ta.ldv = bs;
             ta.R = R;
-            ta.Y = r;
+            ta.Y = HV;
             ta.ldy = n;
             ta.sf2 = kp.sf2;
-            ta.alpha = -1.0f;
-            ta.beta = 1.0f;
-            ta.diag_coef = -kp.sigma2;
-            ta.Vd = delta;
-            ta.ldvd = bs;
-            ta.ndiag = bs;
+            ta.alpha = 1.0f;
+            ta.beta = 0.0f;
+            ta.diag_coef = 0.0f;
             ta.done = &sd->done;
+            ta.V16pre = D16;  // written by the block update kernel (null: the product converts delta)
+            ta.vinv_pre = vinv16;
         }
     }
     const dim3 gdel((unsigned)cdiv(bs, 64), (unsigned)cdiv(R, 16), (unsigned)kSplitK);
@@ -561,7 +635,11 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             // the scores of the current residual come from the previous pass over r
             ap_select_kernel<<<1, 1024, 0, st>>>(score, nb, bs, col0, sd);
             ap_delta_kernel<T><<<gdel, 256, 0, st>>>(Hb, bsp, bs, r, n, R, col0, dpart, sd);
-            ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, R, col0, dpart, delta, sd);
+            if (d16)
+                ap_vupdate_kernel<T><<<dim3(1, R), 1024, 0, st>>>(V, n, bs, R, col0, dpart, delta, sd, D16, p2b, vinv16);
+            else
+                ap_vupdate_kernel<T><<<dim3((unsigned)cdiv(bs, 256), R), 256, 0, st>>>(V, n, bs, R, col0, dpart, delta,
+                                                                                       sd, nullptr, 0, nullptr);
             GP_TRY(check_launch("ap iteration", 3));
             if constexpr (std::is_same<T, float>::value) {
                 if (tc_panel) {
@@ -572,8 +650,9 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             } else {
                 GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
             }
-            ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 1);
-            ap_norm_kernel<<<1, 256, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule, 0);
+            ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 1, tc_panel ? HV : nullptr,
+                                                        delta, col0, kp.sigma2);
+            ap_norm_kernel<<<1, kNormThreads, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule, 0);
             GP_TRY(check_launch("ap norms", 2));
         }
         chunk = std::min<int64_t>(chunk * 2, 64);
@@ -591,7 +670,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     }
     true_state_kernel<<<1, 256, 0, st>>>(R, P, nullptr, part, nullptr, sd, (long long)max_iters, tol, stop_rule, 1);
     // the block scores of the replaced residual (for the next selection; its norms are set)
-    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0);
+    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0, nullptr, nullptr, nullptr, T(0));
     GP_TRY(check_launch("ap true residual", 3));
     GP_TRY(poll_state(sd, &hs, st));
     t = hs.iter;
