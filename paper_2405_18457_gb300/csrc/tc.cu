@@ -573,28 +573,29 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                     tmem_ld16((SPLIT ? tYs : tY) + lane_off + c0, r);
                     tmem_ld_wait();
                     if (i < n1) {
-                        // every load of the chunk (scales, previous Y, diagonal vector) before the
-                        // first store, so that they are in flight together; the beta and diagonal
-                        // terms are combined as they arrive (add)
-                        float v[16], add[16];
+                        // the loads of the chunk (scales, diagonal vector) before the first store,
+                        // so that they are in flight together (a previous Y, beta != 0, is read
+                        // with the store)
+                        float v[16], vd[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             const int c = c0 + e;
-                            const bool okc = c < p.R && p.nsplit <= 1;
-                            v[e] = c < p.R ? sf2 * vinv[c] * __uint_as_float(r[e]) : 0.0f;
-                            float a = 0.0f;
-                            if (okc && p.beta != 0.0f) a = p.beta * Yp[(int64_t)c * ldy + i];
-                            if (okc && diag) a += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
-                            add[e] = a;
+                            const bool okc = c < p.R;
+                            v[e] = okc ? sf2 * vinv[c] * __uint_as_float(r[e]) : 0.0f;
+                            vd[e] = (okc && p.nsplit <= 1 && diag) ? Vd[(int64_t)c * ldvd + (i - drow0)] : 0.0f;
                         }
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             const int c = c0 + e;
                             if (c >= p.R) break;
-                            if (p.nsplit > 1)
+                            if (p.nsplit > 1) {
                                 p.partial[((int64_t)blockIdx.y * p.R + c) * n1 + i] = v[e];
-                            else
-                                Yp[(int64_t)c * ldy + i] = p.alpha * v[e] + add[e];
+                            } else {
+                                float y = p.alpha * v[e];
+                                if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
+                                if (diag) y += diag_coef * vd[e];
+                                Yp[(int64_t)c * ldy + i] = y;
+                            }
                         }
                     }
                 }
@@ -757,20 +758,17 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                 }
             };
             // Final row i of Y for the 16 columns c0 .. c0 + 15 from their product sums v (alpha,
-            // beta and diagonal terms, the last two combined as they arrive in add), and the
-            // products dotv y into pr.  Every load of the chunk is issued before the first store,
-            // so that the loads are in flight together.
+            // beta and diagonal terms), and the products dotv y into pr.  The loads of the chunk
+            // are issued before the first store, so that they are in flight together (a previous
+            // Y, beta != 0, is read with the store).
             auto finish16 = [&](int64_t i, int c0, const float (&v)[16], float (&pr)[16]) {
                 const bool diag = diag_coef != 0.0f && i >= drow0 && i < drow0 + ndiag;
-                float add[16], dv[16];
+                float vd[16], dv[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int c = c0 + e;
                     const bool okc = i < n1 && c < p.R;
-                    float a = 0.0f;
-                    if (okc && p.beta != 0.0f) a = p.beta * Yp[(int64_t)c * ldy + i];
-                    if (okc && diag) a += diag_coef * Vd[(int64_t)c * ldvd + (i - drow0)];
-                    add[e] = a;
+                    vd[e] = (okc && diag) ? Vd[(int64_t)c * ldvd + (i - drow0)] : 0.0f;
                     dv[e] = (okc && dot) ? __ldg(&p.dotv[(int64_t)c * p.lddv + i]) : 0.0f;
                 }
 #pragma unroll
@@ -778,7 +776,9 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
                     const int c = c0 + e;
                     pr[e] = 0.0f;
                     if (i < n1 && c < p.R) {
-                        const float y = p.alpha * v[e] + add[e];
+                        float y = p.alpha * v[e];
+                        if (p.beta != 0.0f) y += p.beta * Yp[(int64_t)c * ldy + i];
+                        if (diag) y += diag_coef * vd[e];
                         Yp[(int64_t)c * ldy + i] = y;
                         pr[e] = dv[e] * y;
                     }
