@@ -197,32 +197,36 @@ __global__ void identity_kernel(T *Zb, int bsp, int nb) {
     }
 }
 
-// One pass over r per iteration for both of the solver's reductions: score[b] = sum over the rows
-// of block b of (sum_c r_c[row])^2 (the row sums in the vectors' precision) and bpart[c][b] =
-// sum over the rows of block b of r_c[row]^2 (the split norms' partials).  One CTA of 256
-// threads per block of at most 1024 rows; each warp sums its rows' squares per column by
-// shuffles into its own shared-memory slot (no block barrier inside the column loop), the
-// warps' slots are added in a fixed order at the end (FP64).  R <= 512.
+// The score pass of one block iteration, grid (blocks of rows, kScoreGroups column groups), 256
+// threads per block of at most 1024 rows (four rows per thread):
+//  * with Kd, first the residual update r -= K(X, X_blk) delta + sigma^2 delta on the selected
+//    block's rows (Kd = K(X, X_blk) delta from the panel product);
+//  * bpart[c][b] = sum over the block's rows of r_c^2 (the split norms' partials): each warp sums
+//    its rows' squares per column by shuffles into its own shared-memory slot, the warps' slots
+//    added in a fixed order at the end (FP64);
+//  * rowsum[g][i] = sum of r_c[i] over the group's columns (the block score's row sums, in the
+//    vectors' precision; ap_score_kernel adds the groups).
+// The column groups put several CTAs on each block of rows, so that enough loads are in flight,
+// and the loads of kCols columns are issued before their stores.  R <= 512.
+constexpr int kScoreGroups = 4;
 template <typename T>
-__global__ void __launch_bounds__(256) ap_score_norm_kernel(T *r, int64_t n, int R, int bs, double *score,
+__global__ void __launch_bounds__(256) ap_score_norm_kernel(T *r, int64_t n, int R, int bs, T *rowsum,
                                                             double *bpart, const SolverState *st, int skip_done,
                                                             const T *Kd, const T *delta, const int64_t *col0,
                                                             T sigma2) {
     if (skip_done && st->done) return;
-    const int b = blockIdx.x, nb = gridDim.x;
+    const int b = blockIdx.x, nb = gridDim.x, g = blockIdx.y;
+    const int cpg = (R + (int)gridDim.y - 1) / (int)gridDim.y, cbeg = g * cpg, cend = min(R, cbeg + cpg);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t lo = (int64_t)b * bs, hi = min(n, lo + bs);
-    // with Kd: first the residual update of the block iteration, r -= K(X, X_blk) delta + sigma^2
-    // delta on the selected block's rows (Kd = K(X, X_blk) delta from the panel product)
     const int64_t c0 = Kd ? *col0 : -1;
     constexpr int kRows = 4;  // rows per thread (bs <= 1024)
-    constexpr int kCols = 4;  // columns whose loads are issued together (before any store)
+    constexpr int kCols = 2;  // columns whose loads are issued together (before any store)
     __shared__ T wsq[8][512];  // in the vectors' precision (FP32 squares of an FP64 residual underflow)
-    __shared__ double red[8];
     T t[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; ++k) t[k] = T(0);
-    for (int cb = 0; cb < R; cb += kCols) {
+    for (int cb = cbeg; cb < cend; cb += kCols) {
         T x[kCols][kRows];
 #pragma unroll
         for (int j = 0; j < kCols; ++j) {
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(256) ap_score_norm_kernel(T *r, int64_t n, int
                 const int c = cb + j;
                 const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
                 T v = T(0);
-                if (c < R && i < hi) {
+                if (c < cend && i < hi) {
                     v = r[(int64_t)c * n + i];
                     if (Kd) {
                         v -= Kd[(int64_t)c * n + i];
@@ -248,28 +252,48 @@ __global__ void __launch_bounds__(256) ap_score_norm_kernel(T *r, int64_t n, int
 #pragma unroll
             for (int k = 0; k < kRows; ++k) {
                 const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
-                if (Kd && c < R && i < hi) r[(int64_t)c * n + i] = x[j][k];
+                if (Kd && c < cend && i < hi) r[(int64_t)c * n + i] = x[j][k];
                 t[k] += x[j][k];
                 sq += x[j][k] * x[j][k];
             }
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0 && c < R) wsq[warp][c] = sq;
+            if (lane == 0 && c < cend) wsq[warp][c] = sq;
         }
     }
-    double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < kRows; ++k) s += (double)(t[k] * t[k]);
-    s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
+    for (int k = 0; k < kRows; ++k) {
+        const int64_t i = lo + threadIdx.x + (int64_t)k * blockDim.x;
+        if (i < hi) rowsum[(int64_t)g * n + i] = t[k];
+    }
     __syncthreads();
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+    for (int c = cbeg + (int)threadIdx.x; c < cend; c += blockDim.x) {
         double a = 0.0;
         for (int w = 0; w < 8; ++w) a += (double)wsq[w][c];
         bpart[(int64_t)c * nb + b] = a;
     }
+}
+
+// Alg. 2's block score, score[b] = sum over the block's rows of (sum_g rowsum[g][i])^2 (the
+// column groups added in order, FP64 squares).  One block of 256 threads per block of rows.
+template <typename T>
+__global__ void __launch_bounds__(256) ap_score_kernel(const T *rowsum, int64_t n, int bs, int G, double *score,
+                                                       const SolverState *st, int skip_done) {
+    if (skip_done && st->done) return;
+    const int b = blockIdx.x;
+    const int64_t lo = (int64_t)b * bs, hi = min(n, lo + bs);
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T t = T(0);
+        for (int g = 0; g < G; ++g) t += rowsum[(int64_t)g * n + i];
+        s += (double)(t * t);
+    }
+    __shared__ double red[8];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0;
-        for (int w = 0; w < 8; ++w) a += red[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
         score[b] = a;
     }
 }
@@ -451,6 +475,7 @@ size_t ap_workspace(int64_t n, int d, int R, int64_t bs, int prec) {
     c.take<double>((size_t)R);
     c.take<double>((size_t)nb);
     c.take<double>((size_t)R * nb);        // per-block partials of ||r_c||^2
+    c.take<T>((size_t)kScoreGroups * n);   // the score's row sums per column group
     c.take<int64_t>(1);
     c.take<int>(1);
     c.take<SolverState>(1);
@@ -486,6 +511,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     double *scale = c.take<double>(R);
     double *score = c.take<double>(nb);
     double *bpart = c.take<double>((size_t)R * nb);
+    T *rowsum = c.take<T>((size_t)kScoreGroups * n);
     int64_t *col0 = c.take<int64_t>(1);
     int *fail = c.take<int>(1);
     SolverState *sd = c.take<SolverState>(1);
@@ -507,6 +533,13 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     // the true residual the tolerance is judged on: the tensor-core form's split product (the
     // initial residual uses the form's own product; the final check catches its error)
     const int prec_true = prec == GP_PREC_TC16 ? GP_PREC_TC16X3 : prec;
+    // block scores and norm partials of the current residual; update: first apply the block
+    // iteration's r -= K delta + sigma^2 delta (K delta in HV from the tensor-core panel)
+    auto score_pass = [&](int skip_done, bool update) {
+        ap_score_norm_kernel<T><<<dim3((unsigned)nb, kScoreGroups), 256, 0, st>>>(
+            r, n, R, bs, rowsum, bpart, sd, skip_done, update ? HV : nullptr, delta, col0, kp.sigma2);
+        ap_score_kernel<T><<<nb, 256, 0, st>>>(rowsum, n, bs, kScoreGroups, score, sd, skip_done);
+    };
     const bool exact_start = !(std::is_same<T, float>::value && (prec == GP_PREC_TC16 || prec == GP_PREC_FP32));
     // ---- block inverses H[i,i]^-1 (cached for the whole solve)
     GP_TRY_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
@@ -546,10 +579,10 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(check_launch("ap setup", 3));
     GP_TRY(apply_mvm<T>(kp, X, n, X, n, V, n, R, HV, n, 1, prec, mw, mwb, st));
     init_residual_kernel<T><<<gv, 256, 0, st>>>(B, HV, r, (T *)nullptr, n, scale);
-    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0, nullptr, nullptr, nullptr, T(0));
+    score_pass(0, false);
     ap_norm_kernel<<<1, kNormThreads, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule,
                                               exact_start ? 2 : 1);
-    GP_TRY(check_launch("ap start", 3));
+    GP_TRY(check_launch("ap start", 4));
 
     int hfail = 0;
     GP_TRY_CUDA(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -650,10 +683,9 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
             } else {
                 GP_TRY(mvm_simt<T>(pa, mw, mwb, st));
             }
-            ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 1, tc_panel ? HV : nullptr,
-                                                        delta, col0, kp.sigma2);
+            score_pass(1, tc_panel);
             ap_norm_kernel<<<1, kNormThreads, 0, st>>>(R, nb, bpart, sd, (long long)max_iters, tol, stop_rule, 0);
-            GP_TRY(check_launch("ap norms", 2));
+            GP_TRY(check_launch("ap norms", 3));
         }
         chunk = std::min<int64_t>(chunk * 2, 64);
         GP_TRY(poll_state(sd, &hs, st));
@@ -670,8 +702,8 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     }
     true_state_kernel<<<1, 256, 0, st>>>(R, P, nullptr, part, nullptr, sd, (long long)max_iters, tol, stop_rule, 1);
     // the block scores of the replaced residual (for the next selection; its norms are set)
-    ap_score_norm_kernel<T><<<nb, 256, 0, st>>>(r, n, R, bs, score, bpart, sd, 0, nullptr, nullptr, nullptr, T(0));
-    GP_TRY(check_launch("ap true residual", 3));
+    score_pass(0, false);
+    GP_TRY(check_launch("ap true residual", 4));
     GP_TRY(poll_state(sd, &hs, st));
     t = hs.iter;
     if (hs.done) break;
