@@ -528,7 +528,7 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
     if (d16) GP_TRY_CUDA(cudaMemsetAsync(D16, 0, sizeof(__half) * (size_t)tc_rhs_pad(R) * p2b, st));
 
-    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
+    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 2048), 1024), (unsigned)R);  // about 8 rows per thread
     const dim3 gp_((unsigned)P, (unsigned)R);
     // the true residual the tolerance is judged on: the tensor-core form's split product (the
     // initial residual uses the form's own product; the final check catches its error)

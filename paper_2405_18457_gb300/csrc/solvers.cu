@@ -540,7 +540,7 @@ int cg_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(op.init(kp, X, n, R, prec, opw, opb, st));
     Precond<T> pcd{};
     if (pc) GP_TRY(precond_build<T>(kp, X, n, R, pc_rank, pcw, pcb, &pcd, st));
-    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 1024), (unsigned)R);
+    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 2048), 1024), (unsigned)R);  // about 8 rows per thread
     const dim3 gp_((unsigned)P, (unsigned)R);
     // direction update: about four float4 per thread
     const dim3 gd((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 4096), 1024)), (unsigned)R);
@@ -1059,7 +1059,7 @@ int sgd_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, i
     float *pvm = v16 ? c.take<float>(2 * (size_t)R * 2048) : nullptr;   // per-block maxima of v, m
     GP_TRY(check_ws(ws, ws_bytes, c.bytes()));
 
-    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 256), 2048), (unsigned)R);
+    const dim3 gv((unsigned)std::min<int64_t>(cdiv(n, 2048), 1024), (unsigned)R);  // about 8 rows per thread
     const dim3 gp_((unsigned)P, (unsigned)R);
     const int nbg = (int)std::min<int64_t>(64, std::max<int64_t>(1, cdiv(batch, 256)));
     // b~ = b / (||b|| + eps), v <- v / scale, m = 0, r = b~
