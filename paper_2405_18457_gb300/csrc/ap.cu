@@ -24,11 +24,19 @@ namespace {
 constexpr int PW = 32;  // panel width of the blocked factorisation
 
 // ---------------------------------------------------------------- batched GEMM
-// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, 64x64 tiles.
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, 64x64 tiles.  Structure of the
+// factorisation's products (GemmShape): lower -- only output tiles on or below the diagonal
+// (n0 <= m0) are computed; mirror -- each off-diagonal tile is also written transposed (a
+// symmetric result); kfrom -- the K loop starts at n0 (op(B) lower-triangular: B[k][j] = 0 for
+// k < j) or at max(m0, n0) (op(A) upper- and op(B) lower-triangular, as in Z^T Z for a lower-
+// triangular Z).  Skipped terms are exact zeros, so the results equal the full products'.
+struct GemmShape {
+    int lower, mirror, kfrom;  // kfrom: 0 = from 0, 1 = from n0, 2 = from max(m0, n0)
+};
 template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm_batched_kernel(int M, int N, int K, T alpha, const T *A, int lda,
                                                            int64_t sA, const T *B, int ldb, int64_t sB, T beta,
-                                                           T *C, int ldc, int64_t sC) {
+                                                           T *C, int ldc, int64_t sC, GemmShape shp) {
     __shared__ T As[16][64 + 1];
     __shared__ T Bs[16][64 + 1];
     const int b = blockIdx.z;
@@ -37,12 +45,14 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(int M, int N, int K, 
     C += b * sC;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    if (shp.lower && n0 > m0) return;
+    const int kbeg = shp.kfrom == 0 ? 0 : (shp.kfrom == 1 ? n0 : max(m0, n0));
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kbeg; k0 < K; k0 += 16) {
         for (int e = tid; e < 16 * 64; e += 256) {
             int kk = e / 64, mm = e % 64;
             int gm = m0 + mm, gk = k0 + kk;
@@ -78,17 +88,20 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(int M, int N, int K, 
             int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
             T *cp = C + (int64_t)gm * ldc + gn;
-            *cp = alpha * acc[i][j] + (beta == T(0) ? T(0) : beta * *cp);
+            const T y = alpha * acc[i][j] + (beta == T(0) ? T(0) : beta * *cp);
+            *cp = y;
+            if (shp.mirror && n0 < m0) C[(int64_t)gn * ldc + gm] = y;
         }
     }
 }
 
 template <typename T, bool TA, bool TB>
 int gemm_batched(int M, int N, int K, T alpha, const T *A, int lda, int64_t sA, const T *B, int ldb, int64_t sB,
-                 T beta, T *C, int ldc, int64_t sC, int batch, cudaStream_t st) {
+                 T beta, T *C, int ldc, int64_t sC, int batch, cudaStream_t st, GemmShape shp = GemmShape{0, 0, 0}) {
     if (M <= 0 || N <= 0) return GP_OK;
     dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64), (unsigned)batch);
-    gemm_batched_kernel<T, TA, TB><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    gemm_batched_kernel<T, TA, TB><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                                         shp);
     return check_launch("gemm_batched_kernel");
 }
 
@@ -551,9 +564,10 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
         if (rest > 0) {
             trsm_right_kernel<T><<<dim3(nb, (unsigned)cdiv(rest, 128)), 128, 0, st>>>(Hb, bsp, p);
             const int64_t off = (int64_t)(p + PW) * bsp;
+            // trailing update: only the lower triangle is read later
             GP_TRY((gemm_batched<T, false, true>(rest, rest, PW, T(-1), Hb + off + p, bsp, (int64_t)bsp * bsp,
                                                  Hb + off + p, bsp, (int64_t)bsp * bsp, T(1), Hb + off + p + PW, bsp,
-                                                 (int64_t)bsp * bsp, nb, st)));
+                                                 (int64_t)bsp * bsp, nb, st, GemmShape{1, 0, 0})));
         }
         GP_TRY(check_launch("blocked cholesky", rest > 0 ? 2 : 1));
     }
@@ -562,15 +576,18 @@ int ap_solve(const KP<T> &kp, const T *X, int64_t n, const T *B, int R, T *V, in
     GP_TRY(check_launch("identity_kernel"));
     for (int p = 0; p < bsp; p += PW) {
         if (p > 0)
+            // Z[0:p, 0:p] is lower-triangular: column j of the product sums over k >= j
             GP_TRY((gemm_batched<T, false, false>(PW, p, p, T(-1), Hb + (int64_t)p * bsp, bsp, (int64_t)bsp * bsp, Zb,
                                                   bsp, (int64_t)bsp * bsp, T(1), Zb + (int64_t)p * bsp, bsp,
-                                                  (int64_t)bsp * bsp, nb, st)));
+                                                  (int64_t)bsp * bsp, nb, st, GemmShape{0, 0, 1})));
         trsm_left_kernel<T><<<dim3(nb, (unsigned)cdiv(p + PW, 128)), 128, 0, st>>>(Hb, Zb, bsp, p);
         GP_TRY(check_launch("blocked triangular inverse"));
     }
     // H^-1 = L^-T L^-1
+    // H^-1 = Z^T Z: symmetric, and (Z^T Z)_ij sums over k >= max(i, j) for the lower-triangular Z
     GP_TRY((gemm_batched<T, true, false>(bsp, bsp, bsp, T(1), Zb, bsp, (int64_t)bsp * bsp, Zb, bsp,
-                                         (int64_t)bsp * bsp, T(0), Hb, bsp, (int64_t)bsp * bsp, nb, st)));
+                                         (int64_t)bsp * bsp, T(0), Hb, bsp, (int64_t)bsp * bsp, nb, st,
+                                         GemmShape{1, 1, 2})));
 
     // ---- normalisation and initial residual r = b~ - H v~
     coldot_kernel<T><<<gp_, 256, 0, st>>>(B, B, n, P, part, nullptr);
