@@ -225,10 +225,11 @@ struct KParams {
     int diag_from_col0;     // diagonal rows start at *col0_dev, clipped to ncols_total
     int64_t ncols_total;
     // persistent schedule: arrival counters of the shared row tiles' pieces (8 per row tile;
-    // high word the launch's generation pgen, low word the arrivals), and optionally the
-    // partial sums d^T y per column and CTA (dotpart[c * G + b], d = dotv with stride lddv)
+    // the high 40 bits the launch's generation pgen, the low 24 bits the arrivals), and
+    // optionally the partial sums d^T y per column and CTA (dotpart[c * G + b], d = dotv with
+    // stride lddv)
     unsigned long long *pcnt;
-    unsigned pgen;
+    unsigned long long pgen;
     const float *dotv;
     int64_t lddv;
     double *dotpart;
@@ -238,13 +239,18 @@ struct KParams {
 __device__ __forceinline__ int64_t cta_of_pair(int64_t g, int64_t T, int G) { return ((g + 1) * G + T - 1) / T - 1; }
 
 // Arrival on a shared row tile's piece counter; 1 for the arrival that completes `need` in this
-// launch's generation.  Each retry means another CTA's arrival landed first (a CTA arrives once
-// per piece and launch), so the loop is short; it is bounded all the same.
-__device__ __forceinline__ int arrive_last(unsigned long long *cnt, unsigned gen, unsigned need, volatile int *err) {
+// launch's generation.  A counter whose generation is another launch's (an earlier launch, an
+// aborted one, or whatever a new workspace held: it matches the 40-bit generation by chance with
+// probability 2^-40) counts from zero.  Each retry means another CTA's arrival landed first (a
+// CTA arrives once per piece and launch), so the loop is short; it is bounded all the same.
+constexpr int kCountBits = 24;  // arrivals per piece <= the persistent grid (256)
+__device__ __forceinline__ int arrive_last(unsigned long long *cnt, unsigned long long gen, unsigned need,
+                                           volatile int *err) {
+    constexpr unsigned long long kMask = (1ull << kCountBits) - 1ull;
     unsigned long long old = atomicAdd(cnt, 0ull);
     for (int tries = 0; tries < 4096; ++tries) {
-        const unsigned now = ((unsigned)(old >> 32) == gen) ? (unsigned)old : 0u;
-        const unsigned long long nw = ((unsigned long long)gen << 32) | (unsigned long long)(now + 1);
+        const unsigned now = ((old >> kCountBits) == gen) ? (unsigned)(old & kMask) : 0u;
+        const unsigned long long nw = (gen << kCountBits) | (unsigned long long)(now + 1);
         const unsigned long long seen = atomicCAS(cnt, old, nw);
         if (seen == old) return (now + 1 == need) ? 1 : 0;
         old = seen;
@@ -787,7 +793,7 @@ __global__ void __launch_bounds__(MVM_THREADS, 1)
             // A row tile that several CTAs share: each CTA's warp `piece` has written its rows x
             // columns of the tile's partial sums to its slot; the warp that arrives last on the
             // piece's counter (of any of those CTAs) sums the slots in CTA order and finishes
-            // the piece's rows.  The counters carry the launch's generation in their high word,
+            // the piece's rows.  The counters carry the launch's 40-bit generation above the count,
             // so a count left by an earlier (aborted) launch restarts at zero.
             auto shared_tile = [&](int64_t r) {
                 const int64_t T = p.ptotal;
@@ -1760,12 +1766,14 @@ int tc_prepare_rows(const KP<float> &kp, const float *X1, int64_t n1, const TcPo
     return GP_OK;
 }
 
-// Generation of a persistent launch: distinct for every launch of the process (an odd multiple
-// mod 2^32 of a running count is a bijection), never 0.
-unsigned next_generation() {
-    static std::atomic<unsigned> count{0};
-    unsigned g = 0;
-    while (g == 0) g = (count.fetch_add(1, std::memory_order_relaxed) + 1u) * 0x9E3779B1u;
+// Generation of a persistent launch (40 bits): distinct for every launch of the process (an odd
+// multiple mod 2^40 of a running count is a bijection), never 0, and spread over the 40 bits so
+// that stale memory rarely matches it.
+unsigned long long next_generation() {
+    static std::atomic<unsigned long long> count{0};
+    constexpr unsigned long long kMask = (1ull << 40) - 1ull;
+    unsigned long long g = 0;
+    while (g == 0) g = ((count.fetch_add(1, std::memory_order_relaxed) + 1ull) * 0x9E3779B97F4Bull) & kMask;
     return g;
 }
 
