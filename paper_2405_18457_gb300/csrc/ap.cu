@@ -221,7 +221,7 @@ __global__ void identity_kernel(T *Zb, int bsp, int nb) {
 //    vectors' precision; ap_score_kernel adds the groups).
 // The column groups put several CTAs on each block of rows, so that enough loads are in flight,
 // and the loads of kCols columns are issued before their stores.  R <= 512.
-constexpr int kScoreGroups = 4;
+constexpr int kScoreGroups = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) ap_score_norm_kernel(T *r, int64_t n, int R, int bs, T *rowsum,
                                                             double *bpart, const SolverState *st, int skip_done,
