@@ -395,8 +395,9 @@ __global__ void __launch_bounds__(256) ap_delta_kernel(const T *Hinv, int bsp, i
 // V16[c][a] = fp16(delta * 2^(1-e)) with max_a |delta[c][a]| = f 2^e, f in [0.5, 1), and
 // vinv[c] = 2^(e-1) -- the product's own conversion rule, without its two launches.
 template <typename T>
-__global__ void ap_vupdate_kernel(T *V, int64_t n, int bs, int R, const int64_t *col0, const T *dpart, T *delta,
-                                  const SolverState *st, __half *D16, int64_t p2, float *vinv) {
+__global__ void __launch_bounds__(1024) ap_vupdate_kernel(T *V, int64_t n, int bs, int R, const int64_t *col0,
+                                                         const T *dpart, T *delta, const SolverState *st,
+                                                         __half *D16, int64_t p2, float *vinv) {
     if (st->done) return;
     const int c = blockIdx.y;
     const int64_t lo = *col0;
