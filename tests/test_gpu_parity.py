@@ -529,6 +529,46 @@ def test_persistent_schedule_rows_straddling_ctas(dev, n, R):
         assert close(Vg.double().cpu().numpy(), Vr, 3e-3)
 
 
+@pytest.mark.parametrize("n,R", [(2048, 9), (1500, 65)])
+def test_persistent_schedule_many_ctas_per_row_tile(dev, tmp_path, n, R):
+    """The persistent schedule forced through the tuning table on a small problem: 152 CTAs take
+    the 256 tile pairs of n = 2048, or 144 CTAs one tile pair each at n = 1500, so a 128-row
+    tile is shared by up to 12 CTAs, whose partial sums the last-arriving warps add in CTA
+    order.  The product's rows (twice, bit for bit) and two CG iterations, whose step sizes
+    use the products' d^T H d partials, match the oracle."""
+    p = workloads.pathwise(n=n, d=8, s=R - 1, m=64, seed=21)
+    X32 = p.X.astype(np.float32)
+    V = workloads.vectors(R, n, seed=22).astype(np.float32)
+    tiles = -(-n // 128)
+    r_pad = 16 * (-(-R // 16))
+    gp.gp_autotune_reset()
+    try:
+        # this device's cache header (an empty table), then the product's entry: persistent (-1)
+        f = tmp_path / "force_persistent.txt"
+        gp.gp_autotune_save(f)
+        f.write_text(f.read_text() + "0 %d %d %d 0 -1\n" % (r_pad, tiles, tiles))
+        gp.gp_autotune_load(f)
+        assert gp.gp_autotune_count() == 1
+        Xr = X32.astype(np.float64)
+        Y = gp.gp_kernel_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), add_noise=True,
+                             prec=gp.GP_PREC_TC16).cpu().numpy()
+        ref = oracle.kernel_mvm(p.kind, p.theta, Xr, Xr, V.astype(np.float64), add_noise=True)
+        assert close(Y, ref, 1e-3)
+        Y2 = gp.gp_kernel_mvm(p.kind, p.theta, t(X32, dev), t(V, dev), add_noise=True,
+                              prec=gp.GP_PREC_TC16).cpu().numpy()
+        assert np.array_equal(Y, Y2)
+        B = workloads.vectors(R, n, seed=23).astype(np.float32)
+        V0 = (0.1 * workloads.vectors(R, n, seed=24)).astype(np.float32)
+        Vg, info = gp.gp_solve_cg(p.kind, p.theta, t(X32, dev), t(B, dev), V0=t(V0, dev), max_iters=2, tol=0.0,
+                                  prec=gp.GP_PREC_TC16)
+        Vr, ir = oracle.solve_cg(p.kind, p.theta, Xr, B.astype(np.float64), V0=V0.astype(np.float64), max_iters=2,
+                                 tol=0.0)
+        assert info.iters == ir["iters"] == 2
+        assert close(Vg.double().cpu().numpy(), Vr, 3e-3)
+    finally:
+        gp.gp_autotune_reset()
+
+
 @pytest.mark.parametrize("prec_name,prec,tol", [("f32", gp.GP_PREC_FP32, 1e-5), ("tc16", gp.GP_PREC_TC16, 2e-3)])
 def test_predictions_match_oracle(dev, prec_name, prec, tol):
     """Predictive mean/variance and test RMSE/log-likelihood from the pathwise solutions."""
